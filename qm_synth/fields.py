@@ -1,0 +1,108 @@
+"""Synthetic potential, projectors and random wavefunctions.
+
+* V_loc(r): a periodic sum of Gaussians of depth `depth` (Ha) and standard deviation
+  `width` (bohr) centred on the atom sites, V(r) = depth * sum_{a,R} exp(-|r-tau_a-R|^2 / (2 w^2)),
+  evaluated at the FFT grid points r_j = sum_i (j_i / N_i) a_i.  It stands in for the local
+  part of a norm-conserving pseudopotential (Section 2.3).  Returned flat, x fastest:
+  flat = j1 + N1 * (j2 + N2 * j3).
+* beta(q): unit-norm Gaussian s and p projector functions in the plane-wave basis
+  (Kleinman-Bylander form, Section 2.3), one s and three Cartesian p functions per atom,
+  evaluated at the Cartesian wavevectors q = k + G the caller supplies:
+      beta_s(q)  = Omega^-1/2 2^{3/2} pi^{3/4} rc^{3/2}  exp(-q^2 rc^2 / 2) exp(-i q.tau)
+      beta_pa(q) = Omega^-1/2 4 pi^{3/4} rc^{5/2} q_a    exp(-q^2 rc^2 / 2) exp(-i q.tau)
+  These are the plane-wave coefficients of the real-space functions
+  (pi rc^2)^{-3/4} exp(-r^2/2rc^2) and sqrt(2/(pi^{3/2} rc^5)) x_a exp(-r^2/2rc^2),
+  each of unit L2 norm; the (-i)^l phase is dropped (it cancels in beta D beta^H).
+* D: diag(5.0, 1.5, 1.5, 1.5) Ha per atom, ordered (s, p_x, p_y, p_z).
+* psi_random: complex normal coefficients from a seeded numpy Generator.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+D_PER_ATOM = (5.0, 1.5, 1.5, 1.5)
+
+
+def _grid_fractions(grid):
+    n1, n2, n3 = grid
+    return (np.arange(n1) / n1, np.arange(n2) / n2, np.arange(n3) / n3)
+
+
+def vloc_on_grid(lattice, tau, grid, depth=-1.5, width=1.0, tail=1e-18):
+    """Gaussian-sum potential on the grid, flat, x fastest (float64, length N1*N2*N3).
+
+    Images R are summed while exp(-d^2/2w^2) can exceed `tail`.
+    """
+    lattice = np.asarray(lattice, float)
+    tau = np.atleast_2d(np.asarray(tau, float))
+    n1, n2, n3 = (int(x) for x in grid)
+    rcut = width * math.sqrt(2.0 * math.log(1.0 / tail))
+    fx, fy, fz = _grid_fractions((n1, n2, n3))
+    offdiag = lattice - np.diag(np.diag(lattice))
+    if np.all(offdiag == 0.0):
+        # orthorhombic: the 3D image sum factorises into three 1D image sums
+        L = np.diag(lattice)
+        facs = []
+        for axis, f in enumerate((fx, fy, fz)):
+            nmax = int(math.ceil(rcut / L[axis])) + 1
+            imgs = np.arange(-nmax, nmax + 1)
+            d = (f[None, :, None] * L[axis] - tau[:, axis][:, None, None]
+                 + imgs[None, None, :] * L[axis])                       # (nat, N, nimg)
+            facs.append(np.exp(-d * d / (2.0 * width * width)).sum(axis=2))  # (nat, N)
+        gx, gy, gz = facs
+        zy = (gz[:, :, None] * gy[:, None, :]).reshape(tau.shape[0], n3 * n2)  # (nat, N3*N2)
+        v = zy.T @ gx                                                   # (N3*N2, N1)
+        return (depth * v).reshape(-1)
+    # general lattice: explicit image loop
+    recip = 2.0 * math.pi * np.linalg.inv(lattice).T
+    spacing = 2.0 * math.pi / np.linalg.norm(recip, axis=1)
+    nmax = [int(math.ceil(rcut / s + 0.5)) for s in spacing]
+    F = np.stack(np.meshgrid(fx, fy, fz, indexing="ij"), axis=-1)        # (N1,N2,N3,3)
+    F = F.transpose(2, 1, 0, 3).reshape(-1, 3)                          # x fastest
+    tau_f = tau @ np.linalg.inv(lattice)
+    v = np.zeros(F.shape[0])
+    imgs = np.array([(a, b, c) for a in range(-nmax[0], nmax[0] + 1)
+                     for b in range(-nmax[1], nmax[1] + 1)
+                     for c in range(-nmax[2], nmax[2] + 1)], float)
+    for ta in tau_f:
+        d0 = F - ta
+        d0 -= np.round(d0)
+        for img in imgs:
+            d = (d0 + img) @ lattice
+            r2 = np.einsum("ij,ij->i", d, d)
+            m = r2 < rcut * rcut
+            if np.any(m):
+                v[m] += np.exp(-r2[m] / (2.0 * width * width))
+    return depth * v
+
+
+def beta_of_q(q, tau, omega, rc=1.0):
+    """Projectors (4*nat, npw) complex128 at Cartesian wavevectors q (npw, 3)."""
+    q = np.asarray(q, float)
+    tau = np.atleast_2d(np.asarray(tau, float))
+    q2 = np.einsum("ij,ij->i", q, q)
+    g = np.exp(-0.5 * q2 * rc * rc) / math.sqrt(omega)
+    cs = 2.0 ** 1.5 * math.pi ** 0.75 * rc ** 1.5
+    cp = 4.0 * math.pi ** 0.75 * rc ** 2.5
+    out = np.empty((4 * tau.shape[0], q.shape[0]), np.complex128)
+    for a, t in enumerate(tau):
+        ph = np.exp(-1j * (q @ t)) * g
+        out[4 * a + 0] = cs * ph
+        out[4 * a + 1] = cp * q[:, 0] * ph
+        out[4 * a + 2] = cp * q[:, 1] * ph
+        out[4 * a + 3] = cp * q[:, 2] * ph
+    return out
+
+
+def dvals(nat):
+    """Diagonal D (4*nat,) float64, per atom (s, p_x, p_y, p_z) = (5.0, 1.5, 1.5, 1.5) Ha."""
+    return np.tile(np.array(D_PER_ATOM), nat)
+
+
+def psi_random(seed, nb, npw, stream=0):
+    """Seeded complex normal coefficients (nb, npw) complex128, E|c|^2 = 1."""
+    rng = np.random.default_rng([int(seed), int(stream)])
+    z = rng.standard_normal((nb, npw, 2))
+    return (z[..., 0] + 1j * z[..., 1]) / math.sqrt(2.0)
