@@ -1,0 +1,155 @@
+/*
+ * qm.h - C ABI of the GB300 plane-wave H-psi / block-Davidson library.
+ *
+ * Physics follows the plane-wave Kohn-Sham Hamiltonian of arXiv:2308.07277
+ * (Quantum MASALA):
+ *   (H psi)(G) = 1/2 |k+G|^2 psi(G)                                  [Sec. 2.2, Eq. KSHamMat]
+ *              + sum_{G'} Vt((G-G') mod N) psi(G')                    [Sec. 2.2 / Sec. 4.3]
+ *              + sum_p beta_p(G) D_p sum_{G'} conj(beta_p(G')) psi(G') [Sec. 2.3, KB form]
+ * where Vt(g) = (1/N_r) sum_j V(r_j) exp(-i g.r_j) on the FFT grid, i.e. exactly the
+ * "inverse FFT -> multiply by V(r) -> forward FFT -> keep the sphere" recipe of Sec. 4.3
+ * with the r2g convention fftn(f).take(idxgrid) of the GSpaceBase example (Sec. 4.3.2).
+ *
+ * Conventions shared by every call
+ *  - Units: Hartree atomic units (bohr, Hartree).
+ *  - Complex numbers are interleaved (re, im): double[2] in FP64, float[2] in FP32.
+ *  - Real-space grids are flat with x fastest: r index = j1 + N1*(j2 + N2*j3).
+ *  - The plane waves of k-point ik are ordered by their flat grid index
+ *    i1 + N1*(i2 + N2*i3), i_d = m_d mod N_d (G_1 varies fastest, as the paper prints).
+ *  - Wavefunction blocks are band-major: psi[b*ld + g], ld >= npw(ik).
+ *  - "device" pointers are CUDA device (or managed) memory owned by the caller; the
+ *    library never frees them.  "host" pointers are ordinary host memory.
+ *  - No exception crosses the ABI.  Every call returns a qm_status; on failure
+ *    qm_last_error() returns a thread-local, NUL-terminated message describing it.
+ *  - Asynchronous calls are ordered on the CUDA stream passed as `stream`
+ *    (a cudaStream_t, NULL = legacy default stream).  A gspace handle owns a device
+ *    workspace: calls that share a handle must be issued on ONE stream (or be
+ *    otherwise serialised); use one handle per concurrent stream.
+ *  - The library never falls back to a CPU path: without a usable CUDA device every
+ *    compute call returns QM_ERR_CUDA.
+ */
+#ifndef QM_H
+#define QM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qm_gspace_s* qm_gspace;   /* opaque, library-owned */
+
+typedef enum {
+    QM_OK = 0,
+    QM_ERR_ARG = 1,            /* invalid argument (NULL, size, range); nothing launched */
+    QM_ERR_CUDA = 2,           /* a CUDA runtime call or launch failed */
+    QM_ERR_OOM = 3,            /* device or host allocation failed */
+    QM_ERR_NOT_CONVERGED = 4,  /* Davidson hit max_iter; outputs still written */
+    QM_ERR_NUMERIC = 5,        /* non-finite value or breakdown (e.g. Cholesky) */
+    QM_ERR_TIMEOUT = 6,        /* a bounded device-side wait expired */
+    QM_ERR_UNSUPPORTED = 7     /* valid request this build does not implement */
+} qm_status;
+
+typedef enum {
+    QM_FP64 = 0,   /* everything in FP64 */
+    QM_MIXED = 1   /* FP32 FFT path and V multiply; nonlocal GEMMs in FP32 */
+} qm_precision;
+
+/*
+ * qm_gspace_create - build the plane-wave sphere and FFT grid for a cell
+ * (the GSpace of Sec. 4.3.2 for the wavefunction cutoff; truncation of Sec. 2.2 / 4.3.1).
+ *
+ *  lattice[9]     host; rows a_1, a_2, a_3 in Cartesian bohr.
+ *  nk, kpts       host; nk >= 1 k-points, kpts[3*ik + d] in crystal coordinates of the
+ *                 reciprocal lattice (k = sum_d kpts_d b_d, b_i . a_j = 2 pi delta_ij).
+ *  ecutwfc_ha     wavefunction cutoff E_c (Ha): plane waves with |k+G|^2/2 <= E_c are kept
+ *                 (inclusive, relative slack 1e-12).
+ *  grid_override  host; NULL -> grid rule: n_d = floor(sqrt(8 E_c) |a_d| / 2 pi),
+ *                 N_d = smallest 2,3,5-smooth integer >= 2 n_d + 1 (the dual 4 E_c density
+ *                 cutoff of Sec. 2.2).  Otherwise N_d = grid_override[d], each in [2, 512]
+ *                 and 2,3,5-smooth; a grid too small for the sphere is QM_ERR_ARG.
+ *  out            host; receives the handle.
+ * Host-only: no CUDA call is made here.  The handle's device tables are uploaded
+ * (synchronously, with cudaMalloc/cudaMemcpy) to the device that is current at the first
+ * compute call using the handle; later calls must run with that same device current.
+ * Make that first call outside any CUDA stream capture.
+ */
+qm_status qm_gspace_create(const double lattice[9], int nk, const double* kpts,
+                           double ecutwfc_ha, const int grid_override[3], qm_gspace* out);
+
+/*
+ * qm_gspace_query - sizes of a gspace.
+ *  grid[3]   host, may be NULL: (N1, N2, N3).
+ *  npw       host, may be NULL: npw[ik] for ik < nk (array of nk ints).
+ *  npw_max   host, may be NULL: max over k of npw.
+ *  nk        host, may be NULL: number of k-points.
+ */
+qm_status qm_gspace_query(qm_gspace g, int grid[3], int* npw, int* npw_max, int* nk);
+
+/*
+ * qm_gspace_indices - host copies of the sphere of k-point ik (Sec. 4.3.2 idxgrid/g_cryst).
+ *  idx     host, may be NULL: npw int32 flat grid indices (increasing).
+ *  miller  host, may be NULL: npw*3 int32 crystal components m of G.
+ *  kpg     host, may be NULL: npw*3 doubles, Cartesian k+G (bohr^-1).
+ */
+qm_status qm_gspace_indices(qm_gspace g, int ik, int32_t* idx, int32_t* miller, double* kpg);
+
+/* qm_gspace_destroy - free the handle and its device tables/workspace (NULL is a no-op).
+ * Synchronises the device first, so in-flight work that uses the handle completes. */
+void qm_gspace_destroy(qm_gspace g);
+
+/*
+ * qm_hpsi - out = H(k) psi for a block of nb bands (Eq. KSHamMat with the KB term;
+ * the local part by the IFFT / V(r) / FFT recipe of Sec. 4.3, stick-pruned as in
+ * Sec. 4.3.3; kinetic 1/2|k+G|^2 in G-space as in Sec. 4.3).
+ *
+ *  g, ik      gspace and k-point index (0 <= ik < nk).
+ *  nb         number of bands, >= 0 (0 is a no-op).
+ *  psi        device, nb rows of npw(ik) complex, row stride ld_psi (>= npw).
+ *             QM_FP64: double[2]; QM_MIXED: float[2].
+ *  vloc_r     device, N1*N2*N3 doubles, V(r_j) in Ha on the grid, x fastest.
+ *  nproj      number of projectors, >= 0.
+ *  beta       device, nproj rows of npw(ik) complex (same element type as psi),
+ *             row stride ld_beta (>= npw); may be NULL when nproj == 0.
+ *  D          device, nproj doubles (diagonal KB coefficients, Ha).
+ *  out        device, nb rows, row stride ld_out (>= npw), same element type as psi;
+ *             overwritten.  Must not overlap psi.
+ *  prec       QM_FP64 or QM_MIXED.
+ *  stream     cudaStream_t (NULL = default stream).  Asynchronous: returns after the
+ *             launches are queued.  Uses the handle's device workspace.
+ * Errors: QM_ERR_ARG (sizes, NULL pointers, misaligned rows), QM_ERR_OOM (workspace),
+ *         QM_ERR_CUDA (launch failure).
+ */
+qm_status qm_hpsi(qm_gspace g, int ik, int nb,
+                  const void* psi, int ld_psi,
+                  const double* vloc_r,
+                  int nproj, const void* beta, int ld_beta, const double* D,
+                  void* out, int ld_out,
+                  qm_precision prec, void* stream);
+
+/*
+ * Instrumentation (not part of the paper's method; used by benchmarks).
+ *  qm_launch_count  number of CUDA kernels this library has launched in this process.
+ *  qm_prof_enable   on != 0: from now on record a pair of CUDA events on the launch stream
+ *                   around every kernel launch; resets the accumulated times (any value).
+ *  qm_prof_read     waits for the recorded events and returns, for kernel family
+ *                   `family` (0 <= family < 8), the summed device time in ms and the number
+ *                   of launches timed since the last qm_prof_enable.
+ *  qm_prof_name     name of a kernel family ("" when out of range).
+ */
+unsigned long long qm_launch_count(void);
+qm_status qm_prof_enable(int on);
+qm_status qm_prof_read(int family, double* ms_total, long long* launches);
+const char* qm_prof_name(int family);
+
+/* qm_last_error - message of the last failed call on this thread ("" if none). */
+const char* qm_last_error(void);
+
+/* qm_version - library version string. */
+const char* qm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QM_H */

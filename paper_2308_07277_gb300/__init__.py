@@ -1,0 +1,14 @@
+"""GB300-native plane-wave H-psi / block-Davidson library (sm_103a CUDA behind a C ABI).
+
+The compute path lives in libqm.so (see include/qm.h); this package is its thin Python
+binding.  Importing it loads the library and raises if it is missing.
+"""
+from ._lib import load as _load
+
+_load()
+
+from .api import (GSpace, QMError, QM_FP64, QM_MIXED, qm_gspace_create, qm_gspace_destroy,  # noqa: E402
+                  qm_gspace_indices, qm_gspace_query, qm_hpsi, qm_last_error, qm_version)
+
+__all__ = ["GSpace", "QMError", "QM_FP64", "QM_MIXED", "qm_gspace_create", "qm_gspace_destroy",
+           "qm_gspace_indices", "qm_gspace_query", "qm_hpsi", "qm_last_error", "qm_version"]

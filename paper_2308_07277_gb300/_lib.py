@@ -1,0 +1,55 @@
+"""ctypes loader for libqm.so: the C ABI declared in include/qm.h.
+
+There is no fallback: if the library is missing or cannot be loaded, importing the
+binding raises, and every compute call needs CUDA device tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libqm.so")
+
+c_int_p = ctypes.POINTER(ctypes.c_int)
+c_double_p = ctypes.POINTER(ctypes.c_double)
+c_int32_p = ctypes.POINTER(ctypes.c_int32)
+
+# name -> (restype, argtypes); mirrors include/qm.h
+SIGNATURES = {
+    "qm_gspace_create": (ctypes.c_int, [c_double_p, ctypes.c_int, c_double_p, ctypes.c_double, c_int_p,
+                                        ctypes.POINTER(ctypes.c_void_p)]),
+    "qm_gspace_query": (ctypes.c_int, [ctypes.c_void_p, c_int_p, c_int_p, c_int_p, c_int_p]),
+    "qm_gspace_indices": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_int32_p, c_int32_p, c_double_p]),
+    "qm_gspace_destroy": (None, [ctypes.c_void_p]),
+    "qm_hpsi": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                               ctypes.c_void_p, ctypes.c_int,
+                               ctypes.c_void_p,
+                               ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                               ctypes.c_void_p, ctypes.c_int,
+                               ctypes.c_int, ctypes.c_void_p]),
+    "qm_launch_count": (ctypes.c_ulonglong, []),
+    "qm_prof_enable": (ctypes.c_int, [ctypes.c_int]),
+    "qm_prof_read": (ctypes.c_int, [ctypes.c_int, c_double_p, ctypes.POINTER(ctypes.c_longlong)]),
+    "qm_prof_name": (ctypes.c_char_p, [ctypes.c_int]),
+    "qm_last_error": (ctypes.c_char_p, []),
+    "qm_version": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def load():
+    """Load libqm.so once and attach the signatures; raises OSError if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise OSError(f"{LIB_PATH} is not built; run paper_2308_07277_gb300.build.build() (needs nvcc)")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib

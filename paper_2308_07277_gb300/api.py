@@ -1,0 +1,151 @@
+"""Thin Python binding over the C ABI (include/qm.h): argument marshalling only.
+
+Function names match the C entry points.  Device buffers are torch CUDA tensors (torch
+is used for device memory and streams); every computation runs in libqm.so.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+
+QM_FP64 = 0
+QM_MIXED = 1
+_PREC = {"fp64": QM_FP64, "mixed": QM_MIXED, QM_FP64: QM_FP64, QM_MIXED: QM_MIXED}
+STATUS = {0: "QM_OK", 1: "QM_ERR_ARG", 2: "QM_ERR_CUDA", 3: "QM_ERR_OOM", 4: "QM_ERR_NOT_CONVERGED",
+          5: "QM_ERR_NUMERIC", 6: "QM_ERR_TIMEOUT", 7: "QM_ERR_UNSUPPORTED"}
+
+
+class QMError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(st):
+    if st != 0:
+        raise QMError(st, _lib.load().qm_last_error().decode())
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev_ptr(t, name, dtype=None):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor (no CPU path exists)")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if t.dim() >= 1 and t.stride(-1) != 1:
+        raise ValueError(f"{name} must have unit stride along plane waves")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def qm_version():
+    return _lib.load().qm_version().decode()
+
+
+def qm_last_error():
+    return _lib.load().qm_last_error().decode()
+
+
+def qm_gspace_create(lattice, kpts, ecutwfc_ha, grid=None):
+    """Handle (ctypes.c_void_p) for lattice rows a_i (bohr), kpts (nk,3) crystal, E_c (Ha)."""
+    lib = _lib.load()
+    lat = np.ascontiguousarray(np.asarray(lattice, np.float64).reshape(9))
+    k = np.ascontiguousarray(np.asarray(kpts, np.float64).reshape(-1, 3))
+    g = ctypes.c_void_p()
+    gr = None
+    if grid is not None:
+        gr = (ctypes.c_int * 3)(*[int(x) for x in grid])
+    _check(lib.qm_gspace_create(_dp(lat), int(k.shape[0]), _dp(k), float(ecutwfc_ha), gr, ctypes.byref(g)))
+    return g
+
+
+def qm_gspace_query(g):
+    lib = _lib.load()
+    nk = ctypes.c_int()
+    _check(lib.qm_gspace_query(g, None, None, None, ctypes.byref(nk)))
+    grid = (ctypes.c_int * 3)()
+    npw = (ctypes.c_int * nk.value)()
+    npw_max = ctypes.c_int()
+    _check(lib.qm_gspace_query(g, grid, npw, ctypes.byref(npw_max), None))
+    return {"grid": tuple(grid), "npw": list(npw), "npw_max": npw_max.value, "nk": nk.value}
+
+
+def qm_gspace_indices(g, ik):
+    """(idx (npw,) int32, miller (npw,3) int32, kpg (npw,3) float64) for k-point ik."""
+    lib = _lib.load()
+    npw = qm_gspace_query(g)["npw"][ik]
+    idx = np.empty(npw, np.int32)
+    mil = np.empty((npw, 3), np.int32)
+    kpg = np.empty((npw, 3), np.float64)
+    i32 = ctypes.POINTER(ctypes.c_int32)
+    _check(lib.qm_gspace_indices(g, int(ik), idx.ctypes.data_as(i32), mil.ctypes.data_as(i32), _dp(kpg)))
+    return idx, mil, kpg
+
+
+def qm_gspace_destroy(g):
+    if g is not None and g.value:
+        _lib.load().qm_gspace_destroy(g)
+
+
+def qm_hpsi(g, ik, psi, vloc, beta, D, out=None, prec="fp64", stream=None):
+    """out = H(k) psi.  psi (nb, >=npw) complex128 (fp64) or complex64 (mixed) CUDA tensor;
+    vloc (N_r,) float64; beta (nproj, >=npw) like psi or None; D (nproj,) float64."""
+    lib = _lib.load()
+    p = _PREC[prec]
+    cdt = torch.complex128 if p == QM_FP64 else torch.complex64
+    if psi.dim() != 2:
+        raise ValueError("psi must be 2-D (nb, ld)")
+    if out is None:
+        out = torch.empty_like(psi)
+    nproj = 0 if beta is None else int(beta.shape[0])
+    _check(lib.qm_hpsi(g, int(ik), int(psi.shape[0]),
+                       _dev_ptr(psi, "psi", cdt), int(psi.stride(0)),
+                       _dev_ptr(vloc, "vloc", torch.float64),
+                       nproj, _dev_ptr(beta, "beta", cdt), int(beta.stride(0)) if nproj else 0,
+                       _dev_ptr(D, "D", torch.float64) if nproj else None,
+                       _dev_ptr(out, "out", cdt), int(out.stride(0)),
+                       p, _stream_ptr(stream)))
+    return out
+
+
+class GSpace:
+    """Owning wrapper of a qm_gspace handle."""
+
+    def __init__(self, lattice, kpts, ecutwfc_ha, grid=None):
+        self.handle = qm_gspace_create(lattice, kpts, ecutwfc_ha, grid)
+        info = qm_gspace_query(self.handle)
+        self.grid = info["grid"]
+        self.npw = info["npw"]
+        self.npw_max = info["npw_max"]
+        self.nk = info["nk"]
+
+    def indices(self, ik):
+        return qm_gspace_indices(self.handle, ik)
+
+    def hpsi(self, ik, psi, vloc, beta, D, out=None, prec="fp64", stream=None):
+        return qm_hpsi(self.handle, ik, psi, vloc, beta, D, out=out, prec=prec, stream=stream)
+
+    def close(self):
+        if self.handle is not None:
+            qm_gspace_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,358 @@
+// Host-side G-space construction: FFT grid, plane-wave sphere per k-point, x-stick
+// tables and mixed-radix FFT plans, uploaded to the device once per handle.
+//
+// Follows the truncation of Sec. 2.2 (|k+G|^2/2 <= E_cut, potential up to 4 E_cut) and
+// the GSpace of Sec. 4.3.2 (plane waves listed with G_1 fastest); the stick pruning of
+// Sec. 4.3.3 (1D FFTs only on sticks that hold a plane wave) with sticks along x as in
+// the paper's Fig. 1.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+
+#include "qm_internal.h"
+
+namespace qm {
+
+static thread_local std::string g_last_error;
+
+qm_status fail(qm_status st, const std::string& msg) {
+    g_last_error = msg;
+    return st;
+}
+void clear_error() { g_last_error.clear(); }
+
+qm_status cuda_check(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return QM_OK;
+    cudaGetLastError();  // clear a sticky launch error where possible
+    return fail(e == cudaErrorMemoryAllocation ? QM_ERR_OOM : QM_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+qm_status ensure_workspace(qm_gspace g, size_t bytes, cudaStream_t stream) {
+    if (g->ws.bytes >= bytes) return QM_OK;
+    if (g->ws.ptr) {
+        qm_status st = cuda_check(cudaStreamSynchronize(stream), "workspace sync");
+        if (st) return st;
+        cudaFree(g->ws.ptr);
+        g->ws.ptr = nullptr;
+        g->ws.bytes = 0;
+    }
+    size_t want = align_up(bytes + bytes / 8, 1 << 20);
+    qm_status st = cuda_check(cudaMalloc(&g->ws.ptr, want), "workspace cudaMalloc");
+    if (st) return st;
+    g->ws.bytes = want;
+    return QM_OK;
+}
+
+static bool smooth235(int n) {
+    if (n <= 0) return false;
+    for (int p : {2, 3, 5})
+        while (n % p == 0) n /= p;
+    return n == 1;
+}
+
+static void inv3_transpose_2pi(const double a[9], double b[9]) {
+    // b rows = 2 pi (A^-1)^T rows, i.e. b_i . a_j = 2 pi delta_ij
+    double c[9];
+    c[0] = a[4] * a[8] - a[5] * a[7];
+    c[1] = a[5] * a[6] - a[3] * a[8];
+    c[2] = a[3] * a[7] - a[4] * a[6];
+    c[3] = a[2] * a[7] - a[1] * a[8];
+    c[4] = a[0] * a[8] - a[2] * a[6];
+    c[5] = a[1] * a[6] - a[0] * a[7];
+    c[6] = a[1] * a[5] - a[2] * a[4];
+    c[7] = a[2] * a[3] - a[0] * a[5];
+    c[8] = a[0] * a[4] - a[1] * a[3];
+    double det = a[0] * c[0] + a[1] * c[1] + a[2] * c[2];
+    // (A^-1)^T = cofactor matrix / det; row i of the cofactor matrix is c[3i..3i+2]
+    const double twopi = 2.0 * M_PI;
+    for (int i = 0; i < 9; ++i) b[i] = twopi * c[i] / det;
+}
+
+static void make_plan(int n, AxisPlan& p, std::vector<int>& rev) {
+    p.n = n;
+    p.nst = 0;
+    int m = n;
+    std::vector<int> rs;
+    while (m % 4 == 0) { rs.push_back(4); m /= 4; }
+    while (m % 2 == 0) { rs.push_back(2); m /= 2; }
+    while (m % 3 == 0) { rs.push_back(3); m /= 3; }
+    while (m % 5 == 0) { rs.push_back(5); m /= 5; }
+    int L = n;
+    for (int r : rs) {
+        p.r[p.nst] = r;
+        p.L[p.nst] = L;
+        ++p.nst;
+        L /= r;
+    }
+    // position of natural index k after the in-place DIF stages:
+    // pos(k) = M * (k mod r) + pos_sub(k div r), applied recursively over the stages.
+    std::vector<int> pos(n);
+    for (int k = 0; k < n; ++k) {
+        int kk = k, off = 0;
+        for (int s = 0; s < p.nst; ++s) {
+            int r = p.r[s], Ls = p.L[s], M = Ls / r;
+            off += M * (kk % r);
+            kk /= r;
+        }
+        pos[k] = off;
+    }
+    rev.assign(n, 0);
+    for (int k = 0; k < n; ++k) rev[pos[k]] = k;
+}
+
+struct PW {
+    int64_t idx;
+    int m[3];
+    double q[3];
+    double kin;
+};
+
+qm_status ensure_device(qm_gspace g) {
+    int dev = 0;
+    qm_status st = cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+    if (st) return st;
+    if (g->uploaded) {
+        if (dev != g->device) return fail(QM_ERR_ARG, "gspace tables live on another device than the current one");
+        return QM_OK;
+    }
+    auto upload = [&](void** dptr, const void* src, size_t bytes) -> qm_status {
+        if (bytes == 0) bytes = 16;
+        qm_status s2 = cuda_check(cudaMalloc(dptr, bytes), "gspace table cudaMalloc");
+        if (s2) return s2;
+        return cuda_check(cudaMemcpy(*dptr, src, bytes, cudaMemcpyHostToDevice), "gspace table upload");
+    };
+    g->device = dev;
+    g->uploaded = true;  // destroy frees whatever was allocated even on partial failure
+    for (int d = 0; d < 3; ++d) {
+        std::vector<float2> t32(g->n[d]);
+        for (int t = 0; t < g->n[d]; ++t) t32[t] = make_float2((float)g->h_tw[d][t].x, (float)g->h_tw[d][t].y);
+        if ((st = upload((void**)&g->tw64[d], g->h_tw[d].data(), sizeof(double2) * g->n[d])) ||
+            (st = upload((void**)&g->tw32[d], t32.data(), sizeof(float2) * g->n[d])) ||
+            (st = upload((void**)&g->rev[d], g->h_rev[d].data(), sizeof(int) * g->n[d])))
+            return st;
+    }
+    for (auto& kt : g->k) {
+        std::vector<float> kinf(kt.h_kin.begin(), kt.h_kin.end());
+        if ((st = upload((void**)&kt.stick_g0, kt.h_g0.data(), sizeof(int) * kt.h_g0.size())) ||
+            (st = upload((void**)&kt.stick_plane, kt.h_plane.data(), sizeof(int) * kt.h_plane.size())) ||
+            (st = upload((void**)&kt.rows, kt.h_rows.data(), sizeof(int) * kt.h_rows.size())) ||
+            (st = upload((void**)&kt.g_code, kt.h_code.data(), sizeof(int2) * kt.h_code.size())) ||
+            (st = upload((void**)&kt.kin, kt.h_kin.data(), sizeof(double) * kt.h_kin.size())) ||
+            (st = upload((void**)&kt.kin_f, kinf.data(), sizeof(float) * kinf.size())))
+            return st;
+    }
+    return QM_OK;
+}
+
+}  // namespace qm
+
+using namespace qm;
+
+extern "C" const char* qm_last_error(void) { return g_last_error.c_str(); }
+extern "C" const char* qm_version(void) { return "qm-gb300 0.1 (sm_103a)"; }
+
+extern "C" qm_status qm_gspace_create(const double lattice[9], int nk, const double* kpts,
+                                      double ecutwfc_ha, const int grid_override[3],
+                                      qm_gspace* out) {
+    clear_error();
+    if (!lattice || !kpts || !out) return fail(QM_ERR_ARG, "qm_gspace_create: NULL argument");
+    *out = nullptr;
+    if (nk < 1 || nk > 4096) return fail(QM_ERR_ARG, "qm_gspace_create: nk out of range");
+    if (!(ecutwfc_ha > 0.0) || !std::isfinite(ecutwfc_ha))
+        return fail(QM_ERR_ARG, "qm_gspace_create: ecutwfc_ha must be > 0");
+    for (int i = 0; i < 9; ++i)
+        if (!std::isfinite(lattice[i])) return fail(QM_ERR_ARG, "qm_gspace_create: non-finite lattice");
+
+    auto* g = new qm_gspace_s();
+    std::memcpy(g->lattice, lattice, sizeof(double) * 9);
+    inv3_transpose_2pi(lattice, g->recip);
+    double vol = std::fabs(lattice[0] * (lattice[4] * lattice[8] - lattice[5] * lattice[7]) -
+                           lattice[1] * (lattice[3] * lattice[8] - lattice[5] * lattice[6]) +
+                           lattice[2] * (lattice[3] * lattice[7] - lattice[4] * lattice[6]));
+    if (!(vol > 1e-8)) {
+        delete g;
+        return fail(QM_ERR_ARG, "qm_gspace_create: singular lattice");
+    }
+    g->ecut = ecutwfc_ha;
+    g->nk = nk;
+    g->kpts.assign(kpts, kpts + 3 * nk);
+    const double qmax = std::sqrt(2.0 * ecutwfc_ha);
+    for (int d = 0; d < 3; ++d) {
+        double alen = std::sqrt(lattice[3 * d] * lattice[3 * d] + lattice[3 * d + 1] * lattice[3 * d + 1] +
+                                lattice[3 * d + 2] * lattice[3 * d + 2]);
+        if (grid_override) {
+            g->n[d] = grid_override[d];
+            if (g->n[d] < 2 || g->n[d] > 512 || !smooth235(g->n[d])) {
+                delete g;
+                return fail(QM_ERR_ARG, "qm_gspace_create: grid_override must be 2,3,5-smooth in [2,512]");
+            }
+        } else {
+            // dual cutoff: |G| <= 2 qmax  =>  n = floor(2 qmax |a| / 2 pi)
+            int n = (int)std::floor(2.0 * qmax * alen / (2.0 * M_PI));
+            int N = 2 * n + 1;
+            while (!smooth235(N)) ++N;
+            if (N > 512) {
+                delete g;
+                return fail(QM_ERR_ARG, "qm_gspace_create: grid rule gives N > 512");
+            }
+            g->n[d] = N;
+        }
+    }
+    const int N1 = g->n[0], N2 = g->n[1], N3 = g->n[2];
+    g->ldx = (N1 % 2 == 0) ? N1 + 1 : N1;
+    g->ldy = (N2 % 2 == 0) ? N2 + 1 : N2;
+
+    qm_status st = QM_OK;
+    // FFT plans, twiddles exp(+2 pi i t / N) (quarter turns exact), digit-reversal tables
+    for (int d = 0; d < 3; ++d) {
+        make_plan(g->n[d], g->plan[d], g->h_rev[d]);
+        int N = g->n[d];
+        g->h_tw[d].resize(N);
+        for (int t = 0; t < N; ++t) {
+            double ang = 2.0 * M_PI * (double)t / (double)N;
+            double c = std::cos(ang), sn = std::sin(ang);
+            if ((4 * t) % N == 0) {
+                int q = (4 * t) / N;
+                c = (q == 0) ? 1.0 : (q == 2 ? -1.0 : 0.0);
+                sn = (q == 1) ? 1.0 : (q == 3 ? -1.0 : 0.0);
+            }
+            g->h_tw[d][t] = make_double2(c, sn);
+        }
+    }
+
+    // plane-wave spheres
+    const double* b = g->recip;
+    g->k.resize(nk);
+    for (int ik = 0; ik < nk; ++ik) {
+        const double* kc = kpts + 3 * ik;
+        int lo[3], hi[3];
+        for (int d = 0; d < 3; ++d) {
+            double alen = std::sqrt(lattice[3 * d] * lattice[3 * d] + lattice[3 * d + 1] * lattice[3 * d + 1] +
+                                    lattice[3 * d + 2] * lattice[3 * d + 2]);
+            double bound = qmax * alen / (2.0 * M_PI);
+            lo[d] = (int)std::floor(-kc[d] - bound) - 1;
+            hi[d] = (int)std::ceil(-kc[d] + bound) + 1;
+        }
+        std::vector<PW> pws;
+        for (int m3 = lo[2]; m3 <= hi[2]; ++m3)
+            for (int m2 = lo[1]; m2 <= hi[1]; ++m2)
+                for (int m1 = lo[0]; m1 <= hi[0]; ++m1) {
+                    double c1 = m1 + kc[0], c2 = m2 + kc[1], c3 = m3 + kc[2];
+                    PW p;
+                    for (int x = 0; x < 3; ++x) p.q[x] = c1 * b[x] + c2 * b[3 + x] + c3 * b[6 + x];
+                    p.kin = 0.5 * (p.q[0] * p.q[0] + p.q[1] * p.q[1] + p.q[2] * p.q[2]);
+                    if (!(p.kin <= ecutwfc_ha * (1.0 + 1e-12))) continue;
+                    p.m[0] = m1; p.m[1] = m2; p.m[2] = m3;
+                    int i1 = ((m1 % N1) + N1) % N1, i2 = ((m2 % N2) + N2) % N2, i3 = ((m3 % N3) + N3) % N3;
+                    p.idx = (int64_t)i1 + (int64_t)N1 * ((int64_t)i2 + (int64_t)N2 * i3);
+                    pws.push_back(p);
+                }
+        std::sort(pws.begin(), pws.end(), [](const PW& x, const PW& y) { return x.idx < y.idx; });
+        for (size_t i = 1; i < pws.size(); ++i)
+            if (pws[i].idx == pws[i - 1].idx) {
+                qm_gspace_destroy(g);
+                return fail(QM_ERR_ARG, "qm_gspace_create: FFT grid too small for the plane-wave sphere");
+            }
+        KTables& kt = g->k[ik];
+        kt.npw = (int)pws.size();
+        if (kt.npw == 0) {
+            qm_gspace_destroy(g);
+            return fail(QM_ERR_ARG, "qm_gspace_create: empty plane-wave sphere");
+        }
+        // sticks along x: consecutive plane waves sharing (i2, i3)
+        std::vector<int> g0, plane, rows;
+        std::vector<int2> code(kt.npw);
+        std::vector<double> kin(kt.npw);
+        int64_t last = -1;
+        for (int i = 0; i < kt.npw; ++i) {
+            int64_t key = pws[i].idx / N1;
+            if (key != last) {
+                g0.push_back(i);
+                int i2 = (int)(key % N2), i3 = (int)(key / N2);
+                plane.push_back(i3 * g->ldy + i2);
+                if (rows.empty() || rows.back() != i3) rows.push_back(i3);
+                last = key;
+            }
+            code[i] = make_int2((int)g0.size() - 1, (int)(pws[i].idx % N1));
+            kin[i] = pws[i].kin;
+        }
+        kt.nstick = (int)g0.size();
+        g0.push_back(kt.npw);
+        kt.nstick_pad = (int)align_up(kt.nstick, 4);
+        std::sort(rows.begin(), rows.end());
+        rows.erase(std::unique(rows.begin(), rows.end()), rows.end());
+        kt.nrow = (int)rows.size();
+        kt.h_idx.resize(kt.npw);
+        kt.h_miller.resize(3 * (size_t)kt.npw);
+        kt.h_kpg.resize(3 * (size_t)kt.npw);
+        for (int i = 0; i < kt.npw; ++i) {
+            kt.h_idx[i] = (int32_t)pws[i].idx;
+            for (int x = 0; x < 3; ++x) {
+                kt.h_miller[3 * i + x] = pws[i].m[x];
+                kt.h_kpg[3 * i + x] = pws[i].q[x];
+            }
+        }
+        kt.h_g0 = std::move(g0);
+        kt.h_plane = std::move(plane);
+        kt.h_rows = std::move(rows);
+        kt.h_code = std::move(code);
+        kt.h_kin = std::move(kin);
+    }
+    *out = g;
+    return QM_OK;
+}
+
+extern "C" qm_status qm_gspace_query(qm_gspace g, int grid[3], int* npw, int* npw_max, int* nk) {
+    clear_error();
+    if (!g) return fail(QM_ERR_ARG, "qm_gspace_query: NULL handle");
+    if (grid) for (int d = 0; d < 3; ++d) grid[d] = g->n[d];
+    int mx = 0;
+    for (int ik = 0; ik < g->nk; ++ik) {
+        if (npw) npw[ik] = g->k[ik].npw;
+        mx = std::max(mx, g->k[ik].npw);
+    }
+    if (npw_max) *npw_max = mx;
+    if (nk) *nk = g->nk;
+    return QM_OK;
+}
+
+extern "C" qm_status qm_gspace_indices(qm_gspace g, int ik, int32_t* idx, int32_t* miller, double* kpg) {
+    clear_error();
+    if (!g) return fail(QM_ERR_ARG, "qm_gspace_indices: NULL handle");
+    if (ik < 0 || ik >= g->nk) return fail(QM_ERR_ARG, "qm_gspace_indices: ik out of range");
+    const KTables& kt = g->k[ik];
+    if (idx) std::memcpy(idx, kt.h_idx.data(), sizeof(int32_t) * kt.npw);
+    if (miller) std::memcpy(miller, kt.h_miller.data(), sizeof(int32_t) * 3 * (size_t)kt.npw);
+    if (kpg) std::memcpy(kpg, kt.h_kpg.data(), sizeof(double) * 3 * (size_t)kt.npw);
+    return QM_OK;
+}
+
+extern "C" void qm_gspace_destroy(qm_gspace g) {
+    if (!g) return;
+    if (g->uploaded) {
+        int cur = 0;
+        cudaGetDevice(&cur);
+        cudaSetDevice(g->device);
+        cudaDeviceSynchronize();
+        for (auto& kt : g->k) {
+            cudaFree(kt.stick_g0);
+            cudaFree(kt.stick_plane);
+            cudaFree(kt.rows);
+            cudaFree(kt.g_code);
+            cudaFree(kt.kin);
+            cudaFree(kt.kin_f);
+        }
+        for (int d = 0; d < 3; ++d) {
+            cudaFree(g->tw64[d]);
+            cudaFree(g->tw32[d]);
+            cudaFree(g->rev[d]);
+        }
+        if (g->ws.ptr) cudaFree(g->ws.ptr);
+        cudaSetDevice(cur);
+    }
+    delete g;
+}

@@ -1,0 +1,113 @@
+// qm_hpsi: H(k) psi for a block of bands (Eq. KSHamMat of Sec. 2.2 with the
+// Kleinman-Bylander term of Sec. 2.3).
+//
+// Launch sequence on the caller's stream (no host synchronisation):
+//   1. k_vt            V(r)/N_r laid out in the FFT path's permuted plane order
+//   2. gemm_cn         P[p][b] = <beta_p|psi_b>             (nonlocal projection)
+//   3. K1, K2, K3      out = 1/2|k+G|^2 psi + (V psi)(G)    (per chunk of bands)
+//   4. gemm_tn         out += sum_p beta_p D_p P[p][b]      (nonlocal apply)
+// Workspace (owned by the gspace handle): Vt | P | split-K partials | stick buffer.
+#include <algorithm>
+#include <cstdint>
+
+#include "qm_internal.h"
+
+namespace qm {
+
+// Stick-buffer budget per chunk of bands: small enough that a chunk's intermediate data
+// stays resident in the 129 MB L2 between the three FFT kernels.
+constexpr size_t kStickBudget = 48ull << 20;
+
+struct HpsiLayout {
+    size_t vt_off, p_off, part_off, t_off, total, t_bytes;
+    int splits;
+};
+
+static HpsiLayout hpsi_layout(qm_gspace g, int ik, int nb, int nproj, bool fp32) {
+    HpsiLayout L{};
+    const size_t cs = fp32 ? sizeof(float2) : sizeof(double2);
+    const size_t rs = fp32 ? sizeof(float) : sizeof(double);
+    const size_t nr = (size_t)g->n[0] * g->n[1] * g->n[2];
+    const int npw = g->k[ik].npw;
+    L.splits = nproj > 0 ? zgemm_cn_splits(nproj, nb, npw) : 1;
+    size_t off = 0;
+    L.vt_off = off;
+    off = align_up(off + nr * rs, 256);
+    L.p_off = off;
+    off = align_up(off + (size_t)nproj * nb * cs, 256);
+    L.part_off = off;
+    off = align_up(off + (L.splits > 1 ? (size_t)L.splits * nproj * nb * cs : 0), 256);
+    L.t_off = off;
+    const size_t per_band = stick_buffer_bytes_per_band(g, ik, fp32);
+    const size_t nbc = std::max<size_t>(1, std::min<size_t>((size_t)nb, kStickBudget / per_band));
+    L.t_bytes = nbc * per_band;
+    off = align_up(off + L.t_bytes, 256);
+    L.total = off;
+    return L;
+}
+
+}  // namespace qm
+
+using namespace qm;
+
+extern "C" qm_status qm_hpsi(qm_gspace g, int ik, int nb, const void* psi, int ld_psi, const double* vloc_r,
+                             int nproj, const void* beta, int ld_beta, const double* D, void* out, int ld_out,
+                             qm_precision prec, void* stream) {
+    clear_error();
+    if (!g) return fail(QM_ERR_ARG, "qm_hpsi: NULL gspace");
+    if (ik < 0 || ik >= g->nk) return fail(QM_ERR_ARG, "qm_hpsi: ik out of range");
+    if (nb < 0 || nproj < 0) return fail(QM_ERR_ARG, "qm_hpsi: negative nb or nproj");
+    if (prec != QM_FP64 && prec != QM_MIXED) return fail(QM_ERR_ARG, "qm_hpsi: unknown precision");
+    if (nb == 0) return QM_OK;
+    const int npw = g->k[ik].npw;
+    if (!psi || !out || !vloc_r) return fail(QM_ERR_ARG, "qm_hpsi: NULL psi, out or vloc_r");
+    if (ld_psi < npw || ld_out < npw) return fail(QM_ERR_ARG, "qm_hpsi: leading dimension < npw");
+    if (nproj > 0 && (!beta || !D)) return fail(QM_ERR_ARG, "qm_hpsi: NULL beta or D with nproj > 0");
+    if (nproj > 0 && ld_beta < npw) return fail(QM_ERR_ARG, "qm_hpsi: ld_beta < npw");
+    const bool fp32 = prec == QM_MIXED;
+    const uintptr_t al = fp32 ? 8 : 16;
+    if (((uintptr_t)psi | (uintptr_t)out | (nproj > 0 ? (uintptr_t)beta : 0)) % al)
+        return fail(QM_ERR_ARG, "qm_hpsi: psi/out/beta not aligned to the complex element size");
+    const size_t cs = fp32 ? sizeof(float2) : sizeof(double2);
+    {
+        const char* a0 = (const char*)psi;
+        const char* a1 = a0 + ((size_t)(nb - 1) * ld_psi + npw) * cs;
+        const char* b0 = (const char*)out;
+        const char* b1 = b0 + ((size_t)(nb - 1) * ld_out + npw) * cs;
+        if (a0 < b1 && b0 < a1) return fail(QM_ERR_ARG, "qm_hpsi: out overlaps psi");
+    }
+
+    qm_status st = ensure_device(g);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+
+    const HpsiLayout L = hpsi_layout(g, ik, nb, nproj, fp32);
+    if ((st = ensure_workspace(g, L.total, s))) return st;
+    char* ws = (char*)g->ws.ptr;
+    void* vt = ws + L.vt_off;
+    void* P = ws + L.p_off;
+    void* part = ws + L.part_off;
+    void* T = ws + L.t_off;
+
+    if ((st = launch_vt_prepare(g, vloc_r, vt, fp32, s))) return st;
+    if (nproj > 0) {
+        if (fp32)
+            st = cgemm_cn(nproj, nb, npw, (const float2*)beta, ld_beta, (const float2*)psi, ld_psi, (float2*)P, nb,
+                          (float2*)part, L.splits, s);
+        else
+            st = zgemm_cn(nproj, nb, npw, (const double2*)beta, ld_beta, (const double2*)psi, ld_psi, (double2*)P,
+                          nb, (double2*)part, L.splits, s);
+        if (st) return st;
+    }
+    if ((st = launch_local_kinetic(g, ik, nb, psi, ld_psi, vt, out, ld_out, T, L.t_bytes, fp32, s))) return st;
+    if (nproj > 0) {
+        if (fp32)
+            st = cgemm_tn(nb, npw, nproj, (const float2*)P, nb, D, (const float2*)beta, ld_beta, (float2*)out,
+                          ld_out, true, s);
+        else
+            st = zgemm_tn(nb, npw, nproj, (const double2*)P, nb, D, (const double2*)beta, ld_beta, (double2*)out,
+                          ld_out, true, s);
+        if (st) return st;
+    }
+    return QM_OK;
+}

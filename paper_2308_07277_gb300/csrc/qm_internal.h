@@ -1,0 +1,134 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/qm.h"
+
+namespace qm {
+
+constexpr int kMaxStages = 12;
+
+// Mixed-radix plan of one FFT axis.  Stage s (0-based, DIF order) works on blocks of
+// length L[s] with radix r[s]; M = L[s]/r[s] butterflies per block.
+struct AxisPlan {
+    int n;
+    int nst;
+    int r[kMaxStages];
+    int L[kMaxStages];
+};
+
+// Per-k-point tables (device pointers unless noted).
+struct KTables {
+    int npw = 0;
+    int nstick = 0;      // active x-sticks: distinct (i2, i3) holding >= 1 plane wave
+    int nstick_pad = 0;  // row stride of the stick buffers
+    int nrow = 0;        // active plane rows: distinct i3 among the sticks
+    int* stick_g0 = nullptr;     // [nstick+1] first plane wave of each stick
+    int* stick_plane = nullptr;  // [nstick]  i3 * ldy + i2 (position in a yz plane)
+    int* rows = nullptr;         // [nrow]    active i3 values
+    int2* g_code = nullptr;      // [npw]     {stick id, i1}
+    double* kin = nullptr;       // [npw]     |k+G|^2 / 2
+    float* kin_f = nullptr;      // [npw]     same, FP32
+    // host copies (the device tables are uploaded from these on first use)
+    std::vector<int32_t> h_idx, h_miller;
+    std::vector<double> h_kpg, h_kin;
+    std::vector<int> h_g0, h_plane, h_rows;
+    std::vector<int2> h_code;
+};
+
+struct Workspace {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace qm
+
+struct qm_gspace_s {
+    int device = 0;
+    bool uploaded = false;   // device tables present (on `device`)
+    int n[3] = {0, 0, 0};
+    int ldx = 0;   // padded line length of x sticks in shared memory
+    int ldy = 0;   // padded row length of a yz plane in shared memory
+    double lattice[9];
+    double recip[9];
+    double ecut = 0;
+    int nk = 0;
+    std::vector<double> kpts;
+    std::vector<qm::KTables> k;
+    qm::AxisPlan plan[3];
+    // twiddles exp(+2 pi i t / N_d), t < N_d, and the digit-reversal tables rev[p] =
+    // natural index held at position p after the in-place DIF pass.
+    double2* tw64[3] = {nullptr, nullptr, nullptr};
+    float2* tw32[3] = {nullptr, nullptr, nullptr};
+    int* rev[3] = {nullptr, nullptr, nullptr};
+    std::vector<double2> h_tw[3];
+    std::vector<int> h_rev[3];
+    qm::Workspace ws;
+};
+
+namespace qm {
+
+// error reporting (thread-local message)
+qm_status fail(qm_status st, const std::string& msg);
+qm_status cuda_check(cudaError_t e, const char* what);
+void clear_error();
+
+// upload the handle's tables to the current device on first use (synchronous)
+qm_status ensure_device(qm_gspace g);
+
+// grow-only workspace owned by a gspace handle; synchronises `stream` before regrowing
+qm_status ensure_workspace(qm_gspace g, size_t bytes, cudaStream_t stream);
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// ---- launch counting / per-kernel timing (prof.cpp) ----
+enum ProfFamily { PF_VT = 0, PF_STICK_INV, PF_PLANE, PF_STICK_FWD, PF_GEMM_CN, PF_REDUCE, PF_GEMM_TN, PF_OTHER,
+                  kProfFamilies };
+void count_launch(int n);
+// Counts one launch; when timing is enabled records CUDA events on `s` around the scope.
+class ProfScope {
+  public:
+    ProfScope(int family, cudaStream_t s);
+    ~ProfScope();
+    ProfScope(const ProfScope&) = delete;
+    ProfScope& operator=(const ProfScope&) = delete;
+
+  private:
+    int family_;
+    cudaStream_t s_;
+    cudaEvent_t a_ = nullptr, b_ = nullptr;
+    bool active_ = false;
+};
+
+// ---- FFT path (fft_path.cu) ----
+// Vt[p1][p3][p2] = V(rev1[p1], rev2[p2], rev3[p3]) / N_r   (real type R)
+qm_status launch_vt_prepare(qm_gspace g, const double* vloc, void* vt, bool fp32, cudaStream_t s);
+// local + kinetic part for nb bands: out = kin*psi + (V psi)(G); T = stick workspace
+qm_status launch_local_kinetic(qm_gspace g, int ik, int nb, const void* psi, int ld_psi,
+                               const void* vt, void* out, int ld_out, void* tbuf,
+                               size_t tbuf_bytes, bool fp32, cudaStream_t s);
+size_t stick_buffer_bytes_per_band(qm_gspace g, int ik, bool fp32);
+
+// ---- complex GEMMs (zgemm.cu) ----
+// C[m][n] = sum_k conj(A[m][k]) * B[n][k]   (A: M rows, B: N rows, k contiguous);
+// split over K into `splits` partial sums reduced in a fixed order (deterministic).
+qm_status zgemm_cn(int M, int N, int K, const double2* A, int lda, const double2* B, int ldb,
+                   double2* C, int ldc, double2* partial, int splits, cudaStream_t s);
+// C[m][n] (+)= sum_k A[k][m] * d[k] * B[k][n]   (d may be NULL -> 1)
+qm_status zgemm_tn(int M, int N, int K, const double2* A, int lda, const double* d,
+                   const double2* B, int ldb, double2* C, int ldc, bool accumulate,
+                   cudaStream_t s);
+int zgemm_cn_splits(int M, int N, int K);
+
+qm_status cgemm_cn(int M, int N, int K, const float2* A, int lda, const float2* B, int ldb,
+                   float2* C, int ldc, float2* partial, int splits, cudaStream_t s);
+qm_status cgemm_tn(int M, int N, int K, const float2* A, int lda, const double* d,
+                   const float2* B, int ldb, float2* C, int ldc, bool accumulate,
+                   cudaStream_t s);
+
+}  // namespace qm
