@@ -127,6 +127,53 @@ qm_status qm_hpsi(qm_gspace g, int ik, int nb,
                   void* out, int ld_out,
                   qm_precision prec, void* stream);
 
+/* Options of qm_davidson (zero-initialise, then set what you need; 0 / 0.0 = default). */
+typedef struct {
+    double tol;          /* convergence: max_n ||H x_n - eps_n x_n||_2 <= tol (Ha), ||x_n||_2 = 1;
+                            default 1e-8 */
+    int max_iter;        /* maximum Rayleigh-Ritz steps; default 100 */
+    int nvecx;           /* maximum basis size, >= 2 nb (clamped to npw); default 4 nb */
+    qm_precision prec;   /* H psi precision inside the iterations; QM_FP64 */
+    int precond;         /* 0 = Teter-Payne-Allan diagonal preconditioner */
+    int reserved[4];     /* must be 0 */
+} qm_davidson_opts;
+
+/* Counters of one qm_davidson call (the paper's "H-psi calls" are band_applies / nb). */
+typedef struct {
+    int iterations;          /* Rayleigh-Ritz steps taken */
+    int converged;           /* 1 if every residual norm reached tol */
+    long long band_applies;  /* number of single-band H psi applications */
+    double max_residual;     /* max_n ||H x_n - eps_n x_n||_2 at exit (Ha) */
+    double seconds;          /* host wall time of the call */
+} qm_davidson_stats;
+
+/*
+ * qm_davidson - lowest nb eigenpairs of H(k) by block Davidson (Sec. 5, dft module:
+ * matrix-free Davidson that only applies H to blocks of trial vectors; Eq. KSHamMat
+ * with the KB term is the operator, applied as in qm_hpsi).
+ *
+ *  g, ik, nb      gspace, k-point, number of bands (1 <= nb <= npw/2).
+ *  psi_inout      device, nb rows of npw(ik) complex double, row stride ld_psi >= npw.
+ *                 In: starting block (any linearly independent vectors; orthonormalised
+ *                 internally).  Out: orthonormal Ritz vectors, ordered like eig_out.
+ *  vloc_r, nproj, beta, ld_beta, D   as in qm_hpsi (FP64 element types).
+ *  opts           host, may be NULL (defaults).
+ *  eig_out        host, nb doubles: Ritz values in increasing order (Ha).
+ *  stats          host, may be NULL.
+ *  stream         cudaStream_t.  Synchronous with respect to the host: the call returns
+ *                 after the last iteration; it reads small results (Ritz values, residual
+ *                 norms) back every iteration.
+ * Uses a grow-only device workspace owned by the handle (about (2 nvecx + 5 nb) npw
+ * complex doubles plus O(nvecx^2)).
+ * Errors: QM_ERR_ARG, QM_ERR_OOM, QM_ERR_CUDA; QM_ERR_NUMERIC (non-finite values,
+ * rank-deficient start); QM_ERR_NOT_CONVERGED (max_iter reached: outputs hold the last
+ * Ritz pairs); QM_ERR_UNSUPPORTED (opts->prec other than QM_FP64 in this build).
+ */
+qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, int ld_psi,
+                      const double* vloc_r, int nproj, const void* beta, int ld_beta,
+                      const double* D, const qm_davidson_opts* opts, double* eig_out,
+                      qm_davidson_stats* stats, void* stream);
+
 /*
  * Instrumentation (not part of the paper's method; used by benchmarks).
  *  qm_launch_count  number of CUDA kernels this library has launched in this process.

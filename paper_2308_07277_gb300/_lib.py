@@ -53,3 +53,21 @@ def load():
         fn.argtypes = args
     _lib = lib
     return lib
+
+
+class DavidsonOpts(ctypes.Structure):
+    """qm_davidson_opts of include/qm.h."""
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("nvecx", ctypes.c_int),
+                ("prec", ctypes.c_int), ("precond", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+
+
+class DavidsonStats(ctypes.Structure):
+    """qm_davidson_stats of include/qm.h."""
+    _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("band_applies", ctypes.c_longlong),
+                ("max_residual", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+
+SIGNATURES["qm_davidson"] = (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                            ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                            ctypes.c_void_p, ctypes.POINTER(DavidsonOpts), c_double_p,
+                                            ctypes.POINTER(DavidsonStats), ctypes.c_void_p])

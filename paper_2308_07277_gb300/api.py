@@ -122,6 +122,31 @@ def qm_hpsi(g, ik, psi, vloc, beta, D, out=None, prec="fp64", stream=None):
     return out
 
 
+def qm_davidson(g, ik, psi, vloc, beta, D, tol=1e-8, max_iter=100, nvecx=0, prec="fp64", stream=None,
+                raise_not_converged=True):
+    """Lowest nb eigenpairs; psi (nb, >=npw) complex128 CUDA tensor is overwritten by the
+    Ritz vectors.  Returns (eigenvalues ndarray (nb,), stats dict)."""
+    lib = _lib.load()
+    if psi.dim() != 2:
+        raise ValueError("psi must be 2-D (nb, ld)")
+    nb = int(psi.shape[0])
+    nproj = 0 if beta is None else int(beta.shape[0])
+    opts = _lib.DavidsonOpts(tol=float(tol), max_iter=int(max_iter), nvecx=int(nvecx), prec=_PREC[prec], precond=0)
+    stats = _lib.DavidsonStats()
+    eig = np.zeros(nb, np.float64)
+    st = lib.qm_davidson(g, int(ik), nb, _dev_ptr(psi, "psi", torch.complex128), int(psi.stride(0)),
+                         _dev_ptr(vloc, "vloc", torch.float64), nproj,
+                         _dev_ptr(beta, "beta", torch.complex128), int(beta.stride(0)) if nproj else 0,
+                         _dev_ptr(D, "D", torch.float64) if nproj else None, ctypes.byref(opts), _dp(eig),
+                         ctypes.byref(stats), _stream_ptr(stream))
+    info = {"iterations": stats.iterations, "converged": bool(stats.converged),
+            "band_applies": stats.band_applies, "max_residual": stats.max_residual, "seconds": stats.seconds,
+            "status": STATUS.get(st, st)}
+    if st != 0 and not (st == 4 and not raise_not_converged):
+        _check(st)
+    return eig, info
+
+
 class GSpace:
     """Owning wrapper of a qm_gspace handle."""
 
@@ -138,6 +163,9 @@ class GSpace:
 
     def hpsi(self, ik, psi, vloc, beta, D, out=None, prec="fp64", stream=None):
         return qm_hpsi(self.handle, ik, psi, vloc, beta, D, out=out, prec=prec, stream=stream)
+
+    def davidson(self, ik, psi, vloc, beta, D, **kw):
+        return qm_davidson(self.handle, ik, psi, vloc, beta, D, **kw)
 
     def close(self):
         if self.handle is not None:

@@ -31,21 +31,24 @@ qm_status cuda_check(cudaError_t e, const char* what) {
                 std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-qm_status ensure_workspace(qm_gspace g, size_t bytes, cudaStream_t stream) {
-    if (g->ws.bytes >= bytes) return QM_OK;
-    if (g->ws.ptr) {
+static qm_status grow(Workspace& ws, size_t bytes, cudaStream_t stream) {
+    if (ws.bytes >= bytes) return QM_OK;
+    if (ws.ptr) {
         qm_status st = cuda_check(cudaStreamSynchronize(stream), "workspace sync");
         if (st) return st;
-        cudaFree(g->ws.ptr);
-        g->ws.ptr = nullptr;
-        g->ws.bytes = 0;
+        cudaFree(ws.ptr);
+        ws.ptr = nullptr;
+        ws.bytes = 0;
     }
     size_t want = align_up(bytes + bytes / 8, 1 << 20);
-    qm_status st = cuda_check(cudaMalloc(&g->ws.ptr, want), "workspace cudaMalloc");
+    qm_status st = cuda_check(cudaMalloc(&ws.ptr, want), "workspace cudaMalloc");
     if (st) return st;
-    g->ws.bytes = want;
+    ws.bytes = want;
     return QM_OK;
 }
+
+qm_status ensure_workspace(qm_gspace g, size_t bytes, cudaStream_t stream) { return grow(g->ws, bytes, stream); }
+qm_status ensure_dav_workspace(qm_gspace g, size_t bytes, cudaStream_t stream) { return grow(g->dws, bytes, stream); }
 
 static bool smooth235(int n) {
     if (n <= 0) return false;
@@ -352,6 +355,7 @@ extern "C" void qm_gspace_destroy(qm_gspace g) {
             cudaFree(g->rev[d]);
         }
         if (g->ws.ptr) cudaFree(g->ws.ptr);
+        if (g->dws.ptr) cudaFree(g->dws.ptr);
         cudaSetDevice(cur);
     }
     delete g;

@@ -36,7 +36,7 @@ static HpsiLayout hpsi_layout(qm_gspace g, int ik, int nb, int nproj, bool fp32)
     L.p_off = off;
     off = align_up(off + (size_t)nproj * nb * cs, 256);
     L.part_off = off;
-    off = align_up(off + (L.splits > 1 ? (size_t)L.splits * nproj * nb * cs : 0), 256);
+    off = align_up(off + (L.splits > 1 ? std::min((size_t)L.splits * nproj * nb * cs, gemm_cn_partial_bytes(fp32)) : 0), 256);
     L.t_off = off;
     const size_t per_band = stick_buffer_bytes_per_band(g, ik, fp32);
     const size_t nbc = std::max<size_t>(1, std::min<size_t>((size_t)nb, kStickBudget / per_band));

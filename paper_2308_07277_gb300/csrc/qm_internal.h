@@ -68,7 +68,8 @@ struct qm_gspace_s {
     int* rev[3] = {nullptr, nullptr, nullptr};
     std::vector<double2> h_tw[3];
     std::vector<int> h_rev[3];
-    qm::Workspace ws;
+    qm::Workspace ws;    // qm_hpsi workspace
+    qm::Workspace dws;   // qm_davidson workspace
 };
 
 namespace qm {
@@ -83,6 +84,7 @@ qm_status ensure_device(qm_gspace g);
 
 // grow-only workspace owned by a gspace handle; synchronises `stream` before regrowing
 qm_status ensure_workspace(qm_gspace g, size_t bytes, cudaStream_t stream);
+qm_status ensure_dav_workspace(qm_gspace g, size_t bytes, cudaStream_t stream);
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -119,16 +121,27 @@ size_t stick_buffer_bytes_per_band(qm_gspace g, int ik, bool fp32);
 // split over K into `splits` partial sums reduced in a fixed order (deterministic).
 qm_status zgemm_cn(int M, int N, int K, const double2* A, int lda, const double2* B, int ldb,
                    double2* C, int ldc, double2* partial, int splits, cudaStream_t s);
-// C[m][n] (+)= sum_k A[k][m] * d[k] * B[k][n]   (d may be NULL -> 1)
+// C[m][n] (+)= alpha * sum_k A[k][m] * d[k] * B[k][n]   (d may be NULL -> 1)
 qm_status zgemm_tn(int M, int N, int K, const double2* A, int lda, const double* d,
                    const double2* B, int ldb, double2* C, int ldc, bool accumulate,
-                   cudaStream_t s);
+                   cudaStream_t s, double alpha = 1.0);
 int zgemm_cn_splits(int M, int N, int K);
+// upper bound of the split-K partial buffer any gemm_cn call needs
+size_t gemm_cn_partial_bytes(bool fp32);
+
+// ---- dense FP64 subspace kernels (dense.cu) ----
+constexpr int kJacobiMaxBlocks = 1024;
+// eigenpairs of the Hermitian m x m matrix H: evals_dev[m] unsorted, eigenvectors = columns
+// of Z (n x n, n = m + (m odd)); A, Z n x n scratch; rot jacobi_rot_bytes(m); red
+// 2*kJacobiMaxBlocks doubles; info 1 int (sweeps used)
+qm_status jacobi_eigh(const double2* H, int ldh, int m, double2* A, double2* Z, void* rot, double* red, int* info,
+                      double* evals_dev, cudaStream_t s);
+size_t jacobi_rot_bytes(int m);
 
 qm_status cgemm_cn(int M, int N, int K, const float2* A, int lda, const float2* B, int ldb,
                    float2* C, int ldc, float2* partial, int splits, cudaStream_t s);
 qm_status cgemm_tn(int M, int N, int K, const float2* A, int lda, const double* d,
                    const float2* B, int ldb, float2* C, int ldc, bool accumulate,
-                   cudaStream_t s);
+                   cudaStream_t s, double alpha = 1.0);
 
 }  // namespace qm

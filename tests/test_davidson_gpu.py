@@ -1,0 +1,121 @@
+"""GPU block Davidson (qm_davidson through the C ABI) against the FP64 oracle.
+
+Bar: eigenvalues within 1e-9 Ha of the oracle's (dense brute force on small cells,
+the oracle Davidson's stored eigenvalues at full size), residual norms <= tol checked
+independently with the oracle's H psi, Ritz vectors orthonormal to 1e-12.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import qm_synth as S
+from oracle import hamiltonian as OH
+
+from cases import make_case
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_EIG = 1e-9
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def Q():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2308_07277_gb300 as Q
+    return Q
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def run_gpu(Q, cell, ik, c, **kw):
+    g = Q.qm_gspace_create(cell.lattice, cell.kpts, cell.ecut_ha, cell.grid)
+    try:
+        psi = dev(c["psi"])
+        eig, info = Q.qm_davidson(g, ik, psi, dev(c["v"]), dev(c["beta"]), dev(c["D"]), **kw)
+        torch.cuda.synchronize()
+        return eig, psi.cpu().numpy(), info
+    finally:
+        Q.qm_gspace_destroy(g)
+
+
+def check_pairs(c, eig, X, tol):
+    """Independent oracle checks: orthonormality, Rayleigh quotients, residual norms."""
+    np.testing.assert_allclose(X @ X.conj().T, np.eye(X.shape[0]), atol=1e-12)
+    HX = OH.hpsi_fft(X, c["gs"], c["v"], c["beta"], c["D"])
+    rq = np.einsum("ij,ij->i", X.conj(), HX).real
+    np.testing.assert_allclose(rq, eig, atol=1e-11)
+    res = np.linalg.norm(HX - eig[:, None] * X, axis=1)
+    assert res.max() <= tol * 1.01, res.max()
+
+
+@pytest.mark.parametrize("cell", [S.config1(), S.fcc_si2(16.0, nbnd=6, kpts=[[0.25, -0.25, 0.25]]),
+                                  S.cubic_si8(10.0, nbnd=8, kpts=[[0.25, 0.25, 0.25]]),
+                                  S.cubic_si8(12.0, nbnd=12, reps=(2, 1, 1))],
+                         ids=lambda c: f"{c.name}_{c.ecutwfc_ry:g}Ry_nb{c.nbnd}")
+def test_davidson_matches_dense_brute_force(Q, cell):
+    c = make_case(cell, 0)
+    ev = np.linalg.eigvalsh(OH.dense_h(c["gs"], c["v"], c["beta"], c["D"]))[: cell.nbnd]
+    eig, X, info = run_gpu(Q, cell, 0, c, tol=1e-9, max_iter=300)
+    assert info["converged"], info
+    np.testing.assert_allclose(eig, ev, atol=TOL_EIG)
+    check_pairs(c, eig, X, 1e-9)
+
+
+def test_davidson_config1_twenty_iterations(Q):
+    """The Si2 workload: 20 Rayleigh-Ritz steps; every Ritz value is then within its own
+    residual norm of a true eigenvalue, and the ordered values bound the true ones from above."""
+    cell = S.config1()
+    c = make_case(cell, 0)
+    ev = np.linalg.eigvalsh(OH.dense_h(c["gs"], c["v"], c["beta"], c["D"]))[: cell.nbnd]
+    eig, X, info = run_gpu(Q, cell, 0, c, tol=1e-14, max_iter=20, raise_not_converged=False)
+    assert info["iterations"] == 20
+    assert np.all(eig >= ev - 1e-12)            # Cauchy interlacing: Ritz values bound from above
+    HX = OH.hpsi_fft(X, c["gs"], c["v"], c["beta"], c["D"])
+    res = np.linalg.norm(HX - eig[:, None] * X, axis=1)
+    assert np.all(np.abs(eig - ev) <= res + 1e-12)
+    assert np.abs(eig - ev).max() <= 1e-6
+
+
+@pytest.mark.parametrize("ik", [0, 3])
+def test_davidson_config2_full_size(Q, ik):
+    gold = os.path.join(ROOT, "tests", "golden", "config2_eigs.txt")
+    if not os.path.exists(gold):
+        pytest.skip("tests/golden/config2_eigs.txt not generated")
+    want = None
+    for line in open(gold):
+        if line.startswith(f"k{ik} "):
+            want = np.array([float(x) for x in line.split()[1:]])
+    cell = S.config2()
+    c = make_case(cell, ik)
+    eig, X, info = run_gpu(Q, cell, ik, c, tol=1e-8, max_iter=200)
+    assert info["converged"], info
+    np.testing.assert_allclose(eig, want, atol=TOL_EIG)
+    sample = [0, 1, 79, 158, 159]
+    HX = OH.hpsi_fft(X[sample], c["gs"], c["v"], c["beta"], c["D"])
+    res = np.linalg.norm(HX - eig[sample, None] * X[sample], axis=1)
+    assert res.max() <= 1.01e-8
+
+
+def test_davidson_not_converged_and_errors(Q):
+    cell = S.config1()
+    c = make_case(cell, 0)
+    eig, X, info = run_gpu(Q, cell, 0, c, tol=1e-13, max_iter=2, raise_not_converged=False)
+    assert info["status"] == "QM_ERR_NOT_CONVERGED" and not info["converged"]
+    assert np.all(np.isfinite(eig)) and np.all(np.diff(eig) >= 0)
+    g = Q.qm_gspace_create(cell.lattice, cell.kpts, cell.ecut_ha, cell.grid)
+    try:
+        big = dev(S.psi_random(1, 300, c["psi"].shape[1]))       # nb > npw / 2
+        with pytest.raises(Q.QMError):
+            Q.qm_davidson(g, 0, big, dev(c["v"]), dev(c["beta"]), dev(c["D"]))
+        dup = np.repeat(c["psi"][:1], 4, axis=0)                 # rank-deficient start
+        with pytest.raises(Q.QMError) as e:
+            Q.qm_davidson(g, 0, dev(dup), dev(c["v"]), dev(c["beta"]), dev(c["D"]))
+        assert e.value.status == 5
+    finally:
+        Q.qm_gspace_destroy(g)
