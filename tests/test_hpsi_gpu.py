@@ -124,9 +124,10 @@ def test_hpsi_full_size_properties(Q):
         c = make_case(cell, 1, nb=24)
         zero = np.zeros_like(c["v"])
         got = gpu_hpsi(Q, g, 1, c, with_nl=False, v=zero)
-        # exact up to the last-bit rounding of 1/2|k+G|^2, which host C++ and numpy may differ in
+        # exact up to the rounding of 1/2|k+G|^2, which the host C++ and numpy evaluate in a
+        # different order (a few ulps)
         want = c["gs"]["kin"] * c["psi"]
-        assert np.all(np.abs(got - want) <= 4e-16 * np.abs(want))
+        assert np.all(np.abs(got - want) <= 2e-15 * np.abs(want))
         v0 = -0.37
         shifted = gpu_hpsi(Q, g, 1, c, v=c["v"] + v0)
         base = gpu_hpsi(Q, g, 1, c)
