@@ -127,6 +127,42 @@ qm_status qm_hpsi(qm_gspace g, int ik, int nb,
                   void* out, int ld_out,
                   qm_precision prec, void* stream);
 
+/*
+ * qm_hpsi_noalloc - the same H psi as qm_hpsi, for callers that cannot allocate device
+ * memory.  The paper has no counterpart: this is a deployment variant of qm_hpsi.
+ *
+ * Who needs it: code running under an allocator that owns the whole device heap (for
+ * example a host framework that reserves the free memory up front and forbids cudaMalloc
+ * afterwards), and latency-critical loops where cudaMalloc/cudaFree would synchronise the
+ * device or could fail for lack of free memory.  This call allocates nothing: it calls
+ * no cudaMalloc, cudaFree or other allocating routine, not even on first use of a handle.
+ * The caller still passes every input and output (same arguments and meaning as qm_hpsi).
+ * All scratch - a copy of the k-point's gspace tables, V(r) in the FFT layout, the
+ * projections, the split-K partial sums and the FFT stick buffer - lives in one fixed
+ * device array of QM_HPSI_NOALLOC_SCRATCH_BYTES inside the library; every GPU that loads
+ * the library holds it until the process exits (the driver makes it resident when the
+ * library's device code and data are loaded on that GPU, which with CUDA's lazy loading
+ * can be the first call of this entry point).
+ *
+ *  - The first call on each device looks up the array's device address once; make that
+ *    first call before any CUDA stream capture.
+ *  - Every call shares the one array and leaves its contents behind.  Calls whose GPU work
+ *    overlaps (different streams, or different threads without ordering) race on it:
+ *    issue them on one stream.  No scratch byte needs to start at zero; each call writes
+ *    everything it reads.
+ *  - A problem whose scratch exceeds the array is rejected with QM_ERR_ARG and a message
+ *    giving the bytes it needs (tables + N1*N2*N3 reals + nproj*nb complex + one band of
+ *    the stick buffer); use qm_hpsi for those.
+ * Errors: as qm_hpsi, plus the size rejection above.
+ */
+#define QM_HPSI_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
+qm_status qm_hpsi_noalloc(qm_gspace g, int ik, int nb,
+                          const void* psi, int ld_psi,
+                          const double* vloc_r,
+                          int nproj, const void* beta, int ld_beta, const double* D,
+                          void* out, int ld_out,
+                          qm_precision prec, void* stream);
+
 /* Options of qm_davidson (zero-initialise, then set what you need; 0 / 0.0 = default). */
 typedef struct {
     double tol;          /* convergence: max_n ||H x_n - eps_n x_n||_2 <= tol (Ha), ||x_n||_2 = 1;

@@ -71,3 +71,5 @@ SIGNATURES["qm_davidson"] = (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctype
                                             ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
                                             ctypes.c_void_p, ctypes.POINTER(DavidsonOpts), c_double_p,
                                             ctypes.POINTER(DavidsonStats), ctypes.c_void_p])
+
+SIGNATURES["qm_hpsi_noalloc"] = SIGNATURES["qm_hpsi"]

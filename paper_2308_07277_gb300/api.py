@@ -14,6 +14,7 @@ from . import _lib
 
 QM_FP64 = 0
 QM_MIXED = 1
+QM_HPSI_NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024   # include/qm.h
 _PREC = {"fp64": QM_FP64, "mixed": QM_MIXED, QM_FP64: QM_FP64, QM_MIXED: QM_MIXED}
 STATUS = {0: "QM_OK", 1: "QM_ERR_ARG", 2: "QM_ERR_CUDA", 3: "QM_ERR_OOM", 4: "QM_ERR_NOT_CONVERGED",
           5: "QM_ERR_NUMERIC", 6: "QM_ERR_TIMEOUT", 7: "QM_ERR_UNSUPPORTED"}
@@ -177,3 +178,23 @@ class GSpace:
             self.close()
         except Exception:
             pass
+
+
+def qm_hpsi_noalloc(g, ik, psi, vloc, beta, D, out, prec="fp64", stream=None):
+    """qm_hpsi for callers that cannot allocate device memory: same arguments, but `out`
+    must be passed (pre-allocated by the caller) and the library's fixed scratch array is
+    used instead of any allocation."""
+    lib = _lib.load()
+    p = _PREC[prec]
+    cdt = torch.complex128 if p == QM_FP64 else torch.complex64
+    if psi.dim() != 2 or out is None:
+        raise ValueError("psi must be 2-D and out must be given")
+    nproj = 0 if beta is None else int(beta.shape[0])
+    _check(lib.qm_hpsi_noalloc(g, int(ik), int(psi.shape[0]),
+                               _dev_ptr(psi, "psi", cdt), int(psi.stride(0)),
+                               _dev_ptr(vloc, "vloc", torch.float64),
+                               nproj, _dev_ptr(beta, "beta", cdt), int(beta.stride(0)) if nproj else 0,
+                               _dev_ptr(D, "D", torch.float64) if nproj else None,
+                               _dev_ptr(out, "out", cdt), int(out.stride(0)),
+                               p, _stream_ptr(stream)))
+    return out

@@ -370,4 +370,71 @@ qm_status launch_local_kinetic(qm_gspace g, int ik, int nb, const void* psi, int
     return local_kinetic_impl<double>(g, ik, nb, psi, ld_psi, vt, out, ld_out, tbuf, tbuf_bytes, s);
 }
 
+
+// ---------------------------------------------------------------- launchers on explicit tables
+// Same launch sequence as above, with every table given by pointer (used by the entry point
+// whose scratch and tables live in caller-independent fixed device memory).
+qm_status launch_vt_prepare_tab(const DevTables& t, const double* vloc, void* vt, bool fp32, cudaStream_t s) {
+    const size_t nr = (size_t)t.n[0] * t.n[1] * t.n[2];
+    const double scale = 1.0 / (double)nr;
+    int blocks = (int)std::min<size_t>((nr + 255) / 256, 152 * 8);
+    ProfScope ps(PF_VT, s);
+    if (fp32)
+        k_vt<float><<<blocks, 256, 0, s>>>(vloc, (float*)vt, t.n[0], t.n[1], t.n[2], t.rev[0], t.rev[1], t.rev[2], scale);
+    else
+        k_vt<double><<<blocks, 256, 0, s>>>(vloc, (double*)vt, t.n[0], t.n[1], t.n[2], t.rev[0], t.rev[1], t.rev[2], scale);
+    return cuda_check(cudaGetLastError(), "k_vt launch");
+}
+
+template <class R>
+static qm_status local_kinetic_tab_impl(const DevTables& t, int nb, const void* psi, int ld_psi, const void* vt,
+                                        void* out, int ld_out, void* tbuf, size_t tbuf_bytes, cudaStream_t s) {
+    using C = typename Cx<R>::T;
+    const int N1 = t.n[0], N2 = t.n[1], N3 = t.n[2];
+    const size_t per_band = (size_t)N1 * t.nstick_pad * sizeof(C);
+    if (tbuf_bytes < per_band) return fail(QM_ERR_ARG, "stick buffer smaller than one band");
+    const int nbc = (int)std::max<size_t>(1, std::min<size_t>((size_t)nb, tbuf_bytes / per_band));
+    const size_t sm_stick = (size_t)(kSticksPerCta * t.ldx + N1) * sizeof(C);
+    const size_t sm_plane = (size_t)(N3 * t.ldy + N2 + N3) * sizeof(C);
+    if (sm_plane > 227 * 1024 || sm_stick > 227 * 1024)
+        return fail(QM_ERR_UNSUPPORTED, "FFT plane does not fit in shared memory");
+    cudaFuncSetAttribute(k_plane<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_plane);
+    cudaFuncSetAttribute(k_stick_inverse<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_stick);
+    cudaFuncSetAttribute(k_stick_forward<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_stick);
+    const int ntile = (t.nstick + kSticksPerCta - 1) / kSticksPerCta;
+    const C* tw_x = (const C*)t.tw[0];
+    const C* tw_y = (const C*)t.tw[1];
+    const C* tw_z = (const C*)t.tw[2];
+    const R* kin = (const R*)t.kin;
+    C* T = (C*)tbuf;
+    for (int b0 = 0; b0 < nb; b0 += nbc) {
+        const int nbx = std::min(nbc, nb - b0);
+        const C* ps = (const C*)psi + (size_t)b0 * ld_psi;
+        C* po = (C*)out + (size_t)b0 * ld_out;
+        {
+            ProfScope pf(PF_STICK_INV, s);
+            k_stick_inverse<R><<<dim3(ntile, nbx), kThreads, sm_stick, s>>>(
+                ps, ld_psi, t.stick_g0, t.g_code, t.nstick, t.nstick_pad, t.plan[0], tw_x, t.ldx, T);
+        }
+        {
+            ProfScope pf(PF_PLANE, s);
+            k_plane<R><<<dim3(N1, nbx), kThreads, sm_plane, s>>>(
+                T, t.nstick, t.nstick_pad, t.stick_plane, t.rows, t.nrow, t.plan[1], t.plan[2], tw_y, tw_z, t.ldy,
+                (const R*)vt, N1);
+        }
+        {
+            ProfScope pf(PF_STICK_FWD, s);
+            k_stick_forward<R><<<dim3(ntile, nbx), kThreads, sm_stick, s>>>(
+                T, t.nstick, t.nstick_pad, t.stick_g0, t.g_code, kin, t.plan[0], tw_x, t.ldx, ps, ld_psi, po, ld_out);
+        }
+    }
+    return cuda_check(cudaGetLastError(), "FFT path launch");
+}
+
+qm_status launch_local_kinetic_tab(const DevTables& t, int nb, const void* psi, int ld_psi, const void* vt, void* out,
+                                   int ld_out, void* tbuf, size_t tbuf_bytes, bool fp32, cudaStream_t s) {
+    if (fp32) return local_kinetic_tab_impl<float>(t, nb, psi, ld_psi, vt, out, ld_out, tbuf, tbuf_bytes, s);
+    return local_kinetic_tab_impl<double>(t, nb, psi, ld_psi, vt, out, ld_out, tbuf, tbuf_bytes, s);
+}
+
 }  // namespace qm

@@ -116,6 +116,26 @@ qm_status launch_local_kinetic(qm_gspace g, int ik, int nb, const void* psi, int
                                size_t tbuf_bytes, bool fp32, cudaStream_t s);
 size_t stick_buffer_bytes_per_band(qm_gspace g, int ik, bool fp32);
 
+// The FFT path's tables of one k-point given by explicit device pointers (twiddles and kin
+// in the precision of the call).
+struct DevTables {
+    int n[3];
+    int ldx, ldy;
+    AxisPlan plan[3];
+    const void* tw[3];
+    const int* rev[3];
+    int nstick, nstick_pad, nrow;
+    const int* stick_g0;
+    const int* stick_plane;
+    const int* rows;
+    const int2* g_code;
+    const void* kin;
+};
+qm_status launch_vt_prepare_tab(const DevTables& t, const double* vloc, void* vt, bool fp32, cudaStream_t s);
+qm_status launch_local_kinetic_tab(const DevTables& t, int nb, const void* psi, int ld_psi, const void* vt,
+                                   void* out, int ld_out, void* tbuf, size_t tbuf_bytes, bool fp32,
+                                   cudaStream_t s);
+
 // ---- complex GEMMs (zgemm.cu) ----
 // C[m][n] = sum_k conj(A[m][k]) * B[n][k]   (A: M rows, B: N rows, k contiguous);
 // split over K into `splits` partial sums reduced in a fixed order (deterministic).
