@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--cpu-sample-bands", type=int, default=48)
+    ap.add_argument("--davidson", type=int, default=1, help="also time block Davidson to tol (0: skip)")
+    ap.add_argument("--davidson-tol", type=float, default=1e-8)
     return ap.parse_args()
 
 
@@ -168,6 +170,43 @@ def fft_flops_per_plane_launch(grid, nrow):
     return 2.0 * (nrow * f(n2) + n2 * f(n3)) + 2.0 * n2 * n3
 
 
+def read_prof(lib):
+    import ctypes
+    fam = {}
+    for f in range(9):
+        t = ctypes.c_double()
+        c = ctypes.c_longlong()
+        lib.qm_prof_read(f, ctypes.byref(t), ctypes.byref(c))
+        if c.value:
+            fam[lib.qm_prof_name(f).decode()] = {"ms_total": t.value, "launches": c.value}
+    return fam
+
+
+def run_davidson(args, Q, lib, g, cell, psi_host, v, beta, D, nk, nb):
+    """Block Davidson to a residual of args.davidson_tol at every k-point (FP64 H psi),
+    from the seeded random start; wall time of the qm_davidson calls."""
+    import torch
+    if args.prec != "fp64":
+        return {"skipped": "the Davidson leg runs the FP64 form"}
+    per_k = []
+    lib.qm_prof_enable(1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for ik in range(nk):
+        p = psi_host[ik].to(torch.complex128).cuda()
+        eig, info = Q.qm_davidson(g.handle, ik, p, v, beta[ik].to(torch.complex128), D, tol=args.davidson_tol,
+                                  max_iter=300, raise_not_converged=False)
+        per_k.append({"iterations": info["iterations"], "band_applies": info["band_applies"],
+                      "max_residual": info["max_residual"], "converged": info["converged"],
+                      "seconds": info["seconds"], "eig_min": float(eig[0]), "eig_max": float(eig[-1])})
+    torch.cuda.synchronize()
+    total = time.perf_counter() - t0
+    fam = read_prof(lib)
+    lib.qm_prof_enable(0)
+    return {"precision": "fp64", "tol_ha": args.davidson_tol, "seconds_total": total, "nbnd": nb,
+            "per_k": per_k, "kernels": fam}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -231,7 +270,7 @@ def run_ours(args):
     ms = e0.elapsed_time(e1) / args.steps
     fam = {}
     import ctypes
-    for f in range(8):
+    for f in range(9):
         t = ctypes.c_double()
         c = ctypes.c_longlong()
         lib.qm_prof_read(f, ctypes.byref(t), ctypes.byref(c))
@@ -262,6 +301,8 @@ def run_ours(args):
     ems = e2.elapsed_time(e3) / esteps
     h2d = sum(t.numel() * t.element_size() for t in psi_host)
     d2h = sum(t.numel() * t.element_size() for t in out_host)
+
+    dav = run_davidson(args, Q, lib, g, cell, psi_host, v, beta, D, nk, nb) if args.davidson else None
 
     if world > 1:
         t = torch.tensor([ms, ems], device=dev, dtype=torch.float64)
@@ -314,7 +355,8 @@ def run_ours(args):
                 "kernels": fam,
                 "roofline": roof,
                 "cpu_baseline": cpu,
-                "clocks": clk}
+                "clocks": clk,
+                "davidson": dav}
         print(json.dumps(line))
     g.close()
     if world > 1:

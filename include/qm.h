@@ -211,12 +211,30 @@ qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, int ld_psi,
                       qm_davidson_stats* stats, void* stream);
 
 /*
+ * qm_eigh_lowest - lowest nev eigenpairs of a complex Hermitian m x m matrix in FP64: the
+ * dense eigensolver of the Davidson Rayleigh-Ritz step, exposed on its own.  Householder
+ * reduction to real tridiagonal form, multisection on Sturm counts for the wanted
+ * eigenvalues, inverse iteration (orthogonalised within clusters closer than 1e-5 |T|),
+ * back-transformation (Golub & Van Loan, Matrix Computations, Ch. 8).
+ *
+ *  A       device, m x m complex double (row-major, ld lda >= m); only read (the Hermitian
+ *          part (A + A^H)/2 is what is diagonalised).
+ *  evals   device, nev doubles, increasing.
+ *  Y       device, m x nev complex double, row-major with ld ldy >= nev: column j is the
+ *          unit eigenvector of evals[j].
+ *  stream  cudaStream_t.  Allocates its workspace with cudaMallocAsync on the stream.
+ * 1 <= nev <= m <= 6400.  Errors: QM_ERR_ARG, QM_ERR_UNSUPPORTED, QM_ERR_CUDA, QM_ERR_OOM.
+ */
+qm_status qm_eigh_lowest(int m, int nev, const void* A, int lda, double* evals, void* Y, int ldy,
+                         void* stream);
+
+/*
  * Instrumentation (not part of the paper's method; used by benchmarks).
  *  qm_launch_count  number of CUDA kernels this library has launched in this process.
  *  qm_prof_enable   on != 0: from now on record a pair of CUDA events on the launch stream
  *                   around every kernel launch; resets the accumulated times (any value).
  *  qm_prof_read     waits for the recorded events and returns, for kernel family
- *                   `family` (0 <= family < 8), the summed device time in ms and the number
+ *                   `family` (0 <= family < 9), the summed device time in ms and the number
  *                   of launches timed since the last qm_prof_enable.
  *  qm_prof_name     name of a kernel family ("" when out of range).
  */

@@ -8,8 +8,9 @@ from ._lib import load as _load
 _load()
 
 from .api import (GSpace, QMError, QM_FP64, QM_HPSI_NOALLOC_SCRATCH_BYTES, QM_MIXED, qm_gspace_create, qm_gspace_destroy,  # noqa: E402
-                  qm_davidson, qm_gspace_indices, qm_gspace_query, qm_hpsi, qm_hpsi_noalloc, qm_last_error,
+                  qm_davidson, qm_eigh_lowest, qm_gspace_indices, qm_gspace_query, qm_hpsi, qm_hpsi_noalloc,
+                  qm_last_error,
                   qm_version)
 
 __all__ = ["GSpace", "QMError", "QM_FP64", "QM_HPSI_NOALLOC_SCRATCH_BYTES", "QM_MIXED", "qm_gspace_create", "qm_gspace_destroy",
-           "qm_davidson", "qm_gspace_indices", "qm_gspace_query", "qm_hpsi", "qm_hpsi_noalloc", "qm_last_error", "qm_version"]
+           "qm_davidson", "qm_eigh_lowest", "qm_gspace_indices", "qm_gspace_query", "qm_hpsi", "qm_hpsi_noalloc", "qm_last_error", "qm_version"]

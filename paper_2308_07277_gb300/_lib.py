@@ -73,3 +73,6 @@ SIGNATURES["qm_davidson"] = (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctype
                                             ctypes.POINTER(DavidsonStats), ctypes.c_void_p])
 
 SIGNATURES["qm_hpsi_noalloc"] = SIGNATURES["qm_hpsi"]
+
+SIGNATURES["qm_eigh_lowest"] = (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                               ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p])

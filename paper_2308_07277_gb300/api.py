@@ -198,3 +198,18 @@ def qm_hpsi_noalloc(g, ik, psi, vloc, beta, D, out, prec="fp64", stream=None):
                                _dev_ptr(out, "out", cdt), int(out.stride(0)),
                                p, _stream_ptr(stream)))
     return out
+
+
+def qm_eigh_lowest(A, nev, stream=None):
+    """Lowest nev eigenpairs of the Hermitian (m, m) complex128 CUDA tensor A.
+    Returns (evals (nev,) float64 CUDA tensor, Y (m, nev) complex128 CUDA tensor)."""
+    lib = _lib.load()
+    if A.dim() != 2 or A.shape[0] != A.shape[1]:
+        raise ValueError("A must be square")
+    m = int(A.shape[0])
+    ev = torch.empty(nev, dtype=torch.float64, device=A.device)
+    Y = torch.empty((m, nev), dtype=torch.complex128, device=A.device)
+    _check(lib.qm_eigh_lowest(m, int(nev), _dev_ptr(A, "A", torch.complex128), int(A.stride(0)),
+                              _dev_ptr(ev, "evals", torch.float64), _dev_ptr(Y, "Y", torch.complex128),
+                              int(Y.stride(0)), _stream_ptr(stream)))
+    return ev, Y

@@ -77,18 +77,6 @@ __global__ void k_tpa(const double2* __restrict__ R, int ld, int npw, const int*
     }
 }
 
-// C[i][k] = Z[i][idx[k]] * scale[k]   (i < m, k < nsel)
-__global__ void k_gather_cols(const double2* __restrict__ Z, int ldz, int m, const int* __restrict__ idx,
-                              const double* __restrict__ scale, int nsel, double2* __restrict__ C, int ldc) {
-    const long total = (long)m * nsel;
-    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
-        const int i = (int)(e / nsel), k = (int)(e % nsel);
-        double2 v = Z[(size_t)i * ldz + idx[k]];
-        const double s = scale ? scale[k] : 1.0;
-        C[(size_t)i * ldc + k] = make_double2(s * v.x, s * v.y);
-    }
-}
-
 // Hermitian completion after new columns [m0, m) of H were computed for rows [0, m):
 // H[j][i] = conj(H[i][j]) for i < m0 <= j; the new diagonal block is symmetrised.
 __global__ void k_herm_fill(double2* __restrict__ H, int ld, int m0, int m) {
@@ -107,6 +95,16 @@ __global__ void k_herm_fill(double2* __restrict__ H, int ld, int m0, int m) {
         } else if (i == j) {
             H[(size_t)i * ld + i].y = 0.0;
         }
+    }
+}
+
+// A[i][j] = Hermitian part of H (m x m)
+__global__ void k_herm_copy(const double2* __restrict__ H, int ldh, int m, double2* __restrict__ A, int lda) {
+    const long total = (long)m * m;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / m), j = (int)(e % m);
+        const double2 a = H[(size_t)i * ldh + j], b = H[(size_t)j * ldh + i];
+        A[(size_t)i * lda + j] = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
     }
 }
 
@@ -156,6 +154,7 @@ struct Ws {
     double *eval, *eps, *rn2, *tk, *red, *invs, *wk;
     int *sel, *info;
     void* rot;
+    void* heev;
 };
 
 }  // namespace
@@ -199,7 +198,7 @@ struct DavidsonRun {
             ProfScope pf(PF_OTHER, s);
             k_scale_sym<<<grid_for((long)nd * nd), 256, 0, s>>>(w.Cs, lds, nd, w.invs, w.G, lds);
         }
-        if ((st = jacobi_eigh(w.G, lds, nd, w.A, w.Z, w.rot, w.red, w.info, w.eval, s))) return st;
+        if ((st = heev_lowest(w.G, lds, nd, nd, w.eval, w.Z, nd, w.heev, s))) return st;
         std::vector<double> lam(nd);
         if ((st = cuda_check(cudaMemcpyAsync(lam.data(), w.eval, sizeof(double) * nd, cudaMemcpyDeviceToHost, s),
                              "D2H Gram eigenvalues")))
@@ -220,7 +219,7 @@ struct DavidsonRun {
         cudaMemcpyAsync(w.wk, wk.data(), sizeof(double) * wk.size(), cudaMemcpyHostToDevice, s);
         {
             ProfScope pf(PF_OTHER, s);
-            k_lowdin_coef<<<grid_for((long)nd * sel.size()), 256, 0, s>>>(w.Z, lds, nd, w.invs, w.sel, w.wk,
+            k_lowdin_coef<<<grid_for((long)nd * sel.size()), 256, 0, s>>>(w.Z, nd, nd, w.invs, w.sel, w.wk,
                                                                          (int)sel.size(), w.Cs, (int)sel.size());
         }
         // out[k] = sum_i W[i][k] Y_i
@@ -296,7 +295,7 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
                  oRn = take(sizeof(double) * nsq), oTk = take(sizeof(double) * nsq),
                  oRed = take(sizeof(double) * 2 * kJacobiMaxBlocks), oInvs = take(sizeof(double) * nsq),
                  oWk = take(sizeof(double) * nsq), oSel = take(sizeof(int) * nsq), oInfo = take(sizeof(int) * 4),
-                 oRot = take(jacobi_rot_bytes(nsq));
+                 oRot = take(jacobi_rot_bytes(nsq)), oHeev = take(heev_work_bytes(nsq, nsq));
     if ((st = ensure_dav_workspace(g, off, s))) return st;
     char* base = (char*)g->dws.ptr;
     Ws& w = run.w;
@@ -323,6 +322,7 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
     w.sel = (int*)(base + oSel);
     w.info = (int*)(base + oInfo);
     w.rot = base + oRot;
+    w.heev = base + oHeev;
     const double* kin = g->k[ik].kin;
 
     // initial block: psi -> rows of Tmp (dense ld), orthonormalised into V
@@ -335,7 +335,7 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
     if (kept < nb) return fail(QM_ERR_NUMERIC, "qm_davidson: initial psi block is rank deficient");
     if ((st = run.hpsi(w.V, w.HV, nb))) return st;
     int m = nb, m0 = 0;
-    std::vector<double> ev(nsq), rn2(nb), eps(nb);
+    std::vector<double> rn2(nb), eps(nb);
     int it = 0;
     bool converged = false;
     double max_res = 0.0;
@@ -348,24 +348,12 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
             ProfScope pf(PF_OTHER, s);
             k_herm_fill<<<grid_for((long)m * (m - m0)), 256, 0, s>>>(w.Hs, nsq, m0, m);
         }
-        if ((st = jacobi_eigh(w.Hs, nsq, m, w.A, w.Z, w.rot, w.red, w.info, w.eval, s))) return st;
-        if ((st = cuda_check(cudaMemcpyAsync(ev.data(), w.eval, sizeof(double) * m, cudaMemcpyDeviceToHost, s),
-                             "D2H eigenvalues")) ||
-            (st = cuda_check(cudaStreamSynchronize(s), "stream sync")))
-            return st;
-        std::vector<int> order(m);
-        std::iota(order.begin(), order.end(), 0);
-        for (int i = 0; i < m; ++i)
-            if (!std::isfinite(ev[i])) return fail(QM_ERR_NUMERIC, "qm_davidson: non-finite Ritz value");
-        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return ev[a] < ev[b]; });
-        for (int n = 0; n < nb; ++n) eps[n] = ev[order[n]];
-        cudaMemcpyAsync(w.sel, order.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, s);
-        cudaMemcpyAsync(w.eps, eps.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, s);
-        const int nz = m + (m & 1);
         {
             ProfScope pf(PF_OTHER, s);
-            k_gather_cols<<<grid_for((long)m * nb), 256, 0, s>>>(w.Z, nz, m, w.sel, nullptr, nb, w.Cs, nb);
+            k_herm_copy<<<grid_for((long)m * m), 256, 0, s>>>(w.Hs, nsq, m, w.A, m);
         }
+        // lowest nb eigenpairs: values -> eps (device, increasing), vectors -> Cs [m][nb]
+        if ((st = heev_lowest(w.A, m, m, nb, w.eps, w.Cs, nb, w.heev, s))) return st;
         if ((st = zgemm_tn(nb, npw, m, w.Cs, nb, nullptr, w.V, ld, w.X, ld, false, s)) ||
             (st = zgemm_tn(nb, npw, m, w.Cs, nb, nullptr, w.HV, ld, w.HX, ld, false, s)))
             return st;
@@ -375,8 +363,12 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
         }
         if ((st = cuda_check(cudaMemcpyAsync(rn2.data(), w.rn2, sizeof(double) * nb, cudaMemcpyDeviceToHost, s),
                              "D2H residual norms")) ||
+            (st = cuda_check(cudaMemcpyAsync(eps.data(), w.eps, sizeof(double) * nb, cudaMemcpyDeviceToHost, s),
+                             "D2H Ritz values")) ||
             (st = cuda_check(cudaStreamSynchronize(s), "stream sync")))
             return st;
+        for (int n = 0; n < nb; ++n)
+            if (!std::isfinite(eps[n])) return fail(QM_ERR_NUMERIC, "qm_davidson: non-finite Ritz value");
         std::vector<int> unc;
         max_res = 0.0;
         for (int n = 0; n < nb; ++n) {

@@ -206,7 +206,7 @@ qm_status jacobi_eigh(const double2* H, int ldh, int m, double2* A, double2* Z, 
     void* args[] = {(void*)&A, (void*)&ld, (void*)&Z, (void*)&ld, (void*)&n, (void*)&mm, (void*)&max_sweeps, (void*)&tol2,
                     (void*)&rp, (void*)&red, (void*)&info};
     {
-        ProfScope pf(PF_OTHER, s);
+        ProfScope pf(PF_JACOBI, s);
         qm_status st = cuda_check(cudaLaunchCooperativeKernel((void*)k_jacobi, dim3(blocks), dim3(256), args, 0, s),
                                   "k_jacobi cooperative launch");
         if (st) return st;

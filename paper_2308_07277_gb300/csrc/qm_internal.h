@@ -89,7 +89,7 @@ qm_status ensure_dav_workspace(qm_gspace g, size_t bytes, cudaStream_t stream);
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // ---- launch counting / per-kernel timing (prof.cpp) ----
-enum ProfFamily { PF_VT = 0, PF_STICK_INV, PF_PLANE, PF_STICK_FWD, PF_GEMM_CN, PF_REDUCE, PF_GEMM_TN, PF_OTHER,
+enum ProfFamily { PF_VT = 0, PF_STICK_INV, PF_PLANE, PF_STICK_FWD, PF_GEMM_CN, PF_REDUCE, PF_GEMM_TN, PF_OTHER, PF_JACOBI,
                   kProfFamilies };
 void count_launch(int n);
 // Counts one launch; when timing is enabled records CUDA events on `s` around the scope.
@@ -157,6 +157,11 @@ constexpr int kJacobiMaxBlocks = 1024;
 qm_status jacobi_eigh(const double2* H, int ldh, int m, double2* A, double2* Z, void* rot, double* red, int* info,
                       double* evals_dev, cudaStream_t s);
 size_t jacobi_rot_bytes(int m);
+// lowest nev eigenpairs of the Hermitian m x m matrix A (lda, destroyed): evals[nev] device,
+// increasing; Y (m x nev, ld ldy) eigenvectors as columns; work heev_work_bytes(m, nev)
+qm_status heev_lowest(double2* A, int lda, int m, int nev, double* evals, double2* Y, int ldy, void* work,
+                      cudaStream_t s);
+size_t heev_work_bytes(int m, int nev);
 
 qm_status cgemm_cn(int M, int N, int K, const float2* A, int lda, const float2* B, int ldb,
                    float2* C, int ldc, float2* partial, int splits, cudaStream_t s);
