@@ -1,19 +1,24 @@
-"""H-psi throughput benchmark on the 64-atom Si-like cubic cell (a = 20.52 bohr, 25 Ry,
-FFT grid 72^3, 4 shifted k-points, 160 bands, 256 projectors, 18,232 plane waves per k).
+"""H-psi throughput and Davidson time-to-solution on the 64-atom Si-like cubic cell
+(a = 20.52 bohr, 25 Ry, FFT grid 72^3, 4 shifted k-points, 160 bands, 256 projectors,
+18,232 plane waves per k).
 
 One step = H psi applied to every band at every k-point (640 band-applies) through the
-C ABI (qm_hpsi).  Prints one JSON line (rank 0).
+C ABI (qm_hpsi).  The headline `value` is the precision form (FP32 FFT path and FP32
+nonlocal GEMMs, QM_MIXED); the plain FP64 form is measured the same way under
+`forms.fp64`.  The `davidson` object times block Davidson to a 1e-8 Ha residual at all 4
+k-points for the plain FP64 form and the mixed-precision forms.  Prints one JSON line.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp64|mixed] [--impl reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--davidson 0|1] [--impl reference]
 
---impl reference times the FP64 CPU oracle (numpy, one thread) on a bounded sample of
-the same workload: it is a deliberately slow baseline, not a competitor.
+--impl reference times the FP64 CPU oracle (numpy, one thread) on a bounded sample of the
+same workload: a deliberately slow baseline, not a competitor.
 Multi-GPU (torchrun, one process per GPU): every rank processes its own copy of the cell
 (independent problems, no collective on the data path), "scaling": "weak".
 """
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import math
 import os
@@ -28,13 +33,13 @@ if ROOT not in sys.path:
 METRIC = "Hψ band-applies/s & Davidson time-to-1e-8 Ha: mixed/learned vs FP64 plain"
 UNIT = "band-applies/s"
 WORKLOAD = "si64_cubic_72^3_4k_160b"
+N_FAMILIES = 14
 
-# FP64 / FP32 ALU peaks derived from SM count x per-SM FMA units x max clock:
-#   FP64: nominal 1.25 TFLOP/s over 152 SMs at 2.07 GHz = 4 flop/clk/SM (2 DFMA/clk/SM)
+# ALU peaks from SM count x per-SM FMA rate x max clock:
+#   FP64: the nominal 1.25 TFLOP/s over 152 SMs at 2.07 GHz = 4 flop/clk/SM (2 DFMA/clk/SM)
 #   FP32: 128 FMA/clk/SM
 N_SM = 152
-FP64_FLOP_PER_CLK_SM = 4
-FP32_FLOP_PER_CLK_SM = 256
+FLOP_PER_CLK_SM = {"fp64": 4, "mixed": 256}
 
 
 def parse():
@@ -43,7 +48,6 @@ def parse():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--cpu-sample-bands", type=int, default=48)
     ap.add_argument("--davidson", type=int, default=1, help="also time block Davidson to tol (0: skip)")
     ap.add_argument("--davidson-tol", type=float, default=1e-8)
@@ -51,10 +55,8 @@ def parse():
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
 
 
 def load_peaks():
@@ -93,18 +95,15 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.f.close()
-        rows = []
-        for line in open(self.path):
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
-                continue
-            rows.append(parts)
+        rows = [[p.strip() for p in line.split(",")] for line in open(self.path)]
+        rows = [r for r in rows if len(r) >= 9]
         os.unlink(self.path)
         if not rows:
             return None
         mine = [r for r in rows if self.bus and self.bus[-12:] in r[0].lower()] or rows
-        sm = sorted(float(r[1]) for r in mine if r[1].replace(".", "").isdigit())
-        mx = max((float(r[2]) for r in mine if r[2].replace(".", "").isdigit()), default=None)
+        num = lambda x: x.replace(".", "").isdigit()
+        sm = sorted(float(r[1]) for r in mine if num(r[1]))
+        mx = max((float(r[2]) for r in mine if num(r[2])), default=None)
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in mine for i in range(4) if r[5 + i].lower() == "active"})
         return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": reasons,
@@ -163,17 +162,26 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ GPU leg
-def fft_flops_per_plane_launch(grid, nrow):
-    """Algorithmic flops of one k_plane CTA (one band, one yz plane), 5 L log2 L per FFT."""
+def fft_flops_per_plane(grid, nrow):
+    """Algorithmic flops of one band's yz plane: 5 L log2 L per FFT of length L, both
+    directions, plus the V multiply."""
     n1, n2, n3 = grid
     f = lambda L: 5.0 * L * math.log2(L)
     return 2.0 * (nrow * f(n2) + n2 * f(n3)) + 2.0 * n2 * n3
 
 
+def max_over_ranks(vals, device):
+    """Element-wise maximum of per-rank timings over the process group (the slowest rank
+    sets the whole job's time)."""
+    import torch
+    t = torch.tensor([float(x) for x in vals], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return [float(x) for x in t]
+
+
 def read_prof(lib):
-    import ctypes
     fam = {}
-    for f in range(9):
+    for f in range(N_FAMILIES):
         t = ctypes.c_double()
         c = ctypes.c_longlong()
         lib.qm_prof_read(f, ctypes.byref(t), ctypes.byref(c))
@@ -182,69 +190,34 @@ def read_prof(lib):
     return fam
 
 
-def run_davidson(args, Q, lib, g, cell, psi_host, v, beta, D, nk, nb):
-    """Block Davidson to a residual of args.davidson_tol at every k-point (FP64 H psi),
-    from the seeded random start; wall time of the qm_davidson calls."""
+class Workload:
+    """Device-resident inputs of the 64-atom cell for one precision."""
+
+    def __init__(self, S, g, cell, rank, prec, dev):
+        import numpy as np
+        import torch
+        cdt = torch.complex128 if prec == "fp64" else torch.complex64
+        self.prec = prec
+        self.psi, self.beta, self.out, self.psi_host, self.out_host, self.nrow = [], [], [], [], [], []
+        for ik in range(len(cell.kpts)):
+            idx, _, kpg = g.indices(ik)
+            self.nrow.append(len(np.unique(idx // (cell.grid[0] * cell.grid[1]))))  # yz rows holding sticks
+            p = S.psi_random(cell.seed + rank, cell.nbnd, g.npw[ik], stream=ik)
+            self.psi_host.append(torch.from_numpy(p).to(cdt).pin_memory())
+            self.psi.append(self.psi_host[-1].to(dev))
+            self.beta.append(torch.from_numpy(S.beta_of_q(kpg, cell.tau, cell.omega)).to(cdt).to(dev))
+            self.out.append(torch.empty_like(self.psi[-1]))
+            self.out_host.append(torch.empty_like(self.psi_host[-1]).pin_memory())
+
+
+def measure_hpsi(args, Q, lib, g, cell, wl, v, D, world, dev, peaks, sample_clocks):
     import torch
-    if args.prec != "fp64":
-        return {"skipped": "the Davidson leg runs the FP64 form"}
-    per_k = []
-    lib.qm_prof_enable(1)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for ik in range(nk):
-        p = psi_host[ik].to(torch.complex128).cuda()
-        eig, info = Q.qm_davidson(g.handle, ik, p, v, beta[ik].to(torch.complex128), D, tol=args.davidson_tol,
-                                  max_iter=300, raise_not_converged=False)
-        per_k.append({"iterations": info["iterations"], "band_applies": info["band_applies"],
-                      "max_residual": info["max_residual"], "converged": info["converged"],
-                      "seconds": info["seconds"], "eig_min": float(eig[0]), "eig_max": float(eig[-1])})
-    torch.cuda.synchronize()
-    total = time.perf_counter() - t0
-    fam = read_prof(lib)
-    lib.qm_prof_enable(0)
-    return {"precision": "fp64", "tol_ha": args.davidson_tol, "seconds_total": total, "nbnd": nb,
-            "per_k": per_k, "kernels": fam}
-
-
-def run_ours(args):
-    import numpy as np
-    import torch
-
-    import paper_2308_07277_gb300 as Q
-    import qm_synth as S
-    from paper_2308_07277_gb300 import _lib
-
-    rank, world, local = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    dev = torch.device("cuda", torch.cuda.current_device())
-    lib = _lib.load()
-    cell = S.config2()
-    prec = args.prec
-    cdt = torch.complex128 if prec == "fp64" else torch.complex64
-    g = Q.GSpace(cell.lattice, cell.kpts, cell.ecut_ha, cell.grid)
     nk, nb, nproj = len(cell.kpts), cell.nbnd, cell.nproj
-    v = torch.from_numpy(S.vloc_on_grid(cell.lattice, cell.tau, cell.grid)).to(dev)
-    D = torch.from_numpy(S.dvals(cell.nat)).to(dev)
-    psi, beta, out, psi_host, out_host, nrow = [], [], [], [], [], []
-    for ik in range(nk):
-        idx, _, kpg = g.indices(ik)
-        nrow.append(len(np.unique(idx // (cell.grid[0] * cell.grid[1]))))   # yz-plane rows holding sticks
-        npw = g.npw[ik]
-        p = S.psi_random(cell.seed + rank, nb, npw, stream=ik)
-        psi_host.append(torch.from_numpy(p).to(cdt).pin_memory())
-        psi.append(psi_host[-1].to(dev))
-        beta.append(torch.from_numpy(S.beta_of_q(kpg, cell.tau, cell.omega)).to(cdt).to(dev))
-        out.append(torch.empty_like(psi[-1]))
-        out_host.append(torch.empty_like(psi_host[-1]).pin_memory())
     stream = torch.cuda.current_stream()
 
     def step():
         for ik in range(nk):
-            Q.qm_hpsi(g.handle, ik, psi[ik], v, beta[ik], D, out=out[ik], prec=prec, stream=stream)
+            Q.qm_hpsi(g.handle, ik, wl.psi[ik], v, wl.beta[ik], D, out=wl.out[ik], prec=wl.prec, stream=stream)
 
     def barrier():
         if world > 1:
@@ -254,9 +227,10 @@ def run_ours(args):
     for _ in range(args.warmup):
         step()
     barrier()
-    clocks = ClockSampler(getattr(torch.cuda.get_device_properties(dev), "pci_bus_id", ""))
-    clocks.start()
-    time.sleep(0.3)
+    clocks = ClockSampler(getattr(torch.cuda.get_device_properties(dev), "pci_bus_id", "")) if sample_clocks else None
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
     lib.qm_prof_enable(1)
     n0 = lib.qm_launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -268,95 +242,142 @@ def run_ours(args):
     barrier()
     launches = int(lib.qm_launch_count() - n0)
     ms = e0.elapsed_time(e1) / args.steps
-    fam = {}
-    import ctypes
-    for f in range(9):
-        t = ctypes.c_double()
-        c = ctypes.c_longlong()
-        lib.qm_prof_read(f, ctypes.byref(t), ctypes.byref(c))
-        if c.value:
-            fam[lib.qm_prof_name(f).decode()] = {"ms_total": t.value, "launches": c.value}
+    fam = read_prof(lib)
     lib.qm_prof_enable(0)
-    clk = clocks.stop()
+    clk = clocks.stop() if clocks else None
 
     # end to end: pinned host psi -> device, H psi, device -> pinned host, every step
-    for _ in range(2):
+    def e2e_step():
         for ik in range(nk):
-            psi[ik].copy_(psi_host[ik], non_blocking=True)
+            wl.psi[ik].copy_(wl.psi_host[ik], non_blocking=True)
         step()
         for ik in range(nk):
-            out_host[ik].copy_(out[ik], non_blocking=True)
+            wl.out_host[ik].copy_(wl.out[ik], non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
     barrier()
     e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e2.record(stream)
     esteps = max(3, args.steps // 3)
     for _ in range(esteps):
-        for ik in range(nk):
-            psi[ik].copy_(psi_host[ik], non_blocking=True)
-        step()
-        for ik in range(nk):
-            out_host[ik].copy_(out[ik], non_blocking=True)
+        e2e_step()
     e3.record(stream)
     barrier()
     ems = e2.elapsed_time(e3) / esteps
-    h2d = sum(t.numel() * t.element_size() for t in psi_host)
-    d2h = sum(t.numel() * t.element_size() for t in out_host)
-
-    dav = run_davidson(args, Q, lib, g, cell, psi_host, v, beta, D, nk, nb) if args.davidson else None
-
+    h2d = sum(t.numel() * t.element_size() for t in wl.psi_host)
+    d2h = sum(t.numel() * t.element_size() for t in wl.out_host)
     if world > 1:
-        t = torch.tensor([ms, ems], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms, ems = float(t[0]), float(t[1])
+        ms, ems = max_over_ranks([ms, ems], dev)
     band_applies = nb * nk * world
-    value = band_applies / (ms * 1e-3)
 
-    line = None
+    # roofline of the dominant kernel (largest summed device time in the timed region)
+    roof = None
+    if fam:
+        name, d = max(fam.items(), key=lambda kv: kv[1]["ms_total"])
+        avg_ms = d["ms_total"] / d["launches"]
+        per_step = d["launches"] / args.steps
+        smax = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+        fl_pk = FLOP_PER_CLK_SM[wl.prec] * N_SM * smax / 1e12
+        fl = None
+        if name == "k_plane":
+            fl = sum(nb * cell.grid[0] * fft_flops_per_plane(cell.grid, wl.nrow[ik]) for ik in range(nk))
+        elif name in ("k_gemm_tn", "k_gemm_cn"):
+            fl = 8.0 * nproj * nb * sum(g.npw)   # 8 flops per complex multiply-add, all k
+        if fl is not None:
+            fl /= per_step
+            roof = {"bound": "alu", "achieved": fl / (avg_ms * 1e-3) / 1e12, "peak": fl_pk, "unit": "TFLOP/s"}
+            roof["frac"] = roof["achieved"] / roof["peak"]
+        else:
+            roof = {"bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"), "unit": "GB/s", "frac": None}
+        roof.update({"kernel": name, "traffic": None, "avg_launch_ms": avg_ms,
+                     "peak_source": "derived: %d SMs x %d flop/clk/SM x %.0f MHz" % (
+                         N_SM, FLOP_PER_CLK_SM[wl.prec], smax / 1e6)})
+    return {"value": band_applies / (ms * 1e-3), "ms_per_step": ms, "gpu_launches": launches, "kernels": fam,
+            "roofline": roof, "clocks": clk,
+            "e2e": {"value": band_applies / (ems * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": ems},
+            "l2": "inputs larger than L2: psi %.0f MB + beta %.0f MB per step" % (
+                h2d / 1e6, sum(b.numel() * b.element_size() for b in wl.beta) / 1e6)}
+
+
+def run_davidson(args, Q, lib, g, cell, wl64, v, D):
+    """Block Davidson to args.davidson_tol at every k-point from the seeded random start:
+    the plain FP64 form, the precision form (QM_MIXED), and the precision form with 10 %
+    buffer bands (only the lowest 160 must converge).  Wall time of the qm_davidson calls."""
+    import numpy as np
+    import torch
+
+    import qm_synth as S
+    nk, nb = len(cell.kpts), cell.nbnd
+    out = {"tol_ha": args.davidson_tol, "nbnd": nb, "nk": nk}
+    eigs = {}
+    nextra = max(1, nb // 10)
+    for form, prec, extra in (("fp64", "fp64", 0), ("mixed", "mixed", 0), ("mixed_buffer", "mixed", nextra)):
+        per_k = []
+        lib.qm_prof_enable(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for ik in range(nk):
+            p = torch.from_numpy(S.psi_random(cell.seed, nb + extra, g.npw[ik], stream=ik)).cuda()
+            eig, info = Q.qm_davidson(g.handle, ik, p, v, wl64.beta[ik], D, tol=args.davidson_tol, max_iter=300,
+                                      raise_not_converged=False, prec=prec, nconv=nb)
+            eigs.setdefault(form, []).append(eig[:nb])
+            rec = {k: info[k] for k in ("iterations", "iterations_mixed", "band_applies", "band_applies_mixed",
+                                        "max_residual", "converged", "seconds")}
+            h = info["history"]
+            rec["history_every_10"] = [h[i] for i in range(0, len(h), 10)]
+            per_k.append(rec)
+        torch.cuda.synchronize()
+        out[form] = {"seconds_total": time.perf_counter() - t0, "nbnd_solved": nb + extra, "per_k": per_k,
+                     "kernels": read_prof(lib)}
+        lib.qm_prof_enable(0)
+    for form in ("mixed", "mixed_buffer"):
+        out[f"speedup_{form}_vs_fp64"] = out["fp64"]["seconds_total"] / out[form]["seconds_total"]
+        out[f"max_eig_diff_{form}_vs_fp64_ha"] = float(max(np.abs(a - b).max()
+                                                         for a, b in zip(eigs["fp64"], eigs[form])))
+    return out
+
+
+def run_ours(args):
+    import torch
+
+    import paper_2308_07277_gb300 as Q
+    import qm_synth as S
+    from paper_2308_07277_gb300 import _lib
+
+    rank, world, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        torch.distributed.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    lib = _lib.load()
+    peaks, _ = load_peaks()
+    cell = S.config2()
+    g = Q.GSpace(cell.lattice, cell.kpts, cell.ecut_ha, cell.grid)
+    v = torch.from_numpy(S.vloc_on_grid(cell.lattice, cell.tau, cell.grid)).to(dev)
+    D = torch.from_numpy(S.dvals(cell.nat)).to(dev)
+    forms, wl = {}, {}
+    for prec in ("mixed", "fp64"):
+        wl[prec] = Workload(S, g, cell, rank, prec, dev)
+        forms[prec] = measure_hpsi(args, Q, lib, g, cell, wl[prec], v, D, world, dev, peaks,
+                                   sample_clocks=(prec == "mixed"))
+    dav = run_davidson(args, Q, lib, g, cell, wl["fp64"], v, D) if args.davidson else None
     if rank == 0:
-        peaks, peak_src = load_peaks()
-        dom = max(fam.items(), key=lambda kv: kv[1]["ms_total"]) if fam else None
-        roof = None
-        if dom is not None:
-            name, d = dom
-            avg_ms = d["ms_total"] / d["launches"]
-            smax = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
-            fl_pk = (FP64_FLOP_PER_CLK_SM if prec == "fp64" else FP32_FLOP_PER_CLK_SM) * N_SM * smax / 1e12
-            if name == "k_plane":
-                # algorithmic flops of one step's planes (nb x N1 per k), spread over its launches
-                per_step = d["launches"] / args.steps
-                fl = sum(nb * cell.grid[0] * fft_flops_per_plane_launch(cell.grid, nrow[ik]) for ik in range(nk))
-                fl /= per_step
-                roof = {"bound": "alu", "achieved": fl / (avg_ms * 1e-3) / 1e12, "peak": fl_pk, "unit": "TFLOP/s"}
-            elif name in ("k_gemm_tn", "k_gemm_cn"):
-                # nonlocal GEMMs: 8 flops per complex multiply-add, nproj x nb x npw per k
-                per_step = d["launches"] / args.steps
-                fl = 8.0 * nproj * nb * g.npw[0] * nk / per_step
-                roof = {"bound": "alu", "achieved": fl / (avg_ms * 1e-3) / 1e12, "peak": fl_pk, "unit": "TFLOP/s"}
-            else:
-                roof = {"bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"), "unit": "GB/s"}
-            roof["kernel"] = name
-            roof["frac"] = (roof["achieved"] / roof["peak"]) if roof.get("achieved") else None
-            roof["traffic"] = None
-            roof["peak_source"] = "derived: %d SMs x %d flop/clk/SM x %.0f MHz (%s clock)" % (
-                N_SM, FP64_FLOP_PER_CLK_SM if prec == "fp64" else FP32_FLOP_PER_CLK_SM, smax / 1e6, peak_src)
-            roof["avg_launch_ms"] = avg_ms
-        cpu = oracle_sample(args.cpu_sample_bands) if world == 1 or rank == 0 else None
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32",
-                "data": "synthetic",
-                "config": {"workload": WORKLOAD, "precision": prec, "band_applies_per_step": nb * nk,
-                           "npw": g.npw[0], "nproj": nproj, "grid": list(cell.grid),
-                           "l2": "inputs larger than L2: psi %.0f MB + beta %.0f MB per step" % (
-                               h2d / 1e6, sum(b.numel() * b.element_size() for b in beta) / 1e6)},
-                "e2e": {"value": band_applies / (ems * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                        "d2h_bytes_per_step": d2h, "ms_per_step": ems},
-                "gpu_launches": launches,
-                "kernels": fam,
-                "roofline": roof,
-                "cpu_baseline": cpu,
-                "clocks": clk,
-                "davidson": dav}
+        head = forms["mixed"]
+        line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "precision": "mixed (FP32 FFT path and nonlocal GEMMs)",
+                           "band_applies_per_step": cell.nbnd * len(cell.kpts), "npw": g.npw[0],
+                           "nproj": cell.nproj, "grid": list(cell.grid), "l2": head["l2"]},
+                "e2e": head["e2e"], "gpu_launches": head["gpu_launches"], "kernels": head["kernels"],
+                "roofline": head["roofline"], "clocks": head["clocks"],
+                "forms": {"fp64": {k: forms["fp64"][k] for k in ("value", "ms_per_step", "e2e", "roofline",
+                                                                  "kernels", "gpu_launches")},
+                          "mixed_over_fp64": head["value"] / forms["fp64"]["value"]},
+                "davidson": dav,
+                "cpu_baseline": oracle_sample(args.cpu_sample_bands)}
         print(json.dumps(line))
     g.close()
     if world > 1:

@@ -169,18 +169,31 @@ typedef struct {
                             default 1e-8 */
     int max_iter;        /* maximum Rayleigh-Ritz steps; default 100 */
     int nvecx;           /* maximum basis size, >= 2 nb (clamped to npw); default 4 nb */
-    qm_precision prec;   /* H psi precision inside the iterations; QM_FP64 */
+    qm_precision prec;   /* QM_FP64: every step in FP64.  QM_MIXED: H psi in FP32 (qm_hpsi
+                            QM_MIXED) and the subspace products in FP32 arithmetic until the
+                            largest residual falls below mixed_switch; then the Ritz vectors are
+                            re-orthonormalised and H applied to them in FP64, and the iterations
+                            continue in FP64 to tol.  Eigensolves, residual norms and band
+                            energies are FP64 in both. */
     int precond;         /* 0 = Teter-Payne-Allan diagonal preconditioner */
-    int reserved[4];     /* must be 0 */
+    double mixed_switch; /* QM_MIXED: residual (Ha) where FP64 takes over (or earlier if the
+                            residual, once below 1e-3, stops halving over 10 steps); 0 -> 1e-4 */
+    int nconv;           /* only the lowest nconv bands must reach tol (1..nb; 0 -> nb); the
+                            other nb - nconv trial vectors are a buffer that speeds convergence */
+    int reserved;        /* must be 0 */
+    double* history;     /* host, may be NULL: max_iter doubles, the largest residual among the
+                            nconv bands after each Rayleigh-Ritz step */
 } qm_davidson_opts;
 
 /* Counters of one qm_davidson call (the paper's "H-psi calls" are band_applies / nb). */
 typedef struct {
     int iterations;          /* Rayleigh-Ritz steps taken */
-    int converged;           /* 1 if every residual norm reached tol */
+    int converged;           /* 1 if the nconv lowest residual norms reached tol */
     long long band_applies;  /* number of single-band H psi applications */
-    double max_residual;     /* max_n ||H x_n - eps_n x_n||_2 at exit (Ha) */
+    double max_residual;     /* max over the nconv bands of ||H x_n - eps_n x_n||_2 at exit (Ha) */
     double seconds;          /* host wall time of the call */
+    int iterations_mixed;    /* QM_MIXED: Rayleigh-Ritz steps taken in the FP32 phase */
+    long long band_applies_mixed;  /* QM_MIXED: H psi applications done in FP32 */
 } qm_davidson_stats;
 
 /*
@@ -203,7 +216,7 @@ typedef struct {
  * complex doubles plus O(nvecx^2)).
  * Errors: QM_ERR_ARG, QM_ERR_OOM, QM_ERR_CUDA; QM_ERR_NUMERIC (non-finite values,
  * rank-deficient start); QM_ERR_NOT_CONVERGED (max_iter reached: outputs hold the last
- * Ritz pairs); QM_ERR_UNSUPPORTED (opts->prec other than QM_FP64 in this build).
+ * Ritz pairs).
  */
 qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, int ld_psi,
                       const double* vloc_r, int nproj, const void* beta, int ld_beta,
@@ -234,7 +247,7 @@ qm_status qm_eigh_lowest(int m, int nev, const void* A, int lda, double* evals, 
  *  qm_prof_enable   on != 0: from now on record a pair of CUDA events on the launch stream
  *                   around every kernel launch; resets the accumulated times (any value).
  *  qm_prof_read     waits for the recorded events and returns, for kernel family
- *                   `family` (0 <= family < 9), the summed device time in ms and the number
+ *                   `family` (0 <= family < 14), the summed device time in ms and the number
  *                   of launches timed since the last qm_prof_enable.
  *  qm_prof_name     name of a kernel family ("" when out of range).
  */

@@ -58,13 +58,15 @@ def load():
 class DavidsonOpts(ctypes.Structure):
     """qm_davidson_opts of include/qm.h."""
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("nvecx", ctypes.c_int),
-                ("prec", ctypes.c_int), ("precond", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+                ("prec", ctypes.c_int), ("precond", ctypes.c_int), ("mixed_switch", ctypes.c_double),
+                ("nconv", ctypes.c_int), ("reserved", ctypes.c_int), ("history", c_double_p)]
 
 
 class DavidsonStats(ctypes.Structure):
     """qm_davidson_stats of include/qm.h."""
     _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("band_applies", ctypes.c_longlong),
-                ("max_residual", ctypes.c_double), ("seconds", ctypes.c_double)]
+                ("max_residual", ctypes.c_double), ("seconds", ctypes.c_double), ("iterations_mixed", ctypes.c_int),
+                ("band_applies_mixed", ctypes.c_longlong)]
 
 
 SIGNATURES["qm_davidson"] = (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,

@@ -124,7 +124,7 @@ def qm_hpsi(g, ik, psi, vloc, beta, D, out=None, prec="fp64", stream=None):
 
 
 def qm_davidson(g, ik, psi, vloc, beta, D, tol=1e-8, max_iter=100, nvecx=0, prec="fp64", stream=None,
-                raise_not_converged=True):
+                raise_not_converged=True, mixed_switch=0.0, nconv=0):
     """Lowest nb eigenpairs; psi (nb, >=npw) complex128 CUDA tensor is overwritten by the
     Ritz vectors.  Returns (eigenvalues ndarray (nb,), stats dict)."""
     lib = _lib.load()
@@ -132,7 +132,9 @@ def qm_davidson(g, ik, psi, vloc, beta, D, tol=1e-8, max_iter=100, nvecx=0, prec
         raise ValueError("psi must be 2-D (nb, ld)")
     nb = int(psi.shape[0])
     nproj = 0 if beta is None else int(beta.shape[0])
-    opts = _lib.DavidsonOpts(tol=float(tol), max_iter=int(max_iter), nvecx=int(nvecx), prec=_PREC[prec], precond=0)
+    hist = np.zeros(max(1, int(max_iter)), np.float64)
+    opts = _lib.DavidsonOpts(tol=float(tol), max_iter=int(max_iter), nvecx=int(nvecx), prec=_PREC[prec], precond=0,
+                             mixed_switch=float(mixed_switch), nconv=int(nconv), history=_dp(hist))
     stats = _lib.DavidsonStats()
     eig = np.zeros(nb, np.float64)
     st = lib.qm_davidson(g, int(ik), nb, _dev_ptr(psi, "psi", torch.complex128), int(psi.stride(0)),
@@ -142,6 +144,8 @@ def qm_davidson(g, ik, psi, vloc, beta, D, tol=1e-8, max_iter=100, nvecx=0, prec
                          ctypes.byref(stats), _stream_ptr(stream))
     info = {"iterations": stats.iterations, "converged": bool(stats.converged),
             "band_applies": stats.band_applies, "max_residual": stats.max_residual, "seconds": stats.seconds,
+            "iterations_mixed": stats.iterations_mixed, "band_applies_mixed": stats.band_applies_mixed,
+            "history": hist[: max(0, stats.iterations)].tolist(),
             "status": STATUS.get(st, st)}
     if st != 0 and not (st == 4 and not raise_not_converged):
         _check(st)

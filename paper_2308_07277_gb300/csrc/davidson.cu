@@ -7,11 +7,18 @@
 //   residuals       r_n = HX_n - eps_n X_n, ||r_n|| and T_n = <X_n|T|X_n> (FP64)
 //   corrections     delta_n = K_TPA(kin / T_n) r_n for the bands with ||r_n|| > tol
 //   restart         if the basis would exceed nvecx: V <- X, HV <- HX
-//   orthonormalise  two classical Gram-Schmidt passes against V, then Loewdin (S^-1/2 via
-//                   the Jacobi eigensolver) within the block, near-dependent directions dropped
+//   orthonormalise  two classical Gram-Schmidt passes against V, then two passes of
+//                   Cholesky-QR within the block, near-dependent directions dropped
 //   expand          V <- [V, delta], HV <- [HV, H delta]
 // The basis is kept orthonormal, so the subspace overlap S_sub is the identity to FP64
-// round-off and Rayleigh-Ritz is a standard Hermitian eigenproblem.
+// round-off and Rayleigh-Ritz is a standard Hermitian eigenproblem (heev.cu).
+//
+// Precision form (QM_MIXED): H psi in FP32 and the subspace products in FP32 arithmetic,
+// except the coefficients of the second Gram-Schmidt pass and the second Cholesky-QR pass,
+// which keep the basis orthonormal to FP64 round-off; eigensolves, residual norms and band
+// energies in FP64.  Once the largest residual is below mixed_switch (or stops falling), the
+// Ritz vectors are re-orthonormalised, H is applied to them in FP64 (refinement sweep), and
+// the iterations continue entirely in FP64.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -116,51 +123,40 @@ __global__ void k_set_diag(double2* __restrict__ H, int ld, int m, const double*
     }
 }
 
-// invs[i] = 1/sqrt(S_ii): scaling that gives the Gram matrix a unit diagonal
-__global__ void k_inv_sqrt_diag(const double2* __restrict__ S, int ld, int n, double* __restrict__ invs) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        invs[i] = 1.0 / sqrt(S[(size_t)i * ld + i].x);
-}
-
-__global__ void k_scale_sym(const double2* __restrict__ S, int lds, int n, const double* __restrict__ invs,
-                            double2* __restrict__ T, int ldt) {
-    const long total = (long)n * n;
+template <class D, class S>
+__global__ void k_convert_rows(const S* __restrict__ in, int ldi, D* __restrict__ out, int ldo, int rows, int cols) {
+    const long total = (long)rows * cols;
     for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
-        const int i = (int)(e / n), j = (int)(e % n);
-        const double f = invs[i] * invs[j];
-        double2 v = S[(size_t)i * lds + j];
-        T[(size_t)i * ldt + j] = make_double2(f * v.x, f * v.y);
-    }
-}
-
-// W[i][k] = invs[i] * U[i][sel[k]] * wk[k]   (Loewdin coefficients)
-__global__ void k_lowdin_coef(const double2* __restrict__ U, int ldu, int n, const double* __restrict__ invs,
-                              const int* __restrict__ sel, const double* __restrict__ wk, int nk,
-                              double2* __restrict__ W, int ldw) {
-    const long total = (long)n * nk;
-    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
-        const int i = (int)(e / nk), k = (int)(e % nk);
-        const double f = invs[i] * wk[k];
-        double2 v = U[(size_t)i * ldu + sel[k]];
-        W[(size_t)i * ldw + k] = make_double2(f * v.x, f * v.y);
+        const int r = (int)(e / cols), c = (int)(e % cols);
+        const S v = in[(size_t)r * ldi + c];
+        D o;
+        o.x = (decltype(o.x))v.x;
+        o.y = (decltype(o.y))v.y;
+        out[(size_t)r * ldo + c] = o;
     }
 }
 
 inline int grid_for(long n) { return (int)std::max<long>(1, std::min<long>((n + 255) / 256, 152 * 8)); }
 
+template <class D, class S>
+qm_status convert_rows(const S* in, int ldi, D* out, int ldo, int rows, int cols, cudaStream_t s) {
+    if (rows <= 0) return QM_OK;
+    ProfScope pf(PF_CONVERT, s);
+    k_convert_rows<D, S><<<grid_for((long)rows * cols), 256, 0, s>>>(in, ldi, out, ldo, rows, cols);
+    return cuda_check(cudaGetLastError(), "k_convert_rows launch");
+}
+
 struct Ws {
     double2 *V, *HV, *X, *HX, *R, *Dl, *Tmp;  // [.. rows][ld]
     double2 *Hs, *G, *A, *Z, *Cs, *Part;      // small
-    double *eval, *eps, *rn2, *tk, *red, *invs, *wk;
-    int *sel, *info;
-    void* rot;
+    double *eval, *eps, *rn2, *tk;
+    int *sel, *rank, *info;
     void* heev;
 };
 
 }  // namespace
 
-qm_status jacobi_eigh(const double2* H, int ldh, int m, double2* A, double2* Z, void* rot, double* red, int* info,
-                      double* evals_dev, cudaStream_t s);
+
 
 }  // namespace qm
 
@@ -176,56 +172,74 @@ struct DavidsonRun {
     const double* D;
     cudaStream_t s;
     Ws w;
-    long long applies = 0;
+    long long applies = 0, applies_mixed = 0;
+    bool mixed = false;          // current phase: FP32 H psi and FP32-arithmetic subspace products
+    float2* psi32 = nullptr;     // [nb][ld] FP32 staging of the vectors H is applied to
+    float2* hpsi32 = nullptr;    // [nb][ld]
+    float2* beta32 = nullptr;    // [nproj][ld]
 
     qm_status hpsi(const double2* in, double2* out, int n) {
         applies += n;
-        return qm_hpsi(g, ik, n, in, ld, vloc, nproj, beta, ldb, D, out, ld, QM_FP64, s);
+        if (!mixed) return qm_hpsi(g, ik, n, in, ld, vloc, nproj, beta, ldb, D, out, ld, QM_FP64, s);
+        applies_mixed += n;
+        qm_status st = convert_rows(in, ld, psi32, ld, n, npw, s);
+        if (st) return st;
+        st = qm_hpsi(g, ik, n, psi32, ld, vloc, nproj, beta32, ld, D, hpsi32, ld, QM_MIXED, s);
+        if (st) return st;
+        return convert_rows(hpsi32, ld, out, ld, n, npw, s);
+    }
+    qm_status gemm_cn(int M, int N, int K, const double2* A, int lda, const double2* B, int ldb_, double2* C,
+                      int ldc) {
+        const int sp = zgemm_cn_splits(M, N, K);
+        return mixed ? zgemm_cn_f32(M, N, K, A, lda, B, ldb_, C, ldc, w.Part, sp, s)
+                     : zgemm_cn(M, N, K, A, lda, B, ldb_, C, ldc, w.Part, sp, s);
+    }
+    qm_status gemm_tn(int M, int N, int K, const double2* A, int lda, const double2* B, int ldb_, double2* C,
+                      int ldc, bool acc, double alpha = 1.0) {
+        return mixed ? zgemm_tn_f32(M, N, K, A, lda, nullptr, B, ldb_, C, ldc, acc, s, alpha)
+                     : zgemm_tn(M, N, K, A, lda, nullptr, B, ldb_, C, ldc, acc, s, alpha);
     }
 
-    // Loewdin-orthonormalise the nd rows of Y (ld) into the rows of out; returns kept count.
-    qm_status lowdin(const double2* Y, int nd, double2* out, int* kept) {
+    // Orthonormalise the nd rows of Y into the rows of out by two passes of Cholesky-QR with
+    // dropping of near-dependent directions (first pass: pivots below `drop` of a vector's
+    // own norm^2); *kept = rows written.  Uses R as scratch.
+    qm_status cholqr(const double2* Y, int nd, double2* out, int* kept) {
         qm_status st;
-        const int lds = nd + (nd & 1);
-        // S[i][j] = <Y_i|Y_j>
-        if ((st = zgemm_cn(nd, nd, npw, Y, ld, Y, ld, w.Cs, lds, w.Part, zgemm_cn_splits(nd, nd, npw), s))) return st;
-        // Loewdin on the unit-diagonal Gram matrix G = D^-1/2 S D^-1/2, D = diag(S)
-        {
-            ProfScope pf(PF_OTHER, s);
-            k_inv_sqrt_diag<<<grid_for(nd), 256, 0, s>>>(w.Cs, lds, nd, w.invs);
-        }
-        {
-            ProfScope pf(PF_OTHER, s);
-            k_scale_sym<<<grid_for((long)nd * nd), 256, 0, s>>>(w.Cs, lds, nd, w.invs, w.G, lds);
-        }
-        if ((st = heev_lowest(w.G, lds, nd, nd, w.eval, w.Z, nd, w.heev, s))) return st;
-        std::vector<double> lam(nd);
-        if ((st = cuda_check(cudaMemcpyAsync(lam.data(), w.eval, sizeof(double) * nd, cudaMemcpyDeviceToHost, s),
-                             "D2H Gram eigenvalues")))
-            return st;
-        if ((st = cuda_check(cudaStreamSynchronize(s), "stream sync"))) return st;
-        double lmax = 0.0;
-        for (double l : lam) lmax = std::max(lmax, l);
-        std::vector<int> sel;
-        std::vector<double> wk;
-        for (int k = 0; k < nd; ++k)
-            if (lam[k] > 1e-8 * lmax && std::isfinite(lam[k])) {
-                sel.push_back(k);
-                wk.push_back(1.0 / std::sqrt(lam[k]));
+        const double drop = mixed ? 1e-5 : 1e-12;  // FP32-arithmetic Gram matrices carry ~1e-7 noise
+        const double2* src = Y;
+        int n_in = nd;
+        const bool was_mixed = mixed;
+        for (int pass = 0; pass < 2; ++pass) {
+            double2* dst = pass == 0 ? w.R : out;
+            mixed = was_mixed && pass == 0;  // the second pass is FP64: orthonormal to round-off
+            if ((st = gemm_cn(n_in, n_in, npw, src, ld, src, ld, w.G, n_in))) {
+                mixed = was_mixed;
+                return st;
             }
-        *kept = (int)sel.size();
-        if (sel.empty()) return QM_OK;
-        cudaMemcpyAsync(w.sel, sel.data(), sizeof(int) * sel.size(), cudaMemcpyHostToDevice, s);
-        cudaMemcpyAsync(w.wk, wk.data(), sizeof(double) * wk.size(), cudaMemcpyHostToDevice, s);
-        {
-            ProfScope pf(PF_OTHER, s);
-            k_lowdin_coef<<<grid_for((long)nd * sel.size()), 256, 0, s>>>(w.Z, nd, nd, w.invs, w.sel, w.wk,
-                                                                         (int)sel.size(), w.Cs, (int)sel.size());
+            int k = 0;
+            if ((st = chol_transform(w.G, n_in, n_in, pass == 0 ? drop : 1e-14, w.sel, w.rank, w.info, w.A, w.Cs, 0,
+                                     s)) ||
+                (st = cuda_check(cudaMemcpyAsync(&k, w.info, sizeof(int), cudaMemcpyDeviceToHost, s), "D2H kept")) ||
+                (st = cuda_check(cudaStreamSynchronize(s), "stream sync"))) {
+                mixed = was_mixed;
+                return st;
+            }
+            if (k == 0) {
+                mixed = was_mixed;
+                *kept = 0;
+                return QM_OK;
+            }
+            if ((st = chol_transform_rows(w.G, n_in, n_in, w.sel, w.rank, k, w.A, w.Cs, s)) ||
+                (st = gemm_tn(k, npw, n_in, w.Cs, k, src, ld, dst, ld, false))) {
+                mixed = was_mixed;
+                return st;
+            }
+            src = dst;
+            n_in = k;
         }
-        // out[k] = sum_i W[i][k] Y_i
-        st = zgemm_tn((int)sel.size(), npw, nd, w.Cs, (int)sel.size(), nullptr, Y, ld, out, ld, false, s);
-        if (st) return st;
-        return cuda_check(cudaGetLastError(), "lowdin launches");
+        mixed = was_mixed;
+        *kept = n_in;
+        return QM_OK;
     }
 };
 
@@ -246,17 +260,20 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
     if (nb > npw / 2) return fail(QM_ERR_ARG, "qm_davidson: nb must be <= npw / 2");
     if ((uintptr_t)psi_inout % 16 || (nproj > 0 && (uintptr_t)beta % 16))
         return fail(QM_ERR_ARG, "qm_davidson: psi/beta not 16-byte aligned");
-    qm_davidson_opts o;
+    qm_davidson_opts o{};
     o.tol = 1e-8;
     o.max_iter = 100;
     o.nvecx = 4 * nb;
     o.prec = QM_FP64;
+    o.mixed_switch = 1e-4;
     if (opts) o = *opts;
     if (o.nvecx <= 0) o.nvecx = 4 * nb;
     o.nvecx = std::min(o.nvecx, npw);
     if (o.nvecx < 2 * nb) return fail(QM_ERR_ARG, "qm_davidson: nvecx must be >= 2 nb");
     if (!(o.tol > 0.0) || o.max_iter < 1) return fail(QM_ERR_ARG, "qm_davidson: tol must be > 0, max_iter >= 1");
-    if (o.prec != QM_FP64) return fail(QM_ERR_UNSUPPORTED, "qm_davidson: only QM_FP64 H psi in this build");
+    if (o.prec != QM_FP64 && o.prec != QM_MIXED) return fail(QM_ERR_ARG, "qm_davidson: unknown precision");
+    if (!(o.mixed_switch > 0.0)) o.mixed_switch = 1e-4;
+    if (o.nconv <= 0 || o.nconv > nb) o.nconv = nb;
 
     qm_status st = ensure_device(g);
     if (st) return st;
@@ -288,14 +305,17 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
     };
     const size_t oV = take(big * nvx), oHV = take(big * nvx), oX = take(big * nb), oHX = take(big * nb),
                  oR = take(big * nb), oDl = take(big * nb), oTmp = take(big * nb);
+    const size_t big32 = (size_t)ld * sizeof(float2);
+    const bool use_mixed = o.prec == QM_MIXED;
+    const size_t oP32 = take(use_mixed ? big32 * nb : 0), oH32 = take(use_mixed ? big32 * nb : 0),
+                 oB32 = take(use_mixed ? big32 * std::max(nproj, 1) : 0);
     const size_t sq = (size_t)nsq * nsq * sizeof(double2);
     const size_t oHs = take(sq), oG = take(sq), oA = take(sq), oZ = take(sq), oCs = take(sq);
     const size_t oPart = take(gemm_cn_partial_bytes(false));
     const size_t oEval = take(sizeof(double) * nsq), oEps = take(sizeof(double) * nsq),
                  oRn = take(sizeof(double) * nsq), oTk = take(sizeof(double) * nsq),
-                 oRed = take(sizeof(double) * 2 * kJacobiMaxBlocks), oInvs = take(sizeof(double) * nsq),
-                 oWk = take(sizeof(double) * nsq), oSel = take(sizeof(int) * nsq), oInfo = take(sizeof(int) * 4),
-                 oRot = take(jacobi_rot_bytes(nsq)), oHeev = take(heev_work_bytes(nsq, nsq));
+                 oSel = take(sizeof(int) * nsq), oRank = take(sizeof(int) * nsq), oInfo = take(sizeof(int) * 4),
+                 oHeev = take(heev_work_bytes(nsq, nsq));
     if ((st = ensure_dav_workspace(g, off, s))) return st;
     char* base = (char*)g->dws.ptr;
     Ws& w = run.w;
@@ -306,6 +326,13 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
     w.R = (double2*)(base + oR);
     w.Dl = (double2*)(base + oDl);
     w.Tmp = (double2*)(base + oTmp);
+    if (use_mixed) {
+        run.psi32 = (float2*)(base + oP32);
+        run.hpsi32 = (float2*)(base + oH32);
+        run.beta32 = (float2*)(base + oB32);
+        if (nproj > 0 && (st = convert_rows((const double2*)beta, ld_beta, run.beta32, ld, nproj, npw, s))) return st;
+        run.mixed = true;
+    }
     w.Hs = (double2*)(base + oHs);
     w.G = (double2*)(base + oG);
     w.A = (double2*)(base + oA);
@@ -316,12 +343,9 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
     w.eps = (double*)(base + oEps);
     w.rn2 = (double*)(base + oRn);
     w.tk = (double*)(base + oTk);
-    w.red = (double*)(base + oRed);
-    w.invs = (double*)(base + oInvs);
-    w.wk = (double*)(base + oWk);
     w.sel = (int*)(base + oSel);
+    w.rank = (int*)(base + oRank);
     w.info = (int*)(base + oInfo);
-    w.rot = base + oRot;
     w.heev = base + oHeev;
     const double* kin = g->k[ik].kin;
 
@@ -331,19 +355,18 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
                          "copy psi")))
         return st;
     int kept = 0;
-    if ((st = run.lowdin(w.Tmp, nb, w.V, &kept))) return st;
+    if ((st = run.cholqr(w.Tmp, nb, w.V, &kept))) return st;
     if (kept < nb) return fail(QM_ERR_NUMERIC, "qm_davidson: initial psi block is rank deficient");
     if ((st = run.hpsi(w.V, w.HV, nb))) return st;
     int m = nb, m0 = 0;
     std::vector<double> rn2(nb), eps(nb);
-    int it = 0;
+    int it = 0, it_mixed = 0;
+    std::vector<double> hist_mixed;
     bool converged = false;
     double max_res = 0.0;
     for (it = 1; it <= o.max_iter; ++it) {
         // new columns of H_sub
-        if ((st = zgemm_cn(m, m - m0, npw, w.V, ld, w.HV + (size_t)m0 * ld, ld, w.Hs + m0, nsq, w.Part,
-                           zgemm_cn_splits(m, m - m0, npw), s)))
-            return st;
+        if ((st = run.gemm_cn(m, m - m0, npw, w.V, ld, w.HV + (size_t)m0 * ld, ld, w.Hs + m0, nsq))) return st;
         {
             ProfScope pf(PF_OTHER, s);
             k_herm_fill<<<grid_for((long)m * (m - m0)), 256, 0, s>>>(w.Hs, nsq, m0, m);
@@ -354,8 +377,8 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
         }
         // lowest nb eigenpairs: values -> eps (device, increasing), vectors -> Cs [m][nb]
         if ((st = heev_lowest(w.A, m, m, nb, w.eps, w.Cs, nb, w.heev, s))) return st;
-        if ((st = zgemm_tn(nb, npw, m, w.Cs, nb, nullptr, w.V, ld, w.X, ld, false, s)) ||
-            (st = zgemm_tn(nb, npw, m, w.Cs, nb, nullptr, w.HV, ld, w.HX, ld, false, s)))
+        if ((st = run.gemm_tn(nb, npw, m, w.Cs, nb, w.V, ld, w.X, ld, false)) ||
+            (st = run.gemm_tn(nb, npw, m, w.Cs, nb, w.HV, ld, w.HX, ld, false)))
             return st;
         {
             ProfScope pf(PF_OTHER, s);
@@ -371,13 +394,36 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
             if (!std::isfinite(eps[n])) return fail(QM_ERR_NUMERIC, "qm_davidson: non-finite Ritz value");
         std::vector<int> unc;
         max_res = 0.0;
+        bool all_conv = true;
         for (int n = 0; n < nb; ++n) {
             double r = std::sqrt(rn2[n]);
             if (!std::isfinite(r)) return fail(QM_ERR_NUMERIC, "qm_davidson: non-finite residual");
-            max_res = std::max(max_res, r);
+            if (n < o.nconv) {
+                max_res = std::max(max_res, r);
+                all_conv = all_conv && r <= o.tol;
+            }
             if (r > o.tol) unc.push_back(n);
         }
-        if (unc.empty()) {
+        if (o.history && it - 1 < o.max_iter) o.history[it - 1] = max_res;
+        if (run.mixed) hist_mixed.push_back(max_res);
+        // FP32 round-off can only stall the residual well below 1e-3: there, no halving over the
+        // last 10 FP32 iterations hands over to FP64 early
+        bool stalled = false;
+        if (run.mixed && max_res < 1e-3 && hist_mixed.size() > 10)
+            stalled = max_res > 0.5 * hist_mixed[hist_mixed.size() - 11];
+        if (run.mixed && (max_res <= std::max(o.mixed_switch, o.tol) || stalled)) {
+            // FP64 refinement: re-orthonormalise the Ritz vectors in FP64, apply H to them in
+            // FP64, and continue the iterations in FP64 from this basis
+            run.mixed = false;
+            it_mixed = it;
+            if ((st = run.cholqr(w.X, nb, w.V, &kept))) return st;
+            if (kept < nb) return fail(QM_ERR_NUMERIC, "qm_davidson: Ritz vectors lost rank at the FP64 switch");
+            if ((st = run.hpsi(w.V, w.HV, nb))) return st;
+            m0 = 0;
+            m = nb;
+            continue;
+        }
+        if (all_conv) {
             converged = true;
             break;
         }
@@ -398,13 +444,16 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
             }
             m = nb;
         }
-        // two classical Gram-Schmidt passes against the basis
+        // two classical Gram-Schmidt passes against the basis; the second pass's coefficients
+        // (tiny, but they decide the basis' orthogonality) are always formed in FP64
         for (int pass = 0; pass < 2; ++pass) {
-            if ((st = zgemm_cn(m, nu, npw, w.V, ld, w.Dl, ld, w.Cs, nu, w.Part, zgemm_cn_splits(m, nu, npw), s)) ||
-                (st = zgemm_tn(nu, npw, m, w.Cs, nu, nullptr, w.V, ld, w.Dl, ld, true, s, -1.0)))
-                return st;
+            if (pass == 1 && run.mixed)
+                st = zgemm_cn(m, nu, npw, w.V, ld, w.Dl, ld, w.Cs, nu, w.Part, zgemm_cn_splits(m, nu, npw), s);
+            else
+                st = run.gemm_cn(m, nu, npw, w.V, ld, w.Dl, ld, w.Cs, nu);
+            if (st || (st = run.gemm_tn(nu, npw, m, w.Cs, nu, w.V, ld, w.Dl, ld, true, -1.0))) return st;
         }
-        if ((st = run.lowdin(w.Dl, nu, w.V + (size_t)m * ld, &kept))) return st;
+        if ((st = run.cholqr(w.Dl, nu, w.V + (size_t)m * ld, &kept))) return st;
         if (kept == 0) break;  // no new directions: stagnation
         if ((st = run.hpsi(w.V + (size_t)m * ld, w.HV + (size_t)m * ld, kept))) return st;
         m0 = m;
@@ -423,6 +472,8 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
         stats->max_residual = max_res;
         stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         stats->converged = converged ? 1 : 0;
+        stats->iterations_mixed = run.mixed ? stats->iterations : it_mixed;
+        stats->band_applies_mixed = run.applies_mixed;
     }
     if (!converged) return fail(QM_ERR_NOT_CONVERGED, "qm_davidson: max_iter reached before tol");
     return QM_OK;

@@ -202,58 +202,73 @@ __global__ void k_multisect(const double* __restrict__ d, const double* __restri
     if (lane == 0) evals[j] = 0.5 * (lo + hi);
 }
 
-// solve (T - lam) x = b in place (b -> x), T = tridiag(e, d, e); LU with partial pivoting;
-// work: 3 arrays of m doubles
+// solve (T - lam) x = b in place (b -> x), T = tridiag(e, d, e); LU with partial pivoting.
+// The row being eliminated is carried in registers (each finished row is stored once and only
+// read back by the back substitution), so the loop has no read-after-write through memory.
+// work: 3 arrays of m doubles (finished rows: pivot, first and second super-diagonal).
 __device__ void tri_solve(const double* __restrict__ d, const double* __restrict__ e, int m, double lam,
                           double tiny, double* __restrict__ a, double* __restrict__ c, double* __restrict__ c2,
                           double* __restrict__ b) {
-    // a = diagonal, c = first super-diagonal, c2 = second super-diagonal (fill-in), sub = e
-    for (int i = 0; i < m; ++i) {
-        a[i] = d[i] - lam;
-        c[i] = (i < m - 1) ? e[i] : 0.0;
-        c2[i] = 0.0;
-    }
+    // current row i: diag ai, super ci (and super-super c2i = 0 unless a swap put it there), rhs bi
+    double ai = d[0] - lam, ci = (m > 1) ? e[0] : 0.0, bi = b[0];
     for (int i = 0; i < m - 1; ++i) {
         const double sub = e[i];
-        if (fabs(a[i]) >= fabs(sub)) {
-            if (a[i] == 0.0) a[i] = tiny;
-            const double f = sub / a[i];
-            a[i + 1] -= f * c[i];
-            b[i + 1] -= f * b[i];
+        // next original row i+1: sub, diag, sup, rhs
+        double an = d[i + 1] - lam, cn = (i + 1 < m - 1) ? e[i + 1] : 0.0, bn = b[i + 1];
+        double c2i = 0.0;
+        if (fabs(ai) >= fabs(sub)) {
+            if (ai == 0.0) ai = tiny;
+            const double f = sub / ai;
+            an -= f * ci;
+            bn -= f * bi;
         } else {  // swap rows i and i+1
-            const double f = a[i] / sub;
-            a[i] = sub;
-            const double ci = c[i];
-            c[i] = a[i + 1];
-            a[i + 1] = ci - f * a[i + 1];
-            if (i + 1 < m - 1) {
-                c2[i] = c[i + 1];
-                c[i + 1] = -f * c[i + 1];
-            }
-            const double bi = b[i];
-            b[i] = b[i + 1];
-            b[i + 1] = bi - f * b[i + 1];
+            const double f = ai / sub;
+            const double ai0 = ai, ci0 = ci, bi0 = bi;
+            ai = sub;
+            ci = an;
+            c2i = cn;
+            bi = bn;
+            an = ci0 - f * an;
+            cn = -f * cn;
+            bn = bi0 - f * bn;
+            (void)ai0;
         }
+        a[i] = ai;
+        c[i] = ci;
+        c2[i] = c2i;
+        b[i] = bi;
+        ai = an;
+        ci = cn;
+        bi = bn;
     }
-    if (a[m - 1] == 0.0) a[m - 1] = tiny;
-    b[m - 1] /= a[m - 1];
-    if (m > 1) b[m - 2] = (b[m - 2] - c[m - 2] * b[m - 1]) / a[m - 2];
-    for (int i = m - 3; i >= 0; --i) b[i] = (b[i] - c[i] * b[i + 1] - c2[i] * b[i + 2]) / a[i];
+    if (ai == 0.0) ai = tiny;
+    a[m - 1] = ai;
+    double x1 = bi / ai, x2 = 0.0;  // x[i+1], x[i+2]
+    b[m - 1] = x1;
+    for (int i = m - 2; i >= 0; --i) {
+        const double xi = (b[i] - c[i] * x1 - c2[i] * x2) / a[i];
+        b[i] = xi;
+        x2 = x1;
+        x1 = xi;
+    }
 }
 
-// one CTA (lane 0 working) per cluster leader; eigenvector j of T -> Y[i*ldy + j] (complex, imag 0)
-__global__ void k_inviter(const double* __restrict__ d, const double* __restrict__ e, int m, int nev,
-                          const double* __restrict__ evals, double* __restrict__ work,
-                          double2* __restrict__ Y, int ldy) {
-    const int j0 = blockIdx.x;
-    if (threadIdx.x != 0 || j0 >= nev) return;
-    double tnorm = 0.0;  // infinity norm of T
-    for (int i = 0; i < m; ++i)
-        tnorm = fmax(tnorm, fabs(d[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < m - 1 ? fabs(e[i]) : 0.0));
+// one warp per cluster leader: lane 0 runs the (sequential) tridiagonal solves, the warp
+// shares the O(m) vector work (start vector, Gram-Schmidt within the cluster, scaling).
+// Eigenvector j of T -> Y[i*ldy + j] (complex, imag 0).
+__global__ void __launch_bounds__(32)
+k_inviter(const double* __restrict__ d, const double* __restrict__ e, int m, int nev,
+          const double* __restrict__ evals, double* __restrict__ work, double2* __restrict__ Y, int ldy) {
+    const int j0 = blockIdx.x, lane = threadIdx.x;
+    if (j0 >= nev) return;
+    double tn = 0.0;  // infinity norm of T
+    for (int i = lane; i < m; i += 32)
+        tn = fmax(tn, fabs(d[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < m - 1 ? fabs(e[i]) : 0.0));
+    for (int o = 16; o > 0; o >>= 1) tn = fmax(tn, __shfl_xor_sync(0xffffffffu, tn, o));
     // eigenvalues closer than ctol form a cluster whose vectors are orthogonalised explicitly;
     // outside clusters inverse iteration alone leaves a non-orthogonality of about
     // eps * |T| / gap <= 1e-11
-    const double ctol = 1e-5 * tnorm;
+    const double ctol = 1e-5 * tn;
     if (j0 > 0 && evals[j0] - evals[j0 - 1] <= ctol) return;  // not a cluster leader
     int j1 = j0 + 1;
     while (j1 < nev && evals[j1] - evals[j1 - 1] <= ctol) ++j1;
@@ -261,28 +276,43 @@ __global__ void k_inviter(const double* __restrict__ d, const double* __restrict
     double* c = a + m;
     double* c2 = c + m;
     double* x = c2 + m;
-    const double tiny = 2.2e-16 * fmax(tnorm, 1e-300);
+    const double tiny = 2.2e-16 * fmax(tn, 1e-200);
     for (int j = j0; j < j1; ++j) {
         const double lam = evals[j];
-        // deterministic pseudo-random start
-        unsigned s = 2654435761u * (unsigned)(j + 1);
-        for (int i = 0; i < m; ++i) {
-            s = s * 1664525u + 1013904223u;
-            x[i] = ((double)(s >> 8) / 16777216.0) - 0.5;
+        // deterministic pseudo-random start (a counter hash of (j, i))
+        for (int i = lane; i < m; i += 32) {
+            unsigned h = 2654435761u * (unsigned)(j + 1) ^ (2246822519u * (unsigned)(i + 1));
+            h ^= h >> 15;
+            h *= 2246822519u;
+            h ^= h >> 13;
+            x[i] = ((double)(h >> 8) / 16777216.0) - 0.5;
         }
+        __syncwarp();
         for (int it = 0; it < 3; ++it) {
-            tri_solve(d, e, m, lam, tiny, a, c, c2, x);
+            if (lane == 0) tri_solve(d, e, m, lam, tiny, a, c, c2, x);
+            __syncwarp();
+            double xm = 0.0;  // rescale before any sum of squares can overflow
+            for (int i = lane; i < m; i += 32) xm = fmax(xm, fabs(x[i]));
+            for (int o = 16; o > 0; o >>= 1) xm = fmax(xm, __shfl_xor_sync(0xffffffffu, xm, o));
+            const double r = (xm > 0.0 && xm < 1e300) ? 1.0 / xm : 1.0;
+            for (int i = lane; i < m; i += 32) x[i] *= r;
+            __syncwarp();
             for (int q = j0; q < j; ++q) {  // orthogonalise against the cluster's earlier vectors
                 double dot = 0.0;
-                for (int i = 0; i < m; ++i) dot += Y[(size_t)i * ldy + q].x * x[i];
-                for (int i = 0; i < m; ++i) x[i] -= dot * Y[(size_t)i * ldy + q].x;
+                for (int i = lane; i < m; i += 32) dot += Y[(size_t)i * ldy + q].x * x[i];
+                for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+                for (int i = lane; i < m; i += 32) x[i] -= dot * Y[(size_t)i * ldy + q].x;
+                __syncwarp();
             }
             double nrm = 0.0;
-            for (int i = 0; i < m; ++i) nrm += x[i] * x[i];
+            for (int i = lane; i < m; i += 32) nrm += x[i] * x[i];
+            for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
             nrm = 1.0 / sqrt(nrm);
-            for (int i = 0; i < m; ++i) x[i] *= nrm;
+            for (int i = lane; i < m; i += 32) x[i] *= nrm;
+            __syncwarp();
         }
-        for (int i = 0; i < m; ++i) Y[(size_t)i * ldy + j] = make_double2(x[i], 0.0);
+        for (int i = lane; i < m; i += 32) Y[(size_t)i * ldy + j] = make_double2(x[i], 0.0);
+        __syncwarp();
     }
 }
 
@@ -363,31 +393,32 @@ qm_status heev_lowest(double2* A, int lda, int m, int nev, double* evals, double
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tridiag, 256, smem);
-        int blocks = std::max(1, std::min(std::max(1, occ) * sms, std::max(1, (m + 3) / 4)));
-        blocks = std::min(blocks, sms);
+        // fewer CTAs than SMs: the FP64 work per column is small and grid barriers get cheaper
+        int blocks = std::max(1, std::min(std::max(1, occ) * sms, std::max(1, (m + 7) / 8)));
+        blocks = std::min(blocks, 64);
         void* args[] = {(void*)&A, (void*)&lda, (void*)&m, (void*)&Vh, (void*)&tau, (void*)&d, (void*)&e,
                         (void*)&wbuf};
-        ProfScope pf(PF_JACOBI, s);
+        ProfScope pf(PF_TRIDIAG, s);
         if ((st = cuda_check(cudaLaunchCooperativeKernel((void*)k_tridiag, dim3(blocks), dim3(256), args, smem, s),
                              "k_tridiag cooperative launch")))
             return st;
     }
     {
-        ProfScope pf(PF_JACOBI, s);
+        ProfScope pf(PF_MULTISECT, s);
         k_sq<<<(m + 255) / 256, 256, 0, s>>>(e, e2, m - 1);
     }
     {
-        ProfScope pf(PF_JACOBI, s);
-        k_multisect<<<(nev + 3) / 4, 128, 0, s>>>(d, e, e2, m, nev, evals);
+        ProfScope pf(PF_MULTISECT, s);
+        k_multisect<<<nev, 32, 0, s>>>(d, e, e2, m, nev, evals);
     }
     {
-        ProfScope pf(PF_JACOBI, s);
+        ProfScope pf(PF_INVITER, s);
         k_inviter<<<nev, 32, 0, s>>>(d, e, m, nev, evals, iw, Y, ldy);
     }
     {
         const size_t smem = (size_t)m * sizeof(double2);
         cudaFuncSetAttribute(k_backtransf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        ProfScope pf(PF_JACOBI, s);
+        ProfScope pf(PF_BACKTR, s);
         k_backtransf<<<nev, 256, smem, s>>>(Vh, tau, m, Y, ldy);
     }
     return cuda_check(cudaGetLastError(), "heev launches");

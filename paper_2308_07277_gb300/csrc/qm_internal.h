@@ -89,7 +89,8 @@ qm_status ensure_dav_workspace(qm_gspace g, size_t bytes, cudaStream_t stream);
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // ---- launch counting / per-kernel timing (prof.cpp) ----
-enum ProfFamily { PF_VT = 0, PF_STICK_INV, PF_PLANE, PF_STICK_FWD, PF_GEMM_CN, PF_REDUCE, PF_GEMM_TN, PF_OTHER, PF_JACOBI,
+enum ProfFamily { PF_VT = 0, PF_STICK_INV, PF_PLANE, PF_STICK_FWD, PF_GEMM_CN, PF_REDUCE, PF_GEMM_TN, PF_OTHER, PF_CHOL,
+                  PF_TRIDIAG, PF_MULTISECT, PF_INVITER, PF_BACKTR, PF_CONVERT,
                   kProfFamilies };
 void count_launch(int n);
 // Counts one launch; when timing is enabled records CUDA events on `s` around the scope.
@@ -146,22 +147,28 @@ qm_status zgemm_tn(int M, int N, int K, const double2* A, int lda, const double*
                    const double2* B, int ldb, double2* C, int ldc, bool accumulate,
                    cudaStream_t s, double alpha = 1.0);
 int zgemm_cn_splits(int M, int N, int K);
+// the same products with FP64 storage and FP32 arithmetic
+qm_status zgemm_cn_f32(int M, int N, int K, const double2* A, int lda, const double2* B, int ldb,
+                       double2* C, int ldc, double2* partial, int splits, cudaStream_t s);
+qm_status zgemm_tn_f32(int M, int N, int K, const double2* A, int lda, const double* d,
+                       const double2* B, int ldb, double2* C, int ldc, bool accumulate,
+                       cudaStream_t s, double alpha = 1.0);
 // upper bound of the split-K partial buffer any gemm_cn call needs
 size_t gemm_cn_partial_bytes(bool fp32);
 
-// ---- dense FP64 subspace kernels (dense.cu) ----
-constexpr int kJacobiMaxBlocks = 1024;
-// eigenpairs of the Hermitian m x m matrix H: evals_dev[m] unsorted, eigenvectors = columns
-// of Z (n x n, n = m + (m odd)); A, Z n x n scratch; rot jacobi_rot_bytes(m); red
-// 2*kJacobiMaxBlocks doubles; info 1 int (sweeps used)
-qm_status jacobi_eigh(const double2* H, int ldh, int m, double2* A, double2* Z, void* rot, double* red, int* info,
-                      double* evals_dev, cudaStream_t s);
-size_t jacobi_rot_bytes(int m);
+// ---- dense FP64 subspace kernels (heev.cu, dense.cu) ----
 // lowest nev eigenpairs of the Hermitian m x m matrix A (lda, destroyed): evals[nev] device,
 // increasing; Y (m x nev, ld ldy) eigenvectors as columns; work heev_work_bytes(m, nev)
 qm_status heev_lowest(double2* A, int lda, int m, int nev, double* evals, double2* Y, int ldy, void* work,
                       cudaStream_t s);
 size_t heev_work_bytes(int m, int nev);
+// Cholesky-with-dropping orthonormalisation: chol_transform factors S (nd x nd Gram matrix,
+// destroyed) and counts the kept vectors into kept_dev; chol_transform_rows then writes the
+// nd x kept transform W for gemm_tn.  keep, rank: nd ints; X: nd x nd scratch.
+qm_status chol_transform(double2* S, int lds, int nd, double drop_rel, int* keep, int* rank, int* kept_dev,
+                         double2* X, double2* W, int ldw_max, cudaStream_t s);
+qm_status chol_transform_rows(const double2* L, int lds, int nd, const int* keep, const int* rank, int kept,
+                              double2* X, double2* W, cudaStream_t s);
 
 qm_status cgemm_cn(int M, int N, int K, const float2* A, int lda, const float2* B, int ldb,
                    float2* C, int ldc, float2* partial, int splits, cudaStream_t s);

@@ -33,14 +33,23 @@ __device__ __forceinline__ C czero() {
     return z;
 }
 
-template <class C, int TM, int TN>
+template <class D, class S>
+__device__ __forceinline__ D cvt(S a) {
+    D r;
+    r.x = (decltype(r.x))a.x;
+    r.y = (decltype(r.y))a.y;
+    return r;
+}
+
+// C: storage type of A, B and the output; W: arithmetic type (FP64 or FP32 complex)
+template <class C, class W, int TM, int TN>
 __global__ void __launch_bounds__(NTH)
 k_gemm_cn(int M, int N, int K, const C* __restrict__ A, int lda, const C* __restrict__ B, int ldb,
           C* __restrict__ out, int ldo, int kchunk) {
-    using R = typename Real<C>::T;
+    using R = typename Real<W>::T;
     constexpr int BM = 16 * TM, BN = 16 * TN;
-    __shared__ C As[BK][BM + 1];
-    __shared__ C Bs[BK][BN + 1];
+    __shared__ W As[BK][BM + 1];
+    __shared__ W Bs[BK][BN + 1];
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
@@ -55,17 +64,17 @@ k_gemm_cn(int M, int N, int K, const C* __restrict__ A, int lda, const C* __rest
         for (int e = tid; e < BM * BK; e += NTH) {
             int row = e / BK, kk = e % BK;
             int gm = m0 + row, gk = k0 + kk;
-            As[kk][row] = (gm < M && gk < ke) ? A[(size_t)gm * lda + gk] : czero<C>();
+            As[kk][row] = (gm < M && gk < ke) ? cvt<W>(A[(size_t)gm * lda + gk]) : czero<W>();
         }
         for (int e = tid; e < BN * BK; e += NTH) {
             int row = e / BK, kk = e % BK;
             int gn = n0 + row, gk = k0 + kk;
-            Bs[kk][row] = (gn < N && gk < ke) ? B[(size_t)gn * ldb + gk] : czero<C>();
+            Bs[kk][row] = (gn < N && gk < ke) ? cvt<W>(B[(size_t)gn * ldb + gk]) : czero<W>();
         }
         __syncthreads();
 #pragma unroll 4
         for (int kk = 0; kk < BK; ++kk) {
-            C a[TM], b[TN];
+            W a[TM], b[TN];
 #pragma unroll
             for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
@@ -91,8 +100,8 @@ k_gemm_cn(int M, int N, int K, const C* __restrict__ A, int lda, const C* __rest
             int gn = n0 + tx + 16 * j;
             if (gn < N) {
                 C v;
-                v.x = acc[i][j][0];
-                v.y = acc[i][j][1];
+                v.x = (decltype(v.x))acc[i][j][0];
+                v.y = (decltype(v.y))acc[i][j][1];
                 o[(size_t)gm * ldo + gn] = v;
             }
         }
@@ -114,14 +123,14 @@ __global__ void k_reduce_splits(int M, int N, const C* __restrict__ part, int sp
     }
 }
 
-template <class C, int TM, int TN>
+template <class C, class W, int TM, int TN>
 __global__ void __launch_bounds__(NTH)
 k_gemm_tn(int M, int N, int K, const C* __restrict__ A, int lda, const double* __restrict__ d, double alpha,
           const C* __restrict__ B, int ldb, C* __restrict__ Cm, int ldc, int accumulate) {
-    using R = typename Real<C>::T;
+    using R = typename Real<W>::T;
     constexpr int BM = 16 * TM, BN = 16 * TN;
-    __shared__ C As[BK][BM + 1];
-    __shared__ C Bs[BK][BN + 1];
+    __shared__ W As[BK][BM + 1];
+    __shared__ W Bs[BK][BN + 1];
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
@@ -134,9 +143,9 @@ k_gemm_tn(int M, int N, int K, const C* __restrict__ A, int lda, const double* _
         for (int e = tid; e < BM * BK; e += NTH) {
             int kk = e / BM, col = e % BM;
             int gk = k0 + kk, gm = m0 + col;
-            C av = czero<C>();
+            W av = czero<W>();
             if (gk < K && gm < M) {
-                av = A[(size_t)gk * lda + gm];
+                av = cvt<W>(A[(size_t)gk * lda + gm]);
                 R s = (R)(d ? alpha * d[gk] : alpha);
                 av.x *= s;
                 av.y *= s;
@@ -146,12 +155,12 @@ k_gemm_tn(int M, int N, int K, const C* __restrict__ A, int lda, const double* _
         for (int e = tid; e < BN * BK; e += NTH) {
             int kk = e / BN, col = e % BN;
             int gk = k0 + kk, gn = n0 + col;
-            Bs[kk][col] = (gk < K && gn < N) ? B[(size_t)gk * ldb + gn] : czero<C>();
+            Bs[kk][col] = (gk < K && gn < N) ? cvt<W>(B[(size_t)gk * ldb + gn]) : czero<W>();
         }
         __syncthreads();
 #pragma unroll 4
         for (int kk = 0; kk < BK; ++kk) {
-            C a[TM], b[TN];
+            W a[TM], b[TN];
 #pragma unroll
             for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
@@ -176,8 +185,8 @@ k_gemm_tn(int M, int N, int K, const C* __restrict__ A, int lda, const double* _
             if (gn < N) {
                 C* p = Cm + (size_t)gm * ldc + gn;
                 C v;
-                v.x = acc[i][j][0];
-                v.y = acc[i][j][1];
+                v.x = (decltype(v.x))acc[i][j][0];
+                v.y = (decltype(v.y))acc[i][j][1];
                 if (accumulate) {
                     C o = *p;
                     v.x += o.x;
@@ -219,12 +228,12 @@ int resident_slots(F* kernel) {
     return cached;
 }
 
-template <class C, int TM, int TN>
+template <class C, class W, int TM, int TN>
 qm_status cn_launch(int M, int N, int K, const C* A, int lda, const C* B, int ldb, C* Cm, int ldc, C* partial,
                     int max_splits, cudaStream_t s) {
     constexpr int BM = 16 * TM, BN = 16 * TN;
     const int tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
-    const int kSlots = resident_slots(k_gemm_cn<C, TM, TN>);
+    const int kSlots = resident_slots(k_gemm_cn<C, W, TM, TN>);
     // splits: fill the resident slots in whole waves, each split at least 128 deep
     int splits = std::max(1, std::min({kSlots / std::max(1, tiles), std::max(1, K / 128), max_splits}));
     if (!partial) splits = 1;
@@ -234,11 +243,11 @@ qm_status cn_launch(int M, int N, int K, const C* A, int lda, const C* B, int ld
     dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, splits);
     if (splits == 1) {
         ProfScope pf(PF_GEMM_CN, s);
-        k_gemm_cn<C, TM, TN><<<grid, NTH, 0, s>>>(M, N, K, A, lda, B, ldb, Cm, ldc, kchunk);
+        k_gemm_cn<C, W, TM, TN><<<grid, NTH, 0, s>>>(M, N, K, A, lda, B, ldb, Cm, ldc, kchunk);
     } else {
         {
             ProfScope pf(PF_GEMM_CN, s);
-            k_gemm_cn<C, TM, TN><<<grid, NTH, 0, s>>>(M, N, K, A, lda, B, ldb, partial, N, kchunk);
+            k_gemm_cn<C, W, TM, TN><<<grid, NTH, 0, s>>>(M, N, K, A, lda, B, ldb, partial, N, kchunk);
         }
         size_t total = (size_t)M * N;
         int blocks = (int)std::min<size_t>((total + 255) / 256, 152 * 8);
@@ -248,36 +257,36 @@ qm_status cn_launch(int M, int N, int K, const C* A, int lda, const C* B, int ld
     return cuda_check(cudaGetLastError(), "gemm_cn launch");
 }
 
-template <class C>
+template <class C, class W>
 qm_status gemm_cn_impl(int M, int N, int K, const C* A, int lda, const C* B, int ldb, C* Cm, int ldc,
                        C* partial, int max_splits, cudaStream_t s) {
     if (M <= 0 || N <= 0) return QM_OK;
     const int tm = pick_t(M), tn = pick_t(N);
 #define QM_CN(a, b) \
-    if (tm == a && tn == b) return cn_launch<C, a, b>(M, N, K, A, lda, B, ldb, Cm, ldc, partial, max_splits, s);
+    if (tm == a && tn == b) return cn_launch<C, W, a, b>(M, N, K, A, lda, B, ldb, Cm, ldc, partial, max_splits, s);
     QM_CN(5, 5) QM_CN(5, 4) QM_CN(4, 5) QM_CN(4, 4) QM_CN(2, 4) QM_CN(4, 2) QM_CN(2, 5) QM_CN(5, 2) QM_CN(2, 2)
 #undef QM_CN
     return fail(QM_ERR_UNSUPPORTED, "gemm_cn: no tile");
 }
 
-template <class C, int TM, int TN>
+template <class C, class W, int TM, int TN>
 qm_status tn_launch(int M, int N, int K, const C* A, int lda, const double* d, double alpha, const C* B, int ldb,
                     C* Cm, int ldc, bool accumulate, cudaStream_t s) {
     constexpr int BM = 16 * TM, BN = 16 * TN;
     dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, 1);
     ProfScope pf(PF_GEMM_TN, s);
-    k_gemm_tn<C, TM, TN><<<grid, NTH, 0, s>>>(M, N, K, A, lda, d, alpha, B, ldb, Cm, ldc, accumulate ? 1 : 0);
+    k_gemm_tn<C, W, TM, TN><<<grid, NTH, 0, s>>>(M, N, K, A, lda, d, alpha, B, ldb, Cm, ldc, accumulate ? 1 : 0);
     return cuda_check(cudaGetLastError(), "gemm_tn launch");
 }
 
-template <class C>
+template <class C, class W>
 qm_status gemm_tn_impl(int M, int N, int K, const C* A, int lda, const double* d, double alpha, const C* B,
                        int ldb, C* Cm, int ldc, bool accumulate, cudaStream_t s) {
     if (M <= 0 || N <= 0) return QM_OK;
     const int tm = pick_t(M);
     // the N dimension (plane waves) is long: TN = 4 keeps 256-wide rows of whole tiles
 #define QM_TN(a) \
-    if (tm == a) return tn_launch<C, a, 4>(M, N, K, A, lda, d, alpha, B, ldb, Cm, ldc, accumulate, s);
+    if (tm == a) return tn_launch<C, W, a, 4>(M, N, K, A, lda, d, alpha, B, ldb, Cm, ldc, accumulate, s);
     QM_TN(5) QM_TN(4) QM_TN(2)
 #undef QM_TN
     return fail(QM_ERR_UNSUPPORTED, "gemm_tn: no tile");
@@ -298,19 +307,29 @@ int zgemm_cn_splits(int M, int N, int K) {
 
 qm_status zgemm_cn(int M, int N, int K, const double2* A, int lda, const double2* B, int ldb, double2* C,
                    int ldc, double2* partial, int splits, cudaStream_t s) {
-    return gemm_cn_impl<double2>(M, N, K, A, lda, B, ldb, C, ldc, partial, splits, s);
+    return gemm_cn_impl<double2, double2>(M, N, K, A, lda, B, ldb, C, ldc, partial, splits, s);
 }
 qm_status cgemm_cn(int M, int N, int K, const float2* A, int lda, const float2* B, int ldb, float2* C, int ldc,
                    float2* partial, int splits, cudaStream_t s) {
-    return gemm_cn_impl<float2>(M, N, K, A, lda, B, ldb, C, ldc, partial, splits, s);
+    return gemm_cn_impl<float2, float2>(M, N, K, A, lda, B, ldb, C, ldc, partial, splits, s);
 }
 qm_status zgemm_tn(int M, int N, int K, const double2* A, int lda, const double* d, const double2* B, int ldb,
                    double2* C, int ldc, bool accumulate, cudaStream_t s, double alpha) {
-    return gemm_tn_impl<double2>(M, N, K, A, lda, d, alpha, B, ldb, C, ldc, accumulate, s);
+    return gemm_tn_impl<double2, double2>(M, N, K, A, lda, d, alpha, B, ldb, C, ldc, accumulate, s);
 }
 qm_status cgemm_tn(int M, int N, int K, const float2* A, int lda, const double* d, const float2* B, int ldb,
                    float2* C, int ldc, bool accumulate, cudaStream_t s, double alpha) {
-    return gemm_tn_impl<float2>(M, N, K, A, lda, d, alpha, B, ldb, C, ldc, accumulate, s);
+    return gemm_tn_impl<float2, float2>(M, N, K, A, lda, d, alpha, B, ldb, C, ldc, accumulate, s);
+}
+
+// FP64 storage, FP32 arithmetic (the subspace products of the mixed Davidson phase)
+qm_status zgemm_cn_f32(int M, int N, int K, const double2* A, int lda, const double2* B, int ldb, double2* C,
+                       int ldc, double2* partial, int splits, cudaStream_t s) {
+    return gemm_cn_impl<double2, float2>(M, N, K, A, lda, B, ldb, C, ldc, partial, splits, s);
+}
+qm_status zgemm_tn_f32(int M, int N, int K, const double2* A, int lda, const double* d, const double2* B, int ldb,
+                       double2* C, int ldc, bool accumulate, cudaStream_t s, double alpha) {
+    return gemm_tn_impl<double2, float2>(M, N, K, A, lda, d, alpha, B, ldb, C, ldc, accumulate, s);
 }
 
 }  // namespace qm

@@ -119,3 +119,29 @@ def test_davidson_not_converged_and_errors(Q):
         assert e.value.status == 5
     finally:
         Q.qm_gspace_destroy(g)
+
+
+@pytest.mark.parametrize("cell", [S.config1(), S.cubic_si8(12.0, nbnd=12, reps=(2, 1, 1))],
+                         ids=lambda c: f"{c.name}_{c.ecutwfc_ry:g}Ry_nb{c.nbnd}")
+def test_davidson_mixed_precision_matches_dense(Q, cell):
+    """Precision form: FP32 H psi and FP32-arithmetic subspace products until the residual
+    reaches 1e-4, then FP64; eigenvalues still within 1e-9 Ha of brute force."""
+    c = make_case(cell, 0)
+    ev = np.linalg.eigvalsh(OH.dense_h(c["gs"], c["v"], c["beta"], c["D"]))[: cell.nbnd]
+    eig, X, info = run_gpu(Q, cell, 0, c, tol=1e-9, max_iter=300, prec="mixed")
+    assert info["converged"] and info["iterations_mixed"] > 0 and info["band_applies_mixed"] > 0, info
+    np.testing.assert_allclose(eig, ev, atol=TOL_EIG)
+    check_pairs(c, eig, X, 1e-9)
+
+
+@pytest.mark.parametrize("ik", [1])
+def test_davidson_mixed_config2_full_size(Q, ik):
+    gold = os.path.join(ROOT, "tests", "golden", "config2_eigs.txt")
+    if not os.path.exists(gold):
+        pytest.skip("tests/golden/config2_eigs.txt not generated")
+    want = [np.array([float(x) for x in line.split()[1:]]) for line in open(gold) if line.startswith(f"k{ik} ")][0]
+    cell = S.config2()
+    c = make_case(cell, ik)
+    eig, X, info = run_gpu(Q, cell, ik, c, tol=1e-8, max_iter=300, prec="mixed")
+    assert info["converged"], info
+    np.testing.assert_allclose(eig, want, atol=1e-8)
