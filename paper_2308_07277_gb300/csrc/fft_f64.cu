@@ -1,0 +1,10 @@
+// FFT-path kernels instantiated for double (one translation unit per precision so the two
+// compile in parallel).
+#include "fft_kernels.cuh"
+
+namespace qm {
+template qm_status local_kinetic_impl<double>(qm_gspace, int, int, const void*, int, const void*, void*, int, void*,
+                                         size_t, cudaStream_t);
+template qm_status local_kinetic_tab_impl<double>(const DevTables&, int, const void*, int, const void*, void*, int,
+                                             void*, size_t, cudaStream_t);
+}  // namespace qm

@@ -1,304 +1,17 @@
-// Local-potential + kinetic part of H psi by stick-pruned 3D FFTs staged in shared memory.
-//
-// The operator is the recipe of Sec. 4.3 (IFFT of psi(G), multiply by V(r), FFT, keep the
-// sphere) with the kinetic term 1/2|k+G|^2 applied in G-space (Sec. 4.3), and the stick
-// pruning of Sec. 4.3.3: 1D transforms run only on lines that can hold non-zero data.
-//
-// Data flow for one band (x fastest on the grid, sticks along x as in the paper's Fig. 1):
-//   K1 k_stick_inverse : scatter the sphere into the x-sticks that hold plane waves
-//                        (zero fill), inverse FFT along x  -> stick buffer T[b][p1][s]
-//   K2 k_plane         : one yz plane per (band, p1): expand sticks into the plane,
-//                        inverse FFT along y (active rows only) and z, multiply by V(r)/N_r,
-//                        forward FFT along z and y (active rows), compact back into T
-//   K3 k_stick_forward : forward FFT along x, gather the sphere, add 1/2|k+G|^2 psi(G)
-//
-// Every 1D transform is an in-place mixed-radix (2/3/4/5) FFT in shared memory.  The
-// inverse passes are decimation-in-frequency (natural order in, digit-reversed out) and the
-// forward passes decimation-in-time (digit-reversed in, natural out), so the digit
-// reversal never has to be undone: the only quantity that lives in the permuted order is
-// V(r), which is laid out once per call in that order (k_vt).
-#include <algorithm>
-
-#include "qm_internal.h"
+// Host launchers of the FFT path; the kernels live in fft_kernels.cuh and are compiled once
+// per precision (fft_f64.cu, fft_f32.cu).
+#include "fft_kernels.cuh"
 
 namespace qm {
 
-template <class R> struct Cx;
-template <> struct Cx<double> { using T = double2; };
-template <> struct Cx<float> { using T = float2; };
-
-template <class C> __device__ __forceinline__ C mk(decltype(C::x) a, decltype(C::x) b) {
-    C r;
-    r.x = a;
-    r.y = b;
-    return r;
-}
-template <class C> __device__ __forceinline__ C add(C a, C b) { return mk<C>(a.x + b.x, a.y + b.y); }
-template <class C> __device__ __forceinline__ C sub(C a, C b) { return mk<C>(a.x - b.x, a.y - b.y); }
-template <class C> __device__ __forceinline__ C cmul(C a, C w) {
-    return mk<C>(a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x);
-}
-// multiply by SG * i
-template <class C, int SG> __device__ __forceinline__ C mul_si(C a) {
-    return SG > 0 ? mk<C>(-a.y, a.x) : mk<C>(a.y, -a.x);
-}
-template <class C, int SG> __device__ __forceinline__ C twid(const C* tw, int t) {
-    C w = tw[t];
-    if (SG < 0) w.y = -w.y;
-    return w;
-}
-
-// In-register DFT of length R with kernel exp(SG * 2 pi i n k / R).
-template <class C, int SG, int R> struct Dft;
-
-template <class C, int SG> struct Dft<C, SG, 2> {
-    static __device__ __forceinline__ void run(C* u) {
-        C a = u[0], b = u[1];
-        u[0] = add(a, b);
-        u[1] = sub(a, b);
-    }
-};
-template <class C, int SG> struct Dft<C, SG, 4> {
-    static __device__ __forceinline__ void run(C* u) {
-        C a = add(u[0], u[2]), b = sub(u[0], u[2]);
-        C c = add(u[1], u[3]), d = mul_si<C, SG>(sub(u[1], u[3]));
-        u[0] = add(a, c);
-        u[2] = sub(a, c);
-        u[1] = add(b, d);
-        u[3] = sub(b, d);
-    }
-};
-template <class C, int SG> struct Dft<C, SG, 3> {
-    static __device__ __forceinline__ void run(C* u) {
-        using R = decltype(C::x);
-        const R h = (R)0.86602540378443864676;  // sin(2 pi / 3)
-        C t = add(u[1], u[2]);
-        C d = mul_si<C, SG>(sub(u[1], u[2]));
-        C m = mk<C>(u[0].x - (R)0.5 * t.x, u[0].y - (R)0.5 * t.y);
-        u[0] = add(u[0], t);
-        u[1] = mk<C>(m.x + h * d.x, m.y + h * d.y);
-        u[2] = mk<C>(m.x - h * d.x, m.y - h * d.y);
-    }
-};
-template <class C, int SG> struct Dft<C, SG, 5> {
-    static __device__ __forceinline__ void run(C* u) {
-        using R = decltype(C::x);
-        const R c1 = (R)0.30901699437494742410;   // cos(2 pi / 5)
-        const R c2 = (R)-0.80901699437494742410;  // cos(4 pi / 5)
-        const R s1 = (R)0.95105651629515357212;   // sin(2 pi / 5)
-        const R s2 = (R)0.58778525229247312917;   // sin(4 pi / 5)
-        C t1 = add(u[1], u[4]), t2 = add(u[2], u[3]);
-        C d1 = mul_si<C, SG>(sub(u[1], u[4])), d2 = mul_si<C, SG>(sub(u[2], u[3]));
-        C a1 = mk<C>(u[0].x + c1 * t1.x + c2 * t2.x, u[0].y + c1 * t1.y + c2 * t2.y);
-        C a2 = mk<C>(u[0].x + c2 * t1.x + c1 * t2.x, u[0].y + c2 * t1.y + c1 * t2.y);
-        C b1 = mk<C>(s1 * d1.x + s2 * d2.x, s1 * d1.y + s2 * d2.y);
-        C b2 = mk<C>(s2 * d1.x - s1 * d2.x, s2 * d1.y - s1 * d2.y);
-        u[0] = add(u[0], add(t1, t2));
-        u[1] = add(a1, b1);
-        u[4] = sub(a1, b1);
-        u[2] = add(a2, b2);
-        u[3] = sub(a2, b2);
-    }
-};
-
-// One in-place stage over `nlines` lines of length N.  Element j of line l is
-// buf[lmap(l) * ls + j * es].  DIF: butterfly then twiddle; DIT: twiddle then butterfly.
-// LINE_FAST maps consecutive threads to consecutive lines (column passes), otherwise to
-// consecutive butterflies of one line (row passes).
-template <class C, int SG, int R, bool DIF, bool LINE_FAST>
-__device__ __forceinline__ void fft_stage(C* buf, int es, int ls, int nlines, const int* lmap,
-                                          int L, int N, const C* tw, int tid, int nt) {
-    const int M = L / R;
-    const int nbf = N / R;
-    const int step = N / L;
-    const int total = nlines * nbf;
-    for (int t = tid; t < total; t += nt) {
-        int line, bf;
-        if (LINE_FAST) {
-            line = t % nlines;
-            bf = t / nlines;
-        } else {
-            line = t / nbf;
-            bf = t - line * nbf;
-        }
-        const int blk = bf / M;
-        const int n1 = bf - blk * M;
-        const int lrow = lmap ? __ldg(lmap + line) : line;
-        C* p = buf + lrow * ls + (blk * L + n1) * es;
-        const int me = M * es;
-        C u[R];
-#pragma unroll
-        for (int j = 0; j < R; ++j) u[j] = p[j * me];
-        if (DIF) {
-            Dft<C, SG, R>::run(u);
-#pragma unroll
-            for (int k2 = 1; k2 < R; ++k2) u[k2] = cmul(u[k2], twid<C, SG>(tw, n1 * k2 * step));
-        } else {
-#pragma unroll
-            for (int k2 = 1; k2 < R; ++k2) u[k2] = cmul(u[k2], twid<C, SG>(tw, n1 * k2 * step));
-            Dft<C, SG, R>::run(u);
-        }
-#pragma unroll
-        for (int j = 0; j < R; ++j) p[j * me] = u[j];
-    }
-}
-
-template <class C, int SG, bool DIF, bool LINE_FAST>
-__device__ __forceinline__ void fft_stage_any(int r, C* buf, int es, int ls, int nlines, const int* lmap,
-                                              int L, int N, const C* tw, int tid, int nt) {
-    switch (r) {
-        case 2: fft_stage<C, SG, 2, DIF, LINE_FAST>(buf, es, ls, nlines, lmap, L, N, tw, tid, nt); break;
-        case 3: fft_stage<C, SG, 3, DIF, LINE_FAST>(buf, es, ls, nlines, lmap, L, N, tw, tid, nt); break;
-        case 4: fft_stage<C, SG, 4, DIF, LINE_FAST>(buf, es, ls, nlines, lmap, L, N, tw, tid, nt); break;
-        default: fft_stage<C, SG, 5, DIF, LINE_FAST>(buf, es, ls, nlines, lmap, L, N, tw, tid, nt); break;
-    }
-}
-
-// Full 1D transform of `nlines` lines; ends with __syncthreads().
-template <class C, int SG, bool DIF, bool LINE_FAST>
-__device__ void fft_lines(C* buf, int es, int ls, int nlines, const int* lmap, const AxisPlan& pl,
-                          const C* tw, int tid, int nt) {
-    if (DIF) {
-        for (int s = 0; s < pl.nst; ++s) {
-            fft_stage_any<C, SG, DIF, LINE_FAST>(pl.r[s], buf, es, ls, nlines, lmap, pl.L[s], pl.n, tw, tid, nt);
-            __syncthreads();
-        }
-    } else {
-        for (int s = pl.nst - 1; s >= 0; --s) {
-            fft_stage_any<C, SG, DIF, LINE_FAST>(pl.r[s], buf, es, ls, nlines, lmap, pl.L[s], pl.n, tw, tid, nt);
-            __syncthreads();
-        }
-    }
-}
-
-constexpr int kSticksPerCta = 32;
-constexpr int kThreads = 256;
-
-// ---------------------------------------------------------------- K1
-template <class R>
-__global__ void __launch_bounds__(kThreads)
-k_stick_inverse(const typename Cx<R>::T* __restrict__ psi, int ld_psi, const int* __restrict__ stick_g0,
-                const int2* __restrict__ g_code, int nstick, int nstick_pad, AxisPlan px,
-                const typename Cx<R>::T* __restrict__ tw_x, int ldx, typename Cx<R>::T* __restrict__ T) {
-    using C = typename Cx<R>::T;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* lines = reinterpret_cast<C*>(smem_raw);
-    C* tw = lines + kSticksPerCta * ldx;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int b = blockIdx.y;
-    const int s0 = blockIdx.x * kSticksPerCta;
-    const int ns = min(kSticksPerCta, nstick - s0);
-    const int N1 = px.n;
-    for (int i = tid; i < N1; i += nt) tw[i] = tw_x[i];
-    for (int i = tid; i < ns * ldx; i += nt) lines[i] = mk<C>(0, 0);
-    __syncthreads();
-    const int gb = __ldg(stick_g0 + s0), ge = __ldg(stick_g0 + s0 + ns);
-    const C* src = psi + (size_t)b * ld_psi;
-    for (int g = gb + tid; g < ge; g += nt) {
-        int2 c = __ldg(g_code + g);
-        lines[(c.x - s0) * ldx + c.y] = src[g];
-    }
-    __syncthreads();
-    fft_lines<C, +1, true, false>(lines, 1, ldx, ns, nullptr, px, tw, tid, nt);
-    C* dst = T + (size_t)b * N1 * nstick_pad + s0;
-    for (int i = tid; i < N1 * ns; i += nt) {
-        int p = i / ns, l = i - p * ns;
-        dst[(size_t)p * nstick_pad + l] = lines[l * ldx + p];
-    }
-}
-
-// ---------------------------------------------------------------- K2
-template <class R>
-__global__ void __launch_bounds__(kThreads)
-k_plane(typename Cx<R>::T* __restrict__ T, int nstick, int nstick_pad, const int* __restrict__ stick_plane,
-        const int* __restrict__ rows, int nrow, AxisPlan py, AxisPlan pz,
-        const typename Cx<R>::T* __restrict__ tw_y, const typename Cx<R>::T* __restrict__ tw_z, int ldy,
-        const R* __restrict__ Vt, int N1) {
-    using C = typename Cx<R>::T;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int N2 = py.n, N3 = pz.n;
-    C* plane = reinterpret_cast<C*>(smem_raw);
-    C* twy = plane + N3 * ldy;
-    C* twz = twy + N2;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int p1 = blockIdx.x, b = blockIdx.y;
-    for (int i = tid; i < N2; i += nt) twy[i] = tw_y[i];
-    for (int i = tid; i < N3; i += nt) twz[i] = tw_z[i];
-    for (int i = tid; i < N3 * ldy; i += nt) plane[i] = mk<C>(0, 0);
-    __syncthreads();
-    C* Tp = T + ((size_t)b * N1 + p1) * nstick_pad;
-    for (int s = tid; s < nstick; s += nt) plane[__ldg(stick_plane + s)] = Tp[s];
-    __syncthreads();
-    // inverse: y on the active rows, then z on every column
-    fft_lines<C, +1, true, false>(plane, 1, ldy, nrow, rows, py, twy, tid, nt);
-    fft_lines<C, +1, true, true>(plane, ldy, 1, N2, nullptr, pz, twz, tid, nt);
-    // V(r)/N_r in the permuted (digit-reversed) order of all three axes
-    const R* v = Vt + (size_t)p1 * N3 * N2;
-    for (int i = tid; i < N3 * N2; i += nt) {
-        int r = i / N2, c = i - r * N2;
-        R s = __ldg(v + i);
-        C x = plane[r * ldy + c];
-        plane[r * ldy + c] = mk<C>(x.x * s, x.y * s);
-    }
-    __syncthreads();
-    // forward: z on every column, then y on the active rows
-    fft_lines<C, -1, false, true>(plane, ldy, 1, N2, nullptr, pz, twz, tid, nt);
-    fft_lines<C, -1, false, false>(plane, 1, ldy, nrow, rows, py, twy, tid, nt);
-    for (int s = tid; s < nstick; s += nt) Tp[s] = plane[__ldg(stick_plane + s)];
-}
-
-// ---------------------------------------------------------------- K3
-template <class R>
-__global__ void __launch_bounds__(kThreads)
-k_stick_forward(const typename Cx<R>::T* __restrict__ T, int nstick, int nstick_pad,
-                const int* __restrict__ stick_g0, const int2* __restrict__ g_code, const R* __restrict__ kin,
-                AxisPlan px, const typename Cx<R>::T* __restrict__ tw_x, int ldx,
-                const typename Cx<R>::T* __restrict__ psi, int ld_psi, typename Cx<R>::T* __restrict__ out,
-                int ld_out) {
-    using C = typename Cx<R>::T;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* lines = reinterpret_cast<C*>(smem_raw);
-    C* tw = lines + kSticksPerCta * ldx;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int b = blockIdx.y;
-    const int s0 = blockIdx.x * kSticksPerCta;
-    const int ns = min(kSticksPerCta, nstick - s0);
-    const int N1 = px.n;
-    for (int i = tid; i < N1; i += nt) tw[i] = tw_x[i];
-    const C* srcT = T + (size_t)b * N1 * nstick_pad + s0;
-    for (int i = tid; i < N1 * ns; i += nt) {
-        int p = i / ns, l = i - p * ns;
-        lines[l * ldx + p] = srcT[(size_t)p * nstick_pad + l];
-    }
-    __syncthreads();
-    fft_lines<C, -1, false, false>(lines, 1, ldx, ns, nullptr, px, tw, tid, nt);
-    const int gb = __ldg(stick_g0 + s0), ge = __ldg(stick_g0 + s0 + ns);
-    const C* ps = psi + (size_t)b * ld_psi;
-    C* po = out + (size_t)b * ld_out;
-    for (int g = gb + tid; g < ge; g += nt) {
-        int2 c = __ldg(g_code + g);
-        C x = lines[(c.x - s0) * ldx + c.y];
-        C y = ps[g];
-        R k = __ldg(kin + g);
-        po[g] = mk<C>(x.x + k * y.x, x.y + k * y.y);
-    }
-}
-
-// ---------------------------------------------------------------- V layout
-template <class R>
-__global__ void k_vt(const double* __restrict__ V, R* __restrict__ Vt, int N1, int N2, int N3,
-                     const int* __restrict__ rev1, const int* __restrict__ rev2, const int* __restrict__ rev3,
-                     double scale) {
-    const size_t nr = (size_t)N1 * N2 * N3;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nr; i += (size_t)gridDim.x * blockDim.x) {
-        int p2 = (int)(i % N2);
-        size_t q = i / N2;
-        int p3 = (int)(q % N3);
-        int p1 = (int)(q / N3);
-        size_t src = (size_t)__ldg(rev1 + p1) + (size_t)N1 * ((size_t)__ldg(rev2 + p2) + (size_t)N2 * __ldg(rev3 + p3));
-        Vt[i] = (R)(__ldg(V + src) * scale);
-    }
-}
+extern template qm_status local_kinetic_impl<double>(qm_gspace, int, int, const void*, int, const void*, void*, int,
+                                                     void*, size_t, cudaStream_t);
+extern template qm_status local_kinetic_impl<float>(qm_gspace, int, int, const void*, int, const void*, void*, int,
+                                                    void*, size_t, cudaStream_t);
+extern template qm_status local_kinetic_tab_impl<double>(const DevTables&, int, const void*, int, const void*, void*,
+                                                         int, void*, size_t, cudaStream_t);
+extern template qm_status local_kinetic_tab_impl<float>(const DevTables&, int, const void*, int, const void*, void*,
+                                                        int, void*, size_t, cudaStream_t);
 
 // ---------------------------------------------------------------- host launchers
 size_t stick_buffer_bytes_per_band(qm_gspace g, int ik, bool fp32) {
@@ -315,53 +28,6 @@ qm_status launch_vt_prepare(qm_gspace g, const double* vloc, void* vt, bool fp32
     else
         k_vt<double><<<blocks, 256, 0, s>>>(vloc, (double*)vt, g->n[0], g->n[1], g->n[2], g->rev[0], g->rev[1], g->rev[2], scale);
     return cuda_check(cudaGetLastError(), "k_vt launch");
-}
-
-template <class R>
-static qm_status local_kinetic_impl(qm_gspace g, int ik, int nb, const void* psi, int ld_psi, const void* vt,
-                                    void* out, int ld_out, void* tbuf, size_t tbuf_bytes, cudaStream_t s) {
-    using C = typename Cx<R>::T;
-    const KTables& kt = g->k[ik];
-    const int N1 = g->n[0], N2 = g->n[1], N3 = g->n[2];
-    const size_t per_band = (size_t)N1 * kt.nstick_pad * sizeof(C);
-    const int nbc = (int)std::max<size_t>(1, std::min<size_t>((size_t)nb, tbuf_bytes / per_band));
-    const size_t sm_stick = (size_t)(kSticksPerCta * g->ldx + N1) * sizeof(C);
-    const size_t sm_plane = (size_t)(N3 * g->ldy + N2 + N3) * sizeof(C);
-    if (sm_plane > 227 * 1024 || sm_stick > 227 * 1024)
-        return fail(QM_ERR_UNSUPPORTED, "qm_hpsi: FFT plane does not fit in shared memory");
-    // opt in to large dynamic shared memory (per function and device; cheap to repeat)
-    cudaFuncSetAttribute(k_plane<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_plane);
-    cudaFuncSetAttribute(k_stick_inverse<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_stick);
-    cudaFuncSetAttribute(k_stick_forward<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_stick);
-    const int ntile = (kt.nstick + kSticksPerCta - 1) / kSticksPerCta;
-    const C* tw_x = (const C*)(sizeof(R) == 8 ? (const void*)g->tw64[0] : (const void*)g->tw32[0]);
-    const C* tw_y = (const C*)(sizeof(R) == 8 ? (const void*)g->tw64[1] : (const void*)g->tw32[1]);
-    const C* tw_z = (const C*)(sizeof(R) == 8 ? (const void*)g->tw64[2] : (const void*)g->tw32[2]);
-    const R* kin = (const R*)(sizeof(R) == 8 ? (const void*)kt.kin : (const void*)kt.kin_f);
-    C* T = (C*)tbuf;
-    for (int b0 = 0; b0 < nb; b0 += nbc) {
-        const int nbx = std::min(nbc, nb - b0);
-        const C* ps = (const C*)psi + (size_t)b0 * ld_psi;
-        C* po = (C*)out + (size_t)b0 * ld_out;
-        {
-            ProfScope pf(PF_STICK_INV, s);
-            k_stick_inverse<R><<<dim3(ntile, nbx), kThreads, sm_stick, s>>>(
-                ps, ld_psi, kt.stick_g0, kt.g_code, kt.nstick, kt.nstick_pad, g->plan[0], tw_x, g->ldx, T);
-        }
-        {
-            ProfScope pf(PF_PLANE, s);
-            k_plane<R><<<dim3(N1, nbx), kThreads, sm_plane, s>>>(
-                T, kt.nstick, kt.nstick_pad, kt.stick_plane, kt.rows, kt.nrow, g->plan[1], g->plan[2], tw_y, tw_z,
-                g->ldy, (const R*)vt, N1);
-        }
-        {
-            ProfScope pf(PF_STICK_FWD, s);
-            k_stick_forward<R><<<dim3(ntile, nbx), kThreads, sm_stick, s>>>(
-                T, kt.nstick, kt.nstick_pad, kt.stick_g0, kt.g_code, kin, g->plan[0], tw_x, g->ldx, ps, ld_psi, po,
-                ld_out);
-        }
-    }
-    return cuda_check(cudaGetLastError(), "FFT path launch");
 }
 
 qm_status launch_local_kinetic(qm_gspace g, int ik, int nb, const void* psi, int ld_psi, const void* vt,
@@ -384,51 +50,6 @@ qm_status launch_vt_prepare_tab(const DevTables& t, const double* vloc, void* vt
     else
         k_vt<double><<<blocks, 256, 0, s>>>(vloc, (double*)vt, t.n[0], t.n[1], t.n[2], t.rev[0], t.rev[1], t.rev[2], scale);
     return cuda_check(cudaGetLastError(), "k_vt launch");
-}
-
-template <class R>
-static qm_status local_kinetic_tab_impl(const DevTables& t, int nb, const void* psi, int ld_psi, const void* vt,
-                                        void* out, int ld_out, void* tbuf, size_t tbuf_bytes, cudaStream_t s) {
-    using C = typename Cx<R>::T;
-    const int N1 = t.n[0], N2 = t.n[1], N3 = t.n[2];
-    const size_t per_band = (size_t)N1 * t.nstick_pad * sizeof(C);
-    if (tbuf_bytes < per_band) return fail(QM_ERR_ARG, "stick buffer smaller than one band");
-    const int nbc = (int)std::max<size_t>(1, std::min<size_t>((size_t)nb, tbuf_bytes / per_band));
-    const size_t sm_stick = (size_t)(kSticksPerCta * t.ldx + N1) * sizeof(C);
-    const size_t sm_plane = (size_t)(N3 * t.ldy + N2 + N3) * sizeof(C);
-    if (sm_plane > 227 * 1024 || sm_stick > 227 * 1024)
-        return fail(QM_ERR_UNSUPPORTED, "FFT plane does not fit in shared memory");
-    cudaFuncSetAttribute(k_plane<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_plane);
-    cudaFuncSetAttribute(k_stick_inverse<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_stick);
-    cudaFuncSetAttribute(k_stick_forward<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_stick);
-    const int ntile = (t.nstick + kSticksPerCta - 1) / kSticksPerCta;
-    const C* tw_x = (const C*)t.tw[0];
-    const C* tw_y = (const C*)t.tw[1];
-    const C* tw_z = (const C*)t.tw[2];
-    const R* kin = (const R*)t.kin;
-    C* T = (C*)tbuf;
-    for (int b0 = 0; b0 < nb; b0 += nbc) {
-        const int nbx = std::min(nbc, nb - b0);
-        const C* ps = (const C*)psi + (size_t)b0 * ld_psi;
-        C* po = (C*)out + (size_t)b0 * ld_out;
-        {
-            ProfScope pf(PF_STICK_INV, s);
-            k_stick_inverse<R><<<dim3(ntile, nbx), kThreads, sm_stick, s>>>(
-                ps, ld_psi, t.stick_g0, t.g_code, t.nstick, t.nstick_pad, t.plan[0], tw_x, t.ldx, T);
-        }
-        {
-            ProfScope pf(PF_PLANE, s);
-            k_plane<R><<<dim3(N1, nbx), kThreads, sm_plane, s>>>(
-                T, t.nstick, t.nstick_pad, t.stick_plane, t.rows, t.nrow, t.plan[1], t.plan[2], tw_y, tw_z, t.ldy,
-                (const R*)vt, N1);
-        }
-        {
-            ProfScope pf(PF_STICK_FWD, s);
-            k_stick_forward<R><<<dim3(ntile, nbx), kThreads, sm_stick, s>>>(
-                T, t.nstick, t.nstick_pad, t.stick_g0, t.g_code, kin, t.plan[0], tw_x, t.ldx, ps, ld_psi, po, ld_out);
-        }
-    }
-    return cuda_check(cudaGetLastError(), "FFT path launch");
 }
 
 qm_status launch_local_kinetic_tab(const DevTables& t, int nb, const void* psi, int ld_psi, const void* vt, void* out,

@@ -79,10 +79,14 @@ static void make_plan(int n, AxisPlan& p, std::vector<int>& rev) {
     p.n = n;
     p.nst = 0;
     int m = n;
+    // radix order: 8s, at most one 4 and one 2, 9s, at most one 3, 5s (must match the
+    // compile-time plans of the FFT kernels)
     std::vector<int> rs;
-    while (m % 4 == 0) { rs.push_back(4); m /= 4; }
-    while (m % 2 == 0) { rs.push_back(2); m /= 2; }
-    while (m % 3 == 0) { rs.push_back(3); m /= 3; }
+    while (m % 8 == 0) { rs.push_back(8); m /= 8; }
+    if (m % 4 == 0) { rs.push_back(4); m /= 4; }
+    if (m % 2 == 0) { rs.push_back(2); m /= 2; }
+    while (m % 9 == 0) { rs.push_back(9); m /= 9; }
+    if (m % 3 == 0) { rs.push_back(3); m /= 3; }
     while (m % 5 == 0) { rs.push_back(5); m /= 5; }
     int L = n;
     for (int r : rs) {
