@@ -33,7 +33,7 @@ if ROOT not in sys.path:
 METRIC = "Hψ band-applies/s & Davidson time-to-1e-8 Ha: mixed/learned vs FP64 plain"
 UNIT = "band-applies/s"
 WORKLOAD = "si64_cubic_72^3_4k_160b"
-N_FAMILIES = 14
+N_FAMILIES = 16
 
 # ALU peaks from SM count x per-SM FMA rate x max clock:
 #   FP64: the nominal 1.25 TFLOP/s over 152 SMs at 2.07 GHz = 4 flop/clk/SM (2 DFMA/clk/SM)

@@ -52,7 +52,8 @@ typedef enum {
 
 typedef enum {
     QM_FP64 = 0,   /* everything in FP64 */
-    QM_MIXED = 1   /* FP32 FFT path and V multiply; nonlocal GEMMs in FP32 */
+    QM_MIXED = 1   /* FP32 FFT path and V multiply; nonlocal projection and application as
+                      3-term BF16 split products on the tensor cores, FP32 accumulation */
 } qm_precision;
 
 /*
@@ -247,7 +248,7 @@ qm_status qm_eigh_lowest(int m, int nev, const void* A, int lda, double* evals, 
  *  qm_prof_enable   on != 0: from now on record a pair of CUDA events on the launch stream
  *                   around every kernel launch; resets the accumulated times (any value).
  *  qm_prof_read     waits for the recorded events and returns, for kernel family
- *                   `family` (0 <= family < 14), the summed device time in ms and the number
+ *                   `family` (0 <= family < 16), the summed device time in ms and the number
  *                   of launches timed since the last qm_prof_enable.
  *  qm_prof_name     name of a kernel family ("" when out of range).
  */

@@ -3,9 +3,10 @@
 //
 // Launch sequence on the caller's stream (no host synchronisation):
 //   1. k_vt            V(r)/N_r laid out in the FFT path's permuted plane order
-//   2. gemm_cn         P[p][b] = <beta_p|psi_b>             (nonlocal projection)
+//   2. gemm_cn         P[p][b] = <beta_p|psi_b>             (nonlocal projection, FP64)
 //   3. K1, K2, K3      out = 1/2|k+G|^2 psi + (V psi)(G)    (per chunk of bands)
-//   4. gemm_tn         out += sum_p beta_p D_p P[p][b]      (nonlocal apply)
+//   4. gemm_tn         out += sum_p beta_p D_p P[p][b]      (nonlocal apply, FP64)
+//      QM_MIXED: 2 and 4 run after 3 as BF16x3 split tcgen05 products (umma.cu)
 // Workspace (owned by the gspace handle): Vt | P | split-K partials | stick buffer.
 #include <algorithm>
 #include <cstdint>
@@ -19,7 +20,7 @@ namespace qm {
 constexpr size_t kStickBudget = 48ull << 20;
 
 struct HpsiLayout {
-    size_t vt_off, p_off, part_off, t_off, total, t_bytes;
+    size_t vt_off, p_off, part_off, t_off, nl_off, err_off, total, t_bytes;
     int splits;
 };
 
@@ -42,6 +43,10 @@ static HpsiLayout hpsi_layout(qm_gspace g, int ik, int nb, int nproj, bool fp32)
     const size_t nbc = std::max<size_t>(1, std::min<size_t>((size_t)nb, kStickBudget / per_band));
     L.t_bytes = nbc * per_band;
     off = align_up(off + L.t_bytes, 256);
+    L.nl_off = off;  // tensor-core split operands (precision form)
+    off = align_up(off + (fp32 && nproj > 0 ? nonlocal_bf16x3_bytes(nproj, nb, npw) : 0), 256);
+    L.err_off = off;
+    off = align_up(off + 256, 256);
     L.total = off;
     return L;
 }
@@ -90,23 +95,24 @@ extern "C" qm_status qm_hpsi(qm_gspace g, int ik, int nb, const void* psi, int l
     void* T = ws + L.t_off;
 
     if ((st = launch_vt_prepare(g, vloc_r, vt, fp32, s))) return st;
-    if (nproj > 0) {
-        if (fp32)
-            st = cgemm_cn(nproj, nb, npw, (const float2*)beta, ld_beta, (const float2*)psi, ld_psi, (float2*)P, nb,
-                          (float2*)part, L.splits, s);
-        else
-            st = zgemm_cn(nproj, nb, npw, (const double2*)beta, ld_beta, (const double2*)psi, ld_psi, (double2*)P,
-                          nb, (double2*)part, L.splits, s);
+    if (nproj > 0 && !fp32) {
+        st = zgemm_cn(nproj, nb, npw, (const double2*)beta, ld_beta, (const double2*)psi, ld_psi, (double2*)P, nb,
+                      (double2*)part, L.splits, s);
         if (st) return st;
     }
     if ((st = launch_local_kinetic(g, ik, nb, psi, ld_psi, vt, out, ld_out, T, L.t_bytes, fp32, s))) return st;
     if (nproj > 0) {
-        if (fp32)
-            st = cgemm_tn(nb, npw, nproj, (const float2*)P, nb, D, (const float2*)beta, ld_beta, (float2*)out,
-                          ld_out, true, s);
-        else
+        if (fp32) {
+            // projection and application on the tensor cores (BF16x3 split, FP32 accumulation)
+            int* err = (int*)(ws + L.err_off);
+            if ((st = cuda_check(cudaMemsetAsync(err, 0, sizeof(int), s), "reset tensor-core error word")))
+                return st;
+            st = nonlocal_bf16x3(nproj, nb, npw, (const float2*)beta, ld_beta, (const float2*)psi, ld_psi, D,
+                                 (float2*)out, ld_out, ws + L.nl_off, err, s);
+        } else {
             st = zgemm_tn(nb, npw, nproj, (const double2*)P, nb, D, (const double2*)beta, ld_beta, (double2*)out,
                           ld_out, true, s);
+        }
         if (st) return st;
     }
     return QM_OK;

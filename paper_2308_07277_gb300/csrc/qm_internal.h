@@ -90,7 +90,7 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // ---- launch counting / per-kernel timing (prof.cpp) ----
 enum ProfFamily { PF_VT = 0, PF_STICK_INV, PF_PLANE, PF_STICK_FWD, PF_GEMM_CN, PF_REDUCE, PF_GEMM_TN, PF_OTHER, PF_CHOL,
-                  PF_TRIDIAG, PF_MULTISECT, PF_INVITER, PF_BACKTR, PF_CONVERT,
+                  PF_TRIDIAG, PF_MULTISECT, PF_INVITER, PF_BACKTR, PF_CONVERT, PF_UMMA, PF_SPLIT,
                   kProfFamilies };
 void count_launch(int n);
 // Counts one launch; when timing is enabled records CUDA events on `s` around the scope.
@@ -153,6 +153,15 @@ qm_status zgemm_cn_f32(int M, int N, int K, const double2* A, int lda, const dou
 qm_status zgemm_tn_f32(int M, int N, int K, const double2* A, int lda, const double* d,
                        const double2* B, int ldb, double2* C, int ldc, bool accumulate,
                        cudaStream_t s, double alpha = 1.0);
+// ---- tensor-core nonlocal step of the precision form (umma.cu) ----
+constexpr int kMaxUmmaSplits = 64;
+// out[b][g] += sum_p beta[p][g] D_p <beta_p|psi_b> (FP32 complex in/out) as BF16x3 split
+// tcgen05 products; work: nonlocal_bf16x3_bytes(); err: device int set on a timed-out wait
+qm_status nonlocal_bf16x3(int nproj, int nb, int npw, const float2* beta, int ld_beta, const float2* psi,
+                          int ld_psi, const double* D, float2* out, int ld_out, void* work, int* err,
+                          cudaStream_t s);
+size_t nonlocal_bf16x3_bytes(int nproj, int nb, int npw);
+
 // upper bound of the split-K partial buffer any gemm_cn call needs
 size_t gemm_cn_partial_bytes(bool fp32);
 

@@ -1,0 +1,390 @@
+// Tensor-core (tcgen05) GEMMs of the precision form: the nonlocal projection P = beta^H psi
+// and application beta D P of the Kleinman-Bylander term (Sec. 2.3) as 3-term BF16 split
+// products accumulated in FP32.
+//
+// Splitting: an FP32 value x is written x = x0 + x1 + x2 with x0 = bf16(x),
+// x1 = bf16(x - x0), x2 = bf16(x - x0 - x1); a product a*b keeps the six terms a_i b_j with
+// i + j <= 2 (the dropped terms are below 2^-24 |a b|), each a BF16 x BF16 tensor-core product
+// accumulated in FP32 in tensor memory.
+//
+// Complex -> real: with re/im interleaved along K, sum_k A[m][k] B[n][k] becomes a real GEMM
+// over 2K in which the B operand is "expanded" to two real rows per complex row:
+//   C = A B:        rows (b_re, -b_im), (b_im,  b_re)
+//   C = conj(A) B:  rows (b_re,  b_im), (b_im, -b_re)
+// so the real output C'[m][2n + t] is the interleaved complex result.
+//
+// Kernel: one CTA of 8 warps per 128 x 128 real output tile (and a K range for split-K).
+// The operands are read as FP32 complex from global memory and split / expanded on the fly
+// into shared memory (canonical no-swizzle K-major layout of 8 x 16-byte core matrices), so no
+// split copy ever goes to HBM.  Two shared-memory stages: while the tensor core multiplies
+// tile k (one thread issues 6 products x 4 K-steps of tcgen05.mma, M = N = 128, K = 16, into a
+// 128-column FP32 accumulator in tensor memory, then commits to the stage's mbarrier), the
+// CTA's loads of tile k+1 are in flight and are split into the other stage.  Every mbarrier wait is bounded and sets an error word
+// instead of hanging.  The epilogue reads the accumulator with tcgen05.ld.
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "qm_internal.h"
+
+namespace qm {
+namespace {
+
+constexpr int UM = 128, UN = 128, UK = 64;       // CTA tile: M x N x K (K in real elements)
+constexpr int TILE_BYTES = UM * UK * 2;          // one BF16 split component of one operand tile
+constexpr int STAGE_BYTES = 6 * TILE_BYTES;      // A and B, 3 components each
+constexpr int kThreads = 256;
+constexpr long kSpinLimit = 1L << 26;            // bounded mbarrier waits
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: no swizzle, K-major; lbo = byte stride between core
+// matrices along K, sbo = byte stride between 8-row groups
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version (fixed 0b001)
+    return d;                // base offset 0, relative LBO, swizzle none
+}
+
+// instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M x N
+constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
+    for (long i = 0; i < kSpinLimit; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(phase)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b) {
+    return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+}
+
+// split two FP32 values into the three BF16 components, packed in pairs
+__device__ __forceinline__ void split_pair(float x, float y, uint32_t& c0, uint32_t& c1, uint32_t& c2) {
+    const __nv_bfloat16 x0 = __float2bfloat16_rn(x), y0 = __float2bfloat16_rn(y);
+    const float rx = x - __bfloat162float(x0), ry = y - __bfloat162float(y0);
+    const __nv_bfloat16 x1 = __float2bfloat16_rn(rx), y1 = __float2bfloat16_rn(ry);
+    const __nv_bfloat16 x2 = __float2bfloat16_rn(rx - __bfloat162float(x1));
+    const __nv_bfloat16 y2 = __float2bfloat16_rn(ry - __bfloat162float(y1));
+    c0 = pack2(x0, y0);
+    c1 = pack2(x1, y1);
+    c2 = pack2(x2, y2);
+}
+
+__device__ __forceinline__ void put_pair(unsigned char* dst, int off, float x, float y) {
+    uint32_t c0, c1, c2;
+    split_pair(x, y, c0, c1, c2);
+    *reinterpret_cast<uint32_t*>(dst + off) = c0;
+    *reinterpret_cast<uint32_t*>(dst + TILE_BYTES + off) = c1;
+    *reinterpret_cast<uint32_t*>(dst + 2 * TILE_BYTES + off) = c2;
+}
+
+// Operand sources (FP32 complex in global memory).  A tile covers 128 real rows and 64 real
+// K columns = 32 complex columns: 16 row groups x 8 K chunks = 128 core matrices of 8 rows x
+// 16 bytes.  Each warp fills one core matrix per step (16 per tile), lane i writing the i-th
+// 4-byte word (one (re, im) pair of BF16) of each split component, so the shared-memory stores
+// are free of bank conflicts.  fetch() issues the tile's global loads into registers;
+// stash() splits them into shared memory.  Fetching tile k+1 before the products of tile k are
+// issued hides the global latency behind the tensor core.
+constexpr int kCmPerWarp = 128 / (kThreads / 32);
+
+__device__ __forceinline__ void put_word(unsigned char* dst, int cm, int lane, float x, float y) {
+    put_pair(dst, cm * 128 + lane * 4, x, y);
+}
+
+struct PlainRows {  // rows = complex rows of src, K = the complex columns (interleaved re, im)
+    const float2* src;
+    int ld, rows, K;
+    // core matrix cm = (row group) * 8 + (K chunk); lane = 4 * (row in group) + (complex col in chunk)
+    __device__ __forceinline__ void fetch(float2* v, int r0, int kc0, int tid) const {
+        const int warp = tid >> 5, lane = tid & 31;
+#pragma unroll
+        for (int it = 0; it < kCmPerWarp; ++it) {
+            const int cm = warp + 8 * it;
+            const int gr = r0 + (cm >> 3) * 8 + (lane >> 2), gk = kc0 + (cm & 7) * 4 + (lane & 3);
+            v[it] = (gr < rows && gk < K) ? __ldg(src + (size_t)gr * ld + gk) : make_float2(0.f, 0.f);
+        }
+    }
+    __device__ __forceinline__ void stash(unsigned char* dst, const float2* v, int tid) const {
+        const int warp = tid >> 5, lane = tid & 31;
+#pragma unroll
+        for (int it = 0; it < kCmPerWarp; ++it) put_word(dst, warp + 8 * it, lane, v[it].x, v[it].y);
+    }
+};
+
+// two real rows (2c, 2c+1) per complex element; lane = 8 a + 2 b + c: complex row a of the 4 in
+// the row group, complex column b of the 4 in the K chunk, c = which of the two real rows
+// (word (2a + c) * 4 + b of the core matrix)
+__device__ __forceinline__ int expand_word(int lane) { return ((2 * (lane >> 3) + (lane & 1)) << 2) + ((lane >> 1) & 3); }
+
+struct ExpandRows {  // B rows from complex rows of src (conj_a: pattern of conj(A) B)
+    const float2* src;
+    int ld, rows, K, conj_a;
+    __device__ __forceinline__ void fetch(float2* v, int r0, int kc0, int tid) const {
+        const int warp = tid >> 5, lane = tid & 31;
+#pragma unroll
+        for (int it = 0; it < kCmPerWarp; ++it) {
+            const int cm = warp + 8 * it;
+            const int gr = (r0 >> 1) + (cm >> 3) * 4 + (lane >> 3), gk = kc0 + (cm & 7) * 4 + ((lane >> 1) & 3);
+            v[it] = (gr < rows && gk < K) ? __ldg(src + (size_t)gr * ld + gk) : make_float2(0.f, 0.f);
+        }
+    }
+    __device__ __forceinline__ void stash(unsigned char* dst, const float2* v, int tid) const {
+        const int warp = tid >> 5, lane = tid & 31, w = expand_word(lane), odd = lane & 1;
+#pragma unroll
+        for (int it = 0; it < kCmPerWarp; ++it) {
+            const float2 a = v[it];
+            float x, y;
+            if (!conj_a) {
+                x = odd ? a.y : a.x;
+                y = odd ? a.x : -a.y;
+            } else {
+                x = odd ? a.y : a.x;
+                y = odd ? -a.x : a.y;
+            }
+            put_pair(dst, (warp + 8 * it) * 128 + w * 4, x, y);
+        }
+    }
+};
+
+struct ExpandTRows {  // B = src^T expanded: src [P][G] (G contiguous); rows 2g, 2g+1; K = p
+    const float2* src;
+    int ld, P, G;
+    __device__ __forceinline__ void fetch(float2* v, int r0, int kc0, int tid) const {
+        const int warp = tid >> 5, lane = tid & 31;
+#pragma unroll
+        for (int it = 0; it < kCmPerWarp; ++it) {
+            const int cm = warp + 8 * it;
+            const int gg = (r0 >> 1) + (cm >> 3) * 4 + (lane >> 3), gp = kc0 + (cm & 7) * 4 + ((lane >> 1) & 3);
+            v[it] = (gp < P && gg < G) ? __ldg(src + (size_t)gp * ld + gg) : make_float2(0.f, 0.f);
+        }
+    }
+    __device__ __forceinline__ void stash(unsigned char* dst, const float2* v, int tid) const {
+        const int warp = tid >> 5, lane = tid & 31, w = expand_word(lane), odd = lane & 1;
+#pragma unroll
+        for (int it = 0; it < kCmPerWarp; ++it) {
+            const float2 b = v[it];  // rows (b_re, -b_im), (b_im, b_re)
+            put_pair(dst, (warp + 8 * it) * 128 + w * 4, odd ? b.y : b.x, odd ? b.x : -b.y);
+        }
+    }
+};
+
+// C'[m][n] (+)= sum_k A[m][k] B[n][k] over the real K range of this split.  Output FP32 with
+// row stride ldc; rows >= M or columns >= N are not written.  Split z writes at
+// C + z * zstride.  accumulate: add to the existing output.
+template <class LA, class LB>
+__global__ void __launch_bounds__(kThreads)
+k_umma_split(LA la, LB lb, int M, int N, int ktiles_per_split, int ktiles_total, float* __restrict__ C, size_t ldc,
+             size_t zstride, int accumulate, int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int m0 = blockIdx.y * UM, n0 = blockIdx.x * UN;
+    const int kt0 = blockIdx.z * ktiles_per_split;
+    const int kt1 = min(ktiles_total, kt0 + ktiles_per_split);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_base)),
+                     "r"(UN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[1])));
+        asm volatile("fence.mbarrier_init.release.cluster;\n");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    const uint32_t tmem = tmem_base;
+    constexpr uint32_t idesc = idesc_bf16(UM, UN);
+    uint32_t ph[2] = {0u, 0u};
+    int issued[2] = {0, 0}, waited[2] = {0, 0};
+    bool ok = true;
+    float2 va[kCmPerWarp], vb[kCmPerWarp];
+    if (kt0 < kt1) {
+        la.fetch(va, m0, kt0 * (UK / 2), tid);
+        lb.fetch(vb, n0, kt0 * (UK / 2), tid);
+    }
+    for (int kt = kt0; kt < kt1 && ok; ++kt) {
+        const int s = (kt - kt0) & 1;
+        unsigned char* sA = smem + s * STAGE_BYTES;
+        unsigned char* sB = sA + 3 * TILE_BYTES;
+        if (issued[s] > waited[s]) {  // the products of tile kt-2 must have read this stage
+            const bool w = mbar_wait(smem_u32(&mbar[s]), ph[s]);
+            ph[s] ^= 1u;
+            ++waited[s];
+            if (!__syncthreads_and(w)) {  // a uniform decision: no thread is left at a barrier
+                ok = false;
+                if (tid == 0) atomicExch(err, 1);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;\n");
+        }
+        la.stash(sA, va, tid);
+        lb.stash(sB, vb, tid);
+        if (kt + 1 < kt1) {  // next tile's loads are in flight while this tile is multiplied
+            la.fetch(va, m0, (kt + 1) * (UK / 2), tid);
+            lb.fetch(vb, n0, (kt + 1) * (UK / 2), tid);
+        }
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;\n");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n");
+            // products a_i b_j with i + j <= 2, smallest terms first
+            const int pa[6] = {2, 1, 0, 1, 0, 0}, pb[6] = {0, 1, 2, 0, 1, 0};
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+#pragma unroll
+                for (int ks = 0; ks < UK / 16; ++ks) {
+                    const uint64_t da = sdesc(smem_u32(sA + pa[q] * TILE_BYTES) + ks * 256, 128, 1024);
+                    const uint64_t db = sdesc(smem_u32(sB + pb[q] * TILE_BYTES) + ks * 256, 128, 1024);
+                    const uint32_t acc = (kt > kt0 || q > 0 || ks > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                        "l"(da), "l"(db), "r"(idesc), "r"(acc));
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                smem_u32(&mbar[s])));
+        }
+        ++issued[s];
+    }
+    // wait for the products still in flight (every thread runs the same waits)
+    for (int s = 0; s < 2 && ok; ++s) {
+        while (issued[s] > waited[s] && ok) {
+            const bool w = mbar_wait(smem_u32(&mbar[s]), ph[s]);
+            ph[s] ^= 1u;
+            ++waited[s];
+            if (!__syncthreads_and(w)) {
+                ok = false;
+                if (tid == 0) atomicExch(err, 1);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    if (ok && kt1 > kt0) {
+        // warp w reads accumulator lanes 32 (w % 4) + 0..31 (tile rows); warps 0-3 take
+        // columns 0..63, warps 4-7 columns 64..127
+        const int q = warp & 3, chalf = (warp >> 2) * 64;
+        const int row = m0 + q * 32 + (tid & 31);
+        float* crow = C + (size_t)blockIdx.z * zstride + (size_t)row * ldc;
+#pragma unroll 1
+        for (int c0 = chalf; c0 < chalf + 64; c0 += 16) {
+            uint32_t v[16];
+            const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+                "%14, %15}, [%16];\n"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                  "=r"(v[15])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+            if (row < M) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int col = n0 + c0 + j;
+                    if (col < N) {
+                        const float x = __uint_as_float(v[j]);
+                        crow[col] = accumulate ? crow[col] + x : x;
+                    }
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(UN));
+}
+
+// sum the split-K partials of the projection C'[p][2b + t] and write the application's A
+// operand P'[b][p] = D_p * P[p][b] (FP32 complex, ld nproj)
+__global__ void k_reduce_proj(const float* __restrict__ part, int Z, size_t zstride, int ldc, int nproj, int nb,
+                              const double* __restrict__ D, float2* __restrict__ Pd) {
+    const size_t total = (size_t)nb * nproj;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const int b = (int)(e / nproj), p = (int)(e % nproj);
+        float sr = 0.f, si = 0.f;
+        for (int z = 0; z < Z; ++z) {
+            const float* q = part + (size_t)z * zstride + (size_t)p * ldc + 2 * b;
+            sr += q[0];
+            si += q[1];
+        }
+        const float d = (float)D[p];
+        Pd[e] = make_float2(d * sr, d * si);
+    }
+}
+
+inline size_t rup(size_t x, size_t a) { return (x + a - 1) / a * a; }
+inline int grid_for(size_t n) { return (int)std::max<size_t>(1, std::min<size_t>((n + 255) / 256, 152 * 16)); }
+
+template <class LA, class LB>
+qm_status umma_launch(const LA& la, const LB& lb, int M, int N, int kreal, int splits, float* C, size_t ldc,
+                      size_t zstride, bool accumulate, int* err, cudaStream_t s, int* zout) {
+    const int ktiles = (int)((rup((size_t)kreal, UK)) / UK);
+    splits = std::max(1, std::min(splits, ktiles));
+    const int per = (ktiles + splits - 1) / splits;
+    splits = (ktiles + per - 1) / per;
+    if (zout) *zout = splits;
+    const size_t smem = 2 * (size_t)STAGE_BYTES;
+    cudaFuncSetAttribute(k_umma_split<LA, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    dim3 grid((N + UN - 1) / UN, (M + UM - 1) / UM, splits);
+    ProfScope pf(PF_UMMA, s);
+    k_umma_split<LA, LB><<<grid, kThreads, smem, s>>>(la, lb, M, N, per, ktiles, C, ldc, zstride, accumulate ? 1 : 0,
+                                                     err);
+    return cuda_check(cudaGetLastError(), "k_umma_split launch");
+}
+
+}  // namespace
+
+size_t nonlocal_bf16x3_bytes(int nproj, int nb, int npw) {
+    (void)npw;
+    const size_t rP = rup(nproj, UM), r2B = rup(2 * (size_t)nb, UN);
+    return rup((size_t)kMaxUmmaSplits * rP * r2B * 4, 256) + rup((size_t)nb * nproj * sizeof(float2), 256);
+}
+
+// out[b][g] += sum_p beta[p][g] D_p sum_g' conj(beta[p][g']) psi[b][g']   (FP32 complex in/out)
+qm_status nonlocal_bf16x3(int nproj, int nb, int npw, const float2* beta, int ld_beta, const float2* psi, int ld_psi,
+                          const double* D, float2* out, int ld_out, void* work, int* err, cudaStream_t s) {
+    if (nproj <= 0 || nb <= 0) return QM_OK;
+    const size_t rP = rup(nproj, UM), r2B = rup(2 * (size_t)nb, UN);
+    float* part = (float*)work;
+    float2* Pd = (float2*)((char*)work + rup((size_t)kMaxUmmaSplits * rP * r2B * 4, 256));
+    // projection: C'[p][2b + t] = <beta_p | psi_b>, split over K (2 npw real columns)
+    const int tiles = (int)((rP / UM) * (r2B / UN));
+    const int splits = std::max(1, std::min(kMaxUmmaSplits, 152 / std::max(1, tiles)));
+    const size_t zstride = rP * r2B;
+    PlainRows la{beta, ld_beta, nproj, npw};
+    ExpandRows lb{psi, ld_psi, nb, npw, 1};
+    int Z = 1;
+    qm_status st = umma_launch(la, lb, nproj, 2 * nb, 2 * npw, splits, part, r2B, zstride, false, err, s, &Z);
+    if (st) return st;
+    {
+        ProfScope pf(PF_SPLIT, s);
+        k_reduce_proj<<<grid_for((size_t)nb * nproj), 256, 0, s>>>(part, Z, zstride, (int)r2B, nproj, nb, D, Pd);
+    }
+    if ((st = cuda_check(cudaGetLastError(), "k_reduce_proj launch"))) return st;
+    // application: out'[b][2g + t] += sum_p (D P)[b][p] beta[p][g]
+    PlainRows la2{Pd, nproj, nb, nproj};
+    ExpandTRows lb2{beta, ld_beta, nproj, npw};
+    return umma_launch(la2, lb2, nb, 2 * npw, 2 * nproj, 1, (float*)out, 2 * (size_t)ld_out, 0, true, err, s,
+                       nullptr);
+}
+
+}  // namespace qm
