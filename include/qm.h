@@ -164,6 +164,89 @@ qm_status qm_hpsi_noalloc(qm_gspace g, int ik, int nb,
                           void* out, int ld_out,
                           qm_precision prec, void* stream);
 
+/*
+ * Batched H psi (the batched form: every band x k-point x cell of many independent cells of
+ * uneven size in ONE persistent launch, captured in a CUDA graph).
+ *
+ * A batch is a plan bound to its buffers: qm_batch_create takes the jobs (each one the
+ * argument list of qm_hpsi), lays the work of all of them out as one list of work items
+ * (V layout, partial projections, x-stick transforms, yz-plane transforms with the V
+ * multiply, projection reductions, x-stick forward transforms with the gather and kinetic
+ * term, nonlocal application), allocates the intermediate buffers, and captures the launch
+ * in a CUDA graph.  qm_batch_run then replays it: one kernel launch computes
+ * out_j = H(k_j) psi_j for every job j, with the numerics of qm_hpsi in the same precision
+ * (FFT path identical; nonlocal products accumulated in the working precision, FP32 in
+ * QM_MIXED instead of the single-call tensor-core path).
+ *
+ * The shape of the launch (resident CTAs per SM; grid points per FFT work item, from which
+ * the lines per x-stick item and the bands per yz-plane item follow) is either given or
+ * picked by the autotuner, which builds every feasible shape, times three replays of each
+ * (after one warm-up) with CUDA events on `stream`, and keeps the fastest.
+ */
+typedef struct {
+    qm_gspace g;            /* gspace of the job's cell (device tables on the current device) */
+    int ik;                 /* k-point of g */
+    int nb;                 /* bands, >= 1 */
+    const void* psi;        /* device, as qm_hpsi */
+    int ld_psi;
+    int nproj;              /* >= 0 */
+    const double* vloc_r;   /* device, as qm_hpsi; jobs with the same (g, vloc_r) share its layout */
+    const void* beta;       /* device, as qm_hpsi (may be NULL when nproj == 0) */
+    int ld_beta;
+    int ld_out;
+    const double* D;        /* device, as qm_hpsi */
+    void* out;              /* device, as qm_hpsi; the out blocks of different jobs must not overlap */
+} qm_hpsi_job;
+
+typedef struct qm_batch_s* qm_batch;   /* opaque, library-owned */
+
+typedef struct {
+    int ctas_per_sm;   /* resident CTAs per SM, 1..8; 0 = autotune */
+    int item_points;   /* target grid points per FFT work item, 256..65536; 0 = autotune */
+} qm_batch_shape;
+
+typedef struct {
+    int ctas_per_sm, item_points;  /* shape in use */
+    int grid;                      /* CTAs of the persistent launch */
+    int items;                     /* work items per replay */
+    int cells;                     /* distinct (gspace, vloc_r) pairs */
+    int candidates;                /* shapes the autotuner timed (0: shape given) */
+    long long band_applies;        /* sum over jobs of nb */
+    long long smem_bytes;          /* dynamic shared memory per CTA */
+    long long device_bytes;        /* device memory owned by the batch */
+    double tuned_ms;               /* autotuner's best median time per replay (ms; 0 if not tuned) */
+} qm_batch_info;
+
+/*
+ * qm_batch_create - build (and, with shape NULL or zero fields, autotune) a batch.
+ *  njobs, jobs   host array of njobs >= 1 job descriptions (copied; the buffers they point
+ *                to must stay valid and keep their addresses for the life of the batch).
+ *  prec          QM_FP64 or QM_MIXED (element types of psi/beta/out as in qm_hpsi).
+ *  shape         host, may be NULL (autotune both fields).
+ *  stream        cudaStream_t used by the autotuner.  Autotuning REPLAYS THE BATCH several
+ *                times: every out block is written.  Synchronous (returns when done).
+ *  out           host; receives the batch.
+ * Make this call outside any stream capture.  Errors: QM_ERR_ARG (a job fails qm_hpsi's
+ * checks, or two out blocks overlap), QM_ERR_UNSUPPORTED (shape does not fit an SM, more
+ * than 1024 projectors in a job), QM_ERR_OOM, QM_ERR_CUDA, QM_ERR_TIMEOUT (while tuning).
+ */
+qm_status qm_batch_create(int njobs, const qm_hpsi_job* jobs, qm_precision prec,
+                          const qm_batch_shape* shape, void* stream, qm_batch* out);
+
+/* qm_batch_run - replay the batch's graph on `stream` (asynchronous; one kernel launch and
+ * one memset).  Replays of one batch must be serialised (they share its buffers). */
+qm_status qm_batch_run(qm_batch b, void* stream);
+
+/* qm_batch_check - synchronise `stream` and read the batch's device error word:
+ * QM_ERR_TIMEOUT if a bounded device-side wait of the last replay expired, else QM_OK. */
+qm_status qm_batch_check(qm_batch b, void* stream);
+
+/* qm_batch_query - shape, sizes and tuning result of a batch. */
+qm_status qm_batch_query(qm_batch b, qm_batch_info* info);
+
+/* qm_batch_destroy - synchronise the device and free the batch (NULL is a no-op). */
+void qm_batch_destroy(qm_batch b);
+
 /* Options of qm_davidson (zero-initialise, then set what you need; 0 / 0.0 = default). */
 typedef struct {
     double tol;          /* convergence: max_n ||H x_n - eps_n x_n||_2 <= tol (Ha), ||x_n||_2 = 1;
@@ -248,7 +331,7 @@ qm_status qm_eigh_lowest(int m, int nev, const void* A, int lda, double* evals, 
  *  qm_prof_enable   on != 0: from now on record a pair of CUDA events on the launch stream
  *                   around every kernel launch; resets the accumulated times (any value).
  *  qm_prof_read     waits for the recorded events and returns, for kernel family
- *                   `family` (0 <= family < 16), the summed device time in ms and the number
+ *                   `family` (0 <= family < 17), the summed device time in ms and the number
  *                   of launches timed since the last qm_prof_enable.
  *  qm_prof_name     name of a kernel family ("" when out of range).
  */

@@ -78,3 +78,33 @@ SIGNATURES["qm_hpsi_noalloc"] = SIGNATURES["qm_hpsi"]
 
 SIGNATURES["qm_eigh_lowest"] = (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                                ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p])
+
+
+class HpsiJob(ctypes.Structure):
+    """qm_hpsi_job of include/qm.h."""
+    _fields_ = [("g", ctypes.c_void_p), ("ik", ctypes.c_int), ("nb", ctypes.c_int), ("psi", ctypes.c_void_p),
+                ("ld_psi", ctypes.c_int), ("nproj", ctypes.c_int), ("vloc_r", ctypes.c_void_p),
+                ("beta", ctypes.c_void_p), ("ld_beta", ctypes.c_int), ("ld_out", ctypes.c_int),
+                ("D", ctypes.c_void_p), ("out", ctypes.c_void_p)]
+
+
+class BatchShape(ctypes.Structure):
+    """qm_batch_shape of include/qm.h."""
+    _fields_ = [("ctas_per_sm", ctypes.c_int), ("item_points", ctypes.c_int)]
+
+
+class BatchInfo(ctypes.Structure):
+    """qm_batch_info of include/qm.h."""
+    _fields_ = [("ctas_per_sm", ctypes.c_int), ("item_points", ctypes.c_int), ("grid", ctypes.c_int),
+                ("items", ctypes.c_int), ("cells", ctypes.c_int), ("candidates", ctypes.c_int),
+                ("band_applies", ctypes.c_longlong), ("smem_bytes", ctypes.c_longlong),
+                ("device_bytes", ctypes.c_longlong), ("tuned_ms", ctypes.c_double)]
+
+
+SIGNATURES["qm_batch_create"] = (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(HpsiJob), ctypes.c_int,
+                                                ctypes.POINTER(BatchShape), ctypes.c_void_p,
+                                                ctypes.POINTER(ctypes.c_void_p)])
+SIGNATURES["qm_batch_run"] = (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p])
+SIGNATURES["qm_batch_check"] = (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p])
+SIGNATURES["qm_batch_query"] = (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(BatchInfo)])
+SIGNATURES["qm_batch_destroy"] = (None, [ctypes.c_void_p])

@@ -217,3 +217,63 @@ def qm_eigh_lowest(A, nev, stream=None):
                               _dev_ptr(ev, "evals", torch.float64), _dev_ptr(Y, "Y", torch.complex128),
                               int(Y.stride(0)), _stream_ptr(stream)))
     return ev, Y
+
+
+class Batch:
+    """A batched H psi plan (qm_batch of include/qm.h) bound to its buffers.
+
+    jobs: list of dicts with keys g (gspace handle), ik, psi, vloc, beta, D, out (CUDA
+    tensors as for qm_hpsi; beta/D may be None).  The tensors are referenced by the plan
+    and must stay alive and in place while it exists."""
+
+    def __init__(self, jobs, prec="fp64", ctas_per_sm=0, item_points=0, stream=None):
+        lib = _lib.load()
+        self.prec = _PREC[prec]
+        cdt = torch.complex128 if self.prec == QM_FP64 else torch.complex64
+        arr = (_lib.HpsiJob * len(jobs))()
+        self._keep = []
+        for i, j in enumerate(jobs):
+            psi, out, beta = j["psi"], j["out"], j.get("beta")
+            if psi.dim() != 2 or out.dim() != 2 or psi.shape[0] != out.shape[0]:
+                raise ValueError(f"job {i}: psi and out must be 2-D with the same number of bands")
+            nproj = 0 if beta is None else int(beta.shape[0])
+            arr[i] = _lib.HpsiJob(g=j["g"].value if isinstance(j["g"], ctypes.c_void_p) else j["g"],
+                                  ik=int(j["ik"]), nb=int(psi.shape[0]),
+                                  psi=_dev_ptr(psi, "psi", cdt), ld_psi=int(psi.stride(0)), nproj=nproj,
+                                  vloc_r=_dev_ptr(j["vloc"], "vloc", torch.float64),
+                                  beta=_dev_ptr(beta, "beta", cdt) if nproj else None,
+                                  ld_beta=int(beta.stride(0)) if nproj else 0, ld_out=int(out.stride(0)),
+                                  D=_dev_ptr(j["D"], "D", torch.float64) if nproj else None,
+                                  out=_dev_ptr(out, "out", cdt))
+            self._keep.append((psi, out, beta, j["vloc"], j.get("D")))
+        shape = _lib.BatchShape(int(ctas_per_sm), int(item_points))
+        h = ctypes.c_void_p()
+        _check(lib.qm_batch_create(len(jobs), arr, self.prec, ctypes.byref(shape), _stream_ptr(stream),
+                                   ctypes.byref(h)))
+        self.handle = h
+
+    def run(self, stream=None):
+        _check(_lib.load().qm_batch_run(self.handle, _stream_ptr(stream)))
+
+    def check(self, stream=None):
+        _check(_lib.load().qm_batch_check(self.handle, _stream_ptr(stream)))
+
+    def info(self):
+        inf = _lib.BatchInfo()
+        _check(_lib.load().qm_batch_query(self.handle, ctypes.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in _lib.BatchInfo._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            _lib.load().qm_batch_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def qm_batch_create(jobs, prec="fp64", ctas_per_sm=0, item_points=0, stream=None):
+    return Batch(jobs, prec=prec, ctas_per_sm=ctas_per_sm, item_points=item_points, stream=stream)

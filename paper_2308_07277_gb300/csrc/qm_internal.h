@@ -90,7 +90,7 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // ---- launch counting / per-kernel timing (prof.cpp) ----
 enum ProfFamily { PF_VT = 0, PF_STICK_INV, PF_PLANE, PF_STICK_FWD, PF_GEMM_CN, PF_REDUCE, PF_GEMM_TN, PF_OTHER, PF_CHOL,
-                  PF_TRIDIAG, PF_MULTISECT, PF_INVITER, PF_BACKTR, PF_CONVERT, PF_UMMA, PF_SPLIT,
+                  PF_TRIDIAG, PF_MULTISECT, PF_INVITER, PF_BACKTR, PF_CONVERT, PF_UMMA, PF_SPLIT, PF_BATCH,
                   kProfFamilies };
 void count_launch(int n);
 // Counts one launch; when timing is enabled records CUDA events on `s` around the scope.

@@ -47,6 +47,7 @@ class Cell:
     width: float = 1.0             # Gaussian V_loc sigma, bohr
     rc: float = 1.0                # projector radius, bohr
     seed: int = 1
+    ortho_period: tuple | None = None  # orthorhombic box whose edges are lattice vectors (fast V_loc)
 
     @property
     def nat(self) -> int:
@@ -135,3 +136,53 @@ def small_cells() -> list[Cell]:
         cubic_si8(12.0, nbnd=7, reps=(2, 1, 1), kpts=[[0.25, 0.25, -0.25]]),  # N1 != N2 = N3
         cubic_si8(10.0, nbnd=6, reps=(1, 1, 1)),
     ]
+
+
+# the full 2x2x2 shifted Monkhorst-Pack set {+-1/4}^3 (no symmetry reduction), in a fixed order
+KPTS_MP222_SHIFTED_FULL = np.array([[s1, s2, s3] for s1 in (0.25, -0.25) for s2 in (0.25, -0.25)
+                                    for s3 in (0.25, -0.25)])
+
+
+def fcc_supercell(n1: int, n2: int, n3: int, a: float = A0_SI) -> tuple[np.ndarray, np.ndarray]:
+    """n1 x n2 x n3 supercell of the two-atom fcc cell: lattice rows n_i a_i, Cartesian sites."""
+    prim = fcc_lattice(a)
+    basis = np.array([[0.0, 0.0, 0.0], [0.25 * a, 0.25 * a, 0.25 * a]])
+    lat = prim * np.array([[n1], [n2], [n3]], float)
+    sites = [basis + i1 * prim[0] + i2 * prim[1] + i3 * prim[2]
+             for i3 in range(n3) for i2 in range(n2) for i1 in range(n1)]
+    return lat, np.concatenate(sites, axis=0)
+
+
+# the cell families of the batched workload (2-16 atoms)
+BATCH_FAMILIES = (("fcc_si2", "fcc", (1, 1, 1)), ("fcc_si4", "fcc", (2, 1, 1)), ("fcc_si8", "fcc", (2, 2, 1)),
+                  ("cubic_si8", "cubic", (1, 1, 1)), ("fcc_si16", "fcc", (2, 2, 2)))
+
+
+def config3_cells(grid_fn, n: int = 256, seed: int = 3, grid_range=(18, 48)) -> list[Cell]:
+    """The batched workload: n independent cells of uneven size, cell i drawn from its own
+    seeded generator [seed, 3, i].
+
+    Per cell: a family of BATCH_FAMILIES (uniform), ecutwfc ~ U(15, 30) Ry, the FFT grid
+    given by ``grid_fn(cell)`` (the caller's grid rule), redrawn until every N_d lies in
+    ``grid_range``; then nbnd ~ U{8..48}, nk ~ U{1..8} (the first nk points of
+    KPTS_MP222_SHIFTED_FULL) and the V_loc depth -1.5 * (1 + U(-0.2, 0.2)) Ha.
+    """
+    cells = []
+    for i in range(n):
+        rng = np.random.default_rng([int(seed), 3, i])
+        while True:
+            name, kind, reps = BATCH_FAMILIES[int(rng.integers(len(BATCH_FAMILIES)))]
+            ecut = float(rng.uniform(15.0, 30.0))
+            lat, tau = fcc_supercell(*reps) if kind == "fcc" else cubic_supercell(*reps)
+            cell = Cell(f"{name}_{i}", lat, tau, ecut, None)
+            grid = tuple(int(x) for x in grid_fn(cell))
+            if all(grid_range[0] <= x <= grid_range[1] for x in grid):
+                break
+        cell.grid = grid
+        cell.nbnd = int(rng.integers(8, 49))
+        cell.kpts = KPTS_MP222_SHIFTED_FULL[: int(rng.integers(1, 9))].copy()
+        cell.depth = -1.5 * (1.0 + float(rng.uniform(-0.2, 0.2)))
+        cell.seed = 1000 + i
+        cell.ortho_period = (2 * A0_SI,) * 3   # every family is diamond Si: 2 a0 cube is a superlattice
+        cells.append(cell)
+    return cells

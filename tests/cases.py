@@ -15,7 +15,7 @@ def make_case(cell, ik=0, nb=None, seed=None):
     """Oracle G-sphere of k-point ik and the synthetic V, beta, D, psi on it."""
     grid = grid_of(cell)
     gs = OG.gsphere(cell.lattice, grid, cell.ecut_ha, cell.kpts[ik])
-    v = S.vloc_on_grid(cell.lattice, cell.tau, grid, cell.depth, cell.width)
+    v = S.vloc_on_grid(cell.lattice, cell.tau, grid, cell.depth, cell.width, ortho_period=cell.ortho_period)
     beta = S.beta_of_q(gs["q"], cell.tau, cell.omega, cell.rc)
     D = S.dvals(cell.nat)
     nb = cell.nbnd if nb is None else nb
