@@ -1,0 +1,135 @@
+"""Pins of the learned-preconditioner oracle (oracle/mlp.py) against things other than itself:
+central finite differences of the loss, closed forms of degenerate networks, invariances of the
+features and the loss, and the defining properties of the exact correction on a cell solved by
+brute-force diagonalisation."""
+import math
+
+import numpy as np
+import pytest
+
+import qm_synth as S
+from oracle import hamiltonian as OH
+from oracle import mlp as M
+from oracle.precond import tpa_k
+
+from cases import make_case
+
+
+def random_data(seed, nb=4, npw=23):
+    rng = np.random.default_rng(seed)
+    F = np.stack([rng.uniform(0, 4, nb * npw), np.repeat(rng.uniform(-1, 1, nb), npw),
+                  rng.normal(0, 1, nb * npw)], axis=1)
+    r2 = rng.uniform(0.01, 1.0, nb * npw)
+    c = rng.normal(0, 1, nb * npw)
+    D = rng.uniform(0.5, 2.0, nb)
+    D[1] = 0.0                                           # excluded band
+    off = np.arange(0, nb * npw + 1, npw)
+    return F, r2, c, D, off
+
+
+def test_param_count_and_layout():
+    assert M.NPARAM == 4481
+    th = np.arange(M.NPARAM, dtype=float)
+    W1, b1, W2, b2, w3, b3 = M.unpack(th)
+    assert W1.shape == (64, 3) and W1[1, 0] == 3 and b1[0] == 192 and W2[0, 1] == 257
+    assert b2[0] == 192 + 64 + 4096 and w3[0] == b2[0] + 64 and b3 == M.NPARAM - 1
+
+
+def test_loss_gradient_matches_central_differences():
+    F, r2, c, D, off = random_data(1)
+    th = M.init_params(3)
+    th[192:256] = 0.1                                    # nonzero b1
+    th[-1] = 0.3
+    loss, g = M.loss_and_grad(th, F, r2, c, D, off)
+    rng = np.random.default_rng(7)
+    blocks = [(0, 192), (192, 256), (256, 4352), (4352, 4416), (4416, 4480), (4480, 4481)]
+    idx = sorted(set(int(rng.integers(a, b)) for a, b in blocks for _ in range(8)))
+    h = 1e-5
+    for i in idx:
+        tp, tm = th.copy(), th.copy()
+        tp[i] += h
+        tm[i] -= h
+        fd = (M.loss_and_grad(tp, F, r2, c, D, off)[0] - M.loss_and_grad(tm, F, r2, c, D, off)[0]) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-7 * max(1e-3, abs(fd)) + 1e-10, (i, fd, g[i])
+
+
+def test_degenerate_network_is_constant_softplus():
+    F, r2, c, D, off = random_data(2)
+    th = M.init_params(4)
+    W1, b1, W2, b2, w3, b3 = M.unpack(th)
+    W2[:] = 0.0
+    w3[:] = 0.0
+    th[-1] = -0.7
+    K, _ = M.forward(th, F)
+    assert np.allclose(K, math.log1p(math.exp(-0.7)), rtol=0, atol=1e-15)
+    # a constant K: the loss is that of K = 1 (scale invariance)
+    assert abs(M.loss_and_grad(th, F, r2, c, D, off)[0] - M.cosine_loss_of_k(np.ones_like(r2), r2, c, D, off)) < 1e-14
+
+
+def test_cosine_loss_zero_for_exact_direction_and_bounded():
+    rng = np.random.default_rng(3)
+    nb, npw = 3, 40
+    off = np.arange(0, nb * npw + 1, npw)
+    r = rng.normal(size=(nb, npw)) + 1j * rng.normal(size=(nb, npw))
+    k = rng.uniform(0.1, 2.0, (nb, npw))
+    dstar = k * r                                         # exactly a diagonal correction
+    r2 = (np.abs(r) ** 2).ravel()
+    c = np.real(np.conj(r) * dstar).ravel()
+    D = (np.abs(dstar) ** 2).sum(axis=1)
+    assert M.cosine_loss_of_k(k.ravel(), r2, c, D, off) < 1e-14
+    assert M.cosine_loss_of_k(5.0 * k.ravel(), r2, c, D, off) < 1e-14       # scale invariance
+    other = M.cosine_loss_of_k(np.ones(nb * npw), r2, c, D, off)
+    assert 0.0 < other < 1.0
+
+
+def test_features_are_scale_free_and_x_is_one_on_a_single_wave():
+    rng = np.random.default_rng(5)
+    nb, npw = 2, 30
+    kin = rng.uniform(0, 5, npw)
+    psi = rng.normal(size=(nb, npw)) + 1j * rng.normal(size=(nb, npw))
+    res = rng.normal(size=(nb, npw)) + 1j * rng.normal(size=(nb, npw))
+    res[0, 3] = 0.0
+    eps = np.array([-0.3, 0.4])
+    F = M.features(kin, psi, res, eps)
+    F2 = M.features(kin, 3.0 * psi, (2 - 1j) * res, eps)
+    assert np.allclose(F, F2, rtol=1e-13, atol=1e-13)
+    assert F[3, 2] == math.log(M.FEAT_LOG_FLOOR)         # zero residual component: floored log
+    one = np.zeros((1, npw), complex)
+    one[0, 7] = 2.0
+    Fo = M.features(kin, one, res[:1], eps[:1])
+    assert abs(Fo[7, 0] - 1.0) < 1e-15 and abs(Fo[0, 1] - eps[0] / kin[7]) < 1e-15
+
+
+def test_exact_correction_lands_in_the_eigenspace():
+    cell = S.fcc_si2(12.0, nbnd=8)
+    c = make_case(cell, 0)
+    H = OH.dense_h(c["gs"], c["v"], c["beta"], c["D"])
+    lam, U = np.linalg.eigh(H)
+    U = U.T.copy()                                       # rows = eigenvectors
+    nu = 12
+    rng = np.random.default_rng(9)
+    noise = rng.normal(size=U[:8].shape) + 1j * rng.normal(size=U[:8].shape)
+    psi = U[:8] + 0.05 * noise / np.linalg.norm(noise, axis=1)[:, None]     # Ritz-like: 5 % error
+    psi /= np.linalg.norm(psi, axis=1)[:, None]
+    eps = np.einsum("ij,jk,ik->i", psi.conj(), H, psi).real
+    dstar = M.exact_corrections(psi, eps, lam[:nu], U[:nu], 1e-6)
+    for n in range(8):
+        assert abs(np.vdot(psi[n], dstar[n])) < 1e-12                 # orthogonal to psi_n
+        assert np.linalg.norm(dstar[n]) > 1e-3                          # not dropped
+        y = psi[n] + dstar[n]
+        m0 = int(np.argmin(np.abs(lam[:nu] - eps[n])))
+        resid = np.linalg.norm(H @ y - lam[m0] * y) / np.linalg.norm(y)
+        assert resid < 1e-10, (n, resid)
+    # the Gamma-point triplet of Si: a cluster of three (the projector is not one vector)
+    gaps = np.diff(lam[:8])
+    assert np.sum(gaps < 1e-6) >= 2
+    # a cluster reaching the last given pair is dropped
+    d2 = M.exact_corrections(psi[:1], np.array([lam[nu - 1]]), lam[:nu], U[:nu], 1e-6)
+    assert np.all(d2 == 0)
+
+
+def test_tpa_factor_is_a_valid_comparison_k():
+    """The TPA factor plugged into the same loss (what the learned K competes with)."""
+    F, r2, c, D, off = random_data(6)
+    L = M.cosine_loss_of_k(tpa_k(F[:, 0]), r2, c, D, off)
+    assert 0.0 <= L <= 1.0
