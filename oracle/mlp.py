@@ -10,8 +10,13 @@ evaluated per plane wave, the correction of band n being delta_n(G) = K(f_nG) r_
 
 Network (3 inputs, two hidden layers of 64, one output):
     z1 = W1 f + b1,  h1 = silu(z1),  z2 = W2 h1 + b2,  h2 = silu(z2),
-    z3 = w3 . h2 + b3,  K = softplus(z3) = log(1 + e^z3)
-    silu(z) = z sigma(z),  sigma(z) = 1 / (1 + e^-z)
+    z3 = w3 . h2 + b3,  K = K_TPA(x) softplus(z3) / log 2
+    silu(z) = z sigma(z),  sigma(z) = 1 / (1 + e^-z),  softplus(z) = log(1 + e^z)
+Reading: the network's softplus output is a positive factor on the TPA curve K_TPA(x) of the
+same plane wave (x the first feature), normalised so that z3 = 0 gives TPA exactly.  The
+network is the correction operator (it replaces TPA in the step); TPA is its prior, so an
+untrained network (w3 = 0, b3 = 0) starts from the TPA correction and training can only move
+the fit away from it where the samples say so.
 Parameters, one flat vector of NPARAM (the layout the library uses):
     W1 (64 x 3, row-major W1[j][k]) | b1 (64) | W2 (64 x 64, W2[j][i]) | b2 (64) | w3 (64) | b3 (1)
 
@@ -40,6 +45,8 @@ from __future__ import annotations
 import math
 
 import numpy as np
+
+from .precond import tpa_k
 
 HIDDEN = 64
 NIN = 3
@@ -80,7 +87,7 @@ def softplus(z):
 
 
 def init_params(seed):
-    """Seeded initial parameters: W ~ N(0, 1/fan_in), zero biases, b3 = 0."""
+    """Seeded parameters with every layer active: W ~ N(0, 1/fan_in), zero biases."""
     rng = np.random.default_rng([int(seed), 22])
     W1 = rng.standard_normal((HIDDEN, NIN)) / math.sqrt(NIN)
     W2 = rng.standard_normal((HIDDEN, HIDDEN)) / math.sqrt(HIDDEN)
@@ -96,7 +103,7 @@ def forward(theta, F):
     z2 = h1 @ W2.T + b2
     h2 = silu(z2)
     z3 = h2 @ w3 + b3
-    return softplus(z3), (F, z1, h1, z2, h2, z3)
+    return tpa_k(F[:, 0]) * softplus(z3) / math.log(2.0), (F, z1, h1, z2, h2, z3)
 
 
 def features(kin, psi, res, eps):
@@ -161,7 +168,7 @@ def loss_and_grad(theta, F, r2, c, D, band_off):
     coef = np.where(use, 2.0 * B / safe, 0.0) / nuse
     ratio = np.where(use, B / np.where(use, A, 1.0), 0.0)
     dK = coef[seg] * (ratio[seg] * K * r2 - c)
-    dz3 = dK * sigmoid(z3)
+    dz3 = dK * tpa_k(F[:, 0]) * sigmoid(z3) / math.log(2.0)
     gw3 = h2.T @ dz3
     gb3 = dz3.sum()
     dz2 = (dz3[:, None] * w3[None, :]) * silu_grad(z2)

@@ -53,7 +53,7 @@ def test_loss_gradient_matches_central_differences():
         assert abs(fd - g[i]) <= 1e-7 * max(1e-3, abs(fd)) + 1e-10, (i, fd, g[i])
 
 
-def test_degenerate_network_is_constant_softplus():
+def test_degenerate_network_is_a_scaled_tpa_curve():
     F, r2, c, D, off = random_data(2)
     th = M.init_params(4)
     W1, b1, W2, b2, w3, b3 = M.unpack(th)
@@ -61,9 +61,14 @@ def test_degenerate_network_is_constant_softplus():
     w3[:] = 0.0
     th[-1] = -0.7
     K, _ = M.forward(th, F)
-    assert np.allclose(K, math.log1p(math.exp(-0.7)), rtol=0, atol=1e-15)
-    # a constant K: the loss is that of K = 1 (scale invariance)
-    assert abs(M.loss_and_grad(th, F, r2, c, D, off)[0] - M.cosine_loss_of_k(np.ones_like(r2), r2, c, D, off)) < 1e-14
+    # the TPA rational function written out (Teter, Payne & Allan 1989) times softplus(b3) / log 2
+    x = F[:, 0]
+    num = 27 + 18 * x + 12 * x ** 2 + 8 * x ** 3
+    assert np.allclose(K, num / (num + 16 * x ** 4) * math.log1p(math.exp(-0.7)) / math.log(2.0), rtol=1e-14, atol=0)
+    # a constant factor on TPA: the loss is TPA's own (scale invariance)
+    assert abs(M.loss_and_grad(th, F, r2, c, D, off)[0] - M.cosine_loss_of_k(num / (num + 16 * x ** 4), r2, c, D, off)) < 1e-14
+    th[-1] = 0.0                                         # an untrained output layer is TPA exactly
+    assert np.allclose(M.forward(th, F)[0], num / (num + 16 * x ** 4), rtol=1e-15, atol=0)
 
 
 def test_cosine_loss_zero_for_exact_direction_and_bounded():
