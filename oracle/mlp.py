@@ -37,8 +37,11 @@ Loss.  Davidson orthonormalises every correction against the basis, so only the 
 of K.r_n matters: per band the squared cosine between K.r_n and delta*_n,
     L_n = 1 - B_n^2 / (A_n D_n),  A_n = sum_G K_G^2 |r_G|^2,  B_n = sum_G K_G c_G,
     c_G = Re(conj(r_G) delta*_G),  D_n = ||delta*_n||^2,
-and the loss is the mean of L_n over the bands with D_n > 0.  A training sample is thus
-(f_G, |r_G|^2, c_G) with its band's D_n.
+and the loss is the weighted mean sum_n W_n L_n / sum_n W_n over the bands with D_n > 0.
+Reading of the weights: Davidson stops on its LARGEST residual, so a band counts by its share
+of the squared residual of the Ritz pairs it was sampled with, W_n = ||r_n||^2 / sum_m ||r_m||^2
+(sum over the bands of that snapshot with D_m > 0); W_n = 1 gives the plain mean.  A training
+sample is (f_G, |r_G|^2, c_G) with its band's D_n and W_n.
 """
 from __future__ import annotations
 
@@ -140,21 +143,25 @@ def exact_corrections(psi, eps, lam, U, cluster_tol):
 
 
 def samples(kin, psi, res, eps, dstar):
-    """Training samples: features (nb*npw, 3), |r|^2 (nb*npw,), c (nb*npw,), D (nb,)."""
+    """Training samples: features (nb*npw, 3), |r|^2 (nb*npw,), c (nb*npw,), D (nb,), W (nb,)."""
     F = features(kin, psi, res, eps)
     r2 = (np.abs(res) ** 2).reshape(-1)
     c = np.real(np.conj(res) * dstar).reshape(-1)
     D = (np.abs(dstar) ** 2).sum(axis=1)
-    return F, r2, c, D
+    rn2 = (np.abs(res) ** 2).sum(axis=1)
+    W = np.where(D > 0, rn2, 0.0)
+    W = W / W.sum() if W.sum() > 0 else W
+    return F, r2, c, D, W
 
 
 def _segsum(x, band_off):
     return np.add.reduceat(x, band_off[:-1], axis=0)
 
 
-def loss_and_grad(theta, F, r2, c, D, band_off):
-    """Mean cosine loss over the bands with D > 0 and its gradient (NPARAM,).  Samples are
-    grouped by band: band n owns samples band_off[n] .. band_off[n+1]-1."""
+def loss_and_grad(theta, F, r2, c, D, band_off, W=None):
+    """Weighted mean cosine loss over the bands with D > 0 and its gradient (NPARAM,).  Samples
+    are grouped by band: band n owns samples band_off[n] .. band_off[n+1]-1.  W: per-band
+    weights (None = 1)."""
     W1, b1, W2, b2, w3, b3 = unpack(theta)
     band_off = np.asarray(band_off)
     K, (F_, z1, h1, z2, h2, z3) = forward(theta, F)
@@ -162,10 +169,11 @@ def loss_and_grad(theta, F, r2, c, D, band_off):
     A = _segsum(K * K * r2, band_off)
     B = _segsum(K * c, band_off)
     use = D > 0
-    nuse = int(use.sum())
+    Wb = np.where(use, np.ones(D.size) if W is None else np.asarray(W, float), 0.0)
+    wsum = Wb.sum()
     safe = np.where(use, A * D, 1.0)
-    loss = float(np.sum(np.where(use, 1.0 - B * B / safe, 0.0)) / nuse)
-    coef = np.where(use, 2.0 * B / safe, 0.0) / nuse
+    loss = float(np.sum(Wb * np.where(use, 1.0 - B * B / safe, 0.0)) / wsum)
+    coef = Wb * np.where(use, 2.0 * B / safe, 0.0) / wsum
     ratio = np.where(use, B / np.where(use, A, 1.0), 0.0)
     dK = coef[seg] * (ratio[seg] * K * r2 - c)
     dz3 = dK * tpa_k(F[:, 0]) * sigmoid(z3) / math.log(2.0)
@@ -181,10 +189,11 @@ def loss_and_grad(theta, F, r2, c, D, band_off):
     return loss, grad
 
 
-def cosine_loss_of_k(K, r2, c, D, band_off):
+def cosine_loss_of_k(K, r2, c, D, band_off, W=None):
     """The same loss for a given K per sample (e.g. the TPA factor), for comparisons."""
     band_off = np.asarray(band_off)
     A = _segsum(K * K * r2, band_off)
     B = _segsum(K * c, band_off)
     use = D > 0
-    return float(np.sum(np.where(use, 1.0 - B * B / np.where(use, A * D, 1.0), 0.0)) / use.sum())
+    Wb = np.where(use, np.ones(D.size) if W is None else np.asarray(W, float), 0.0)
+    return float(np.sum(Wb * np.where(use, 1.0 - B * B / np.where(use, A * D, 1.0), 0.0)) / Wb.sum())

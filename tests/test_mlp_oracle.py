@@ -37,10 +37,11 @@ def test_param_count_and_layout():
 
 def test_loss_gradient_matches_central_differences():
     F, r2, c, D, off = random_data(1)
+    W = np.random.default_rng(11).uniform(0.1, 1.0, D.size)
     th = M.init_params(3)
     th[192:256] = 0.1                                    # nonzero b1
     th[-1] = 0.3
-    loss, g = M.loss_and_grad(th, F, r2, c, D, off)
+    loss, g = M.loss_and_grad(th, F, r2, c, D, off, W)
     rng = np.random.default_rng(7)
     blocks = [(0, 192), (192, 256), (256, 4352), (4352, 4416), (4416, 4480), (4480, 4481)]
     idx = sorted(set(int(rng.integers(a, b)) for a, b in blocks for _ in range(8)))
@@ -49,7 +50,7 @@ def test_loss_gradient_matches_central_differences():
         tp, tm = th.copy(), th.copy()
         tp[i] += h
         tm[i] -= h
-        fd = (M.loss_and_grad(tp, F, r2, c, D, off)[0] - M.loss_and_grad(tm, F, r2, c, D, off)[0]) / (2 * h)
+        fd = (M.loss_and_grad(tp, F, r2, c, D, off, W)[0] - M.loss_and_grad(tm, F, r2, c, D, off, W)[0]) / (2 * h)
         assert abs(fd - g[i]) <= 1e-7 * max(1e-3, abs(fd)) + 1e-10, (i, fd, g[i])
 
 
@@ -69,6 +70,37 @@ def test_degenerate_network_is_a_scaled_tpa_curve():
     assert abs(M.loss_and_grad(th, F, r2, c, D, off)[0] - M.cosine_loss_of_k(num / (num + 16 * x ** 4), r2, c, D, off)) < 1e-14
     th[-1] = 0.0                                         # an untrained output layer is TPA exactly
     assert np.allclose(M.forward(th, F)[0], num / (num + 16 * x ** 4), rtol=1e-15, atol=0)
+
+
+def test_unit_weights_give_the_plain_mean():
+    F, r2, c, D, off = random_data(12)
+    th = M.init_params(5)
+    l1, g1 = M.loss_and_grad(th, F, r2, c, D, off)
+    l2, g2 = M.loss_and_grad(th, F, r2, c, D, off, np.full(D.size, 3.7))    # any constant weight
+    assert abs(l1 - l2) < 1e-15 and np.allclose(g1, g2, rtol=1e-12, atol=1e-14 * np.abs(g1).max())
+    # a single nonzero weight: that band's own loss
+    K, _ = M.forward(th, F)
+    W = np.zeros(D.size)
+    W[2] = 1.0
+    one = off[2:4]
+    Kb, r2b, cb = K[one[0]:one[1]], r2[one[0]:one[1]], c[one[0]:one[1]]
+    want = 1 - (Kb @ cb) ** 2 / ((Kb * Kb) @ r2b * D[2])
+    assert abs(M.loss_and_grad(th, F, r2, c, D, off, W)[0] - want) < 1e-14
+
+
+def test_snapshot_weights_are_residual_shares():
+    rng = np.random.default_rng(13)
+    nb, npw = 4, 9
+    kin = rng.uniform(0, 3, npw)
+    psi = rng.normal(size=(nb, npw)) + 1j * rng.normal(size=(nb, npw))
+    res = rng.normal(size=(nb, npw)) + 1j * rng.normal(size=(nb, npw))
+    res[1] *= 3.0
+    dstar = rng.normal(size=(nb, npw)) + 1j * rng.normal(size=(nb, npw))
+    dstar[3] = 0.0                                        # dropped band: no weight
+    *_, D, W = M.samples(kin, psi, res, rng.normal(size=nb), dstar)
+    rn2 = (np.abs(res) ** 2).sum(axis=1)
+    assert W[3] == 0.0 and abs(W.sum() - 1.0) < 1e-15
+    assert np.allclose(W[:3], rn2[:3] / rn2[:3].sum(), rtol=1e-15)
 
 
 def test_cosine_loss_zero_for_exact_direction_and_bounded():
