@@ -26,12 +26,13 @@ Features of plane wave G of band n (scale-free):
     l  = log(max(|r_n(G)| sqrt(npw) / ||r_n||, 1e-6))
 
 Exact correction (the training target).  Reading: the correction that would turn the Ritz
-vector psi_n into its component in the exact eigenspace of the eigenvalue nearest eps_n,
-    delta*_n = P_c psi_n / (psi_n^H P_c psi_n) - psi_n,   P_c = sum_{m in cluster} u_m u_m^H,
-the cluster being every exact eigenvalue within `cluster_tol` of the nearest one.  It is
-orthogonal to psi_n, and psi_n + delta*_n lies in the eigenspace; for eps_n -> lambda_n it is
-the exact solution of the Jacobi-Davidson correction equation (Sleijpen & van der Vorst,
-SIAM J. Matrix Anal. Appl. 17, 401 (1996)).
+vector psi_n into its component in the exact eigenspace it converges to,
+    delta*_n = P_c psi_n / (psi_n^H P_c psi_n) - psi_n,   P_c = sum_{m in cluster} u_m u_m^H.
+The n-th lowest Ritz pair of Davidson converges to the n-th lowest eigenpair, so the cluster of
+band n is eigenvalue n together with every eigenvalue within `cluster_tol` of it (degenerate
+partners).  delta*_n is orthogonal to psi_n, psi_n + delta*_n lies in the eigenspace, and for
+eps_n -> lambda_n it is the exact solution of the Jacobi-Davidson correction equation (Sleijpen &
+van der Vorst, SIAM J. Matrix Anal. Appl. 17, 401 (1996)).
 
 Loss.  Davidson orthonormalises every correction against the basis, so only the direction
 of K.r_n matters: per band the squared cosine between K.r_n and delta*_n,
@@ -122,17 +123,16 @@ def features(kin, psi, res, eps):
     return np.stack([x, e, l], axis=-1).reshape(-1, 3)
 
 
-def exact_corrections(psi, eps, lam, U, cluster_tol):
-    """delta*_n for each Ritz vector psi_n (rows) with Ritz value eps_n, from exact eigenpairs
-    (lam ascending, rows of U the unit eigenvectors): the cluster of exact eigenvalues nearest
-    eps_n defines P_c.  A band whose cluster reaches the last given eigenpair may be
+def exact_corrections(psi, lam, U, cluster_tol):
+    """delta*_n for each Ritz vector psi_n (rows, n-th lowest), from exact eigenpairs (lam
+    ascending, rows of U the unit eigenvectors): eigenvalue n and its partners within
+    cluster_tol define P_c.  A band whose cluster reaches the last given eigenpair may be
     incomplete and gets a zero row (weight 0 in the loss)."""
     nb = psi.shape[0]
     nu = lam.size
     out = np.zeros_like(psi)
-    for n in range(nb):
-        m0 = int(np.argmin(np.abs(lam - eps[n])))
-        cl = np.nonzero(np.abs(lam - lam[m0]) <= cluster_tol)[0]
+    for n in range(min(nb, nu)):
+        cl = np.nonzero(np.abs(lam - lam[n]) <= cluster_tol)[0]
         if cl.max() == nu - 1:
             continue                                    # cluster may extend past the given pairs
         Uc = U[cl]                                      # (nc, npw)
