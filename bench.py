@@ -33,7 +33,7 @@ if ROOT not in sys.path:
 METRIC = "Hψ band-applies/s & Davidson time-to-1e-8 Ha: mixed/learned vs FP64 plain"
 UNIT = "band-applies/s"
 WORKLOAD = "si64_cubic_72^3_4k_160b"
-N_FAMILIES = 16
+N_FAMILIES = 18
 
 # ALU peaks from SM count x per-SM FMA rate x max clock:
 #   FP64: the nominal 1.25 TFLOP/s over 152 SMs at 2.07 GHz = 4 flop/clk/SM (2 DFMA/clk/SM)
@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--cpu-sample-bands", type=int, default=48)
     ap.add_argument("--davidson", type=int, default=1, help="also time block Davidson to tol (0: skip)")
     ap.add_argument("--davidson-tol", type=float, default=1e-8)
+    ap.add_argument("--batched", type=int, default=1, help="also time the batched form (0: skip)")
     return ap.parse_args()
 
 
@@ -339,6 +340,82 @@ def run_davidson(args, Q, lib, g, cell, wl64, v, D):
     return out
 
 
+def product_grid(Q, cell):
+    """FFT grid the library's rule gives a cell (a throw-away Gamma-point gspace)."""
+    g = Q.GSpace(cell.lattice, [[0.0, 0.0, 0.0]], cell.ecut_ha, None)
+    grid = tuple(g.grid)
+    g.close()
+    return grid
+
+
+def run_batched(args, Q, S, dev):
+    """The batched form: 256 uneven cells (2-16 atoms, 15-30 Ry, grids 18^3-48^3, 8-48 bands,
+    1-8 k-points) as one persistent launch replayed from a CUDA graph (shape autotuned),
+    against the per-cell loop of qm_hpsi calls, in both precisions."""
+    import torch
+    cells = S.config3_cells(lambda c: product_grid(Q, c))
+    out = {"workload": "256 uneven Si-like cells (2-16 atoms, 15-30 Ry, grids 18^3-48^3, 8-48 bands, 1-8 k)"}
+    stream = torch.cuda.current_stream()
+    for prec in ("mixed", "fp64"):
+        cdt = torch.complex128 if prec == "fp64" else torch.complex64
+        gss, jobs = [], []
+        for cell in cells:
+            g = Q.GSpace(cell.lattice, cell.kpts, cell.ecut_ha, cell.grid)
+            gss.append(g)
+            v = torch.from_numpy(S.vloc_on_grid(cell.lattice, cell.tau, cell.grid, cell.depth, cell.width,
+                                                ortho_period=cell.ortho_period)).to(dev)
+            D = torch.from_numpy(S.dvals(cell.nat)).to(dev)
+            for ik in range(len(cell.kpts)):
+                _, _, kpg = g.indices(ik)
+                psi = torch.from_numpy(S.psi_random(cell.seed, cell.nbnd, g.npw[ik], stream=ik)).to(cdt).to(dev)
+                beta = torch.from_numpy(S.beta_of_q(kpg, cell.tau, cell.omega, cell.rc)).to(cdt).to(dev)
+                jobs.append({"g": g.handle, "ik": ik, "psi": psi, "vloc": v, "beta": beta, "D": D,
+                             "out": torch.empty_like(psi)})
+        t0 = time.time()
+        b = Q.Batch(jobs, prec=prec, stream=stream)
+        tune_s = time.time() - t0
+        info = b.info()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(max(3, args.warmup)):
+            b.run(stream)
+        torch.cuda.synchronize()
+        reps = 10
+        e0.record(stream)
+        for _ in range(reps):
+            b.run(stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        b.check(stream)
+        ms = e0.elapsed_time(e1) / reps
+
+        def loop():
+            for j in jobs:
+                Q.qm_hpsi(j["g"], j["ik"], j["psi"], j["vloc"], j["beta"], j["D"], out=j["out"], prec=prec,
+                          stream=stream)
+        for _ in range(2):
+            loop()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(3):
+            loop()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_loop = e0.elapsed_time(e1) / 3
+        ba = info["band_applies"]
+        out[prec] = {"value": ba / ms * 1e3, "unit": UNIT, "ms_per_replay": ms, "band_applies": ba,
+                     "jobs": len(jobs), "launches_per_replay": 1,
+                     "per_cell_loop": {"value": ba / ms_loop * 1e3, "ms": ms_loop},
+                     "speedup_vs_loop": ms_loop / ms, "shape": {k: info[k] for k in (
+                         "ctas_per_sm", "item_points", "grid", "items", "smem_bytes", "candidates")},
+                     "autotune_s": tune_s, "device_bytes": info["device_bytes"]}
+        b.close()
+        del jobs
+        for g in gss:
+            g.close()
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -363,6 +440,7 @@ def run_ours(args):
         forms[prec] = measure_hpsi(args, Q, lib, g, cell, wl[prec], v, D, world, dev, peaks,
                                    sample_clocks=(prec == "mixed"))
     dav = run_davidson(args, Q, lib, g, cell, wl["fp64"], v, D) if args.davidson else None
+    batched = run_batched(args, Q, S, dev) if args.batched else None
     if rank == 0:
         head = forms["mixed"]
         line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -377,6 +455,7 @@ def run_ours(args):
                                                                   "kernels", "gpu_launches")},
                           "mixed_over_fp64": head["value"] / forms["fp64"]["value"]},
                 "davidson": dav,
+                "batched": batched,
                 "cpu_baseline": oracle_sample(args.cpu_sample_bands)}
         print(json.dumps(line))
     g.close()

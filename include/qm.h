@@ -259,7 +259,9 @@ typedef struct {
                             re-orthonormalised and H applied to them in FP64, and the iterations
                             continue in FP64 to tol.  Eigensolves, residual norms and band
                             energies are FP64 in both. */
-    int precond;         /* 0 = Teter-Payne-Allan diagonal preconditioner */
+    int precond;         /* 0 = Teter-Payne-Allan diagonal preconditioner; 1 = learned (the network
+                            `mlp`), with TPA taking over for the rest of the call if the largest
+                            residual fails to fall below precond_stall x its value 4 steps earlier */
     double mixed_switch; /* QM_MIXED: residual (Ha) where FP64 takes over (or earlier if the
                             residual, once below 1e-3, stops halving over 10 steps); 0 -> 1e-4 */
     int nconv;           /* only the lowest nconv bands must reach tol (1..nb; 0 -> nb); the
@@ -267,6 +269,9 @@ typedef struct {
     int reserved;        /* must be 0 */
     double* history;     /* host, may be NULL: max_iter doubles, the largest residual among the
                             nconv bands after each Rayleigh-Ritz step */
+    const float* mlp;    /* precond = 1: device, QM_MLP_NPARAM floats (see qm_mlp_forward) */
+    double precond_stall; /* precond = 1: stall ratio of the fallback rule; 0 -> 0.8, >= 1: never
+                             fall back */
 } qm_davidson_opts;
 
 /* Counters of one qm_davidson call (the paper's "H-psi calls" are band_applies / nb). */
@@ -278,6 +283,8 @@ typedef struct {
     double seconds;          /* host wall time of the call */
     int iterations_mixed;    /* QM_MIXED: Rayleigh-Ritz steps taken in the FP32 phase */
     long long band_applies_mixed;  /* QM_MIXED: H psi applications done in FP32 */
+    int precond_fallback;    /* precond = 1: Rayleigh-Ritz step after which TPA replaced the
+                                network (0: the network was used throughout) */
 } qm_davidson_stats;
 
 /*
@@ -326,12 +333,67 @@ qm_status qm_eigh_lowest(int m, int nev, const void* A, int lda, double* evals, 
                          void* stream);
 
 /*
+ * Learned preconditioner (the learned form): a network K(f) > 0 on per-plane-wave features
+ * replaces the Teter-Payne-Allan factor in the Davidson correction, delta_n(G) = K(f_nG) r_n(G).
+ *
+ * Network: z1 = W1 f + b1, h1 = silu(z1), z2 = W2 h1 + b2, h2 = silu(z2), z3 = w3 . h2 + b3,
+ * K = K_TPA(x) softplus(z3) / log 2, silu(z) = z / (1 + e^-z): a positive factor on the TPA
+ * curve K_TPA(x) = (27+18x+12x^2+8x^3)/(27+18x+12x^2+8x^3+16x^4); z3 = 0 gives TPA exactly.  Parameters: one device array of QM_MLP_NPARAM
+ * floats, W1 (64 x 3, row-major W1[j][k]) | b1 (64) | W2 (64 x 64, W2[j][i], j output) | b2 (64)
+ * | w3 (64) | b3 (1).  Arithmetic: BF16 weights, features and hidden activations, FP32
+ * accumulation (the 64 x 64 layer of inference on the tensor cores, tcgen05).
+ * Features of plane wave G of band n (scale-free): x = T_G / T_n with T_G = |k+G|^2/2 and T_n
+ * the band's kinetic energy per unit norm; e = eps_n / T_n (Ritz value); l =
+ * log(max(|r_n(G)| sqrt(npw) / ||r_n||, 1e-6)).
+ * Training target: the exact correction delta*_n = P_c psi_n / (psi_n^H P_c psi_n) - psi_n,
+ * P_c the projector on the exact eigenspace of eigenvalue n (with its degenerate partners); loss: the mean over bands of
+ * 1 - cos^2 between K.r_n and delta*_n (only the direction matters to Davidson), weighted by
+ * W_n: sum_n W_n (1 - cos^2_n) / sum_n W_n.  A sample is (features, |r_G|^2, c_G =
+ * Re(conj(r_G) delta*_G)); a band adds D_n = ||delta*_n||^2 (D_n = 0 excludes it) and its weight
+ * W_n.  Samples are grouped by band: band b owns samples band_off[b] .. band_off[b+1]-1.
+ */
+#define QM_MLP_NPARAM 4481
+
+/* qm_mlp_forward - K for n feature rows (device feats[3n], theta; K out, n floats).
+ * Synchronous.  Errors: QM_ERR_ARG, QM_ERR_CUDA, QM_ERR_TIMEOUT. */
+qm_status qm_mlp_forward(long long n, const float* feats, const float* theta, float* K, void* stream);
+
+/* qm_mlp_pairs - training samples of n Ritz pairs of k-point ik from exact eigenpairs.
+ *  psi, hpsi   device, n rows (ld_psi, ld_hpsi >= npw) complex double: Ritz vectors and H psi.
+ *  eps         device, n Ritz values.
+ *  U, lam      device: nu exact unit eigenvectors (rows, ld_u >= npw) and eigenvalues, ascending.
+ *  cluster_tol band n (the n-th lowest Ritz pair) targets eigenvalue n and its partners within
+ *              cluster_tol; a band whose cluster reaches lam[nu-1] (or n >= nu) gets D = 0.
+ *  feats       device, n*npw*3 floats; r2, c: n*npw floats; D, W: n floats (band-major samples).
+ *              W_n = ||r_n||^2 / sum_m ||r_m||^2 over the call's bands with D_m > 0 (0 where
+ *              D_n = 0): Davidson stops on its largest residual, so the bands that carry it weigh most.
+ * Synchronous (allocates temporaries with cudaMallocAsync). */
+qm_status qm_mlp_pairs(qm_gspace g, int ik, int n, const void* psi, int ld_psi, const void* hpsi, int ld_hpsi,
+                       const double* eps, int nu, const void* U, int ld_u, const double* lam,
+                       double cluster_tol, float* feats, float* r2, float* c, float* D, float* W, void* stream);
+
+/* qm_mlp_loss_grad - loss (host double) and its gradient (device, QM_MLP_NPARAM floats) over
+ * the samples; band_off: device, nband + 1 long longs; W: device, nband floats or NULL (all 1).
+ * Synchronous. */
+qm_status qm_mlp_loss_grad(int nband, const long long* band_off, const float* feats, const float* r2,
+                           const float* c, const float* D, const float* W, const float* theta, double* loss,
+                           float* grad, void* stream);
+
+/* qm_mlp_train - `steps` full-batch Adam steps (beta1 0.9, beta2 0.999, eps 1e-8, step size
+ * lr) on theta (device, updated in place) with the BF16 forward and backward kernels;
+ * loss_history (host, may be NULL) receives steps + 1 losses (before each step and at the end).
+ * Synchronous. */
+qm_status qm_mlp_train(int nband, const long long* band_off, const float* feats, const float* r2,
+                       const float* c, const float* D, const float* W, float* theta, int steps, double lr,
+                       double* loss_history, void* stream);
+
+/*
  * Instrumentation (not part of the paper's method; used by benchmarks).
  *  qm_launch_count  number of CUDA kernels this library has launched in this process.
  *  qm_prof_enable   on != 0: from now on record a pair of CUDA events on the launch stream
  *                   around every kernel launch; resets the accumulated times (any value).
  *  qm_prof_read     waits for the recorded events and returns, for kernel family
- *                   `family` (0 <= family < 17), the summed device time in ms and the number
+ *                   `family` (0 <= family < 18), the summed device time in ms and the number
  *                   of launches timed since the last qm_prof_enable.
  *  qm_prof_name     name of a kernel family ("" when out of range).
  */

@@ -59,14 +59,15 @@ class DavidsonOpts(ctypes.Structure):
     """qm_davidson_opts of include/qm.h."""
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("nvecx", ctypes.c_int),
                 ("prec", ctypes.c_int), ("precond", ctypes.c_int), ("mixed_switch", ctypes.c_double),
-                ("nconv", ctypes.c_int), ("reserved", ctypes.c_int), ("history", c_double_p)]
+                ("nconv", ctypes.c_int), ("reserved", ctypes.c_int), ("history", c_double_p),
+                ("mlp", ctypes.c_void_p), ("precond_stall", ctypes.c_double)]
 
 
 class DavidsonStats(ctypes.Structure):
     """qm_davidson_stats of include/qm.h."""
     _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("band_applies", ctypes.c_longlong),
                 ("max_residual", ctypes.c_double), ("seconds", ctypes.c_double), ("iterations_mixed", ctypes.c_int),
-                ("band_applies_mixed", ctypes.c_longlong)]
+                ("band_applies_mixed", ctypes.c_longlong), ("precond_fallback", ctypes.c_int)]
 
 
 SIGNATURES["qm_davidson"] = (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
@@ -108,3 +109,19 @@ SIGNATURES["qm_batch_run"] = (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p])
 SIGNATURES["qm_batch_check"] = (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p])
 SIGNATURES["qm_batch_query"] = (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(BatchInfo)])
 SIGNATURES["qm_batch_destroy"] = (None, [ctypes.c_void_p])
+
+
+QM_MLP_NPARAM = 4481
+SIGNATURES["qm_mlp_forward"] = (ctypes.c_int, [ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                               ctypes.c_void_p])
+SIGNATURES["qm_mlp_pairs"] = (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                             ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                             ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_double,
+                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_void_p])
+SIGNATURES["qm_mlp_loss_grad"] = (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                 c_double_p, ctypes.c_void_p, ctypes.c_void_p])
+SIGNATURES["qm_mlp_train"] = (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_int, ctypes.c_double, c_double_p, ctypes.c_void_p])

@@ -124,7 +124,7 @@ def qm_hpsi(g, ik, psi, vloc, beta, D, out=None, prec="fp64", stream=None):
 
 
 def qm_davidson(g, ik, psi, vloc, beta, D, tol=1e-8, max_iter=100, nvecx=0, prec="fp64", stream=None,
-                raise_not_converged=True, mixed_switch=0.0, nconv=0):
+                raise_not_converged=True, mixed_switch=0.0, nconv=0, mlp=None, precond_stall=0.0):
     """Lowest nb eigenpairs; psi (nb, >=npw) complex128 CUDA tensor is overwritten by the
     Ritz vectors.  Returns (eigenvalues ndarray (nb,), stats dict)."""
     lib = _lib.load()
@@ -133,8 +133,10 @@ def qm_davidson(g, ik, psi, vloc, beta, D, tol=1e-8, max_iter=100, nvecx=0, prec
     nb = int(psi.shape[0])
     nproj = 0 if beta is None else int(beta.shape[0])
     hist = np.zeros(max(1, int(max_iter)), np.float64)
-    opts = _lib.DavidsonOpts(tol=float(tol), max_iter=int(max_iter), nvecx=int(nvecx), prec=_PREC[prec], precond=0,
-                             mixed_switch=float(mixed_switch), nconv=int(nconv), history=_dp(hist))
+    opts = _lib.DavidsonOpts(tol=float(tol), max_iter=int(max_iter), nvecx=int(nvecx), prec=_PREC[prec],
+                             precond=0 if mlp is None else 1, mixed_switch=float(mixed_switch), nconv=int(nconv),
+                             history=_dp(hist), mlp=_dev_ptr(mlp, "mlp", torch.float32),
+                             precond_stall=float(precond_stall))
     stats = _lib.DavidsonStats()
     eig = np.zeros(nb, np.float64)
     st = lib.qm_davidson(g, int(ik), nb, _dev_ptr(psi, "psi", torch.complex128), int(psi.stride(0)),
@@ -145,6 +147,7 @@ def qm_davidson(g, ik, psi, vloc, beta, D, tol=1e-8, max_iter=100, nvecx=0, prec
     info = {"iterations": stats.iterations, "converged": bool(stats.converged),
             "band_applies": stats.band_applies, "max_residual": stats.max_residual, "seconds": stats.seconds,
             "iterations_mixed": stats.iterations_mixed, "band_applies_mixed": stats.band_applies_mixed,
+            "precond_fallback": stats.precond_fallback,
             "history": hist[: max(0, stats.iterations)].tolist(),
             "status": STATUS.get(st, st)}
     if st != 0 and not (st == 4 and not raise_not_converged):
@@ -277,3 +280,65 @@ class Batch:
 
 def qm_batch_create(jobs, prec="fp64", ctas_per_sm=0, item_points=0, stream=None):
     return Batch(jobs, prec=prec, ctas_per_sm=ctas_per_sm, item_points=item_points, stream=stream)
+
+
+QM_MLP_NPARAM = 4481   # include/qm.h
+
+
+def qm_mlp_forward(feats, theta, stream=None):
+    """K for the (n, 3) float32 feature rows (CUDA tensors); theta (QM_MLP_NPARAM,) float32."""
+    if feats.dim() != 2 or feats.shape[1] != 3 or not feats.is_contiguous():
+        raise ValueError("feats must be a contiguous (n, 3) tensor")
+    K = torch.empty(feats.shape[0], dtype=torch.float32, device=feats.device)
+    _check(_lib.load().qm_mlp_forward(int(feats.shape[0]), _dev_ptr(feats, "feats", torch.float32),
+                                      _dev_ptr(theta, "theta", torch.float32), _dev_ptr(K, "K", torch.float32),
+                                      _stream_ptr(stream)))
+    return K
+
+
+def qm_mlp_pairs(g, ik, psi, hpsi, eps, U, lam, cluster_tol=1e-6, stream=None):
+    """Training samples of the Ritz pairs (psi, eps) with H psi = hpsi against the exact
+    eigenpairs (U rows, lam ascending); all complex128/float64 CUDA tensors.
+    Returns (feats (n*npw, 3), r2 (n*npw,), c (n*npw,), D (n,), W (n,)) float32 CUDA tensors."""
+    n, npw = int(psi.shape[0]), None
+    info = qm_gspace_query(g)
+    npw = info["npw"][ik]
+    dev = psi.device
+    feats = torch.empty((n * npw, 3), dtype=torch.float32, device=dev)
+    r2 = torch.empty(n * npw, dtype=torch.float32, device=dev)
+    c = torch.empty(n * npw, dtype=torch.float32, device=dev)
+    D = torch.empty(n, dtype=torch.float32, device=dev)
+    W = torch.empty(n, dtype=torch.float32, device=dev)
+    _check(_lib.load().qm_mlp_pairs(g, int(ik), n, _dev_ptr(psi, "psi", torch.complex128), int(psi.stride(0)),
+                                    _dev_ptr(hpsi, "hpsi", torch.complex128), int(hpsi.stride(0)),
+                                    _dev_ptr(eps, "eps", torch.float64), int(U.shape[0]),
+                                    _dev_ptr(U, "U", torch.complex128), int(U.stride(0)),
+                                    _dev_ptr(lam, "lam", torch.float64), float(cluster_tol),
+                                    _dev_ptr(feats, "feats"), _dev_ptr(r2, "r2"), _dev_ptr(c, "c"), _dev_ptr(D, "D"),
+                                    _dev_ptr(W, "W"), _stream_ptr(stream)))
+    return feats, r2, c, D, W
+
+
+def qm_mlp_loss_grad(band_off, feats, r2, c, D, theta, W=None, stream=None):
+    """(loss float, grad (QM_MLP_NPARAM,) float32 CUDA tensor); band_off int64 CUDA tensor;
+    W per-band weights (None: all 1)."""
+    grad = torch.empty(QM_MLP_NPARAM, dtype=torch.float32, device=theta.device)
+    loss = np.zeros(1, np.float64)
+    _check(_lib.load().qm_mlp_loss_grad(int(band_off.numel()) - 1, _dev_ptr(band_off, "band_off", torch.int64),
+                                        _dev_ptr(feats, "feats", torch.float32), _dev_ptr(r2, "r2", torch.float32),
+                                        _dev_ptr(c, "c", torch.float32), _dev_ptr(D, "D", torch.float32),
+                                        _dev_ptr(W, "W", torch.float32), _dev_ptr(theta, "theta", torch.float32), _dp(loss),
+                                        _dev_ptr(grad, "grad", torch.float32), _stream_ptr(stream)))
+    return float(loss[0]), grad
+
+
+def qm_mlp_train(band_off, feats, r2, c, D, theta, steps, lr, W=None, stream=None):
+    """Adam steps on theta (updated in place); returns the loss history (steps + 1,)."""
+    hist = np.zeros(int(steps) + 1, np.float64)
+    _check(_lib.load().qm_mlp_train(int(band_off.numel()) - 1, _dev_ptr(band_off, "band_off", torch.int64),
+                                    _dev_ptr(feats, "feats", torch.float32), _dev_ptr(r2, "r2", torch.float32),
+                                    _dev_ptr(c, "c", torch.float32), _dev_ptr(D, "D", torch.float32),
+                                    _dev_ptr(W, "W", torch.float32), _dev_ptr(theta, "theta", torch.float32),
+                                    int(steps), float(lr), _dp(hist),
+                                    _stream_ptr(stream)))
+    return hist

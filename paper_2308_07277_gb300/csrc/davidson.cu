@@ -274,6 +274,8 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
     if (o.prec != QM_FP64 && o.prec != QM_MIXED) return fail(QM_ERR_ARG, "qm_davidson: unknown precision");
     if (!(o.mixed_switch > 0.0)) o.mixed_switch = 1e-4;
     if (o.nconv <= 0 || o.nconv > nb) o.nconv = nb;
+    if (o.precond != 0 && o.precond != 1) return fail(QM_ERR_ARG, "qm_davidson: unknown preconditioner");
+    if (o.precond == 1 && !o.mlp) return fail(QM_ERR_ARG, "qm_davidson: learned preconditioner without parameters");
 
     qm_status st = ensure_device(g);
     if (st) return st;
@@ -359,6 +361,12 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
     if (kept < nb) return fail(QM_ERR_NUMERIC, "qm_davidson: initial psi block is rank deficient");
     if ((st = run.hpsi(w.V, w.HV, nb))) return st;
     int m = nb, m0 = 0;
+    bool use_mlp = o.precond == 1;
+    const double stall = o.precond_stall > 0.0 ? o.precond_stall : 0.8;
+    int fallback_it = 0;
+    std::vector<double> hist_all;
+    int* mlp_err = w.info + 2;
+    if (use_mlp && (st = cuda_check(cudaMemsetAsync(mlp_err, 0, sizeof(int), s), "reset error word"))) return st;
     std::vector<double> rn2(nb), eps(nb);
     int it = 0, it_mixed = 0;
     std::vector<double> hist_mixed;
@@ -405,6 +413,12 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
             if (r > o.tol) unc.push_back(n);
         }
         if (o.history && it - 1 < o.max_iter) o.history[it - 1] = max_res;
+        hist_all.push_back(max_res);
+        // the learned correction hands over to TPA when the residual stalls
+        if (use_mlp && stall < 1.0 && hist_all.size() > 4 && max_res > stall * hist_all[hist_all.size() - 5]) {
+            use_mlp = false;
+            fallback_it = it;
+        }
         if (run.mixed) hist_mixed.push_back(max_res);
         // FP32 round-off can only stall the residual well below 1e-3: there, no halving over the
         // last 10 FP32 iterations hands over to FP64 early
@@ -430,7 +444,10 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
         if (it == o.max_iter) break;
         const int nu = (int)unc.size();
         cudaMemcpyAsync(w.sel, unc.data(), sizeof(int) * nu, cudaMemcpyHostToDevice, s);
-        {
+        if (use_mlp) {
+            if ((st = mlp_precond_apply(o.mlp, w.R, ld, npw, w.sel, nu, w.tk, w.eps, w.rn2, kin, w.Dl, ld, mlp_err, s)))
+                return st;
+        } else {
             ProfScope pf(PF_OTHER, s);
             k_tpa<<<dim3((npw + 255) / 256 < 64 ? (npw + 255) / 256 : 64, nu), 256, 0, s>>>(w.R, ld, npw, w.sel, w.tk,
                                                                                             kin, w.Dl, ld);
@@ -466,6 +483,12 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
         (st = cuda_check(cudaStreamSynchronize(s), "stream sync")))
         return st;
     for (int n = 0; n < nb; ++n) eig_out[n] = eps[n];
+    if (o.precond == 1) {
+        int e = 0;
+        if ((st = cuda_check(cudaMemcpy(&e, mlp_err, sizeof(int), cudaMemcpyDeviceToHost), "D2H error word")))
+            return st;
+        if (e) return fail(QM_ERR_TIMEOUT, "qm_davidson: a bounded tensor-core wait of the learned preconditioner expired");
+    }
     if (stats) {
         stats->iterations = it > o.max_iter ? o.max_iter : it;
         stats->band_applies = run.applies;
@@ -474,6 +497,7 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
         stats->converged = converged ? 1 : 0;
         stats->iterations_mixed = run.mixed ? stats->iterations : it_mixed;
         stats->band_applies_mixed = run.applies_mixed;
+        stats->precond_fallback = fallback_it;
     }
     if (!converged) return fail(QM_ERR_NOT_CONVERGED, "qm_davidson: max_iter reached before tol");
     return QM_OK;

@@ -25,7 +25,7 @@ static long long g_cnt[kProfFamilies];
 static const char* kNames[kProfFamilies] = {"k_vt", "k_stick_inverse", "k_plane", "k_stick_forward",
                                             "k_gemm_cn", "k_reduce_splits", "k_gemm_tn", "other", "k_chol",
                                             "k_tridiag", "k_multisect", "k_inviter", "k_backtransf", "k_convert",
-                                            "k_umma_bf16x3", "k_split", "k_batch"};
+                                            "k_umma_bf16x3", "k_split", "k_batch", "k_mlp"};
 
 static cudaEvent_t get_event() {
     if (!g_pool.empty()) {

@@ -90,7 +90,7 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // ---- launch counting / per-kernel timing (prof.cpp) ----
 enum ProfFamily { PF_VT = 0, PF_STICK_INV, PF_PLANE, PF_STICK_FWD, PF_GEMM_CN, PF_REDUCE, PF_GEMM_TN, PF_OTHER, PF_CHOL,
-                  PF_TRIDIAG, PF_MULTISECT, PF_INVITER, PF_BACKTR, PF_CONVERT, PF_UMMA, PF_SPLIT, PF_BATCH,
+                  PF_TRIDIAG, PF_MULTISECT, PF_INVITER, PF_BACKTR, PF_CONVERT, PF_UMMA, PF_SPLIT, PF_BATCH, PF_MLP,
                   kProfFamilies };
 void count_launch(int n);
 // Counts one launch; when timing is enabled records CUDA events on `s` around the scope.
@@ -161,6 +161,13 @@ qm_status nonlocal_bf16x3(int nproj, int nb, int npw, const float2* beta, int ld
                           int ld_psi, const double* D, float2* out, int ld_out, void* work, int* err,
                           cudaStream_t s);
 size_t nonlocal_bf16x3_bytes(int nproj, int nb, int npw);
+
+// ---- learned preconditioner (mlp.cu) ----
+// out_j(G) = K(f) R[sel[j]](G) for j < nu: the network's correction of the Davidson step;
+// tk, eps, rn2: per band T_n, Ritz value, ||r_n||^2 (device); err: device int set on a timed-out wait
+qm_status mlp_precond_apply(const float* theta, const double2* R, int ld, int npw, const int* sel, int nu,
+                            const double* tk, const double* eps, const double* rn2, const double* kin, double2* out,
+                            int ldo, int* err, cudaStream_t s);
 
 // upper bound of the split-K partial buffer any gemm_cn call needs
 size_t gemm_cn_partial_bytes(bool fp32);

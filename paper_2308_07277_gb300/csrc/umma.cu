@@ -27,6 +27,7 @@
 #include <algorithm>
 
 #include "qm_internal.h"
+#include "tc_util.cuh"
 
 namespace qm {
 namespace {
@@ -37,36 +38,10 @@ constexpr int STAGE_BYTES = 6 * TILE_BYTES;      // A and B, 3 components each
 constexpr int kThreads = 256;
 constexpr long kSpinLimit = 1L << 26;            // bounded mbarrier waits
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-// shared-memory matrix descriptor: no swizzle, K-major; lbo = byte stride between core
-// matrices along K, sbo = byte stride between 8-row groups
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-    d |= (uint64_t)1 << 46;  // descriptor version (fixed 0b001)
-    return d;                // base offset 0, relative LBO, swizzle none
-}
-
-// instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M x N
-constexpr uint32_t idesc_bf16(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
-    for (long i = 0; i < kSpinLimit; ++i) {
-        uint32_t done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(mbar), "r"(phase)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
+using tc::idesc_bf16;
+using tc::sdesc;
+using tc::smem_u32;
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) { return tc::mbar_wait(mbar, phase, kSpinLimit); }
 
 __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b) {
     return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
