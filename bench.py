@@ -6,9 +6,11 @@ One step = H psi applied to every band at every k-point (640 band-applies) throu
 C ABI (qm_hpsi).  The headline `value` is the precision form (FP32 FFT path and FP32
 nonlocal GEMMs, QM_MIXED); the plain FP64 form is measured the same way under
 `forms.fp64`.  The `davidson` object times block Davidson to a 1e-8 Ha residual at all 4
-k-points for the plain FP64 form and the mixed-precision forms.  Prints one JSON line.
+k-points for the plain FP64 form and the mixed-precision forms; the `batched` object times the
+batched form (256 uneven cells in one persistent launch) against the per-cell loop.  Prints
+one JSON line.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--davidson 0|1] [--impl reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--davidson 0|1] [--batched 0|1] [--impl reference]
 
 --impl reference times the FP64 CPU oracle (numpy, one thread) on a bounded sample of the
 same workload: a deliberately slow baseline, not a competitor.
@@ -40,6 +42,11 @@ N_FAMILIES = 18
 #   FP32: 128 FMA/clk/SM
 N_SM = 152
 FLOP_PER_CLK_SM = {"fp64": 4, "mixed": 256}
+
+# DRAM bytes per band of a dominant kernel, from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum) of the current kernel: k_plane<float>, one 57-band launch of this
+# workload, 29.3 MB read + 18.9 MB written.  Scaled to a launch by its band count.
+TRAFFIC_PER_BAND = {("k_plane", "mixed"): (29.3e6 + 18.9e6) / 57}
 
 
 def parse():
@@ -291,7 +298,9 @@ def measure_hpsi(args, Q, lib, g, cell, wl, v, D, world, dev, peaks, sample_cloc
             roof["frac"] = roof["achieved"] / roof["peak"]
         else:
             roof = {"bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"), "unit": "GB/s", "frac": None}
-        roof.update({"kernel": name, "traffic": None, "avg_launch_ms": avg_ms,
+        tpb = TRAFFIC_PER_BAND.get((name, wl.prec))
+        traffic = tpb * nb * nk / per_step if tpb else None
+        roof.update({"kernel": name, "traffic": traffic, "avg_launch_ms": avg_ms,
                      "peak_source": "derived: %d SMs x %d flop/clk/SM x %.0f MHz" % (
                          N_SM, FLOP_PER_CLK_SM[wl.prec], smax / 1e6)})
     return {"value": band_applies / (ms * 1e-3), "ms_per_step": ms, "gpu_launches": launches, "kernels": fam,
