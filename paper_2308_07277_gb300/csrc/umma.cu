@@ -17,7 +17,7 @@
 // The operands are read as FP32 complex from global memory and split / expanded on the fly
 // into shared memory (canonical no-swizzle K-major layout of 8 x 16-byte core matrices), so no
 // split copy ever goes to HBM.  Two shared-memory stages: while the tensor core multiplies
-// tile k (one thread issues 6 products x 4 K-steps of tcgen05.mma, M = N = 128, K = 16, into a
+// tile k (one thread issues 6 products x 2 K-steps of tcgen05.mma, M = N = 128, K = 16, into a
 // 128-column FP32 accumulator in tensor memory, then commits to the stage's mbarrier), the
 // CTA's loads of tile k+1 are in flight and are split into the other stage.  Every mbarrier wait is bounded and sets an error word
 // instead of hanging.  The epilogue reads the accumulator with tcgen05.ld.
@@ -32,7 +32,8 @@
 namespace qm {
 namespace {
 
-constexpr int UM = 128, UN = 128, UK = 64;       // CTA tile: M x N x K (K in real elements)
+constexpr int UM = 128, UN = 128, UK = 32;       // CTA tile: M x N x K (K in real elements)
+constexpr int KCH = UK / 8;                      // 16-byte K chunks per core-matrix row
 constexpr int TILE_BYTES = UM * UK * 2;          // one BF16 split component of one operand tile
 constexpr int STAGE_BYTES = 6 * TILE_BYTES;      // A and B, 3 components each
 constexpr int kThreads = 256;
@@ -67,14 +68,15 @@ __device__ __forceinline__ void put_pair(unsigned char* dst, int off, float x, f
     *reinterpret_cast<uint32_t*>(dst + 2 * TILE_BYTES + off) = c2;
 }
 
-// Operand sources (FP32 complex in global memory).  A tile covers 128 real rows and 64 real
-// K columns = 32 complex columns: 16 row groups x 8 K chunks = 128 core matrices of 8 rows x
-// 16 bytes.  Each warp fills one core matrix per step (16 per tile), lane i writing the i-th
+// Operand sources (FP32 complex in global memory).  A tile covers 128 real rows and UK = 32
+// real K columns = 16 complex columns: 16 row groups x 4 K chunks = 64 core matrices of 8 rows
+// x 16 bytes (96 KB of shared memory for both stages, so two CTAs fit on an SM).  Each warp
+// fills one core matrix per step (8 per tile), lane i writing the i-th
 // 4-byte word (one (re, im) pair of BF16) of each split component, so the shared-memory stores
 // are free of bank conflicts.  fetch() issues the tile's global loads into registers;
 // stash() splits them into shared memory.  Fetching tile k+1 before the products of tile k are
 // issued hides the global latency behind the tensor core.
-constexpr int kCmPerWarp = 128 / (kThreads / 32);
+constexpr int kCmPerWarp = 16 * KCH / (kThreads / 32);  // 16 row groups x KCH chunks per tile
 
 __device__ __forceinline__ void put_word(unsigned char* dst, int cm, int lane, float x, float y) {
     put_pair(dst, cm * 128 + lane * 4, x, y);
@@ -89,7 +91,7 @@ struct PlainRows {  // rows = complex rows of src, K = the complex columns (inte
 #pragma unroll
         for (int it = 0; it < kCmPerWarp; ++it) {
             const int cm = warp + 8 * it;
-            const int gr = r0 + (cm >> 3) * 8 + (lane >> 2), gk = kc0 + (cm & 7) * 4 + (lane & 3);
+            const int gr = r0 + (cm / KCH) * 8 + (lane >> 2), gk = kc0 + (cm % KCH) * 4 + (lane & 3);
             v[it] = (gr < rows && gk < K) ? __ldg(src + (size_t)gr * ld + gk) : make_float2(0.f, 0.f);
         }
     }
@@ -113,7 +115,7 @@ struct ExpandRows {  // B rows from complex rows of src (conj_a: pattern of conj
 #pragma unroll
         for (int it = 0; it < kCmPerWarp; ++it) {
             const int cm = warp + 8 * it;
-            const int gr = (r0 >> 1) + (cm >> 3) * 4 + (lane >> 3), gk = kc0 + (cm & 7) * 4 + ((lane >> 1) & 3);
+            const int gr = (r0 >> 1) + (cm / KCH) * 4 + (lane >> 3), gk = kc0 + (cm % KCH) * 4 + ((lane >> 1) & 3);
             v[it] = (gr < rows && gk < K) ? __ldg(src + (size_t)gr * ld + gk) : make_float2(0.f, 0.f);
         }
     }
@@ -143,7 +145,7 @@ struct ExpandTRows {  // B = src^T expanded: src [P][G] (G contiguous); rows 2g,
 #pragma unroll
         for (int it = 0; it < kCmPerWarp; ++it) {
             const int cm = warp + 8 * it;
-            const int gg = (r0 >> 1) + (cm >> 3) * 4 + (lane >> 3), gp = kc0 + (cm & 7) * 4 + ((lane >> 1) & 3);
+            const int gg = (r0 >> 1) + (cm / KCH) * 4 + (lane >> 3), gp = kc0 + (cm % KCH) * 4 + ((lane >> 1) & 3);
             v[it] = (gp < P && gg < G) ? __ldg(src + (size_t)gp * ld + gg) : make_float2(0.f, 0.f);
         }
     }
@@ -226,8 +228,8 @@ k_umma_split(LA la, LB lb, int M, int N, int ktiles_per_split, int ktiles_total,
             for (int q = 0; q < 6; ++q) {
 #pragma unroll
                 for (int ks = 0; ks < UK / 16; ++ks) {
-                    const uint64_t da = sdesc(smem_u32(sA + pa[q] * TILE_BYTES) + ks * 256, 128, 1024);
-                    const uint64_t db = sdesc(smem_u32(sB + pb[q] * TILE_BYTES) + ks * 256, 128, 1024);
+                    const uint64_t da = sdesc(smem_u32(sA + pa[q] * TILE_BYTES) + ks * 256, 128, KCH * 128);
+                    const uint64_t db = sdesc(smem_u32(sB + pb[q] * TILE_BYTES) + ks * 256, 128, KCH * 128);
                     const uint32_t acc = (kt > kt0 || q > 0 || ks > 0) ? 1u : 0u;
                     asm volatile(
                         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
@@ -293,16 +295,18 @@ k_umma_split(LA la, LB lb, int M, int N, int ktiles_per_split, int ktiles_total,
 __global__ void k_reduce_proj(const float* __restrict__ part, int Z, size_t zstride, int ldc, int nproj, int nb,
                               const double* __restrict__ D, float2* __restrict__ Pd) {
     const size_t total = (size_t)nb * nproj;
+    // consecutive threads take consecutive bands: the (re, im) pairs of one partial row are
+    // contiguous, so every load of the split loop is coalesced
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-        const int b = (int)(e / nproj), p = (int)(e % nproj);
+        const int p = (int)(e / nb), b = (int)(e % nb);
         float sr = 0.f, si = 0.f;
         for (int z = 0; z < Z; ++z) {
-            const float* q = part + (size_t)z * zstride + (size_t)p * ldc + 2 * b;
-            sr += q[0];
-            si += q[1];
+            const float2 q = __ldg(reinterpret_cast<const float2*>(part + (size_t)z * zstride + (size_t)p * ldc) + b);
+            sr += q.x;
+            si += q.y;
         }
         const float d = (float)D[p];
-        Pd[e] = make_float2(d * sr, d * si);
+        Pd[(size_t)b * nproj + p] = make_float2(d * sr, d * si);
     }
 }
 
@@ -343,7 +347,7 @@ qm_status nonlocal_bf16x3(int nproj, int nb, int npw, const float2* beta, int ld
     float2* Pd = (float2*)((char*)work + rup((size_t)kMaxUmmaSplits * rP * r2B * 4, 256));
     // projection: C'[p][2b + t] = <beta_p | psi_b>, split over K (2 npw real columns)
     const int tiles = (int)((rP / UM) * (r2B / UN));
-    const int splits = std::max(1, std::min(kMaxUmmaSplits, 152 / std::max(1, tiles)));
+    const int splits = std::max(1, std::min(kMaxUmmaSplits, 2 * 152 / std::max(1, tiles)));  // 2 CTAs per SM
     const size_t zstride = rP * r2B;
     PlainRows la{beta, ld_beta, nproj, npw};
     ExpandRows lb{psi, ld_psi, nb, npw, 1};
