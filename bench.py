@@ -288,21 +288,33 @@ def measure_hpsi(args, Q, lib, g, cell, wl, v, D, world, dev, peaks, sample_cloc
         smax = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
         fl_pk = FLOP_PER_CLK_SM[wl.prec] * N_SM * smax / 1e12
         fl = None
+        bound = "alu"
         if name == "k_plane":
             fl = sum(nb * cell.grid[0] * fft_flops_per_plane(cell.grid, wl.nrow[ik]) for ik in range(nk))
         elif name in ("k_gemm_tn", "k_gemm_cn"):
             fl = 8.0 * nproj * nb * sum(g.npw)   # 8 flops per complex multiply-add, all k
+        elif name == "k_umma_bf16x3":
+            # projection + application, 8 flops per complex multiply-add each, counted once
+            # (the tensor core issues 6 BF16 products per useful one); BF16 sustained peak
+            fl = 2 * 8.0 * nproj * nb * sum(g.npw)
+            bound = "tensor"
+            fl_pk = float(peaks.get("bf16_tflops_sustained", 1714.0))
         if fl is not None:
             fl /= per_step
-            roof = {"bound": "alu", "achieved": fl / (avg_ms * 1e-3) / 1e12, "peak": fl_pk, "unit": "TFLOP/s"}
+            roof = {"bound": bound, "achieved": fl / (avg_ms * 1e-3) / 1e12, "peak": fl_pk, "unit": "TFLOP/s"}
             roof["frac"] = roof["achieved"] / roof["peak"]
+            if bound == "tensor":
+                roof["issued_bf16_products_frac"] = 6 * roof["frac"]
+                roof["note"] = ("runs concurrently with the FFT kernels on a second stream; its launch "
+                                "duration includes the time it shares SMs with them")
         else:
             roof = {"bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"), "unit": "GB/s", "frac": None}
         tpb = TRAFFIC_PER_BAND.get((name, wl.prec))
         traffic = tpb * nb * nk / per_step if tpb else None
         roof.update({"kernel": name, "traffic": traffic, "avg_launch_ms": avg_ms,
-                     "peak_source": "derived: %d SMs x %d flop/clk/SM x %.0f MHz" % (
-                         N_SM, FLOP_PER_CLK_SM[wl.prec], smax / 1e6)})
+                     "peak_source": ("measured: cuBLAS bf16, sustained (of measured)" if bound == "tensor" else
+                                     "derived: %d SMs x %d flop/clk/SM x %.0f MHz" % (
+                                         N_SM, FLOP_PER_CLK_SM[wl.prec], smax / 1e6))})
     return {"value": band_applies / (ms * 1e-3), "ms_per_step": ms, "gpu_launches": launches, "kernels": fam,
             "roofline": roof, "clocks": clk,
             "e2e": {"value": band_applies / (ems * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,

@@ -117,7 +117,9 @@ void qm_gspace_destroy(qm_gspace g);
  *             overwritten.  Must not overlap psi.
  *  prec       QM_FP64 or QM_MIXED.
  *  stream     cudaStream_t (NULL = default stream).  Asynchronous: returns after the
- *             launches are queued.  Uses the handle's device workspace.
+ *             launches are queued.  Uses the handle's device workspace.  QM_MIXED with
+ *             nproj > 0 runs the nonlocal part on a second stream owned by the handle,
+ *             forked from and joined back to `stream` with events (capturable in a graph).
  * Errors: QM_ERR_ARG (sizes, NULL pointers, misaligned rows), QM_ERR_OOM (workspace),
  *         QM_ERR_CUDA (launch failure).
  */

@@ -416,7 +416,7 @@ k_stick_forward(const typename Cx<R>::T* __restrict__ T, int nstick, int nstick_
                 const int* __restrict__ stick_g0, const int2* __restrict__ g_code, const R* __restrict__ kin,
                 AxisPlan px, const typename Cx<R>::T* __restrict__ tw_x, int ldx,
                 const typename Cx<R>::T* __restrict__ psi, int ld_psi, typename Cx<R>::T* __restrict__ out,
-                int ld_out) {
+                int ld_out, int accumulate) {
     using C = typename Cx<R>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* lines = reinterpret_cast<C*>(smem_raw);
@@ -442,7 +442,9 @@ k_stick_forward(const typename Cx<R>::T* __restrict__ T, int nstick, int nstick_
         C x = lines[(c.x - s0) * ldx + c.y];
         C y = ps[g];
         R k = __ldg(kin + g);
-        po[g] = mk<C>(x.x + k * y.x, x.y + k * y.y);
+        C r = mk<C>(x.x + k * y.x, x.y + k * y.y);
+        if (accumulate) r = add(r, po[g]);
+        po[g] = r;
     }
 }
 
@@ -463,9 +465,12 @@ __global__ void k_vt(const double* __restrict__ V, R* __restrict__ Vt, int N1, i
 }
 
 // ---------------------------------------------------------------- per-precision launch sequences
+// wait_k3: event the stream waits for before the first x-forward pass (the nonlocal part
+// running concurrently on another stream); accumulate: the x-forward pass adds to `out`.
 template <class R>
 qm_status local_kinetic_impl(qm_gspace g, int ik, int nb, const void* psi, int ld_psi, const void* vt,
-                                    void* out, int ld_out, void* tbuf, size_t tbuf_bytes, cudaStream_t s) {
+                                    void* out, int ld_out, void* tbuf, size_t tbuf_bytes, cudaStream_t s,
+                                    cudaEvent_t wait_k3, bool accumulate) {
     using C = typename Cx<R>::T;
     const KTables& kt = g->k[ik];
     const int N1 = g->n[0], N2 = g->n[1], N3 = g->n[2];
@@ -500,11 +505,15 @@ qm_status local_kinetic_impl(qm_gspace g, int ik, int nb, const void* psi, int l
                 T, kt.nstick, kt.nstick_pad, kt.stick_plane, kt.rows, kt.nrow, g->plan[1], g->plan[2], tw_y, tw_z,
                 g->ldy, (const R*)vt, N1);
         }
+        if (wait_k3 && b0 == 0) {
+            cudaError_t e = cudaStreamWaitEvent(s, wait_k3, 0);
+            if (e != cudaSuccess) return cuda_check(e, "FFT path: wait for the nonlocal part");
+        }
         {
             ProfScope pf(PF_STICK_FWD, s);
             k_stick_forward<R><<<dim3(ntile, nbx), kThreads, sm_stick, s>>>(
                 T, kt.nstick, kt.nstick_pad, kt.stick_g0, kt.g_code, kin, g->plan[0], tw_x, g->ldx, ps, ld_psi, po,
-                ld_out);
+                ld_out, accumulate ? 1 : 0);
         }
     }
     return cuda_check(cudaGetLastError(), "FFT path launch");
@@ -549,7 +558,7 @@ qm_status local_kinetic_tab_impl(const DevTables& t, int nb, const void* psi, in
         {
             ProfScope pf(PF_STICK_FWD, s);
             k_stick_forward<R><<<dim3(ntile, nbx), kThreads, sm_stick, s>>>(
-                T, t.nstick, t.nstick_pad, t.stick_g0, t.g_code, kin, t.plan[0], tw_x, t.ldx, ps, ld_psi, po, ld_out);
+                T, t.nstick, t.nstick_pad, t.stick_g0, t.g_code, kin, t.plan[0], tw_x, t.ldx, ps, ld_psi, po, ld_out, 0);
         }
     }
     return cuda_check(cudaGetLastError(), "FFT path launch");

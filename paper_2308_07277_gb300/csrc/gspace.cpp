@@ -152,6 +152,10 @@ qm_status ensure_device(qm_gspace g) {
             (st = upload((void**)&kt.kin_f, kinf.data(), sizeof(float) * kinf.size())))
             return st;
     }
+    if ((st = cuda_check(cudaStreamCreateWithFlags(&g->aux, cudaStreamNonBlocking), "gspace stream")) ||
+        (st = cuda_check(cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming), "gspace event")) ||
+        (st = cuda_check(cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming), "gspace event")))
+        return st;
     return QM_OK;
 }
 
@@ -360,6 +364,9 @@ extern "C" void qm_gspace_destroy(qm_gspace g) {
         }
         if (g->ws.ptr) cudaFree(g->ws.ptr);
         if (g->dws.ptr) cudaFree(g->dws.ptr);
+        if (g->ev_fork) cudaEventDestroy(g->ev_fork);
+        if (g->ev_join) cudaEventDestroy(g->ev_join);
+        if (g->aux) cudaStreamDestroy(g->aux);
         cudaSetDevice(cur);
     }
     delete g;

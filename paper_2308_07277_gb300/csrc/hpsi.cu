@@ -6,8 +6,11 @@
 //   2. gemm_cn         P[p][b] = <beta_p|psi_b>             (nonlocal projection, FP64)
 //   3. K1, K2, K3      out = 1/2|k+G|^2 psi + (V psi)(G)    (per chunk of bands)
 //   4. gemm_tn         out += sum_p beta_p D_p P[p][b]      (nonlocal apply, FP64)
-//      QM_MIXED: 2 and 4 run after 3 as BF16x3 split tcgen05 products (umma.cu)
-// Workspace (owned by the gspace handle): Vt | P | split-K partials | stick buffer.
+// QM_MIXED: the nonlocal part runs as BF16x3 split tcgen05 products (umma.cu) on the handle's
+// second stream, concurrently with k_vt, K1 and K2 of every band: it writes
+// out = sum_p beta_p D_p P[p][b], and K3 (which waits for it) adds the local and kinetic
+// parts.  The tensor-core kernels (96 KB of shared memory) share SMs with the FFT kernels.
+// Workspace (owned by the gspace handle): Vt | P | split-K partials | stick buffer | nonlocal | err.
 #include <algorithm>
 #include <cstdint>
 
@@ -18,6 +21,7 @@ namespace qm {
 // Stick-buffer budget per chunk of bands: small enough that a chunk's intermediate data
 // stays resident in the 129 MB L2 between the three FFT kernels.
 constexpr size_t kStickBudget = 48ull << 20;
+constexpr size_t kStickBudgetOverlap = 1ull << 30;
 
 struct HpsiLayout {
     size_t vt_off, p_off, part_off, t_off, nl_off, err_off, total, t_bytes;
@@ -40,7 +44,10 @@ static HpsiLayout hpsi_layout(qm_gspace g, int ik, int nb, int nproj, bool fp32)
     off = align_up(off + (L.splits > 1 ? std::min((size_t)L.splits * nproj * nb * cs, gemm_cn_partial_bytes(fp32)) : 0), 256);
     L.t_off = off;
     const size_t per_band = stick_buffer_bytes_per_band(g, ik, fp32);
-    const size_t nbc = std::max<size_t>(1, std::min<size_t>((size_t)nb, kStickBudget / per_band));
+    // the precision form keeps every band's stick buffer (K1 and K2 of all bands overlap the
+    // nonlocal part; K3 runs once it is done), the FP64 form chunks the bands to stay in L2
+    const size_t budget = (fp32 && nproj > 0) ? kStickBudgetOverlap : kStickBudget;
+    const size_t nbc = std::max<size_t>(1, std::min<size_t>((size_t)nb, budget / per_band));
     L.t_bytes = nbc * per_band;
     off = align_up(off + L.t_bytes, 256);
     L.nl_off = off;  // tensor-core split operands (precision form)
@@ -94,6 +101,22 @@ extern "C" qm_status qm_hpsi(qm_gspace g, int ik, int nb, const void* psi, int l
     void* part = ws + L.part_off;
     void* T = ws + L.t_off;
 
+    if (fp32 && nproj > 0) {
+        // fork: the nonlocal part on the second stream writes out; K3 joins and adds to it
+        int* err = (int*)(ws + L.err_off);
+        cudaStream_t a = g->aux;
+        if ((st = cuda_check(cudaEventRecord(g->ev_fork, s), "fork event")) ||
+            (st = cuda_check(cudaStreamWaitEvent(a, g->ev_fork, 0), "fork wait")) ||
+            (st = cuda_check(cudaMemsetAsync(err, 0, sizeof(int), a), "reset tensor-core error word")))
+            return st;
+        if ((st = nonlocal_bf16x3(nproj, nb, npw, (const float2*)beta, ld_beta, (const float2*)psi, ld_psi, D,
+                                  (float2*)out, ld_out, ws + L.nl_off, err, a, false)))
+            return st;
+        if ((st = cuda_check(cudaEventRecord(g->ev_join, a), "join event"))) return st;
+        if ((st = launch_vt_prepare(g, vloc_r, vt, fp32, s))) return st;
+        return launch_local_kinetic(g, ik, nb, psi, ld_psi, vt, out, ld_out, T, L.t_bytes, fp32, s, g->ev_join,
+                                    true);
+    }
     if ((st = launch_vt_prepare(g, vloc_r, vt, fp32, s))) return st;
     if (nproj > 0 && !fp32) {
         st = zgemm_cn(nproj, nb, npw, (const double2*)beta, ld_beta, (const double2*)psi, ld_psi, (double2*)P, nb,
@@ -101,18 +124,9 @@ extern "C" qm_status qm_hpsi(qm_gspace g, int ik, int nb, const void* psi, int l
         if (st) return st;
     }
     if ((st = launch_local_kinetic(g, ik, nb, psi, ld_psi, vt, out, ld_out, T, L.t_bytes, fp32, s))) return st;
-    if (nproj > 0) {
-        if (fp32) {
-            // projection and application on the tensor cores (BF16x3 split, FP32 accumulation)
-            int* err = (int*)(ws + L.err_off);
-            if ((st = cuda_check(cudaMemsetAsync(err, 0, sizeof(int), s), "reset tensor-core error word")))
-                return st;
-            st = nonlocal_bf16x3(nproj, nb, npw, (const float2*)beta, ld_beta, (const float2*)psi, ld_psi, D,
-                                 (float2*)out, ld_out, ws + L.nl_off, err, s);
-        } else {
-            st = zgemm_tn(nb, npw, nproj, (const double2*)P, nb, D, (const double2*)beta, ld_beta, (double2*)out,
-                          ld_out, true, s);
-        }
+    if (nproj > 0 && !fp32) {
+        st = zgemm_tn(nb, npw, nproj, (const double2*)P, nb, D, (const double2*)beta, ld_beta, (double2*)out, ld_out,
+                      true, s);
         if (st) return st;
     }
     return QM_OK;

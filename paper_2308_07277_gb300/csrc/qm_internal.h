@@ -70,6 +70,10 @@ struct qm_gspace_s {
     std::vector<int> h_rev[3];
     qm::Workspace ws;    // qm_hpsi workspace
     qm::Workspace dws;   // qm_davidson workspace
+    // second stream of qm_hpsi(QM_MIXED): the tensor-core nonlocal part runs on it while the
+    // FFT path runs on the caller's stream (fork / join events); created with the tables
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace qm {
@@ -111,10 +115,12 @@ class ProfScope {
 // ---- FFT path (fft_path.cu) ----
 // Vt[p1][p3][p2] = V(rev1[p1], rev2[p2], rev3[p3]) / N_r   (real type R)
 qm_status launch_vt_prepare(qm_gspace g, const double* vloc, void* vt, bool fp32, cudaStream_t s);
-// local + kinetic part for nb bands: out = kin*psi + (V psi)(G); T = stick workspace
+// local + kinetic part for nb bands: out = kin*psi + (V psi)(G) (accumulate: out += ...);
+// T = stick workspace; wait_k3 (may be NULL): event waited for before the first x-forward pass
 qm_status launch_local_kinetic(qm_gspace g, int ik, int nb, const void* psi, int ld_psi,
                                const void* vt, void* out, int ld_out, void* tbuf,
-                               size_t tbuf_bytes, bool fp32, cudaStream_t s);
+                               size_t tbuf_bytes, bool fp32, cudaStream_t s,
+                               cudaEvent_t wait_k3 = nullptr, bool accumulate = false);
 size_t stick_buffer_bytes_per_band(qm_gspace g, int ik, bool fp32);
 
 // The FFT path's tables of one k-point given by explicit device pointers (twiddles and kin
@@ -155,11 +161,11 @@ qm_status zgemm_tn_f32(int M, int N, int K, const double2* A, int lda, const dou
                        cudaStream_t s, double alpha = 1.0);
 // ---- tensor-core nonlocal step of the precision form (umma.cu) ----
 constexpr int kMaxUmmaSplits = 64;
-// out[b][g] += sum_p beta[p][g] D_p <beta_p|psi_b> (FP32 complex in/out) as BF16x3 split
+// out[b][g] (+)= sum_p beta[p][g] D_p <beta_p|psi_b> (FP32 complex in/out) as BF16x3 split
 // tcgen05 products; work: nonlocal_bf16x3_bytes(); err: device int set on a timed-out wait
 qm_status nonlocal_bf16x3(int nproj, int nb, int npw, const float2* beta, int ld_beta, const float2* psi,
                           int ld_psi, const double* D, float2* out, int ld_out, void* work, int* err,
-                          cudaStream_t s);
+                          cudaStream_t s, bool accumulate = true);
 size_t nonlocal_bf16x3_bytes(int nproj, int nb, int npw);
 
 // ---- learned preconditioner (mlp.cu) ----

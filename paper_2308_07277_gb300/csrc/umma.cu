@@ -338,9 +338,10 @@ size_t nonlocal_bf16x3_bytes(int nproj, int nb, int npw) {
     return rup((size_t)kMaxUmmaSplits * rP * r2B * 4, 256) + rup((size_t)nb * nproj * sizeof(float2), 256);
 }
 
-// out[b][g] += sum_p beta[p][g] D_p sum_g' conj(beta[p][g']) psi[b][g']   (FP32 complex in/out)
+// out[b][g] (+)= sum_p beta[p][g] D_p sum_g' conj(beta[p][g']) psi[b][g']   (FP32 complex in/out)
 qm_status nonlocal_bf16x3(int nproj, int nb, int npw, const float2* beta, int ld_beta, const float2* psi, int ld_psi,
-                          const double* D, float2* out, int ld_out, void* work, int* err, cudaStream_t s) {
+                          const double* D, float2* out, int ld_out, void* work, int* err, cudaStream_t s,
+                          bool accumulate) {
     if (nproj <= 0 || nb <= 0) return QM_OK;
     const size_t rP = rup(nproj, UM), r2B = rup(2 * (size_t)nb, UN);
     float* part = (float*)work;
@@ -362,7 +363,7 @@ qm_status nonlocal_bf16x3(int nproj, int nb, int npw, const float2* beta, int ld
     // application: out'[b][2g + t] += sum_p (D P)[b][p] beta[p][g]
     PlainRows la2{Pd, nproj, nb, nproj};
     ExpandTRows lb2{beta, ld_beta, nproj, npw};
-    return umma_launch(la2, lb2, nb, 2 * npw, 2 * nproj, 1, (float*)out, 2 * (size_t)ld_out, 0, true, err, s,
+    return umma_launch(la2, lb2, nb, 2 * npw, 2 * nproj, 1, (float*)out, 2 * (size_t)ld_out, 0, accumulate, err, s,
                        nullptr);
 }
 
