@@ -297,6 +297,53 @@ __device__ __forceinline__ void fft_stages_ct(C* buf, int es, int ls, int nlines
     }
 }
 
+// stages S, S+1, ..., END-1 of the plan of N in DIF order
+template <class C, int SG, bool LINE_FAST, int N, int S, int END>
+__device__ __forceinline__ void fft_stages_ct_to(C* buf, int es, int ls, int nlines, RDiv ld, const int* lmap,
+                                                 const C* tw, int tid, int nt) {
+    constexpr CPlan P = make_cplan(N);
+    if constexpr (S < END) {
+        fft_stage_ct<C, SG, P.r[S], P.L[S], N, true, LINE_FAST>(buf, es, ls, nlines, ld, lmap, tw, tid, nt);
+        __syncthreads();
+        fft_stages_ct_to<C, SG, LINE_FAST, N, S + 1, END>(buf, es, ls, nlines, ld, lmap, tw, tid, nt);
+    }
+}
+
+// Inverse z transform of the ncol columns of a plane, multiplication by the real V, forward z
+// transform.  The last DIF stage of the inverse and the first DIT stage of the forward
+// transform act on the same blocks of consecutive z positions with unit twiddles, so they and
+// the V multiply are one pass in registers (bitwise the same result as three passes).
+// V of element (z, c) is v[z * ldv + c].
+template <class C, class R, int N>
+__device__ __forceinline__ void fft_z_vmul_ct(C* buf, int ldy, int ncol, const R* __restrict__ v, int ldv,
+                                              const C* tw, int tid, int nt) {
+    constexpr CPlan P = make_cplan(N);
+    constexpr int RL = P.r[P.nst - 1];
+    constexpr int NBLK = N / RL;
+    RDiv ld{ncol, 1.0f / (float)ncol};
+    fft_stages_ct_to<C, +1, true, N, 0, P.nst - 1>(buf, ldy, 1, ncol, ld, nullptr, tw, tid, nt);
+    for (int t = tid; t < ncol * NBLK; t += nt) {
+        const int blk = ld.div(t);
+        const int col = t - blk * ncol;
+        C* p = buf + col + blk * RL * ldy;
+        const R* vv = v + col + blk * RL * ldv;
+        C u[RL];
+#pragma unroll
+        for (int j = 0; j < RL; ++j) u[j] = p[j * ldy];
+        Dft<C, +1, RL>::run(u);
+#pragma unroll
+        for (int j = 0; j < RL; ++j) {
+            const R sc = __ldg(vv + j * ldv);
+            u[j] = mk<C>(u[j].x * sc, u[j].y * sc);
+        }
+        Dft<C, -1, RL>::run(u);
+#pragma unroll
+        for (int j = 0; j < RL; ++j) p[j * ldy] = u[j];
+    }
+    __syncthreads();
+    fft_stages_ct<C, -1, false, true, N, P.nst - 2>(buf, ldy, 1, ncol, ld, nullptr, tw, tid, nt);
+}
+
 template <class C, int SG, bool DIF, bool LINE_FAST, int N>
 __device__ __forceinline__ void fft_lines_ct(C* buf, int es, int ls, int nlines, const int* lmap, const C* tw,
                                              int tid, int nt) {
@@ -331,6 +378,28 @@ __device__ void fft_lines(C* buf, int es, int ls, int nlines, const int* lmap, c
             __syncthreads();
         }
     }
+}
+
+// z transforms of a plane with the V multiply between them (ends with __syncthreads())
+template <class C, class R>
+__device__ void fft_z_vmul(C* buf, int ldy, int ncol, const R* __restrict__ v, int ldv, const AxisPlan& pz,
+                           const C* tw, int tid, int nt) {
+    switch (pz.n) {
+#define QM_CASE(n) \
+    case n: fft_z_vmul_ct<C, R, n>(buf, ldy, ncol, v, ldv, tw, tid, nt); return;
+        QM_FFT_LENGTHS(QM_CASE)
+#undef QM_CASE
+        default: break;
+    }
+    fft_lines<C, +1, true, true>(buf, ldy, 1, ncol, nullptr, pz, tw, tid, nt);
+    for (int i = tid; i < pz.n * ncol; i += nt) {
+        const int r = i / ncol, c = i - r * ncol;
+        const R sc = __ldg(v + r * ldv + c);
+        C x = buf[r * ldy + c];
+        buf[r * ldy + c] = mk<C>(x.x * sc, x.y * sc);
+    }
+    __syncthreads();
+    fft_lines<C, -1, false, true>(buf, ldy, 1, ncol, nullptr, pz, tw, tid, nt);
 }
 
 constexpr int kSticksPerCta = 32;
@@ -391,20 +460,10 @@ k_plane(typename Cx<R>::T* __restrict__ T, int nstick, int nstick_pad, const int
     C* Tp = T + ((size_t)b * N1 + p1) * nstick_pad;
     for (int s = tid; s < nstick; s += nt) plane[__ldg(stick_plane + s)] = Tp[s];
     __syncthreads();
-    // inverse: y on the active rows, then z on every column
+    // inverse y on the active rows; z on every column: inverse, V(r)/N_r (in the permuted,
+    // digit-reversed order of all three axes), forward; forward y on the active rows
     fft_lines<C, +1, true, false>(plane, 1, ldy, nrow, rows, py, twy, tid, nt);
-    fft_lines<C, +1, true, true>(plane, ldy, 1, N2, nullptr, pz, twz, tid, nt);
-    // V(r)/N_r in the permuted (digit-reversed) order of all three axes
-    const R* v = Vt + (size_t)p1 * N3 * N2;
-    for (int i = tid; i < N3 * N2; i += nt) {
-        int r = i / N2, c = i - r * N2;
-        R s = __ldg(v + i);
-        C x = plane[r * ldy + c];
-        plane[r * ldy + c] = mk<C>(x.x * s, x.y * s);
-    }
-    __syncthreads();
-    // forward: z on every column, then y on the active rows
-    fft_lines<C, -1, false, true>(plane, ldy, 1, N2, nullptr, pz, twz, tid, nt);
+    fft_z_vmul<C, R>(plane, ldy, N2, Vt + (size_t)p1 * N3 * N2, N2, pz, twz, tid, nt);
     fft_lines<C, -1, false, false>(plane, 1, ldy, nrow, rows, py, twy, tid, nt);
     for (int s = tid; s < nstick; s += nt) Tp[s] = plane[__ldg(stick_plane + s)];
 }
