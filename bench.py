@@ -439,7 +439,7 @@ def run_batched(args, Q, S, dev):
                      "jobs": len(jobs), "launches_per_replay": 1,
                      "per_cell_loop": {"value": ba / ms_loop * 1e3, "ms": ms_loop},
                      "speedup_vs_loop": ms_loop / ms, "shape": {k: info[k] for k in (
-                         "ctas_per_sm", "item_points", "grid", "items", "smem_bytes", "candidates")},
+                         "ctas_per_sm", "item_points", "group_mb", "grid", "items", "smem_bytes", "candidates")},
                      "autotune_s": tune_s, "device_bytes": info["device_bytes"]}
         b.close()
         del jobs

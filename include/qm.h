@@ -180,10 +180,14 @@ qm_status qm_hpsi_noalloc(qm_gspace g, int ik, int nb,
  * (FFT path identical; nonlocal products accumulated in the working precision, FP32 in
  * QM_MIXED instead of the single-call tensor-core path).
  *
- * The shape of the launch (resident CTAs per SM; grid points per FFT work item, from which
- * the lines per x-stick item and the bands per yz-plane item follow) is either given or
- * picked by the autotuner, which builds every feasible shape, times three replays of each
- * (after one warm-up) with CUDA events on `stream`, and keeps the fastest.
+ * The work items are ordered in groups of jobs whose stick buffers hold about group_mb MB,
+ * the phases of consecutive groups interleaved as a software pipeline, so the intermediate
+ * data of a group is still in L2 when its next phase reads it.  The shape of the launch
+ * (resident CTAs per SM; grid points per FFT work item, from which the lines per x-stick item
+ * and the bands per yz-plane item follow; the group size) is either given or picked by the
+ * autotuner, which times three replays of each candidate (after one warm-up) with CUDA events
+ * on `stream`: every feasible (CTAs per SM, points per item) pair at 24 MB groups, then the
+ * other group sizes (48 MB, one group) at the best pair; the fastest is kept.
  */
 typedef struct {
     qm_gspace g;            /* gspace of the job's cell (device tables on the current device) */
@@ -205,10 +209,13 @@ typedef struct qm_batch_s* qm_batch;   /* opaque, library-owned */
 typedef struct {
     int ctas_per_sm;   /* resident CTAs per SM, 1..8; 0 = autotune */
     int item_points;   /* target grid points per FFT work item, 256..65536; 0 = autotune */
+    int group_mb;      /* stick-buffer megabytes per pipelined group of jobs, 1..4096; -1 = one
+                          group (the work items of each phase of all jobs together); 0 = autotune */
 } qm_batch_shape;
 
 typedef struct {
     int ctas_per_sm, item_points;  /* shape in use */
+    int group_mb;                  /* group size in use (-1: one group) */
     int grid;                      /* CTAs of the persistent launch */
     int items;                     /* work items per replay */
     int cells;                     /* distinct (gspace, vloc_r) pairs */

@@ -91,12 +91,13 @@ class HpsiJob(ctypes.Structure):
 
 class BatchShape(ctypes.Structure):
     """qm_batch_shape of include/qm.h."""
-    _fields_ = [("ctas_per_sm", ctypes.c_int), ("item_points", ctypes.c_int)]
+    _fields_ = [("ctas_per_sm", ctypes.c_int), ("item_points", ctypes.c_int), ("group_mb", ctypes.c_int)]
 
 
 class BatchInfo(ctypes.Structure):
     """qm_batch_info of include/qm.h."""
-    _fields_ = [("ctas_per_sm", ctypes.c_int), ("item_points", ctypes.c_int), ("grid", ctypes.c_int),
+    _fields_ = [("ctas_per_sm", ctypes.c_int), ("item_points", ctypes.c_int), ("group_mb", ctypes.c_int),
+                ("grid", ctypes.c_int),
                 ("items", ctypes.c_int), ("cells", ctypes.c_int), ("candidates", ctypes.c_int),
                 ("band_applies", ctypes.c_longlong), ("smem_bytes", ctypes.c_longlong),
                 ("device_bytes", ctypes.c_longlong), ("tuned_ms", ctypes.c_double)]

@@ -229,7 +229,7 @@ class Batch:
     tensors as for qm_hpsi; beta/D may be None).  The tensors are referenced by the plan
     and must stay alive and in place while it exists."""
 
-    def __init__(self, jobs, prec="fp64", ctas_per_sm=0, item_points=0, stream=None):
+    def __init__(self, jobs, prec="fp64", ctas_per_sm=0, item_points=0, group_mb=0, stream=None):
         lib = _lib.load()
         self.prec = _PREC[prec]
         cdt = torch.complex128 if self.prec == QM_FP64 else torch.complex64
@@ -249,7 +249,7 @@ class Batch:
                                   D=_dev_ptr(j["D"], "D", torch.float64) if nproj else None,
                                   out=_dev_ptr(out, "out", cdt))
             self._keep.append((psi, out, beta, j["vloc"], j.get("D")))
-        shape = _lib.BatchShape(int(ctas_per_sm), int(item_points))
+        shape = _lib.BatchShape(int(ctas_per_sm), int(item_points), int(group_mb))
         h = ctypes.c_void_p()
         _check(lib.qm_batch_create(len(jobs), arr, self.prec, ctypes.byref(shape), _stream_ptr(stream),
                                    ctypes.byref(h)))
@@ -278,8 +278,9 @@ class Batch:
             pass
 
 
-def qm_batch_create(jobs, prec="fp64", ctas_per_sm=0, item_points=0, stream=None):
-    return Batch(jobs, prec=prec, ctas_per_sm=ctas_per_sm, item_points=item_points, stream=stream)
+def qm_batch_create(jobs, prec="fp64", ctas_per_sm=0, item_points=0, group_mb=0, stream=None):
+    return Batch(jobs, prec=prec, ctas_per_sm=ctas_per_sm, item_points=item_points, group_mb=group_mb,
+                 stream=stream)
 
 
 QM_MLP_NPARAM = 4481   # include/qm.h

@@ -23,7 +23,7 @@ struct qm_batch_s {
     int device = 0;
     qm_precision prec = QM_FP64;
     std::vector<qm_hpsi_job> jobs;
-    int ctas = 0, points = 0, grid = 0, nitems = 0, ncells = 0, candidates = 0;
+    int ctas = 0, points = 0, group_mb = 0, grid = 0, nitems = 0, ncells = 0, candidates = 0;
     size_t smem = 0, dbytes = 0;
     double tuned_ms = 0.0;
     long long band_applies = 0;
@@ -37,6 +37,7 @@ namespace {
 
 constexpr int kCandCtas[] = {1, 2, 3, 4};
 constexpr int kCandPoints[] = {1024, 2048, 4096, 8192};
+constexpr int kCandGroupMb[] = {24, 48, -1};  // tried at the best (ctas, points) of the first: -1 = one group
 
 struct Region {
     size_t off = 0;
@@ -57,7 +58,7 @@ void release(qm_batch b) {
 
 // Build the work lists and device data for one shape and capture the launch in a graph.
 // `infeasible` is set (and QM_OK returned) when the shape does not fit the SM.
-qm_status build(qm_batch b, int ctas, int points, bool* infeasible) {
+qm_status build(qm_batch b, int ctas, int points, size_t group_bytes, bool* infeasible) {
     *infeasible = false;
     const bool fp32 = b->prec == QM_MIXED;
     const size_t cs = fp32 ? sizeof(float2) : sizeof(double2);
@@ -148,7 +149,11 @@ qm_status build(qm_batch b, int ctas, int points, bool* infeasible) {
     std::vector<int4> items;
     const size_t n_cnt = (size_t)nj * kBatchCounters + nc + 2;
     std::vector<size_t> o_rows(nj), o_cols(nj), o_T(nj), o_part(nj), o_Pd(nj), o_vt(nc);
-    // item lists in phase order; within a phase the largest jobs first
+    // Item list.  Jobs (largest first) are cut into groups whose stick buffers hold at most
+    // `group_bytes` (0: one group); the phases of consecutive groups are interleaved as a
+    // software pipeline, stage t = [NLA of group t-3, K3 of t-2, NLR + K2 of t-1, VT + NLP +
+    // K1 of t], so only the stick buffers of about three groups are live at a time (they stay
+    // in L2) and every item still depends only on items of earlier tickets.
     std::vector<int> order(nj);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
@@ -156,30 +161,57 @@ qm_status build(qm_batch b, int ctas, int points, bool* infeasible) {
         const double wc = (double)J[c].nb * J[c].n1 * J[c].n2 * J[c].n3;
         return wa > wc;
     });
+    std::vector<std::vector<int>> groups(1);
+    {
+        size_t acc = 0;
+        for (int j : order) {
+            const size_t tb = cs * (size_t)J[j].nb * J[j].n1 * J[j].nstick_pad;
+            if (group_bytes > 0 && !groups.back().empty() && acc + tb > group_bytes) {
+                groups.emplace_back();
+                acc = 0;
+            }
+            groups.back().push_back(j);
+            acc += tb;
+        }
+    }
     for (int c = 0; c < nc; ++c) {
         const qm_gspace g = cell_job[c]->g;
         const long long nr = (long long)g->n[0] * g->n[1] * g->n[2];
         Cl[c].nchunk = (int)((nr + kBatchVTC - 1) / kBatchVTC);
-        for (int k = 0; k < Cl[c].nchunk; ++k) items.push_back(make_int4(BK_VT, c, k, 0));
     }
-    for (int j : order)
-        if (J[j].nproj > 0)
-            for (int ch = 0; ch < J[j].nchunk; ++ch)
-                for (int bb = 0; bb < J[j].nbblk; ++bb) items.push_back(make_int4(BK_NLP, j, ch, bb));
-    for (int j : order)
-        for (int t = 0; t < J[j].nk1; ++t) items.push_back(make_int4(BK_K1, j, t, 0));
-    for (int j : order)
-        if (J[j].nproj > 0) items.push_back(make_int4(BK_NLR, j, 0, 0));
-    for (int j : order) {
-        const int ngrp = (J[j].nb + J[j].bpp - 1) / J[j].bpp;
-        for (int p1 = 0; p1 < J[j].n1; ++p1)
-            for (int gr = 0; gr < ngrp; ++gr) items.push_back(make_int4(BK_K2, j, gr, p1));
+    std::vector<char> vt_done(nc, 0);
+    const int ng = (int)groups.size();
+    for (int t = 0; t < ng + 3; ++t) {
+        if (t - 3 >= 0 && t - 3 < ng)
+            for (int j : groups[t - 3])
+                if (J[j].nproj > 0)
+                    for (int q = 0; q < J[j].nnla; ++q) items.push_back(make_int4(BK_NLA, j, q, 0));
+        if (t - 2 >= 0 && t - 2 < ng)
+            for (int j : groups[t - 2])
+                for (int q = 0; q < J[j].nk1; ++q) items.push_back(make_int4(BK_K3, j, q, 0));
+        if (t - 1 >= 0 && t - 1 < ng)
+            for (int j : groups[t - 1]) {
+                if (J[j].nproj > 0) items.push_back(make_int4(BK_NLR, j, 0, 0));
+                const int ngrp = (J[j].nb + J[j].bpp - 1) / J[j].bpp;
+                for (int p1 = 0; p1 < J[j].n1; ++p1)
+                    for (int gr = 0; gr < ngrp; ++gr) items.push_back(make_int4(BK_K2, j, gr, p1));
+            }
+        if (t < ng) {
+            for (int j : groups[t]) {
+                const int c = J[j].cell;
+                if (!vt_done[c]) {
+                    vt_done[c] = 1;
+                    for (int k = 0; k < Cl[c].nchunk; ++k) items.push_back(make_int4(BK_VT, c, k, 0));
+                }
+            }
+            for (int j : groups[t])
+                if (J[j].nproj > 0)
+                    for (int ch = 0; ch < J[j].nchunk; ++ch)
+                        for (int bb = 0; bb < J[j].nbblk; ++bb) items.push_back(make_int4(BK_NLP, j, ch, bb));
+            for (int j : groups[t])
+                for (int q = 0; q < J[j].nk1; ++q) items.push_back(make_int4(BK_K1, j, q, 0));
+        }
     }
-    for (int j : order)
-        for (int t = 0; t < J[j].nk1; ++t) items.push_back(make_int4(BK_K3, j, t, 0));
-    for (int j : order)
-        if (J[j].nproj > 0)
-            for (int t = 0; t < J[j].nnla; ++t) items.push_back(make_int4(BK_NLA, j, t, 0));
     const size_t o_items = R.take(sizeof(int4) * items.size());
     const size_t o_cnt = R.take(sizeof(int) * n_cnt);
     for (int j = 0; j < nj; ++j) {
@@ -278,6 +310,7 @@ qm_status build(qm_batch b, int ctas, int points, bool* infeasible) {
     b->err = L.err;
     b->ctas = ctas;
     b->points = points;
+    b->group_mb = group_bytes ? (int)(group_bytes >> 20) : -1;
     b->grid = L.grid;
     b->nitems = L.nitems;
     b->ncells = nc;
@@ -357,8 +390,11 @@ extern "C" qm_status qm_batch_create(int njobs, const qm_hpsi_job* jobs, qm_prec
     if (prec != QM_FP64 && prec != QM_MIXED) return fail(QM_ERR_ARG, "qm_batch_create: unknown precision");
     const bool fp32 = prec == QM_MIXED;
     int ctas = shape ? shape->ctas_per_sm : 0, points = shape ? shape->item_points : 0;
-    if (ctas < 0 || ctas > 8 || points < 0 || (points > 0 && (points < 256 || points > 65536)))
+    int gmb = shape ? shape->group_mb : 0;
+    if (ctas < 0 || ctas > 8 || points < 0 || (points > 0 && (points < 256 || points > 65536)) || gmb < -1 ||
+        gmb > 4096)
         return fail(QM_ERR_ARG, "qm_batch_create: shape out of range");
+    auto gbytes = [](int mb) { return mb > 0 ? (size_t)mb << 20 : (size_t)0; };
     qm_status st;
     for (int i = 0; i < njobs; ++i)
         if ((st = check_job(jobs[i], fp32, i))) return st;
@@ -390,38 +426,49 @@ extern "C" qm_status qm_batch_create(int njobs, const qm_hpsi_job* jobs, qm_prec
         }
     cudaStream_t s = (cudaStream_t)stream;
     bool infeasible = false;
-    if (ctas > 0 && points > 0) {
-        st = build(b, ctas, points, &infeasible);
+    if (ctas > 0 && points > 0 && gmb != 0) {
+        st = build(b, ctas, points, gbytes(gmb), &infeasible);
         if (!st && infeasible) st = fail(QM_ERR_UNSUPPORTED, "qm_batch_create: shape does not fit the SM");
     } else {
-        // autotune: time every feasible shape (each run executes the whole batch)
+        // autotune (each timed run executes the whole batch): every feasible (CTAs per SM,
+        // points per item) at the first group size, then the group sizes at the best of those
         double best = 1e300;
-        int bc = 0, bp = 0;
+        int bc = 0, bp = 0, bg = gmb != 0 ? gmb : kCandGroupMb[0];
         st = QM_OK;
+        auto try_shape = [&](int c, int p, int g) -> qm_status {
+            qm_status s2 = build(b, c, p, gbytes(g), &infeasible);
+            if (s2 || infeasible) return s2;
+            double ms = 0.0;
+            s2 = time_runs(b, s, 3, &ms);
+            release(b);
+            if (s2) return s2;
+            ++b->candidates;
+            if (ms < best) {
+                best = ms;
+                bc = c;
+                bp = p;
+                bg = g;
+            }
+            return QM_OK;
+        };
+        const int g0 = bg;
         for (int c : kCandCtas) {
             if (ctas > 0 && c != ctas) continue;
             for (int p : kCandPoints) {
                 if (points > 0 && p != points) continue;
-                st = build(b, c, p, &infeasible);
-                if (st) break;
-                if (infeasible) continue;
-                double ms = 0.0;
-                st = time_runs(b, s, 3, &ms);
-                release(b);
-                if (st) break;
-                ++b->candidates;
-                if (ms < best) {
-                    best = ms;
-                    bc = c;
-                    bp = p;
-                }
+                if ((st = try_shape(c, p, g0))) break;
             }
             if (st) break;
+        }
+        if (!st && bc != 0 && gmb == 0) {
+            const int c = bc, p = bp;
+            for (int g : kCandGroupMb)
+                if (g != g0 && (st = try_shape(c, p, g))) break;
         }
         if (!st && bc == 0) st = fail(QM_ERR_UNSUPPORTED, "qm_batch_create: no shape fits the SM");
         if (!st) {
             const int cands = b->candidates;
-            st = build(b, bc, bp, &infeasible);
+            st = build(b, bc, bp, gbytes(bg), &infeasible);
             b->candidates = cands;
             b->tuned_ms = best;
         }
@@ -453,6 +500,7 @@ extern "C" qm_status qm_batch_query(qm_batch b, qm_batch_info* info) {
     if (!b || !info) return fail(QM_ERR_ARG, "qm_batch_query: NULL argument");
     info->ctas_per_sm = b->ctas;
     info->item_points = b->points;
+    info->group_mb = b->group_mb;
     info->grid = b->grid;
     info->items = b->nitems;
     info->cells = b->ncells;

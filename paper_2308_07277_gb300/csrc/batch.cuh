@@ -297,7 +297,7 @@ __device__ void bk_nlp(const BatchJobDev& J, int chunk, int blk, unsigned char* 
     const int nbt = (nbk + 3) >> 2, npt = (np + 3) >> 2;
     const int npad = npt * 4, bpad = nbt * 4;
     C* sb = (C*)sm;               // [kBatchSG][npad]
-    C* sp = sb + kBatchSG * npad;  // [kBatchSG][bpad]
+    C* sp = sb + kBatchSG * npad;  // [kBatchSG][4][nbt]: band 4 bt + i at [q][i][bt] (conflict-free reads)
     const C* beta = (const C*)J.beta;
     const C* psi = (const C*)J.psi;
     const bool active = tid < nbt * npt;
@@ -315,14 +315,15 @@ __device__ void bk_nlp(const BatchJobDev& J, int chunk, int blk, unsigned char* 
         }
         for (int i = tid; i < bpad * kBatchSG; i += nt) {
             const int b = i / kBatchSG, q = i - b * kBatchSG;
-            sp[q * bpad + b] = (b < nbk && q < ng) ? psi[(size_t)(b0 + b) * J.ld_psi + gs + q] : mk<C>(0, 0);
+            sp[q * bpad + (b & 3) * nbt + (b >> 2)] =
+                (b < nbk && q < ng) ? psi[(size_t)(b0 + b) * J.ld_psi + gs + q] : mk<C>(0, 0);
         }
         __syncthreads();
         if (active) {
             for (int q = 0; q < ng; ++q) {
                 C a[4], w[4];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) a[i] = sp[q * bpad + 4 * bt + i];
+                for (int i = 0; i < 4; ++i) a[i] = sp[q * bpad + i * nbt + bt];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) w[j] = sb[q * npad + 4 * pt + j];
 #pragma unroll

@@ -88,11 +88,11 @@ def small_batch_cells():
 def test_batch_matches_oracle_small(Q, prec, tol):
     cells = small_batch_cells()
     gss, jobs, cases = make_batch(Q, cells, prec, drop_proj=(2,))
-    b = Q.Batch(jobs, prec=prec, ctas_per_sm=2, item_points=2048)
+    b = Q.Batch(jobs, prec=prec, ctas_per_sm=2, item_points=2048, group_mb=1)   # several pipelined groups
     b.run()
     b.check()
     info = b.info()
-    assert info["candidates"] == 0 and info["items"] > 0 and info["band_applies"] == sum(j["psi"].shape[0] for j in jobs)
+    assert info["candidates"] == 0 and info["group_mb"] == 1 and info["items"] > 0 and info["band_applies"] == sum(j["psi"].shape[0] for j in jobs)
     for j, (cell, ik, c, off) in zip(jobs, cases):
         want = oracle_hpsi(c, off)
         got = j["out"].cpu().numpy().astype(np.complex128)
@@ -105,8 +105,8 @@ def test_batch_equals_per_cell_loop_and_is_shape_independent(Q):
     cells = small_batch_cells()
     gss, jobs, cases = make_batch(Q, cells, "fp64", drop_proj=(2,))
     outs = []
-    for shape in [(1, 1024), (2, 4096), (1, 8192)]:       # FP64 fits at most 2 CTAs per SM
-        b = Q.Batch(jobs, prec="fp64", ctas_per_sm=shape[0], item_points=shape[1])
+    for shape in [(1, 1024, -1), (2, 4096, 1), (1, 8192, 2)]:   # FP64 fits at most 2 CTAs per SM
+        b = Q.Batch(jobs, prec="fp64", ctas_per_sm=shape[0], item_points=shape[1], group_mb=shape[2])
         b.run()
         b.check()
         outs.append([j["out"].clone() for j in jobs])
@@ -133,7 +133,7 @@ def test_batch_uneven_cells_full_size(Q, prec, tol):
     gss, jobs, cases = make_batch(Q, cells, prec)
     b = Q.Batch(jobs, prec=prec)
     info = b.info()
-    assert info["candidates"] >= 4 and info["ctas_per_sm"] >= 1 and info["cells"] == 256
+    assert info["candidates"] >= 6 and info["ctas_per_sm"] >= 1 and info["cells"] == 256
     b.run()
     b.check()
     njob = len(jobs)
@@ -163,15 +163,15 @@ def test_batch_errors(Q):
     bad = [dict(jobs[0]), dict(jobs[1])]
     bad[1]["out"] = bad[0]["out"][:3]                    # overlapping out blocks
     with pytest.raises(Q.QMError) as e:
-        Q.Batch(bad, ctas_per_sm=1, item_points=2048)
+        Q.Batch(bad, ctas_per_sm=1, item_points=2048, group_mb=-1)
     assert e.value.status == 1
     with pytest.raises(Q.QMError) as e:
-        Q.Batch(jobs, ctas_per_sm=9, item_points=2048)   # shape out of range
+        Q.Batch(jobs, ctas_per_sm=9, item_points=2048, group_mb=-1)   # shape out of range
     assert e.value.status == 1
     with pytest.raises(Q.QMError) as e:
-        Q.Batch(jobs, ctas_per_sm=8, item_points=65536)  # does not fit an SM
+        Q.Batch(jobs, ctas_per_sm=8, item_points=65536, group_mb=-1)  # does not fit an SM
     assert e.value.status == 7
     alias = [dict(jobs[0])]
     alias[0]["out"] = alias[0]["psi"]                    # out == psi
     with pytest.raises(Q.QMError):
-        Q.Batch(alias, ctas_per_sm=1, item_points=2048)
+        Q.Batch(alias, ctas_per_sm=1, item_points=2048, group_mb=-1)
