@@ -337,8 +337,9 @@ def measure_hpsi(args, Q, lib, g, cell, wl, v, D, world, dev, peaks, sample_cloc
 
 def run_davidson(args, Q, lib, g, cell, wl64, v, D):
     """Block Davidson to args.davidson_tol at every k-point from the seeded random start:
-    the plain FP64 form, the precision form (QM_MIXED), and the precision form with 10 %
-    buffer bands (only the lowest 160 must converge).  Wall time of the qm_davidson calls."""
+    the plain FP64 form, the precision form (QM_MIXED), the precision form with 10 % buffer
+    bands (only the lowest 160 must converge), and that form with the 4 k-point solves run
+    concurrently (qm_davidson_batched).  Wall time of the calls."""
     import numpy as np
     import torch
 
@@ -366,7 +367,26 @@ def run_davidson(args, Q, lib, g, cell, wl64, v, D):
         out[form] = {"seconds_total": time.perf_counter() - t0, "nbnd_solved": nb + extra, "per_k": per_k,
                      "kernels": read_prof(lib)}
         lib.qm_prof_enable(0)
-    for form in ("mixed", "mixed_buffer"):
+    # the batched form: the 4 k-point solves of the buffered precision form run concurrently
+    # (qm_davidson_batched, one stream and workspace each)
+    jobs = []
+    for ik in range(nk):
+        p = torch.from_numpy(S.psi_random(cell.seed, nb + nextra, g.npw[ik], stream=ik)).cuda()
+        jobs.append({"g": g.handle, "ik": ik, "psi": p, "vloc": v, "beta": wl64.beta[ik], "D": D})
+    lib.qm_prof_enable(1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = Q.qm_davidson_batched(jobs, tol=args.davidson_tol, max_iter=300, prec="mixed", nconv=nb,
+                                raise_not_converged=False)
+    torch.cuda.synchronize()
+    out["mixed_buffer_batched"] = {
+        "seconds_total": time.perf_counter() - t0, "nbnd_solved": nb + nextra, "concurrent_jobs": nk,
+        "per_k": [{k: info[k] for k in ("iterations", "iterations_mixed", "band_applies", "max_residual", "converged",
+                                        "seconds")} for _, info in res],
+        "kernels": read_prof(lib)}
+    lib.qm_prof_enable(0)
+    eigs["mixed_buffer_batched"] = [eig[:nb] for eig, _ in res]
+    for form in ("mixed", "mixed_buffer", "mixed_buffer_batched"):
         out[f"speedup_{form}_vs_fp64"] = out["fp64"]["seconds_total"] / out[form]["seconds_total"]
         out[f"max_eig_diff_{form}_vs_fp64_ha"] = float(max(np.abs(a - b).max()
                                                          for a, b in zip(eigs["fp64"], eigs[form])))

@@ -323,6 +323,40 @@ qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, int ld_psi,
                       const double* D, const qm_davidson_opts* opts, double* eig_out,
                       qm_davidson_stats* stats, void* stream);
 
+/* One problem of qm_davidson_batched: the arguments of qm_davidson. */
+typedef struct {
+    qm_gspace g;
+    int ik;
+    int nb;
+    void* psi_inout;            /* device, as qm_davidson */
+    int ld_psi;
+    int nproj;
+    const double* vloc_r;       /* device */
+    const void* beta;           /* device */
+    int ld_beta;
+    const double* D;            /* device */
+    double* eig_out;            /* host, nb doubles */
+    qm_davidson_stats* stats;   /* host, may be NULL */
+    double* history;            /* host, may be NULL: max_iter doubles (replaces opts->history) */
+    qm_status status;           /* out: this job's status */
+} qm_davidson_job;
+
+/*
+ * qm_davidson_batched - many independent Davidson problems (the k-points of a cell, or
+ * cells) solved concurrently (the batched form applied to the eigensolver).  Worker host
+ * threads (max_concurrent, 0 = one per job) take the jobs in order; each runs qm_davidson on
+ * its own CUDA stream with its own device workspace (the job's gspace tables are shared, not
+ * copied), so the jobs' latency-bound steps and host synchronisations overlap on the GPU.
+ * The results are those of qm_davidson for each job (the same options `opts`, except the
+ * per-job `history`).  The workers' streams start after the work queued on `stream` and
+ * `stream` is ordered after them; the call returns when every job is done.
+ * Returns QM_OK, the first error of a job other than QM_ERR_NOT_CONVERGED, or
+ * QM_ERR_NOT_CONVERGED if some job did not converge; each job's own status is in
+ * jobs[i].status.  Jobs may share a gspace and a k-point only if their buffers differ.
+ */
+qm_status qm_davidson_batched(int njobs, qm_davidson_job* jobs, const qm_davidson_opts* opts,
+                              int max_concurrent, void* stream);
+
 /*
  * qm_eigh_lowest - lowest nev eigenpairs of a complex Hermitian m x m matrix in FP64: the
  * dense eigensolver of the Davidson Rayleigh-Ritz step, exposed on its own.  Householder

@@ -126,3 +126,16 @@ SIGNATURES["qm_mlp_loss_grad"] = (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, 
 SIGNATURES["qm_mlp_train"] = (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                              ctypes.c_int, ctypes.c_double, c_double_p, ctypes.c_void_p])
+
+
+class DavidsonJob(ctypes.Structure):
+    """qm_davidson_job of include/qm.h."""
+    _fields_ = [("g", ctypes.c_void_p), ("ik", ctypes.c_int), ("nb", ctypes.c_int), ("psi_inout", ctypes.c_void_p),
+                ("ld_psi", ctypes.c_int), ("nproj", ctypes.c_int), ("vloc_r", ctypes.c_void_p),
+                ("beta", ctypes.c_void_p), ("ld_beta", ctypes.c_int), ("D", ctypes.c_void_p),
+                ("eig_out", ctypes.c_void_p), ("stats", ctypes.POINTER(DavidsonStats)), ("history", ctypes.c_void_p),
+                ("status", ctypes.c_int)]
+
+
+SIGNATURES["qm_davidson_batched"] = (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(DavidsonJob),
+                                                    ctypes.POINTER(DavidsonOpts), ctypes.c_int, ctypes.c_void_p])

@@ -343,3 +343,47 @@ def qm_mlp_train(band_off, feats, r2, c, D, theta, steps, lr, W=None, stream=Non
                                     int(steps), float(lr), _dp(hist),
                                     _stream_ptr(stream)))
     return hist
+
+
+def qm_davidson_batched(jobs, tol=1e-8, max_iter=100, nvecx=0, prec="fp64", nconv=0, mixed_switch=0.0, mlp=None,
+                        max_concurrent=0, stream=None, raise_not_converged=True):
+    """Concurrent Davidson solves.  jobs: list of dicts with keys g, ik, psi (overwritten by
+    the Ritz vectors), vloc, beta, D (CUDA tensors as for qm_davidson).  Returns a list of
+    (eigenvalues ndarray, info dict) in job order."""
+    lib = _lib.load()
+    n = len(jobs)
+    arr = (_lib.DavidsonJob * n)()
+    eigs, stats, hists = [], [], []
+    for i, j in enumerate(jobs):
+        psi, beta = j["psi"], j.get("beta")
+        if psi.dim() != 2:
+            raise ValueError("psi must be 2-D (nb, ld)")
+        nb = int(psi.shape[0])
+        nproj = 0 if beta is None else int(beta.shape[0])
+        eigs.append(np.zeros(nb, np.float64))
+        stats.append(_lib.DavidsonStats())
+        hists.append(np.zeros(max(1, int(max_iter)), np.float64))
+        arr[i] = _lib.DavidsonJob(g=j["g"].value if isinstance(j["g"], ctypes.c_void_p) else j["g"], ik=int(j["ik"]),
+                                  nb=nb, psi_inout=_dev_ptr(psi, "psi", torch.complex128), ld_psi=int(psi.stride(0)),
+                                  nproj=nproj, vloc_r=_dev_ptr(j["vloc"], "vloc", torch.float64),
+                                  beta=_dev_ptr(beta, "beta", torch.complex128) if nproj else None,
+                                  ld_beta=int(beta.stride(0)) if nproj else 0,
+                                  D=_dev_ptr(j["D"], "D", torch.float64) if nproj else None,
+                                  eig_out=eigs[-1].ctypes.data_as(ctypes.c_void_p), stats=ctypes.pointer(stats[-1]),
+                                  history=hists[-1].ctypes.data_as(ctypes.c_void_p))
+    opts = _lib.DavidsonOpts(tol=float(tol), max_iter=int(max_iter), nvecx=int(nvecx), prec=_PREC[prec],
+                             precond=0 if mlp is None else 1, mixed_switch=float(mixed_switch), nconv=int(nconv),
+                             history=None, mlp=_dev_ptr(mlp, "mlp", torch.float32))
+    st = lib.qm_davidson_batched(n, arr, ctypes.byref(opts), int(max_concurrent), _stream_ptr(stream))
+    out = []
+    for i in range(n):
+        s = stats[i]
+        out.append((eigs[i], {"iterations": s.iterations, "converged": bool(s.converged),
+                              "band_applies": s.band_applies, "max_residual": s.max_residual, "seconds": s.seconds,
+                              "iterations_mixed": s.iterations_mixed, "band_applies_mixed": s.band_applies_mixed,
+                              "precond_fallback": s.precond_fallback,
+                              "history": hists[i][: max(0, s.iterations)].tolist(),
+                              "status": STATUS.get(arr[i].status, arr[i].status)}))
+    if st != 0 and not (st == 4 and not raise_not_converged):
+        _check(st)
+    return out

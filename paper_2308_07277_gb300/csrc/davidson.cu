@@ -20,9 +20,14 @@
 // Ritz vectors are re-orthonormalised, H is applied to them in FP64 (refinement sweep), and
 // the iterations continue entirely in FP64.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
+#include <map>
+#include <mutex>
 #include <numeric>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "qm_internal.h"
@@ -500,5 +505,97 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
         stats->precond_fallback = fallback_it;
     }
     if (!converged) return fail(QM_ERR_NOT_CONVERGED, "qm_davidson: max_iter reached before tol");
+    return QM_OK;
+}
+
+// Independent Davidson problems (k-points, cells) run concurrently: worker threads take jobs
+// in order, each on its own CUDA stream with its own workspace (a clone of the job's gspace
+// sharing its device tables), so one job's host synchronisations, small eigensolves and
+// latency-bound kernels overlap with the others' work on the GPU.
+extern "C" qm_status qm_davidson_batched(int njobs, qm_davidson_job* jobs, const qm_davidson_opts* opts,
+                                         int max_concurrent, void* stream) {
+    clear_error();
+    if (njobs < 1 || !jobs) return fail(QM_ERR_ARG, "qm_davidson_batched: no jobs");
+    if (max_concurrent < 0) return fail(QM_ERR_ARG, "qm_davidson_batched: max_concurrent < 0");
+    for (int i = 0; i < njobs; ++i) {
+        if (!jobs[i].g || !jobs[i].psi_inout || !jobs[i].eig_out)
+            return fail(QM_ERR_ARG, "qm_davidson_batched: job " + std::to_string(i) + " lacks g, psi or eig_out");
+        jobs[i].status = QM_OK;
+    }
+    qm_status st;
+    int dev = 0;
+    if ((st = cuda_check(cudaGetDevice(&dev), "cudaGetDevice"))) return st;
+    for (int i = 0; i < njobs; ++i)
+        if ((st = ensure_device(jobs[i].g))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t ready = nullptr;
+    if ((st = cuda_check(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming), "event")) ||
+        (st = cuda_check(cudaEventRecord(ready, s), "event record")))
+        return st;
+    const int nw = std::min(njobs, max_concurrent > 0 ? max_concurrent : njobs);
+    std::atomic<int> next{0};
+    std::mutex mu;
+    std::string first_msg;
+    std::vector<cudaStream_t> wstreams(nw, nullptr);
+    auto worker = [&](int w) {
+        cudaSetDevice(dev);
+        std::map<qm_gspace, qm_gspace> clones;
+        cudaStream_t ws = nullptr;
+        qm_status wst = cuda_check(cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking), "worker stream");
+        if (!wst) wst = cuda_check(cudaStreamWaitEvent(ws, ready, 0), "worker wait");
+        wstreams[w] = ws;
+        for (int i; (i = next.fetch_add(1)) < njobs;) {
+            qm_davidson_job& j = jobs[i];
+            qm_status r = wst;
+            qm_gspace c = nullptr;
+            if (!r) {
+                auto it = clones.find(j.g);
+                if (it == clones.end()) {
+                    r = gspace_clone(j.g, &c);
+                    if (!r) clones[j.g] = c;
+                } else {
+                    c = it->second;
+                }
+            }
+            if (!r) {
+                qm_davidson_opts o{};
+                if (opts) o = *opts;
+                o.history = j.history;
+                r = qm_davidson(c, j.ik, j.nb, j.psi_inout, j.ld_psi, j.vloc_r, j.nproj, j.beta, j.ld_beta, j.D, &o,
+                                j.eig_out, j.stats, ws);
+            }
+            j.status = r;
+            if (r && r != QM_ERR_NOT_CONVERGED) {
+                std::lock_guard<std::mutex> lk(mu);
+                if (first_msg.empty()) first_msg = "job " + std::to_string(i) + ": " + qm_last_error();
+            }
+        }
+        for (auto& kv : clones) qm_gspace_destroy(kv.second);  // synchronises the device
+    };
+    std::vector<std::thread> threads;
+    for (int w = 0; w < nw; ++w) threads.emplace_back(worker, w);
+    for (auto& t : threads) t.join();
+    // order the caller's stream after every job
+    for (int w = 0; w < nw; ++w) {
+        if (!wstreams[w]) continue;
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess) {
+            cudaEventRecord(e, wstreams[w]);
+            cudaStreamWaitEvent(s, e, 0);
+            cudaEventDestroy(e);
+        }
+        cudaStreamDestroy(wstreams[w]);
+    }
+    cudaEventDestroy(ready);
+    qm_status out = QM_OK;
+    for (int i = 0; i < njobs; ++i)
+        if (jobs[i].status && jobs[i].status != QM_ERR_NOT_CONVERGED) {
+            out = jobs[i].status;
+            break;
+        }
+    if (out) return fail(out, "qm_davidson_batched: " + first_msg);
+    for (int i = 0; i < njobs; ++i)
+        if (jobs[i].status == QM_ERR_NOT_CONVERGED)
+            return fail(QM_ERR_NOT_CONVERGED, "qm_davidson_batched: job " + std::to_string(i) + " did not converge");
     return QM_OK;
 }

@@ -537,12 +537,11 @@ qm_status local_kinetic_impl(qm_gspace g, int ik, int nb, const void* psi, int l
     const int nbc = (int)std::max<size_t>(1, std::min<size_t>((size_t)nb, tbuf_bytes / per_band));
     const size_t sm_stick = (size_t)(kSticksPerCta * g->ldx + N1) * sizeof(C);
     const size_t sm_plane = (size_t)(N3 * g->ldy + N2 + N3) * sizeof(C);
-    if (sm_plane > 227 * 1024 || sm_stick > 227 * 1024)
-        return fail(QM_ERR_UNSUPPORTED, "qm_hpsi: FFT plane does not fit in shared memory");
-    // opt in to large dynamic shared memory (per function and device; cheap to repeat)
-    cudaFuncSetAttribute(k_plane<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_plane);
-    cudaFuncSetAttribute(k_stick_inverse<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_stick);
-    cudaFuncSetAttribute(k_stick_forward<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_stick);
+    qm_status st;
+    if ((st = allow_dynamic_smem((const void*)k_plane<R>, sm_plane, "qm_hpsi: FFT plane in shared memory")) ||
+        (st = allow_dynamic_smem((const void*)k_stick_inverse<R>, sm_stick, "qm_hpsi: FFT sticks in shared memory")) ||
+        (st = allow_dynamic_smem((const void*)k_stick_forward<R>, sm_stick, "qm_hpsi: FFT sticks in shared memory")))
+        return st;
     const int ntile = (kt.nstick + kSticksPerCta - 1) / kSticksPerCta;
     const C* tw_x = (const C*)(sizeof(R) == 8 ? (const void*)g->tw64[0] : (const void*)g->tw32[0]);
     const C* tw_y = (const C*)(sizeof(R) == 8 ? (const void*)g->tw64[1] : (const void*)g->tw32[1]);
@@ -588,11 +587,11 @@ qm_status local_kinetic_tab_impl(const DevTables& t, int nb, const void* psi, in
     const int nbc = (int)std::max<size_t>(1, std::min<size_t>((size_t)nb, tbuf_bytes / per_band));
     const size_t sm_stick = (size_t)(kSticksPerCta * t.ldx + N1) * sizeof(C);
     const size_t sm_plane = (size_t)(N3 * t.ldy + N2 + N3) * sizeof(C);
-    if (sm_plane > 227 * 1024 || sm_stick > 227 * 1024)
-        return fail(QM_ERR_UNSUPPORTED, "FFT plane does not fit in shared memory");
-    cudaFuncSetAttribute(k_plane<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_plane);
-    cudaFuncSetAttribute(k_stick_inverse<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_stick);
-    cudaFuncSetAttribute(k_stick_forward<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_stick);
+    qm_status st;
+    if ((st = allow_dynamic_smem((const void*)k_plane<R>, sm_plane, "FFT plane in shared memory")) ||
+        (st = allow_dynamic_smem((const void*)k_stick_inverse<R>, sm_stick, "FFT sticks in shared memory")) ||
+        (st = allow_dynamic_smem((const void*)k_stick_forward<R>, sm_stick, "FFT sticks in shared memory")))
+        return st;
     const int ntile = (t.nstick + kSticksPerCta - 1) / kSticksPerCta;
     const C* tw_x = (const C*)t.tw[0];
     const C* tw_y = (const C*)t.tw[1];

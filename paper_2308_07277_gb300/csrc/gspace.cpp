@@ -9,8 +9,12 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <numeric>
 #include <string>
+
+#include <new>
 
 #include "qm_internal.h"
 
@@ -44,6 +48,36 @@ static qm_status grow(Workspace& ws, size_t bytes, cudaStream_t stream) {
     qm_status st = cuda_check(cudaMalloc(&ws.ptr, want), "workspace cudaMalloc");
     if (st) return st;
     ws.bytes = want;
+    return QM_OK;
+}
+
+qm_status allow_dynamic_smem(const void* kernel, size_t need, const char* what) {
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, int> done;  // (kernel, device) -> limit set
+    int dev = 0;
+    qm_status st = cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+    if (st) return st;
+    int max_dyn = 0;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = done.find({kernel, dev});
+        if (it != done.end()) {
+            max_dyn = it->second;
+        } else {
+            int optin = 0;
+            cudaFuncAttributes fa{};
+            if ((st = cuda_check(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), what)) ||
+                (st = cuda_check(cudaFuncGetAttributes(&fa, kernel), what)))
+                return st;
+            max_dyn = optin - (int)fa.sharedSizeBytes;
+            if ((st = cuda_check(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn),
+                                 what)))
+                return st;
+            done[{kernel, dev}] = max_dyn;
+        }
+    }
+    if ((long long)need > (long long)max_dyn)
+        return fail(QM_ERR_UNSUPPORTED, std::string(what) + ": needs more shared memory than a CTA can have");
     return QM_OK;
 }
 
@@ -156,6 +190,26 @@ qm_status ensure_device(qm_gspace g) {
         (st = cuda_check(cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming), "gspace event")) ||
         (st = cuda_check(cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming), "gspace event")))
         return st;
+    return QM_OK;
+}
+
+qm_status gspace_clone(qm_gspace g, qm_gspace* out) {
+    qm_status st = ensure_device(g);
+    if (st) return st;
+    qm_gspace c = new (std::nothrow) qm_gspace_s(*g);
+    if (!c) return fail(QM_ERR_OOM, "gspace clone: host allocation");
+    c->ws = Workspace{};
+    c->dws = Workspace{};
+    c->aux = nullptr;
+    c->ev_fork = c->ev_join = nullptr;
+    c->shared_tables = true;
+    if ((st = cuda_check(cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking), "gspace stream")) ||
+        (st = cuda_check(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming), "gspace event")) ||
+        (st = cuda_check(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming), "gspace event"))) {
+        qm_gspace_destroy(c);
+        return st;
+    }
+    *out = c;
     return QM_OK;
 }
 
@@ -350,6 +404,7 @@ extern "C" void qm_gspace_destroy(qm_gspace g) {
         cudaSetDevice(g->device);
         cudaDeviceSynchronize();
         for (auto& kt : g->k) {
+            if (g->shared_tables) break;
             cudaFree(kt.stick_g0);
             cudaFree(kt.stick_plane);
             cudaFree(kt.rows);
@@ -357,7 +412,7 @@ extern "C" void qm_gspace_destroy(qm_gspace g) {
             cudaFree(kt.kin);
             cudaFree(kt.kin_f);
         }
-        for (int d = 0; d < 3; ++d) {
+        for (int d = 0; d < 3 && !g->shared_tables; ++d) {
             cudaFree(g->tw64[d]);
             cudaFree(g->tw32[d]);
             cudaFree(g->rev[d]);

@@ -18,6 +18,9 @@
 
 #include <algorithm>
 
+#include <map>
+#include <mutex>
+
 #include "qm_internal.h"
 
 namespace cg = cooperative_groups;
@@ -359,6 +362,22 @@ size_t heev_work_bytes(int m, int nev) {
 
 // Lowest nev eigenpairs of the Hermitian m x m matrix A (lda; destroyed).  evals: nev
 // doubles (device, increasing); Y: m x nev (device, row-major, ld ldy) eigenvectors as columns.
+// the process-wide stream of a device for cooperative launches (created on first use)
+static qm_status cooperative_stream(int dev, cudaStream_t* out) {
+    static std::mutex mu;
+    static std::map<int, cudaStream_t> streams;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = streams.find(dev);
+    if (it == streams.end()) {
+        cudaStream_t cs = nullptr;
+        qm_status st = cuda_check(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "cooperative stream");
+        if (st) return st;
+        it = streams.emplace(dev, cs).first;
+    }
+    *out = it->second;
+    return QM_OK;
+}
+
 qm_status heev_lowest(double2* A, int lda, int m, int nev, double* evals, double2* Y, int ldy, void* work,
                       cudaStream_t s) {
     if (m <= 0 || nev <= 0) return QM_OK;
@@ -388,7 +407,7 @@ qm_status heev_lowest(double2* A, int lda, int m, int nev, double* evals, double
     {
         const size_t smem = 2 * (size_t)m * sizeof(double2);
         if (smem > 200 * 1024) return fail(QM_ERR_UNSUPPORTED, "heev_lowest: m too large for the reduction kernel");
-        cudaFuncSetAttribute(k_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if ((st = allow_dynamic_smem((const void*)k_tridiag, smem, "heev_lowest: reduction kernel"))) return st;
         int dev = 0, sms = 152, occ = 1;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -398,10 +417,28 @@ qm_status heev_lowest(double2* A, int lda, int m, int nev, double* evals, double
         blocks = std::min(blocks, 64);
         void* args[] = {(void*)&A, (void*)&lda, (void*)&m, (void*)&Vh, (void*)&tau, (void*)&d, (void*)&e,
                         (void*)&wbuf};
-        ProfScope pf(PF_TRIDIAG, s);
-        if ((st = cuda_check(cudaLaunchCooperativeKernel((void*)k_tridiag, dim3(blocks), dim3(256), args, smem, s),
-                             "k_tridiag cooperative launch")))
+        // Cooperative grids of concurrent callers (other host threads, other streams) must not
+        // be resident at the same time: two partly resident grids could each wait at a grid
+        // barrier for CTAs the other holds.  Every cooperative launch therefore goes through
+        // one stream per device, joined to the caller's stream by events.
+        cudaStream_t cs = nullptr;
+        if ((st = cooperative_stream(dev, &cs))) return st;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if ((st = cuda_check(cudaEventCreateWithFlags(&e0, cudaEventDisableTiming), "event")) ||
+            (st = cuda_check(cudaEventCreateWithFlags(&e1, cudaEventDisableTiming), "event")))
             return st;
+        st = cuda_check(cudaEventRecord(e0, s), "event record");
+        if (!st) st = cuda_check(cudaStreamWaitEvent(cs, e0, 0), "cooperative stream wait");
+        if (!st) {
+            ProfScope pf(PF_TRIDIAG, cs);
+            st = cuda_check(cudaLaunchCooperativeKernel((void*)k_tridiag, dim3(blocks), dim3(256), args, smem, cs),
+                            "k_tridiag cooperative launch");
+        }
+        if (!st) st = cuda_check(cudaEventRecord(e1, cs), "event record");
+        if (!st) st = cuda_check(cudaStreamWaitEvent(s, e1, 0), "stream wait");
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (st) return st;
     }
     {
         ProfScope pf(PF_MULTISECT, s);
@@ -417,7 +454,7 @@ qm_status heev_lowest(double2* A, int lda, int m, int nev, double* evals, double
     }
     {
         const size_t smem = (size_t)m * sizeof(double2);
-        cudaFuncSetAttribute(k_backtransf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if ((st = allow_dynamic_smem((const void*)k_backtransf, smem, "heev_lowest: back-transformation"))) return st;
         ProfScope pf(PF_BACKTR, s);
         k_backtransf<<<nev, 256, smem, s>>>(Vh, tau, m, Y, ldy);
     }

@@ -606,8 +606,10 @@ qm_status loss_grad_dev(int nband, const long long* off, const int* band_of, lon
                         const float* cc, const float* D, const float* W, const float* theta, float* K, double* A, double* B,
                         float* coef, float* ratio, double* loss_dev, float* gpart, int nblk, float* grad,
                         cudaStream_t s) {
-    cudaFuncSetAttribute(k_mlp_tile<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem);
-    cudaFuncSetAttribute(k_mlp_tile<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem);
+    qm_status st0;
+    if ((st0 = allow_dynamic_smem((const void*)k_mlp_tile<0>, kTileSmem, "network training shared memory")) ||
+        (st0 = allow_dynamic_smem((const void*)k_mlp_tile<1>, kTileSmem, "network training shared memory")))
+        return st0;
     {
         ProfScope pf(PF_MLP, s);
         k_mlp_tile<0><<<nblk, kTT, kTileSmem, s>>>(n, feats, theta, K, nullptr, nullptr, nullptr, nullptr, nullptr,

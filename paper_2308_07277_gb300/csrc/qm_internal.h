@@ -74,6 +74,9 @@ struct qm_gspace_s {
     // FFT path runs on the caller's stream (fork / join events); created with the tables
     cudaStream_t aux = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // a clone shares the device tables of its origin (owned there) and has its own
+    // workspaces, stream and events, so calls on the two can run concurrently
+    bool shared_tables = false;
 };
 
 namespace qm {
@@ -85,12 +88,21 @@ void clear_error();
 
 // upload the handle's tables to the current device on first use (synchronous)
 qm_status ensure_device(qm_gspace g);
+// a handle that shares g's uploaded device tables but owns its workspaces, stream and events
+// (free with qm_gspace_destroy; destroy it before g)
+qm_status gspace_clone(qm_gspace g, qm_gspace* out);
 
 // grow-only workspace owned by a gspace handle; synchronises `stream` before regrowing
 qm_status ensure_workspace(qm_gspace g, size_t bytes, cudaStream_t stream);
 qm_status ensure_dav_workspace(qm_gspace g, size_t bytes, cudaStream_t stream);
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Allow `kernel` the device's per-CTA opt-in maximum of dynamic shared memory (minus its
+// static shared memory), once per (kernel, device), and check `need` against it.  The
+// attribute is global per function: setting it to each launch's own size would race between
+// host threads launching the same kernel with different sizes.
+qm_status allow_dynamic_smem(const void* kernel, size_t need, const char* what);
 
 // ---- launch counting / per-kernel timing (prof.cpp) ----
 enum ProfFamily { PF_VT = 0, PF_STICK_INV, PF_PLANE, PF_STICK_FWD, PF_GEMM_CN, PF_REDUCE, PF_GEMM_TN, PF_OTHER, PF_CHOL,

@@ -322,7 +322,8 @@ qm_status umma_launch(const LA& la, const LB& lb, int M, int N, int kreal, int s
     splits = (ktiles + per - 1) / per;
     if (zout) *zout = splits;
     const size_t smem = 2 * (size_t)STAGE_BYTES;
-    cudaFuncSetAttribute(k_umma_split<LA, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    qm_status st = allow_dynamic_smem((const void*)k_umma_split<LA, LB>, smem, "tensor-core GEMM shared memory");
+    if (st) return st;
     dim3 grid((N + UN - 1) / UN, (M + UM - 1) / UM, splits);
     ProfScope pf(PF_UMMA, s);
     k_umma_split<LA, LB><<<grid, kThreads, smem, s>>>(la, lb, M, N, per, ktiles, C, ldc, zstride, accumulate ? 1 : 0,

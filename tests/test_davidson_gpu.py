@@ -145,3 +145,55 @@ def test_davidson_mixed_config2_full_size(Q, ik):
     eig, X, info = run_gpu(Q, cell, ik, c, tol=1e-8, max_iter=300, prec="mixed")
     assert info["converged"], info
     np.testing.assert_allclose(eig, want, atol=1e-8)
+
+
+def test_davidson_batched_matches_brute_force(Q):
+    """Concurrent solves (the batched form): several cells and k-points at once, each on its
+    own stream; every job's eigenvalues equal brute force."""
+    cells = [S.config1(), S.cubic_si8(10.0, nbnd=8, kpts=[[0.25, 0.25, 0.25], [0.25, -0.25, 0.25]]),
+             S.fcc_si2(16.0, nbnd=6, kpts=[[0.25, -0.25, 0.25]])]
+    gs, jobs, want = [], [], []
+    for cell in cells:
+        g = Q.qm_gspace_create(cell.lattice, cell.kpts, cell.ecut_ha, cell.grid)
+        gs.append(g)
+        for ik in range(len(cell.kpts)):
+            c = make_case(cell, ik)
+            want.append(np.linalg.eigvalsh(OH.dense_h(c["gs"], c["v"], c["beta"], c["D"]))[: cell.nbnd])
+            jobs.append({"g": g, "ik": ik, "psi": dev(c["psi"]), "vloc": dev(c["v"]), "beta": dev(c["beta"]),
+                         "D": dev(c["D"])})
+    try:
+        for prec, conc in (("fp64", 0), ("mixed", 2)):
+            js = [dict(j, psi=j["psi"].clone()) for j in jobs]
+            res = Q.qm_davidson_batched(js, tol=1e-9, max_iter=300, prec=prec, max_concurrent=conc)
+            torch.cuda.synchronize()
+            for (eig, info), ev in zip(res, want):
+                assert info["converged"] and info["status"] == "QM_OK", info
+                np.testing.assert_allclose(eig, ev, atol=TOL_EIG)
+    finally:
+        for g in gs:
+            Q.qm_gspace_destroy(g)
+
+
+def test_davidson_batched_config2_all_k(Q):
+    gold = os.path.join(ROOT, "tests", "golden", "config2_eigs.txt")
+    if not os.path.exists(gold):
+        pytest.skip("tests/golden/config2_eigs.txt not generated")
+    want = {}
+    for line in open(gold):
+        if line.startswith("k"):
+            k, *vals = line.split()
+            want[int(k[1:])] = np.array([float(x) for x in vals])
+    cell = S.config2()
+    g = Q.qm_gspace_create(cell.lattice, cell.kpts, cell.ecut_ha, cell.grid)
+    try:
+        jobs = []
+        for ik in range(len(cell.kpts)):
+            c = make_case(cell, ik, nb=cell.nbnd + 16)
+            jobs.append({"g": g, "ik": ik, "psi": dev(c["psi"]), "vloc": dev(c["v"]), "beta": dev(c["beta"]),
+                         "D": dev(c["D"])})
+        res = Q.qm_davidson_batched(jobs, tol=1e-8, max_iter=300, prec="mixed", nconv=cell.nbnd)
+        for ik, (eig, info) in enumerate(res):
+            assert info["converged"], info
+            np.testing.assert_allclose(eig[: cell.nbnd], want[ik], atol=1e-8)
+    finally:
+        Q.qm_gspace_destroy(g)
