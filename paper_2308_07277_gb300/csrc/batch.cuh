@@ -222,21 +222,8 @@ __device__ void bk_k2(const BatchJobDev& J, const R* vt, int grp, int p1, unsign
     }
     __syncthreads();
     fft_lines_b<C, +1, true, false>(plane, 1, ldy, nbp * J.nrow, J.rows2, J.py, twy, tid, nt);
-    fft_lines_b<C, +1, true, true>(plane, ldy, 1, nbp * N2, J.cols2, J.pz, twz, tid, nt);
-    const R* v = vt + (size_t)p1 * N3 * N2;
-    const int npl = N3 * N2;
-    const RDiv dp{npl, 1.0f / (float)npl};
-    const RDiv d2{N2, 1.0f / (float)N2};
-    for (int i = tid; i < nbp * npl; i += nt) {
-        const int bi = dp.div(i), rem = i - bi * npl;
-        const int r = d2.div(rem), c = rem - r * N2;
-        const R s = ldcg(v + rem);
-        C* x = plane + bi * ps + r * ldy + c;
-        const C y = *x;
-        *x = mk<C>(y.x * s, y.y * s);
-    }
-    __syncthreads();
-    fft_lines_b<C, -1, false, true>(plane, ldy, 1, nbp * N2, J.cols2, J.pz, twz, tid, nt);
+    // z: inverse, V(r)/N_r, forward (one fused pass for the compile-time lengths)
+    fft_z_vmul<C, R>(plane, ldy, nbp * N2, J.cols2, N2, vt + (size_t)p1 * N3 * N2, N2, J.pz, twz, tid, nt);
     fft_lines_b<C, -1, false, false>(plane, 1, ldy, nbp * J.nrow, J.rows2, J.py, twy, tid, nt);
     for (int i = tid; i < nbp * nst; i += nt) {
         const int bi = ds.div(i), s = i - bi * nst;

@@ -172,7 +172,7 @@ __device__ __forceinline__ void fft_stage(C* buf, int es, int ls, int nlines, co
         }
         const int blk = bf / M;
         const int n1 = bf - blk * M;
-        const int lrow = lmap ? __ldg(lmap + line) : line;
+        const int lrow = lmap ? lmap[line] : line;  // the map may live in shared memory
         C* p = buf + lrow * ls + (blk * L + n1) * es;
         const int me = M * es;
         C u[R];
@@ -265,7 +265,7 @@ __device__ __forceinline__ void fft_stage_ct(C* buf, int es, int ls, int nlines,
         }
         const int blk = bf / M;
         const int n1 = bf - blk * M;
-        const int lrow = lmap ? __ldg(lmap + line) : line;
+        const int lrow = lmap ? lmap[line] : line;  // the map may live in shared memory
         C* p = buf + lrow * ls + (blk * L + n1) * es;
         const int me = M * es;
         C u[R];
@@ -309,31 +309,35 @@ __device__ __forceinline__ void fft_stages_ct_to(C* buf, int es, int ls, int nli
     }
 }
 
-// Inverse z transform of the ncol columns of a plane, multiplication by the real V, forward z
-// transform.  The last DIF stage of the inverse and the first DIT stage of the forward
-// transform act on the same blocks of consecutive z positions with unit twiddles, so they and
-// the V multiply are one pass in registers (bitwise the same result as three passes).
-// V of element (z, c) is v[z * ldv + c].
+// Inverse z transform of the ncol columns of a plane (or of stacked planes: column l starts
+// at cmap[l], NULL = l), multiplication by the real V, forward z transform.  The last DIF
+// stage of the inverse and the first DIT stage of the forward transform act on the same
+// blocks of consecutive z positions with unit twiddles, so they and the V multiply are one
+// pass in registers (bitwise the same result as three passes).  V of element (z, column l) is
+// v[z * ldv + l % nv] (nv = columns of one plane), read through L2 (it may have been written
+// by the same launch).
 template <class C, class R, int N>
-__device__ __forceinline__ void fft_z_vmul_ct(C* buf, int ldy, int ncol, const R* __restrict__ v, int ldv,
-                                              const C* tw, int tid, int nt) {
+__device__ __forceinline__ void fft_z_vmul_ct(C* buf, int ldy, int ncol, const int* cmap, int nv,
+                                              const R* __restrict__ v, int ldv, const C* tw, int tid, int nt) {
     constexpr CPlan P = make_cplan(N);
     constexpr int RL = P.r[P.nst - 1];
     constexpr int NBLK = N / RL;
     RDiv ld{ncol, 1.0f / (float)ncol};
-    fft_stages_ct_to<C, +1, true, N, 0, P.nst - 1>(buf, ldy, 1, ncol, ld, nullptr, tw, tid, nt);
+    RDiv dv{nv, 1.0f / (float)nv};
+    fft_stages_ct_to<C, +1, true, N, 0, P.nst - 1>(buf, ldy, 1, ncol, ld, cmap, tw, tid, nt);
     for (int t = tid; t < ncol * NBLK; t += nt) {
         const int blk = ld.div(t);
         const int col = t - blk * ncol;
-        C* p = buf + col + blk * RL * ldy;
-        const R* vv = v + col + blk * RL * ldv;
+        const int vc = cmap ? col - dv.div(col) * nv : col;
+        C* p = buf + (cmap ? cmap[col] : col) + blk * RL * ldy;
+        const R* vv = v + vc + blk * RL * ldv;
         C u[RL];
 #pragma unroll
         for (int j = 0; j < RL; ++j) u[j] = p[j * ldy];
         Dft<C, +1, RL>::run(u);
 #pragma unroll
         for (int j = 0; j < RL; ++j) {
-            const R sc = __ldg(vv + j * ldv);
+            const R sc = __ldcg(vv + j * ldv);  // L2 path: V may have been written by the same launch
             u[j] = mk<C>(u[j].x * sc, u[j].y * sc);
         }
         Dft<C, -1, RL>::run(u);
@@ -341,7 +345,7 @@ __device__ __forceinline__ void fft_z_vmul_ct(C* buf, int ldy, int ncol, const R
         for (int j = 0; j < RL; ++j) p[j * ldy] = u[j];
     }
     __syncthreads();
-    fft_stages_ct<C, -1, false, true, N, P.nst - 2>(buf, ldy, 1, ncol, ld, nullptr, tw, tid, nt);
+    fft_stages_ct<C, -1, false, true, N, P.nst - 2>(buf, ldy, 1, ncol, ld, cmap, tw, tid, nt);
 }
 
 template <class C, int SG, bool DIF, bool LINE_FAST, int N>
@@ -380,26 +384,28 @@ __device__ void fft_lines(C* buf, int es, int ls, int nlines, const int* lmap, c
     }
 }
 
-// z transforms of a plane with the V multiply between them (ends with __syncthreads())
+// z transforms of a plane (or stacked planes, see fft_z_vmul_ct) with the V multiply between
+// them (ends with __syncthreads())
 template <class C, class R>
-__device__ void fft_z_vmul(C* buf, int ldy, int ncol, const R* __restrict__ v, int ldv, const AxisPlan& pz,
-                           const C* tw, int tid, int nt) {
+__device__ void fft_z_vmul(C* buf, int ldy, int ncol, const int* cmap, int nv, const R* __restrict__ v, int ldv,
+                           const AxisPlan& pz, const C* tw, int tid, int nt) {
     switch (pz.n) {
 #define QM_CASE(n) \
-    case n: fft_z_vmul_ct<C, R, n>(buf, ldy, ncol, v, ldv, tw, tid, nt); return;
+    case n: fft_z_vmul_ct<C, R, n>(buf, ldy, ncol, cmap, nv, v, ldv, tw, tid, nt); return;
         QM_FFT_LENGTHS(QM_CASE)
 #undef QM_CASE
         default: break;
     }
-    fft_lines<C, +1, true, true>(buf, ldy, 1, ncol, nullptr, pz, tw, tid, nt);
+    fft_lines<C, +1, true, true>(buf, ldy, 1, ncol, cmap, pz, tw, tid, nt);
     for (int i = tid; i < pz.n * ncol; i += nt) {
-        const int r = i / ncol, c = i - r * ncol;
-        const R sc = __ldg(v + r * ldv + c);
-        C x = buf[r * ldy + c];
-        buf[r * ldy + c] = mk<C>(x.x * sc, x.y * sc);
+        const int r = i / ncol, l = i - r * ncol;
+        const R sc = __ldcg(v + r * ldv + l % nv);
+        C* x = buf + (cmap ? cmap[l] : l) + r * ldy;
+        const C y = *x;
+        *x = mk<C>(y.x * sc, y.y * sc);
     }
     __syncthreads();
-    fft_lines<C, -1, false, true>(buf, ldy, 1, ncol, nullptr, pz, tw, tid, nt);
+    fft_lines<C, -1, false, true>(buf, ldy, 1, ncol, cmap, pz, tw, tid, nt);
 }
 
 constexpr int kSticksPerCta = 32;
@@ -463,7 +469,7 @@ k_plane(typename Cx<R>::T* __restrict__ T, int nstick, int nstick_pad, const int
     // inverse y on the active rows; z on every column: inverse, V(r)/N_r (in the permuted,
     // digit-reversed order of all three axes), forward; forward y on the active rows
     fft_lines<C, +1, true, false>(plane, 1, ldy, nrow, rows, py, twy, tid, nt);
-    fft_z_vmul<C, R>(plane, ldy, N2, Vt + (size_t)p1 * N3 * N2, N2, pz, twz, tid, nt);
+    fft_z_vmul<C, R>(plane, ldy, N2, nullptr, N2, Vt + (size_t)p1 * N3 * N2, N2, pz, twz, tid, nt);
     fft_lines<C, -1, false, false>(plane, 1, ldy, nrow, rows, py, twy, tid, nt);
     for (int s = tid; s < nstick; s += nt) Tp[s] = plane[__ldg(stick_plane + s)];
 }
