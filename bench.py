@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--davidson-tol", type=float, default=1e-8)
     ap.add_argument("--batched", type=int, default=1, help="also time the batched form (0: skip)")
     ap.add_argument("--large", type=int, default=1, help="also time H psi on the 216- and 255-atom cells (0: skip)")
+    ap.add_argument("--davidson-large", type=int, default=0,
+                    help="1: also time Davidson on the 216-atom cell (learned vs TPA) and the 255-atom cell (all "
+                         "forms combined vs plain FP64); several minutes")
     return ap.parse_args()
 
 
@@ -516,6 +519,110 @@ def run_large_cells(args, Q, S, dev):
     return out
 
 
+def train_network(Q, S, dev):
+    """The learned preconditioner trained as the library's training driver does it: samples
+    from Davidson snapshots on 12 small cells of the uneven-cell generator (seed 101, disjoint
+    from every workload's), 1500 full-batch Adam steps."""
+    import torch
+    from paper_2308_07277_gb300 import learned
+    cells = [c for c in S.config3_cells(lambda c: product_grid(Q, c), n=40, seed=101)
+             if c.grid[0] * c.grid[1] * c.grid[2] <= 30 ** 3][:12]
+    parts = []
+    t0 = time.time()
+    for cell in cells:
+        nb = min(cell.nbnd, 16)
+        g = Q.GSpace(cell.lattice, cell.kpts[:1], cell.ecut_ha, cell.grid)
+        _, _, kpg = g.indices(0)
+        v = torch.from_numpy(S.vloc_on_grid(cell.lattice, cell.tau, cell.grid, cell.depth, cell.width,
+                                            ortho_period=cell.ortho_period)).to(dev)
+        beta = torch.from_numpy(S.beta_of_q(kpg, cell.tau, cell.omega, cell.rc)).to(dev)
+        D = torch.from_numpy(S.dvals(cell.nat)).to(dev)
+        psi = torch.from_numpy(S.psi_random(cell.seed, nb + 8, g.npw[0], stream=0)).to(dev)
+        parts += learned.collect(g.handle, 0, v, beta, D, psi, nb)
+        g.close()
+    ds = learned.assemble(parts)
+    theta = learned.init_theta(1, dev)
+    hist = learned.train(ds, theta, steps=1500, lr=1e-3)
+    return theta, {"samples": int(ds[1].shape[0]), "bands": int(ds[0].numel() - 1), "loss_first": float(hist[0]),
+                   "loss_last": float(hist[-1]), "seconds": time.time() - t0}
+
+
+def run_davidson_large(args, Q, S, dev):
+    """Davidson to 1e-8 Ha on the learned-form workload (216-atom cell, 480 bands, Gamma;
+    precision form with 10 % buffer bands, TPA vs the trained network) and the combined
+    workload (255-atom cell, 288 bands, 4 k: plain FP64 one k-point after another vs the
+    precision form with buffer bands, the learned preconditioner and the 4 k-points solved
+    concurrently)."""
+    import numpy as np
+    import torch
+    theta, tinfo = train_network(Q, S, dev)
+    out = {"training": tinfo}
+    # learned-form workload
+    cell = S.config4()
+    g = Q.GSpace(cell.lattice, cell.kpts, cell.ecut_ha, cell.grid)
+    _, _, kpg = g.indices(0)
+    v = torch.from_numpy(S.vloc_on_grid(cell.lattice, cell.tau, cell.grid)).to(dev)
+    beta = torch.from_numpy(S.beta_of_q(kpg, cell.tau, cell.omega)).to(dev)
+    D = torch.from_numpy(S.dvals(cell.nat)).to(dev)
+    nb, nextra = cell.nbnd, cell.nbnd // 10
+    rec = {}
+    eigs = {}
+    for name, mlp in (("tpa", None), ("learned", theta)):
+        p = torch.from_numpy(S.psi_random(cell.seed, nb + nextra, g.npw[0], stream=0)).to(dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        eig, info = Q.qm_davidson(g.handle, 0, p, v, beta, D, tol=args.davidson_tol, max_iter=300, prec="mixed",
+                                  nconv=nb, mlp=mlp, raise_not_converged=False)
+        torch.cuda.synchronize()
+        rec[name] = {"seconds": time.perf_counter() - t0, **{k: info[k] for k in (
+            "iterations", "iterations_mixed", "band_applies", "converged", "max_residual", "precond_fallback")}}
+        eigs[name] = eig[:nb]
+    rec["max_eig_diff_ha"] = float(np.abs(eigs["tpa"] - eigs["learned"]).max())
+    out[cell.name] = rec
+    del beta, p
+    g.close()
+    torch.cuda.empty_cache()
+    # combined workload
+    cell = S.config5()
+    g = Q.GSpace(cell.lattice, cell.kpts, cell.ecut_ha, cell.grid)
+    v = torch.from_numpy(S.vloc_on_grid(cell.lattice, cell.tau, cell.grid)).to(dev)
+    D = torch.from_numpy(S.dvals(cell.nat)).to(dev)
+    nk, nb, nextra = len(cell.kpts), cell.nbnd, cell.nbnd // 10
+    betas = []
+    for ik in range(nk):
+        _, _, kpg = g.indices(ik)
+        betas.append(torch.from_numpy(S.beta_of_q(kpg, cell.tau, cell.omega)).to(dev))
+    rec = {}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e64, its = [], []
+    for ik in range(nk):
+        p = torch.from_numpy(S.psi_random(cell.seed, nb, g.npw[ik], stream=ik)).to(dev)
+        eig, info = Q.qm_davidson(g.handle, ik, p, v, betas[ik], D, tol=args.davidson_tol, max_iter=300,
+                                  prec="fp64", raise_not_converged=False)
+        e64.append(eig)
+        its.append((info["iterations"], info["converged"]))
+        del p
+    torch.cuda.synchronize()
+    rec["fp64"] = {"seconds": time.perf_counter() - t0, "iterations_converged": its}
+    jobs = [{"g": g.handle, "ik": ik, "vloc": v, "beta": betas[ik], "D": D,
+             "psi": torch.from_numpy(S.psi_random(cell.seed, nb + nextra, g.npw[ik], stream=ik)).to(dev)}
+            for ik in range(nk)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = Q.qm_davidson_batched(jobs, tol=args.davidson_tol, max_iter=300, prec="mixed", nconv=nb, mlp=theta,
+                                raise_not_converged=False)
+    torch.cuda.synchronize()
+    rec["combined"] = {"seconds": time.perf_counter() - t0,
+                       "iterations_converged": [(i["iterations"], i["converged"]) for _, i in res],
+                       "precond_fallback": [i["precond_fallback"] for _, i in res]}
+    rec["speedup_combined_vs_fp64"] = rec["fp64"]["seconds"] / rec["combined"]["seconds"]
+    rec["max_eig_diff_ha"] = float(max(np.abs(a - e[:nb]).max() for a, (e, _) in zip(e64, res)))
+    out[cell.name] = rec
+    g.close()
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -542,6 +649,7 @@ def run_ours(args):
     dav = run_davidson(args, Q, lib, g, cell, wl["fp64"], v, D) if args.davidson else None
     batched = run_batched(args, Q, S, dev) if args.batched else None
     large = run_large_cells(args, Q, S, dev) if args.large else None
+    dav_large = run_davidson_large(args, Q, S, dev) if args.davidson_large else None
     if rank == 0:
         head = forms["mixed"]
         line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -559,6 +667,7 @@ def run_ours(args):
                 "davidson": dav,
                 "batched": batched,
                 "large_cells": large,
+                "davidson_large": dav_large,
                 "cpu_baseline": oracle_sample(args.cpu_sample_bands)}
         print(json.dumps(line))
     g.close()
