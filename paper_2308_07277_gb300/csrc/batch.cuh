@@ -13,7 +13,8 @@
 //   K3   (job, tile)            forward x transform, gather, + 1/2|k+G|^2 psi
 //   NLA  (job, G tile)          out += sum_p beta_p Pd[b][p]
 //
-// CTAs take items with a global ticket counter (atomicAdd), so items start in array order.
+// CTAs take items with a global ticket counter (atomicAdd; a CTA holds its current ticket and
+// the next one), so items start in array order.
 // An item waits (thread 0 polls a per-job counter with acquire loads) only for items of an
 // earlier phase, which hold smaller tickets and are therefore already running on resident
 // CTAs: the scheme cannot deadlock whatever the grid size.  A finished item publishes its
@@ -414,18 +415,21 @@ __device__ void bk_nla(const BatchJobDev& J, int tile, unsigned char* sm, int ti
 
 // ---------------------------------------------------------------- the persistent kernel
 template <class R>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 3 : 2)  // FP32: 3 CTAs per SM, FP64: 2
 k_batch(const BatchJobDev* __restrict__ jobs, const BatchCellDev* __restrict__ cells, const int4* __restrict__ items,
         int nitems, int* cnt, int* cell_cnt, int* head, int* err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(16) BatchJobDev J;
-    __shared__ int s_item, s_go;
+    __shared__ int s_item, s_next, s_go;
     const int tid = threadIdx.x, nt = blockDim.x;
+    if (tid == 0) s_item = atomicAdd(head, 1);
+    __syncthreads();
     for (;;) {
-        if (tid == 0) s_item = atomicAdd(head, 1);
-        __syncthreads();
         const int it = s_item;
         if (it >= nitems) return;
+        // the next ticket is taken now (its latency hides behind this item); it is larger than
+        // this one, so every wait still points to a smaller ticket than the waiter's
+        if (tid == 0) s_next = atomicAdd(head, 1);
         const int4 w = __ldg(items + it);
         if (w.x != BK_VT) {
             const int* src = reinterpret_cast<const int*>(jobs + w.y);
@@ -479,7 +483,9 @@ k_batch(const BatchJobDev* __restrict__ jobs, const BatchCellDev* __restrict__ c
                 __threadfence();
                 atomicAdd(c, 1);
             }
+            s_item = s_next;
         }
+        __syncthreads();
     }
 }
 

@@ -408,7 +408,8 @@ __device__ void fft_z_vmul(C* buf, int ldy, int ncol, const int* cmap, int nv, c
     fft_lines<C, -1, false, true>(buf, ldy, 1, ncol, cmap, pz, tw, tid, nt);
 }
 
-constexpr int kSticksPerCta = 32;
+// x sticks per CTA of the stick kernels: 64 in FP32 (19 KB of lines), 32 in FP64
+template <class R> constexpr int sticks_per_cta() { return sizeof(R) == 4 ? 64 : 32; }
 constexpr int kThreads = 256;
 
 // ---------------------------------------------------------------- K1
@@ -420,11 +421,11 @@ k_stick_inverse(const typename Cx<R>::T* __restrict__ psi, int ld_psi, const int
     using C = typename Cx<R>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* lines = reinterpret_cast<C*>(smem_raw);
-    C* tw = lines + kSticksPerCta * ldx;
+    C* tw = lines + sticks_per_cta<R>() * ldx;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int b = blockIdx.y;
-    const int s0 = blockIdx.x * kSticksPerCta;
-    const int ns = min(kSticksPerCta, nstick - s0);
+    const int s0 = blockIdx.x * sticks_per_cta<R>();
+    const int ns = min(sticks_per_cta<R>(), nstick - s0);
     const int N1 = px.n;
     for (int i = tid; i < N1; i += nt) tw[i] = tw_x[i];
     for (int i = tid; i < ns * ldx; i += nt) lines[i] = mk<C>(0, 0);
@@ -485,11 +486,11 @@ k_stick_forward(const typename Cx<R>::T* __restrict__ T, int nstick, int nstick_
     using C = typename Cx<R>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* lines = reinterpret_cast<C*>(smem_raw);
-    C* tw = lines + kSticksPerCta * ldx;
+    C* tw = lines + sticks_per_cta<R>() * ldx;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int b = blockIdx.y;
-    const int s0 = blockIdx.x * kSticksPerCta;
-    const int ns = min(kSticksPerCta, nstick - s0);
+    const int s0 = blockIdx.x * sticks_per_cta<R>();
+    const int ns = min(sticks_per_cta<R>(), nstick - s0);
     const int N1 = px.n;
     for (int i = tid; i < N1; i += nt) tw[i] = tw_x[i];
     const C* srcT = T + (size_t)b * N1 * nstick_pad + s0;
@@ -541,14 +542,14 @@ qm_status local_kinetic_impl(qm_gspace g, int ik, int nb, const void* psi, int l
     const int N1 = g->n[0], N2 = g->n[1], N3 = g->n[2];
     const size_t per_band = (size_t)N1 * kt.nstick_pad * sizeof(C);
     const int nbc = (int)std::max<size_t>(1, std::min<size_t>((size_t)nb, tbuf_bytes / per_band));
-    const size_t sm_stick = (size_t)(kSticksPerCta * g->ldx + N1) * sizeof(C);
+    const size_t sm_stick = (size_t)(sticks_per_cta<R>() * g->ldx + N1) * sizeof(C);
     const size_t sm_plane = (size_t)(N3 * g->ldy + N2 + N3) * sizeof(C);
     qm_status st;
     if ((st = allow_dynamic_smem((const void*)k_plane<R>, sm_plane, "qm_hpsi: FFT plane in shared memory")) ||
         (st = allow_dynamic_smem((const void*)k_stick_inverse<R>, sm_stick, "qm_hpsi: FFT sticks in shared memory")) ||
         (st = allow_dynamic_smem((const void*)k_stick_forward<R>, sm_stick, "qm_hpsi: FFT sticks in shared memory")))
         return st;
-    const int ntile = (kt.nstick + kSticksPerCta - 1) / kSticksPerCta;
+    const int ntile = (kt.nstick + sticks_per_cta<R>() - 1) / sticks_per_cta<R>();
     const C* tw_x = (const C*)(sizeof(R) == 8 ? (const void*)g->tw64[0] : (const void*)g->tw32[0]);
     const C* tw_y = (const C*)(sizeof(R) == 8 ? (const void*)g->tw64[1] : (const void*)g->tw32[1]);
     const C* tw_z = (const C*)(sizeof(R) == 8 ? (const void*)g->tw64[2] : (const void*)g->tw32[2]);
@@ -591,14 +592,14 @@ qm_status local_kinetic_tab_impl(const DevTables& t, int nb, const void* psi, in
     const size_t per_band = (size_t)N1 * t.nstick_pad * sizeof(C);
     if (tbuf_bytes < per_band) return fail(QM_ERR_ARG, "stick buffer smaller than one band");
     const int nbc = (int)std::max<size_t>(1, std::min<size_t>((size_t)nb, tbuf_bytes / per_band));
-    const size_t sm_stick = (size_t)(kSticksPerCta * t.ldx + N1) * sizeof(C);
+    const size_t sm_stick = (size_t)(sticks_per_cta<R>() * t.ldx + N1) * sizeof(C);
     const size_t sm_plane = (size_t)(N3 * t.ldy + N2 + N3) * sizeof(C);
     qm_status st;
     if ((st = allow_dynamic_smem((const void*)k_plane<R>, sm_plane, "FFT plane in shared memory")) ||
         (st = allow_dynamic_smem((const void*)k_stick_inverse<R>, sm_stick, "FFT sticks in shared memory")) ||
         (st = allow_dynamic_smem((const void*)k_stick_forward<R>, sm_stick, "FFT sticks in shared memory")))
         return st;
-    const int ntile = (t.nstick + kSticksPerCta - 1) / kSticksPerCta;
+    const int ntile = (t.nstick + sticks_per_cta<R>() - 1) / sticks_per_cta<R>();
     const C* tw_x = (const C*)t.tw[0];
     const C* tw_y = (const C*)t.tw[1];
     const C* tw_z = (const C*)t.tw[2];
