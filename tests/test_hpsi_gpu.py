@@ -184,3 +184,50 @@ def test_hpsi_argument_errors_on_device(Q):
             Q.qm_hpsi(g, 3, psi, dev(c["v"]), None, None)
     finally:
         Q.qm_gspace_destroy(g)
+
+
+@pytest.mark.parametrize("cell", S.small_cells(), ids=lambda c: f"{c.name}_{c.ecutwfc_ry:g}Ry")
+def test_hpsi_mixed_small_cells(Q, cell):
+    """Precision form on the small cells (runtime-plan lengths, radix 5, N1 != N2, k != 0)."""
+    g = _gspace(Q, cell)
+    try:
+        c = make_case(cell, 0)
+        want = OH.hpsi_fft(c["psi"], c["gs"], c["v"], c["beta"], c["D"])
+        assert band_rel_err(gpu_hpsi(Q, g, 0, c, prec="mixed"), want).max() <= TOL_MIXED
+    finally:
+        Q.qm_gspace_destroy(g)
+
+
+def test_hpsi_mixed_padded_rows_local_only_and_repeatable(Q):
+    cell = S.cubic_si8(12.0, nbnd=7, reps=(2, 1, 1), kpts=[[0.25, 0.25, -0.25]])
+    g = _gspace(Q, cell)
+    try:
+        c = make_case(cell, 0)
+        want = OH.hpsi_fft(c["psi"], c["gs"], c["v"], c["beta"], c["D"])
+        a = gpu_hpsi(Q, g, 0, c, prec="mixed", ld_pad=5)
+        assert band_rel_err(a, want).max() <= TOL_MIXED
+        b = gpu_hpsi(Q, g, 0, c, prec="mixed", ld_pad=5)
+        np.testing.assert_array_equal(a, b)             # the two streams give a fixed result
+        want_loc = OH.hpsi_fft(c["psi"], c["gs"], c["v"], None, None)
+        assert band_rel_err(gpu_hpsi(Q, g, 0, c, prec="mixed", with_nl=False, ld_pad=3), want_loc).max() <= TOL_MIXED
+    finally:
+        Q.qm_gspace_destroy(g)
+
+
+@pytest.mark.parametrize("cell,ik", _full_size_cells(), ids=lambda x: getattr(x, "name", str(x)))
+def test_hpsi_mixed_full_size_sampled_bands(Q, cell, ik):
+    """Precision form with every band in one call (the benchmark's launch configuration: one
+    stick buffer for all bands, the tensor-core nonlocal part overlapped on the second stream);
+    sampled bands against the oracle."""
+    g = _gspace(Q, cell)
+    try:
+        c = make_case(cell, ik)
+        got = gpu_hpsi(Q, g, ik, c, prec="mixed")
+        nb = cell.nbnd
+        sample = sorted({0, 1, nb // 2, nb - 2, nb - 1})
+        want = OH.hpsi_fft(c["psi"][sample], c["gs"], c["v"], c["beta"], c["D"])
+        rel = band_rel_err(got[sample], want)
+        print(f"{cell.name} k{ik}: mixed max sampled band rel err {rel.max():.2e}")
+        assert rel.max() <= TOL_MIXED
+    finally:
+        Q.qm_gspace_destroy(g)
