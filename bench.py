@@ -45,8 +45,8 @@ FLOP_PER_CLK_SM = {"fp64": 4, "mixed": 256}
 
 # DRAM bytes per band of a dominant kernel, from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum) of the current kernel on this workload, scaled to a launch by its
-# band count: k_plane<float>, one 160-band launch, 79.4 MB read + 86.4 MB written.
-TRAFFIC_PER_BAND = {("k_plane", "mixed"): (79.41e6 + 86.36e6) / 160}
+# band count: k_plane<float>, one 160-band launch, 79.4 MB read + 86.0 MB written.
+TRAFFIC_PER_BAND = {("k_plane", "mixed"): (79.41e6 + 86.01e6) / 160}
 
 
 def parse():
