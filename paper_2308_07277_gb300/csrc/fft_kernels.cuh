@@ -271,13 +271,18 @@ __device__ __forceinline__ void fft_stage_ct(C* buf, int es, int ls, int nlines,
         C u[R];
 #pragma unroll
         for (int j = 0; j < R; ++j) u[j] = p[j * me];
+        // a stage with one butterfly per block (M = 1) has unit twiddles: no multiply (exact)
         if (DIF) {
             Dft<C, SG, R>::run(u);
+            if constexpr (M > 1) {
 #pragma unroll
-            for (int k2 = 1; k2 < R; ++k2) u[k2] = cmul(u[k2], twid<C, SG>(tw, n1 * k2 * STEP));
+                for (int k2 = 1; k2 < R; ++k2) u[k2] = cmul(u[k2], twid<C, SG>(tw, n1 * k2 * STEP));
+            }
         } else {
+            if constexpr (M > 1) {
 #pragma unroll
-            for (int k2 = 1; k2 < R; ++k2) u[k2] = cmul(u[k2], twid<C, SG>(tw, n1 * k2 * STEP));
+                for (int k2 = 1; k2 < R; ++k2) u[k2] = cmul(u[k2], twid<C, SG>(tw, n1 * k2 * STEP));
+            }
             Dft<C, SG, R>::run(u);
         }
 #pragma unroll
