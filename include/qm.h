@@ -263,7 +263,8 @@ typedef struct {
     int max_iter;        /* maximum Rayleigh-Ritz steps; default 100 */
     int nvecx;           /* maximum basis size, >= 2 nb (clamped to npw); default 4 nb */
     qm_precision prec;   /* QM_FP64: every step in FP64.  QM_MIXED: H psi in FP32 (qm_hpsi
-                            QM_MIXED) and the subspace products in FP32 arithmetic until the
+                            QM_MIXED) and the subspace products as BF16x3 tensor-core products
+                            (FP32 accuracy, see mixed_ortho) until the
                             largest residual falls below mixed_switch; then the Ritz vectors are
                             re-orthonormalised and H applied to them in FP64, and the iterations
                             continue in FP64 to tol.  Eigensolves, residual norms and band
@@ -275,7 +276,10 @@ typedef struct {
                             residual, once below 1e-3, stops halving over 10 steps); 0 -> 1e-4 */
     int nconv;           /* only the lowest nconv bands must reach tol (1..nb; 0 -> nb); the
                             other nb - nconv trial vectors are a buffer that speeds convergence */
-    int reserved;        /* must be 0 */
+    int mixed_ortho;     /* QM_MIXED, FP32 phase: 0 (default) = every subspace product on the
+                            tensor cores (BF16x3 split, FP32 accumulation, basis orthonormal to
+                            about 1e-7); 1 = the second Gram-Schmidt pass's coefficients and the
+                            second Cholesky-QR pass in FP64 (basis orthonormal to FP64 round-off) */
     double* history;     /* host, may be NULL: max_iter doubles, the largest residual among the
                             nconv bands after each Rayleigh-Ritz step */
     const float* mlp;    /* precond = 1: device, QM_MLP_NPARAM floats (see qm_mlp_forward) */

@@ -59,7 +59,7 @@ class DavidsonOpts(ctypes.Structure):
     """qm_davidson_opts of include/qm.h."""
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("nvecx", ctypes.c_int),
                 ("prec", ctypes.c_int), ("precond", ctypes.c_int), ("mixed_switch", ctypes.c_double),
-                ("nconv", ctypes.c_int), ("reserved", ctypes.c_int), ("history", c_double_p),
+                ("nconv", ctypes.c_int), ("mixed_ortho", ctypes.c_int), ("history", c_double_p),
                 ("mlp", ctypes.c_void_p), ("precond_stall", ctypes.c_double)]
 
 

@@ -124,7 +124,7 @@ def qm_hpsi(g, ik, psi, vloc, beta, D, out=None, prec="fp64", stream=None):
 
 
 def qm_davidson(g, ik, psi, vloc, beta, D, tol=1e-8, max_iter=100, nvecx=0, prec="fp64", stream=None,
-                raise_not_converged=True, mixed_switch=0.0, nconv=0, mlp=None, precond_stall=0.0):
+                raise_not_converged=True, mixed_switch=0.0, nconv=0, mlp=None, precond_stall=0.0, mixed_ortho=0):
     """Lowest nb eigenpairs; psi (nb, >=npw) complex128 CUDA tensor is overwritten by the
     Ritz vectors.  Returns (eigenvalues ndarray (nb,), stats dict)."""
     lib = _lib.load()
@@ -135,7 +135,7 @@ def qm_davidson(g, ik, psi, vloc, beta, D, tol=1e-8, max_iter=100, nvecx=0, prec
     hist = np.zeros(max(1, int(max_iter)), np.float64)
     opts = _lib.DavidsonOpts(tol=float(tol), max_iter=int(max_iter), nvecx=int(nvecx), prec=_PREC[prec],
                              precond=0 if mlp is None else 1, mixed_switch=float(mixed_switch), nconv=int(nconv),
-                             history=_dp(hist), mlp=_dev_ptr(mlp, "mlp", torch.float32),
+                             mixed_ortho=int(mixed_ortho), history=_dp(hist), mlp=_dev_ptr(mlp, "mlp", torch.float32),
                              precond_stall=float(precond_stall))
     stats = _lib.DavidsonStats()
     eig = np.zeros(nb, np.float64)
@@ -346,7 +346,7 @@ def qm_mlp_train(band_off, feats, r2, c, D, theta, steps, lr, W=None, stream=Non
 
 
 def qm_davidson_batched(jobs, tol=1e-8, max_iter=100, nvecx=0, prec="fp64", nconv=0, mixed_switch=0.0, mlp=None,
-                        max_concurrent=0, stream=None, raise_not_converged=True):
+                        max_concurrent=0, stream=None, raise_not_converged=True, mixed_ortho=0):
     """Concurrent Davidson solves.  jobs: list of dicts with keys g, ik, psi (overwritten by
     the Ritz vectors), vloc, beta, D (CUDA tensors as for qm_davidson).  Returns a list of
     (eigenvalues ndarray, info dict) in job order."""
@@ -373,7 +373,7 @@ def qm_davidson_batched(jobs, tol=1e-8, max_iter=100, nvecx=0, prec="fp64", ncon
                                   history=hists[-1].ctypes.data_as(ctypes.c_void_p))
     opts = _lib.DavidsonOpts(tol=float(tol), max_iter=int(max_iter), nvecx=int(nvecx), prec=_PREC[prec],
                              precond=0 if mlp is None else 1, mixed_switch=float(mixed_switch), nconv=int(nconv),
-                             history=None, mlp=_dev_ptr(mlp, "mlp", torch.float32))
+                             mixed_ortho=int(mixed_ortho), history=None, mlp=_dev_ptr(mlp, "mlp", torch.float32))
     st = lib.qm_davidson_batched(n, arr, ctypes.byref(opts), int(max_concurrent), _stream_ptr(stream))
     out = []
     for i in range(n):

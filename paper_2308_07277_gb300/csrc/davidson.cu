@@ -13,12 +13,13 @@
 // The basis is kept orthonormal, so the subspace overlap S_sub is the identity to FP64
 // round-off and Rayleigh-Ritz is a standard Hermitian eigenproblem (heev.cu).
 //
-// Precision form (QM_MIXED): H psi in FP32 and the subspace products in FP32 arithmetic,
-// except the coefficients of the second Gram-Schmidt pass and the second Cholesky-QR pass,
-// which keep the basis orthonormal to FP64 round-off; eigensolves, residual norms and band
-// energies in FP64.  Once the largest residual is below mixed_switch (or stops falling), the
-// Ritz vectors are re-orthonormalised, H is applied to them in FP64 (refinement sweep), and
-// the iterations continue entirely in FP64.
+// Precision form (QM_MIXED): H psi in FP32 and the subspace products as BF16x3 split products
+// on the tensor cores (FP64 storage rounded to FP32 on load, FP32 accumulation per K split,
+// splits summed in FP64); with mixed_ortho = 1 the coefficients of the second Gram-Schmidt
+// pass and the second Cholesky-QR pass stay FP64, which keeps the basis orthonormal to FP64
+// round-off; eigensolves, residual norms and band energies in FP64.  Once the largest residual
+// is below mixed_switch (or stops falling), the Ritz vectors are re-orthonormalised, H is
+// applied to them in FP64 (refinement sweep), and the iterations continue entirely in FP64.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -182,6 +183,11 @@ struct DavidsonRun {
     float2* psi32 = nullptr;     // [nb][ld] FP32 staging of the vectors H is applied to
     float2* hpsi32 = nullptr;    // [nb][ld]
     float2* beta32 = nullptr;    // [nproj][ld]
+    bool tc = false;             // precision form: tensor-core subspace products available
+    bool ortho64 = false;        // FP32 phase: second CGS pass coefficients and Cholesky-QR pass in FP64
+    void* sub = nullptr;         // tensor-core subspace products: split-K partials / coefficient operand
+    size_t sub_bytes = 0;
+    int* tc_err = nullptr;       // device error word of the tensor-core waits
 
     qm_status hpsi(const double2* in, double2* out, int n) {
         applies += n;
@@ -193,58 +199,103 @@ struct DavidsonRun {
         if (st) return st;
         return convert_rows(hpsi32, ld, out, ld, n, npw, s);
     }
-    qm_status gemm_cn(int M, int N, int K, const double2* A, int lda, const double2* B, int ldb_, double2* C,
-                      int ldc) {
-        const int sp = zgemm_cn_splits(M, N, K);
-        return mixed ? zgemm_cn_f32(M, N, K, A, lda, B, ldb_, C, ldc, w.Part, sp, s)
-                     : zgemm_cn(M, N, K, A, lda, B, ldb_, C, ldc, w.Part, sp, s);
+    // tensor-core (BF16x3, FP32 accuracy) and FP64 forms of the two subspace products
+    qm_status cn_tc(int M, int N, const double2* A, const double2* B, double2* C, int ldc) {
+        return zgemm_cn_bf16x3(M, N, npw, A, ld, B, ld, C, ldc, sub, sub_bytes, tc_err, s);
     }
-    qm_status gemm_tn(int M, int N, int K, const double2* A, int lda, const double2* B, int ldb_, double2* C,
-                      int ldc, bool acc, double alpha = 1.0) {
-        return mixed ? zgemm_tn_f32(M, N, K, A, lda, nullptr, B, ldb_, C, ldc, acc, s, alpha)
-                     : zgemm_tn(M, N, K, A, lda, nullptr, B, ldb_, C, ldc, acc, s, alpha);
+    qm_status cn64(int M, int N, const double2* A, const double2* B, double2* C, int ldc) {
+        return zgemm_cn(M, N, npw, A, ld, B, ld, C, ldc, w.Part, zgemm_cn_splits(M, N, npw), s);
+    }
+    qm_status tn_tc(int M, int K, const double2* A, int lda, const double2* B, double2* C, bool acc,
+                    double alpha = 1.0, double diag = 0.0) {
+        return zgemm_tn_bf16x3(M, npw, K, A, lda, B, ld, C, ld, acc, alpha, diag, sub, sub_bytes, tc_err, s);
+    }
+    qm_status tn64(int M, int K, const double2* A, int lda, const double2* B, double2* C, bool acc,
+                   double alpha = 1.0) {
+        return zgemm_tn(M, npw, K, A, lda, nullptr, B, ld, C, ld, acc, s, alpha);
+    }
+    // products whose precision follows the phase: H_sub columns and the Ritz vectors
+    qm_status gemm_cn(int M, int N, const double2* A, const double2* B, double2* C, int ldc) {
+        return mixed ? cn_tc(M, N, A, B, C, ldc) : cn64(M, N, A, B, C, ldc);
+    }
+    qm_status gemm_tn(int M, int K, const double2* A, int lda, const double2* B, double2* C, bool acc) {
+        return mixed ? tn_tc(M, K, A, lda, B, C, acc) : tn64(M, K, A, lda, B, C, acc);
+    }
+    // Precision form: the second pass of an orthogonalisation (Gram-Schmidt coefficients,
+    // Cholesky-QR Gram matrix) is FP64 in the FP64 phase (and with ortho64), which keeps the
+    // basis orthonormal to FP64 round-off; every other orthogonalisation product is a
+    // tensor-core product, either of O(1) coefficients followed by that exact pass, or of tiny
+    // coefficients (the exact pass's corrections), whose FP32 relative error is negligible.
+    bool exact_second_pass() const { return !tc || !mixed || ortho64; }
+
+    // One Cholesky-QR pass with dropping: the n_in rows of src -> *k orthonormal rows of dst.
+    // exact: Gram matrix in FP64; in the precision form an exact pass applies its near-identity
+    // transform W as dst = src + src (W - I), the identity part exact (tensor-core product of
+    // the small remainder).  Pass 0 drops directions whose pivot is below `drop` of their own
+    // norm^2; an exact second pass only drops exact null directions.
+    qm_status chol_pass(const double2* src, int n_in, double2* dst, bool exact, double drop, int* kout) {
+        qm_status st = exact ? cn64(n_in, n_in, src, src, w.G, n_in) : cn_tc(n_in, n_in, src, src, w.G, n_in);
+        if (st) return st;
+        int k = 0;
+        if ((st = chol_transform(w.G, n_in, n_in, drop, w.sel, w.rank, w.info, w.A, w.Cs, 0, s)) ||
+            (st = cuda_check(cudaMemcpyAsync(&k, w.info, sizeof(int), cudaMemcpyDeviceToHost, s), "D2H kept")) ||
+            (st = cuda_check(cudaStreamSynchronize(s), "stream sync")))
+            return st;
+        *kout = k;
+        if (k == 0) return QM_OK;
+        if ((st = chol_transform_rows(w.G, n_in, n_in, w.sel, w.rank, k, w.A, w.Cs, s))) return st;
+        if (!tc || (exact && k < n_in)) return tn64(k, n_in, w.Cs, k, src, dst, false);
+        if (exact) {
+            st = cuda_check(cudaMemcpy2DAsync(dst, (size_t)ld * sizeof(double2), src, (size_t)ld * sizeof(double2),
+                                              (size_t)npw * sizeof(double2), k, cudaMemcpyDeviceToDevice, s),
+                            "copy rows");
+            return st ? st : tn_tc(k, n_in, w.Cs, k, src, dst, true, 1.0, -1.0);
+        }
+        return tn_tc(k, n_in, w.Cs, k, src, dst, false);
     }
 
-    // Orthonormalise the nd rows of Y into the rows of out by two passes of Cholesky-QR with
-    // dropping of near-dependent directions (first pass: pivots below `drop` of a vector's
-    // own norm^2); *kept = rows written.  Uses R as scratch.
+    // One classical Gram-Schmidt pass of the nu rows of D against the m basis rows V:
+    // D -= V^T (V^H D) (coefficients in FP64 when exact).
+    qm_status cgs_pass(int m, int nu, double2* D, bool exact) {
+        qm_status st = exact ? cn64(m, nu, w.V, D, w.Cs, nu) : cn_tc(m, nu, w.V, D, w.Cs, nu);
+        if (st) return st;
+        return tc ? tn_tc(nu, m, w.Cs, nu, w.V, D, true, -1.0) : tn64(nu, m, w.Cs, nu, w.V, D, true, -1.0);
+    }
+
+    // Orthonormalise the nd rows of Y into the rows of out by two passes of Cholesky-QR
+    // (first pass with dropping of near-dependent directions); *kept = rows written.  Uses R.
     qm_status cholqr(const double2* Y, int nd, double2* out, int* kept) {
-        qm_status st;
-        const double drop = mixed ? 1e-5 : 1e-12;  // FP32-arithmetic Gram matrices carry ~1e-7 noise
-        const double2* src = Y;
-        int n_in = nd;
-        const bool was_mixed = mixed;
-        for (int pass = 0; pass < 2; ++pass) {
-            double2* dst = pass == 0 ? w.R : out;
-            mixed = was_mixed && pass == 0;  // the second pass is FP64: orthonormal to round-off
-            if ((st = gemm_cn(n_in, n_in, npw, src, ld, src, ld, w.G, n_in))) {
-                mixed = was_mixed;
-                return st;
-            }
-            int k = 0;
-            if ((st = chol_transform(w.G, n_in, n_in, pass == 0 ? drop : 1e-14, w.sel, w.rank, w.info, w.A, w.Cs, 0,
-                                     s)) ||
-                (st = cuda_check(cudaMemcpyAsync(&k, w.info, sizeof(int), cudaMemcpyDeviceToHost, s), "D2H kept")) ||
-                (st = cuda_check(cudaStreamSynchronize(s), "stream sync"))) {
-                mixed = was_mixed;
-                return st;
-            }
-            if (k == 0) {
-                mixed = was_mixed;
-                *kept = 0;
-                return QM_OK;
-            }
-            if ((st = chol_transform_rows(w.G, n_in, n_in, w.sel, w.rank, k, w.A, w.Cs, s)) ||
-                (st = gemm_tn(k, npw, n_in, w.Cs, k, src, ld, dst, ld, false))) {
-                mixed = was_mixed;
-                return st;
-            }
-            src = dst;
-            n_in = k;
+        int k = 0;
+        qm_status st = chol_pass(Y, nd, w.R, !tc, tc ? 1e-5 : 1e-12, &k);  // FP32 Gram: ~1e-7 noise
+        if (st || k == 0) {
+            *kept = 0;
+            return st;
         }
-        mixed = was_mixed;
-        *kept = n_in;
+        const bool ex = exact_second_pass();
+        if ((st = chol_pass(w.R, k, out, ex, ex ? 1e-14 : 1e-10, kept))) return st;
         return QM_OK;
+    }
+
+    // The nu correction rows of D (overwritten) -> *kept rows at `out`, orthonormal and
+    // orthogonal to the m basis rows.  Plain FP64: two Gram-Schmidt passes, then two
+    // Cholesky-QR passes.  Precision form: Gram-Schmidt and Cholesky-QR on the tensor cores,
+    // then an exact Gram-Schmidt pass and an exact Cholesky-QR pass (FP64 coefficients and
+    // Gram matrix, tensor-core products of the small corrections only): the exact passes come
+    // last because a tensor-core transform of O(1) coefficients leaves ~1e-7 components along
+    // the basis, which only an exact pass after it removes.
+    qm_status expand(int m, int nu, double2* out, int* kept) {
+        qm_status st;
+        *kept = 0;
+        if (!tc) {
+            if ((st = cgs_pass(m, nu, w.Dl, true)) || (st = cgs_pass(m, nu, w.Dl, true))) return st;
+            return cholqr(w.Dl, nu, out, kept);
+        }
+        int k = 0;
+        if ((st = cgs_pass(m, nu, w.Dl, false)) || (st = chol_pass(w.Dl, nu, w.R, false, 1e-5, &k))) return st;
+        if (k == 0) return QM_OK;
+        const bool ex = exact_second_pass();
+        if ((st = cgs_pass(m, k, w.R, ex))) return st;
+        return chol_pass(w.R, k, out, ex, ex ? 1e-14 : 1e-10, kept);
     }
 };
 
@@ -280,6 +331,7 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
     if (!(o.mixed_switch > 0.0)) o.mixed_switch = 1e-4;
     if (o.nconv <= 0 || o.nconv > nb) o.nconv = nb;
     if (o.precond != 0 && o.precond != 1) return fail(QM_ERR_ARG, "qm_davidson: unknown preconditioner");
+    if (o.mixed_ortho != 0 && o.mixed_ortho != 1) return fail(QM_ERR_ARG, "qm_davidson: mixed_ortho must be 0 or 1");
     if (o.precond == 1 && !o.mlp) return fail(QM_ERR_ARG, "qm_davidson: learned preconditioner without parameters");
 
     qm_status st = ensure_device(g);
@@ -316,6 +368,8 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
     const bool use_mixed = o.prec == QM_MIXED;
     const size_t oP32 = take(use_mixed ? big32 * nb : 0), oH32 = take(use_mixed ? big32 * nb : 0),
                  oB32 = take(use_mixed ? big32 * std::max(nproj, 1) : 0);
+    const size_t sub_bytes = use_mixed ? subspace_bf16x3_bytes(nvx, nb) : 0;
+    const size_t oSub = take(sub_bytes);
     const size_t sq = (size_t)nsq * nsq * sizeof(double2);
     const size_t oHs = take(sq), oG = take(sq), oA = take(sq), oZ = take(sq), oCs = take(sq);
     const size_t oPart = take(gemm_cn_partial_bytes(false));
@@ -339,6 +393,10 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
         run.beta32 = (float2*)(base + oB32);
         if (nproj > 0 && (st = convert_rows((const double2*)beta, ld_beta, run.beta32, ld, nproj, npw, s))) return st;
         run.mixed = true;
+        run.tc = true;
+        run.ortho64 = o.mixed_ortho == 1;
+        run.sub = base + oSub;
+        run.sub_bytes = sub_bytes;
     }
     w.Hs = (double2*)(base + oHs);
     w.G = (double2*)(base + oG);
@@ -354,6 +412,8 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
     w.rank = (int*)(base + oRank);
     w.info = (int*)(base + oInfo);
     w.heev = base + oHeev;
+    run.tc_err = w.info + 3;
+    if (use_mixed && (st = cuda_check(cudaMemsetAsync(run.tc_err, 0, sizeof(int), s), "reset error word"))) return st;
     const double* kin = g->k[ik].kin;
 
     // initial block: psi -> rows of Tmp (dense ld), orthonormalised into V
@@ -379,7 +439,7 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
     double max_res = 0.0;
     for (it = 1; it <= o.max_iter; ++it) {
         // new columns of H_sub
-        if ((st = run.gemm_cn(m, m - m0, npw, w.V, ld, w.HV + (size_t)m0 * ld, ld, w.Hs + m0, nsq))) return st;
+        if ((st = run.gemm_cn(m, m - m0, w.V, w.HV + (size_t)m0 * ld, w.Hs + m0, nsq))) return st;
         {
             ProfScope pf(PF_OTHER, s);
             k_herm_fill<<<grid_for((long)m * (m - m0)), 256, 0, s>>>(w.Hs, nsq, m0, m);
@@ -390,8 +450,7 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
         }
         // lowest nb eigenpairs: values -> eps (device, increasing), vectors -> Cs [m][nb]
         if ((st = heev_lowest(w.A, m, m, nb, w.eps, w.Cs, nb, w.heev, s))) return st;
-        if ((st = run.gemm_tn(nb, npw, m, w.Cs, nb, w.V, ld, w.X, ld, false)) ||
-            (st = run.gemm_tn(nb, npw, m, w.Cs, nb, w.HV, ld, w.HX, ld, false)))
+        if ((st = run.gemm_tn(nb, m, w.Cs, nb, w.V, w.X, false)) || (st = run.gemm_tn(nb, m, w.Cs, nb, w.HV, w.HX, false)))
             return st;
         {
             ProfScope pf(PF_OTHER, s);
@@ -466,16 +525,8 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
             }
             m = nb;
         }
-        // two classical Gram-Schmidt passes against the basis; the second pass's coefficients
-        // (tiny, but they decide the basis' orthogonality) are always formed in FP64
-        for (int pass = 0; pass < 2; ++pass) {
-            if (pass == 1 && run.mixed)
-                st = zgemm_cn(m, nu, npw, w.V, ld, w.Dl, ld, w.Cs, nu, w.Part, zgemm_cn_splits(m, nu, npw), s);
-            else
-                st = run.gemm_cn(m, nu, npw, w.V, ld, w.Dl, ld, w.Cs, nu);
-            if (st || (st = run.gemm_tn(nu, npw, m, w.Cs, nu, w.V, ld, w.Dl, ld, true, -1.0))) return st;
-        }
-        if ((st = run.cholqr(w.Dl, nu, w.V + (size_t)m * ld, &kept))) return st;
+        // orthogonalise the corrections against the basis and orthonormalise them
+        if ((st = run.expand(m, nu, w.V + (size_t)m * ld, &kept))) return st;
         if (kept == 0) break;  // no new directions: stagnation
         if ((st = run.hpsi(w.V + (size_t)m * ld, w.HV + (size_t)m * ld, kept))) return st;
         m0 = m;
@@ -493,6 +544,12 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
         if ((st = cuda_check(cudaMemcpy(&e, mlp_err, sizeof(int), cudaMemcpyDeviceToHost), "D2H error word")))
             return st;
         if (e) return fail(QM_ERR_TIMEOUT, "qm_davidson: a bounded tensor-core wait of the learned preconditioner expired");
+    }
+    if (use_mixed) {
+        int e = 0;
+        if ((st = cuda_check(cudaMemcpy(&e, run.tc_err, sizeof(int), cudaMemcpyDeviceToHost), "D2H error word")))
+            return st;
+        if (e) return fail(QM_ERR_TIMEOUT, "qm_davidson: a bounded tensor-core wait of a subspace product expired");
     }
     if (stats) {
         stats->iterations = it > o.max_iter ? o.max_iter : it;

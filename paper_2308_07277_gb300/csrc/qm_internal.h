@@ -165,12 +165,6 @@ qm_status zgemm_tn(int M, int N, int K, const double2* A, int lda, const double*
                    const double2* B, int ldb, double2* C, int ldc, bool accumulate,
                    cudaStream_t s, double alpha = 1.0);
 int zgemm_cn_splits(int M, int N, int K);
-// the same products with FP64 storage and FP32 arithmetic
-qm_status zgemm_cn_f32(int M, int N, int K, const double2* A, int lda, const double2* B, int ldb,
-                       double2* C, int ldc, double2* partial, int splits, cudaStream_t s);
-qm_status zgemm_tn_f32(int M, int N, int K, const double2* A, int lda, const double* d,
-                       const double2* B, int ldb, double2* C, int ldc, bool accumulate,
-                       cudaStream_t s, double alpha = 1.0);
 // ---- tensor-core nonlocal step of the precision form (umma.cu) ----
 constexpr int kMaxUmmaSplits = 64;
 // out[b][g] (+)= sum_p beta[p][g] D_p <beta_p|psi_b> (FP32 complex in/out) as BF16x3 split
@@ -179,6 +173,19 @@ qm_status nonlocal_bf16x3(int nproj, int nb, int npw, const float2* beta, int ld
                           int ld_psi, const double* D, float2* out, int ld_out, void* work, int* err,
                           cudaStream_t s, bool accumulate = true);
 size_t nonlocal_bf16x3_bytes(int nproj, int nb, int npw);
+// Subspace products of the Davidson FP32 phase on the tensor cores: FP64 storage rounded to
+// FP32 on load, BF16x3 split products accumulated in FP32 per K split, splits summed in FP64.
+//   cn: C[i][j] = sum_k conj(A[i][k]) B[j][k]                (as zgemm_cn)
+//   tn: C[i][n] (+)= sum_k (alpha A[k][i] + diag [k == i]) B[k][n]   (zgemm_tn with d = NULL
+//       when diag = 0; with accumulate and diag = -1, C += B (alpha A - I) applies a near-identity
+//       rotation to rows already copied into C with FP64 accuracy of the identity part)
+// work: subspace_bf16x3_bytes(max M, max N) bytes; err: device int set on a timed-out wait
+qm_status zgemm_cn_bf16x3(int M, int N, int K, const double2* A, int lda, const double2* B, int ldb,
+                          double2* C, int ldc, void* work, size_t work_bytes, int* err, cudaStream_t s);
+qm_status zgemm_tn_bf16x3(int M, int N, int K, const double2* A, int lda, const double2* B, int ldb,
+                          double2* C, int ldc, bool accumulate, double alpha, double diag, void* work,
+                          size_t work_bytes, int* err, cudaStream_t s);
+size_t subspace_bf16x3_bytes(int max_m, int max_n);
 
 // ---- learned preconditioner (mlp.cu) ----
 // out_j(G) = K(f) R[sel[j]](G) for j < nu: the network's correction of the Davidson step;

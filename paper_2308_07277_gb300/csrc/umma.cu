@@ -82,8 +82,17 @@ __device__ __forceinline__ void put_word(unsigned char* dst, int cm, int lane, f
     put_pair(dst, cm * 128 + lane * 4, x, y);
 }
 
+// complex element of the source as FP32: FP32 sources are read as they are, FP64 sources (the
+// Davidson basis) are rounded to FP32 on load
+__device__ __forceinline__ float2 ld_f2(const float2* p) { return __ldg(p); }
+__device__ __forceinline__ float2 ld_f2(const double2* p) {
+    const double2 v = __ldg(p);
+    return make_float2((float)v.x, (float)v.y);
+}
+
+template <class Src>
 struct PlainRows {  // rows = complex rows of src, K = the complex columns (interleaved re, im)
-    const float2* src;
+    const Src* src;
     int ld, rows, K;
     // core matrix cm = (row group) * 8 + (K chunk); lane = 4 * (row in group) + (complex col in chunk)
     __device__ __forceinline__ void fetch(float2* v, int r0, int kc0, int tid) const {
@@ -92,7 +101,7 @@ struct PlainRows {  // rows = complex rows of src, K = the complex columns (inte
         for (int it = 0; it < kCmPerWarp; ++it) {
             const int cm = warp + 8 * it;
             const int gr = r0 + (cm / KCH) * 8 + (lane >> 2), gk = kc0 + (cm % KCH) * 4 + (lane & 3);
-            v[it] = (gr < rows && gk < K) ? __ldg(src + (size_t)gr * ld + gk) : make_float2(0.f, 0.f);
+            v[it] = (gr < rows && gk < K) ? ld_f2(src + (size_t)gr * ld + gk) : make_float2(0.f, 0.f);
         }
     }
     __device__ __forceinline__ void stash(unsigned char* dst, const float2* v, int tid) const {
@@ -107,8 +116,9 @@ struct PlainRows {  // rows = complex rows of src, K = the complex columns (inte
 // (word (2a + c) * 4 + b of the core matrix)
 __device__ __forceinline__ int expand_word(int lane) { return ((2 * (lane >> 3) + (lane & 1)) << 2) + ((lane >> 1) & 3); }
 
+template <class Src>
 struct ExpandRows {  // B rows from complex rows of src (conj_a: pattern of conj(A) B)
-    const float2* src;
+    const Src* src;
     int ld, rows, K, conj_a;
     __device__ __forceinline__ void fetch(float2* v, int r0, int kc0, int tid) const {
         const int warp = tid >> 5, lane = tid & 31;
@@ -116,7 +126,7 @@ struct ExpandRows {  // B rows from complex rows of src (conj_a: pattern of conj
         for (int it = 0; it < kCmPerWarp; ++it) {
             const int cm = warp + 8 * it;
             const int gr = (r0 >> 1) + (cm / KCH) * 4 + (lane >> 3), gk = kc0 + (cm % KCH) * 4 + ((lane >> 1) & 3);
-            v[it] = (gr < rows && gk < K) ? __ldg(src + (size_t)gr * ld + gk) : make_float2(0.f, 0.f);
+            v[it] = (gr < rows && gk < K) ? ld_f2(src + (size_t)gr * ld + gk) : make_float2(0.f, 0.f);
         }
     }
     __device__ __forceinline__ void stash(unsigned char* dst, const float2* v, int tid) const {
@@ -137,8 +147,9 @@ struct ExpandRows {  // B rows from complex rows of src (conj_a: pattern of conj
     }
 };
 
+template <class Src>
 struct ExpandTRows {  // B = src^T expanded: src [P][G] (G contiguous); rows 2g, 2g+1; K = p
-    const float2* src;
+    const Src* src;
     int ld, P, G;
     __device__ __forceinline__ void fetch(float2* v, int r0, int kc0, int tid) const {
         const int warp = tid >> 5, lane = tid & 31;
@@ -146,7 +157,7 @@ struct ExpandTRows {  // B = src^T expanded: src [P][G] (G contiguous); rows 2g,
         for (int it = 0; it < kCmPerWarp; ++it) {
             const int cm = warp + 8 * it;
             const int gg = (r0 >> 1) + (cm / KCH) * 4 + (lane >> 3), gp = kc0 + (cm % KCH) * 4 + ((lane >> 1) & 3);
-            v[it] = (gp < P && gg < G) ? __ldg(src + (size_t)gp * ld + gg) : make_float2(0.f, 0.f);
+            v[it] = (gp < P && gg < G) ? ld_f2(src + (size_t)gp * ld + gg) : make_float2(0.f, 0.f);
         }
     }
     __device__ __forceinline__ void stash(unsigned char* dst, const float2* v, int tid) const {
@@ -159,12 +170,12 @@ struct ExpandTRows {  // B = src^T expanded: src [P][G] (G contiguous); rows 2g,
     }
 };
 
-// C'[m][n] (+)= sum_k A[m][k] B[n][k] over the real K range of this split.  Output FP32 with
-// row stride ldc; rows >= M or columns >= N are not written.  Split z writes at
+// C'[m][n] (+)= sum_k A[m][k] B[n][k] over the real K range of this split.  Output FP32 or
+// FP64 (Out) with row stride ldc; rows >= M or columns >= N are not written.  Split z writes at
 // C + z * zstride.  accumulate: add to the existing output.
-template <class LA, class LB>
+template <class LA, class LB, class Out>
 __global__ void __launch_bounds__(kThreads)
-k_umma_split(LA la, LB lb, int M, int N, int ktiles_per_split, int ktiles_total, float* __restrict__ C, size_t ldc,
+k_umma_split(LA la, LB lb, int M, int N, int ktiles_per_split, int ktiles_total, Out* __restrict__ C, size_t ldc,
              size_t zstride, int accumulate, int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t mbar[2];
@@ -260,7 +271,7 @@ k_umma_split(LA la, LB lb, int M, int N, int ktiles_per_split, int ktiles_total,
         // columns 0..63, warps 4-7 columns 64..127
         const int q = warp & 3, chalf = (warp >> 2) * 64;
         const int row = m0 + q * 32 + (tid & 31);
-        float* crow = C + (size_t)blockIdx.z * zstride + (size_t)row * ldc;
+        Out* crow = C + (size_t)blockIdx.z * zstride + (size_t)row * ldc;
 #pragma unroll 1
         for (int c0 = chalf; c0 < chalf + 64; c0 += 16) {
             uint32_t v[16];
@@ -278,7 +289,7 @@ k_umma_split(LA la, LB lb, int M, int N, int ktiles_per_split, int ktiles_total,
                 for (int j = 0; j < 16; ++j) {
                     const int col = n0 + c0 + j;
                     if (col < N) {
-                        const float x = __uint_as_float(v[j]);
+                        const Out x = (Out)__uint_as_float(v[j]);
                         crow[col] = accumulate ? crow[col] + x : x;
                     }
                 }
@@ -310,11 +321,41 @@ __global__ void k_reduce_proj(const float* __restrict__ part, int Z, size_t zstr
     }
 }
 
+// sum the split-K partials C'[z][i][2j + t] of a subspace product in FP64 and write the complex
+// result C[i][j] (FP64, row stride ldc)
+__global__ void k_reduce_cn(const float* __restrict__ part, int Z, size_t zstride, int ldp, int M, int N,
+                            double2* __restrict__ C, int ldc) {
+    const size_t total = (size_t)M * N;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / N), j = (int)(e % N);
+        double sr = 0.0, si = 0.0;
+        for (int z = 0; z < Z; ++z) {
+            const float2 q = __ldg(reinterpret_cast<const float2*>(part + (size_t)z * zstride + (size_t)i * ldp) + j);
+            sr += (double)q.x;
+            si += (double)q.y;
+        }
+        C[(size_t)i * ldc + j] = make_double2(sr, si);
+    }
+}
+
+// At[i][j] = alpha * A[j][i] + diag * [i == j] in FP32 (the small coefficient matrix of a basis
+// rotation, made K-major for the tensor-core operand; the shift is applied in FP64 first, so
+// a near-identity rotation passes only its small deviation from the identity)
+__global__ void k_coef_t(const double2* __restrict__ A, int lda, int M, int K, double alpha, double diag,
+                         float2* __restrict__ At) {
+    const size_t total = (size_t)M * K;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / K), j = (int)(e % K);
+        const double2 a = A[(size_t)j * lda + i];
+        At[e] = make_float2((float)(alpha * a.x + (i == j ? diag : 0.0)), (float)(alpha * a.y));
+    }
+}
+
 inline size_t rup(size_t x, size_t a) { return (x + a - 1) / a * a; }
 inline int grid_for(size_t n) { return (int)std::max<size_t>(1, std::min<size_t>((n + 255) / 256, 152 * 16)); }
 
-template <class LA, class LB>
-qm_status umma_launch(const LA& la, const LB& lb, int M, int N, int kreal, int splits, float* C, size_t ldc,
+template <class LA, class LB, class Out>
+qm_status umma_launch(const LA& la, const LB& lb, int M, int N, int kreal, int splits, Out* C, size_t ldc,
                       size_t zstride, bool accumulate, int* err, cudaStream_t s, int* zout) {
     const int ktiles = (int)((rup((size_t)kreal, UK)) / UK);
     splits = std::max(1, std::min(splits, ktiles));
@@ -322,11 +363,11 @@ qm_status umma_launch(const LA& la, const LB& lb, int M, int N, int kreal, int s
     splits = (ktiles + per - 1) / per;
     if (zout) *zout = splits;
     const size_t smem = 2 * (size_t)STAGE_BYTES;
-    qm_status st = allow_dynamic_smem((const void*)k_umma_split<LA, LB>, smem, "tensor-core GEMM shared memory");
+    qm_status st = allow_dynamic_smem((const void*)k_umma_split<LA, LB, Out>, smem, "tensor-core GEMM shared memory");
     if (st) return st;
     dim3 grid((N + UN - 1) / UN, (M + UM - 1) / UM, splits);
     ProfScope pf(PF_UMMA, s);
-    k_umma_split<LA, LB><<<grid, kThreads, smem, s>>>(la, lb, M, N, per, ktiles, C, ldc, zstride, accumulate ? 1 : 0,
+    k_umma_split<LA, LB, Out><<<grid, kThreads, smem, s>>>(la, lb, M, N, per, ktiles, C, ldc, zstride, accumulate ? 1 : 0,
                                                      err);
     return cuda_check(cudaGetLastError(), "k_umma_split launch");
 }
@@ -351,8 +392,8 @@ qm_status nonlocal_bf16x3(int nproj, int nb, int npw, const float2* beta, int ld
     const int tiles = (int)((rP / UM) * (r2B / UN));
     const int splits = std::max(1, std::min(kMaxUmmaSplits, 2 * 152 / std::max(1, tiles)));  // 2 CTAs per SM
     const size_t zstride = rP * r2B;
-    PlainRows la{beta, ld_beta, nproj, npw};
-    ExpandRows lb{psi, ld_psi, nb, npw, 1};
+    PlainRows<float2> la{beta, ld_beta, nproj, npw};
+    ExpandRows<float2> lb{psi, ld_psi, nb, npw, 1};
     int Z = 1;
     qm_status st = umma_launch(la, lb, nproj, 2 * nb, 2 * npw, splits, part, r2B, zstride, false, err, s, &Z);
     if (st) return st;
@@ -362,10 +403,65 @@ qm_status nonlocal_bf16x3(int nproj, int nb, int npw, const float2* beta, int ld
     }
     if ((st = cuda_check(cudaGetLastError(), "k_reduce_proj launch"))) return st;
     // application: out'[b][2g + t] += sum_p (D P)[b][p] beta[p][g]
-    PlainRows la2{Pd, nproj, nb, nproj};
-    ExpandTRows lb2{beta, ld_beta, nproj, npw};
+    PlainRows<float2> la2{Pd, nproj, nb, nproj};
+    ExpandTRows<float2> lb2{beta, ld_beta, nproj, npw};
     return umma_launch(la2, lb2, nb, 2 * npw, 2 * nproj, 1, (float*)out, 2 * (size_t)ld_out, 0, accumulate, err, s,
                        nullptr);
+}
+
+// ---- subspace products of the Davidson FP32 phase (FP64 storage, BF16x3 tensor-core products) ----
+
+size_t subspace_bf16x3_bytes(int max_m, int max_n) {
+    // the cn split-K partials: splits x tiles <= 2 x 152 + tiles (see zgemm_cn_bf16x3)
+    const size_t tiles = (rup((size_t)max_m, UM) / UM) * (rup(2 * (size_t)max_n, UN) / UN);
+    const size_t part = rup((2 * 152 + tiles) * UM * UN * sizeof(float), 256);
+    // the tn coefficient operand: M x K FP32 complex.  Calls on one stream reuse the buffer.
+    const size_t coef = rup((size_t)max_m * max_m * sizeof(float2), 256);
+    return std::max(part, coef);
+}
+
+qm_status zgemm_cn_bf16x3(int M, int N, int K, const double2* A, int lda, const double2* B, int ldb, double2* C,
+                          int ldc, void* work, size_t work_bytes, int* err, cudaStream_t s) {
+    if (M <= 0 || N <= 0) return QM_OK;
+    const size_t rM = rup(M, UM), r2N = rup(2 * (size_t)N, UN);
+    const int tiles = (int)((rM / UM) * (r2N / UN));
+    const size_t zstride = rM * r2N;
+    const int cap = (int)std::min<size_t>(kMaxUmmaSplits, work_bytes / (zstride * sizeof(float)));
+    if (cap < 1) return fail(QM_ERR_ARG, "zgemm_cn_bf16x3: workspace too small");
+    const int splits = std::max(1, std::min(cap, (2 * 152 + tiles - 1) / tiles));  // 2 CTAs per SM
+    PlainRows<double2> la{A, lda, M, K};
+    ExpandRows<double2> lb{B, ldb, N, K, 1};
+    int Z = 1;
+    float* part = (float*)work;
+    qm_status st = umma_launch(la, lb, M, 2 * N, 2 * K, splits, part, r2N, zstride, false, err, s, &Z);
+    if (st) return st;
+    {
+        ProfScope pf(PF_SPLIT, s);
+        k_reduce_cn<<<grid_for((size_t)M * N), 256, 0, s>>>(part, Z, zstride, (int)r2N, M, N, C, ldc);
+    }
+    return cuda_check(cudaGetLastError(), "k_reduce_cn launch");
+}
+
+qm_status zgemm_tn_bf16x3(int M, int N, int K, const double2* A, int lda, const double2* B, int ldb, double2* C,
+                          int ldc, bool accumulate, double alpha, double diag, void* work, size_t work_bytes,
+                          int* err, cudaStream_t s) {
+    if (M <= 0 || N <= 0) return QM_OK;
+    if (K <= 0) {
+        if (accumulate) return QM_OK;
+        return cuda_check(cudaMemset2DAsync(C, (size_t)ldc * sizeof(double2), 0, (size_t)N * sizeof(double2), M, s),
+                          "zgemm_tn_bf16x3 zero");
+    }
+    if ((size_t)M * K * sizeof(float2) > work_bytes) return fail(QM_ERR_ARG, "zgemm_tn_bf16x3: workspace too small");
+    float2* at = (float2*)work;
+    {
+        ProfScope pf(PF_SPLIT, s);
+        k_coef_t<<<grid_for((size_t)M * K), 256, 0, s>>>(A, lda, M, K, alpha, diag, at);
+    }
+    qm_status st = cuda_check(cudaGetLastError(), "k_coef_t launch");
+    if (st) return st;
+    PlainRows<float2> la{at, K, M, K};
+    ExpandTRows<double2> lb{B, ldb, K, N};
+    return umma_launch(la, lb, M, 2 * N, 2 * K, 1, (double*)C, 2 * (size_t)ldc, 0, accumulate, err, s, nullptr);
 }
 
 }  // namespace qm

@@ -359,14 +359,4 @@ qm_status cgemm_tn(int M, int N, int K, const float2* A, int lda, const double* 
     return gemm_tn_impl<float2, float2>(M, N, K, A, lda, d, alpha, B, ldb, C, ldc, accumulate, s);
 }
 
-// FP64 storage, FP32 arithmetic (the subspace products of the mixed Davidson phase)
-qm_status zgemm_cn_f32(int M, int N, int K, const double2* A, int lda, const double2* B, int ldb, double2* C,
-                       int ldc, double2* partial, int splits, cudaStream_t s) {
-    return gemm_cn_impl<double2, float2>(M, N, K, A, lda, B, ldb, C, ldc, partial, splits, s);
-}
-qm_status zgemm_tn_f32(int M, int N, int K, const double2* A, int lda, const double* d, const double2* B, int ldb,
-                       double2* C, int ldc, bool accumulate, cudaStream_t s, double alpha) {
-    return gemm_tn_impl<double2, float2>(M, N, K, A, lda, d, alpha, B, ldb, C, ldc, accumulate, s);
-}
-
 }  // namespace qm
