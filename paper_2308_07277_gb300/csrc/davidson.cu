@@ -184,6 +184,8 @@ struct DavidsonRun {
     float2* hpsi32 = nullptr;    // [nb][ld]
     float2* beta32 = nullptr;    // [nproj][ld]
     bool tc = false;             // precision form: tensor-core subspace products available
+    bool anchored = false;       // precision form, FP64 phase: basis rows 0..nb-1 are the Ritz
+                                 // vectors of the last restart (the anchor), see qm_davidson
     bool ortho64 = false;        // FP32 phase: second CGS pass coefficients and Cholesky-QR pass in FP64
     void* sub = nullptr;         // tensor-core subspace products: split-K partials / coefficient operand
     size_t sub_bytes = 0;
@@ -237,7 +239,7 @@ struct DavidsonRun {
         qm_status st = exact ? cn64(n_in, n_in, src, src, w.G, n_in) : cn_tc(n_in, n_in, src, src, w.G, n_in);
         if (st) return st;
         int k = 0;
-        if ((st = chol_transform(w.G, n_in, n_in, drop, w.sel, w.rank, w.info, w.A, w.Cs, 0, s)) ||
+        if ((st = chol_transform(w.G, n_in, n_in, drop, w.sel, w.rank, w.info, w.A, w.Cs, 0, s, !exact)) ||
             (st = cuda_check(cudaMemcpyAsync(&k, w.info, sizeof(int), cudaMemcpyDeviceToHost, s), "D2H kept")) ||
             (st = cuda_check(cudaStreamSynchronize(s), "stream sync")))
             return st;
@@ -437,9 +439,74 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
     std::vector<double> hist_mixed;
     bool converged = false;
     double max_res = 0.0;
+    // Anchored FP64 phase of the precision form.  After every restart the first nb basis rows
+    // are the Ritz vectors X_a, exact in FP64 (so are H X_a), with H_sub block diag(eps_a) and
+    // residuals R_a = H X_a - X_a eps_a (kept in Ra).  Every later direction d is orthogonal
+    // to X_a to FP64 round-off (exact second orthogonalisation pass), hence
+    //   <X_a | H d> = <H X_a | d> = <R_a | d>,
+    // a product of small vectors whose FP32 relative accuracy suffices: the new columns of H_sub
+    // come from tensor-core products (the couplings among later directions enter the Ritz
+    // vectors only at second order).  The Ritz vectors X = X_a c_a + D c_d and H X take the
+    // anchor part in FP64 (K = nb) and the small remainder D c_d on the tensor cores; before a
+    // restart, at convergence and at exit they are recomputed entirely in FP64, so anchors and
+    // reported residuals stay exact.  Used only with buffer bands (nconv < nb): without them the
+    // top band may rotate by O(1) into states outside the block, and its large coefficients on
+    // later directions would carry the FP32-accuracy errors into its residual.
+    double2* Ra = w.Tmp;  // free after the initial orthonormalisation
+    bool need_anchor = false, split_ritz = false;
+    int it_anchor = 0;
+    std::vector<int> unc;
+    bool all_conv = true;
+    auto ritz = [&](bool exact) -> qm_status {
+        qm_status st2;
+        split_ritz = run.anchored && !exact && m > nb;
+        if (split_ritz) {
+            const double2* Cd = w.Cs + (size_t)nb * nb;
+            if ((st2 = run.tn64(nb, nb, w.Cs, nb, w.V, w.X, false)) ||
+                (st2 = run.tn_tc(nb, m - nb, Cd, nb, w.V + (size_t)nb * ld, w.X, true)) ||
+                (st2 = run.tn64(nb, nb, w.Cs, nb, w.HV, w.HX, false)) ||
+                (st2 = run.tn_tc(nb, m - nb, Cd, nb, w.HV + (size_t)nb * ld, w.HX, true)))
+                return st2;
+        } else if ((st2 = run.gemm_tn(nb, m, w.Cs, nb, w.V, w.X, false)) ||
+                   (st2 = run.gemm_tn(nb, m, w.Cs, nb, w.HV, w.HX, false))) {
+            return st2;
+        }
+        {
+            ProfScope pf(PF_OTHER, s);
+            k_residual<<<nb, 256, 0, s>>>(w.X, w.HX, ld, npw, w.eps, kin, w.R, w.rn2, w.tk);
+        }
+        if ((st2 = cuda_check(cudaMemcpyAsync(rn2.data(), w.rn2, sizeof(double) * nb, cudaMemcpyDeviceToHost, s),
+                              "D2H residual norms")) ||
+            (st2 = cuda_check(cudaMemcpyAsync(eps.data(), w.eps, sizeof(double) * nb, cudaMemcpyDeviceToHost, s),
+                              "D2H Ritz values")) ||
+            (st2 = cuda_check(cudaStreamSynchronize(s), "stream sync")))
+            return st2;
+        for (int n = 0; n < nb; ++n)
+            if (!std::isfinite(eps[n])) return fail(QM_ERR_NUMERIC, "qm_davidson: non-finite Ritz value");
+        unc.clear();
+        max_res = 0.0;
+        all_conv = true;
+        for (int n = 0; n < nb; ++n) {
+            double r = std::sqrt(rn2[n]);
+            if (!std::isfinite(r)) return fail(QM_ERR_NUMERIC, "qm_davidson: non-finite residual");
+            if (n < o.nconv) {
+                max_res = std::max(max_res, r);
+                all_conv = all_conv && r <= o.tol;
+            }
+            if (r > o.tol) unc.push_back(n);
+        }
+        return QM_OK;
+    };
     for (it = 1; it <= o.max_iter; ++it) {
         // new columns of H_sub
-        if ((st = run.gemm_cn(m, m - m0, w.V, w.HV + (size_t)m0 * ld, w.Hs + m0, nsq))) return st;
+        if (run.anchored && m0 >= nb) {
+            if ((st = run.cn_tc(nb, m - m0, Ra, w.V + (size_t)m0 * ld, w.Hs + m0, nsq)) ||
+                (st = run.cn_tc(m - nb, m - m0, w.V + (size_t)nb * ld, w.HV + (size_t)m0 * ld,
+                                w.Hs + (size_t)nb * nsq + m0, nsq)))
+                return st;
+        } else if ((st = run.gemm_cn(m, m - m0, w.V, w.HV + (size_t)m0 * ld, w.Hs + m0, nsq))) {
+            return st;
+        }
         {
             ProfScope pf(PF_OTHER, s);
             k_herm_fill<<<grid_for((long)m * (m - m0)), 256, 0, s>>>(w.Hs, nsq, m0, m);
@@ -450,32 +517,16 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
         }
         // lowest nb eigenpairs: values -> eps (device, increasing), vectors -> Cs [m][nb]
         if ((st = heev_lowest(w.A, m, m, nb, w.eps, w.Cs, nb, w.heev, s))) return st;
-        if ((st = run.gemm_tn(nb, m, w.Cs, nb, w.V, w.X, false)) || (st = run.gemm_tn(nb, m, w.Cs, nb, w.HV, w.HX, false)))
+        if ((st = ritz(false))) return st;
+        // the anchored products assume that the bands which must converge take only small
+        // coefficients on the later directions; if the residual stops halving over 10 steps,
+        // the rest of the solve runs in plain FP64 from an exact restart
+        bool deanchor = false;
+        if (run.anchored && it - it_anchor > 11 && hist_all.size() > 10)
+            deanchor = max_res > 0.5 * hist_all[hist_all.size() - 10] && max_res > o.tol;
+        if (split_ritz && (all_conv || deanchor || it == o.max_iter || m + (int)unc.size() > nvx) &&
+            (st = ritz(true)))
             return st;
-        {
-            ProfScope pf(PF_OTHER, s);
-            k_residual<<<nb, 256, 0, s>>>(w.X, w.HX, ld, npw, w.eps, kin, w.R, w.rn2, w.tk);
-        }
-        if ((st = cuda_check(cudaMemcpyAsync(rn2.data(), w.rn2, sizeof(double) * nb, cudaMemcpyDeviceToHost, s),
-                             "D2H residual norms")) ||
-            (st = cuda_check(cudaMemcpyAsync(eps.data(), w.eps, sizeof(double) * nb, cudaMemcpyDeviceToHost, s),
-                             "D2H Ritz values")) ||
-            (st = cuda_check(cudaStreamSynchronize(s), "stream sync")))
-            return st;
-        for (int n = 0; n < nb; ++n)
-            if (!std::isfinite(eps[n])) return fail(QM_ERR_NUMERIC, "qm_davidson: non-finite Ritz value");
-        std::vector<int> unc;
-        max_res = 0.0;
-        bool all_conv = true;
-        for (int n = 0; n < nb; ++n) {
-            double r = std::sqrt(rn2[n]);
-            if (!std::isfinite(r)) return fail(QM_ERR_NUMERIC, "qm_davidson: non-finite residual");
-            if (n < o.nconv) {
-                max_res = std::max(max_res, r);
-                all_conv = all_conv && r <= o.tol;
-            }
-            if (r > o.tol) unc.push_back(n);
-        }
         if (o.history && it - 1 < o.max_iter) o.history[it - 1] = max_res;
         hist_all.push_back(max_res);
         // the learned correction hands over to TPA when the residual stalls
@@ -491,8 +542,12 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
             stalled = max_res > 0.5 * hist_mixed[hist_mixed.size() - 11];
         if (run.mixed && (max_res <= std::max(o.mixed_switch, o.tol) || stalled)) {
             // FP64 refinement: re-orthonormalise the Ritz vectors in FP64, apply H to them in
-            // FP64, and continue the iterations in FP64 from this basis
+            // FP64, and continue the iterations in FP64 from this basis (anchored after the
+            // first Rayleigh-Ritz step)
             run.mixed = false;
+            run.anchored = run.tc && o.nconv < nb;
+            need_anchor = run.anchored;
+            it_anchor = it;
             it_mixed = it;
             if ((st = run.cholqr(w.X, nb, w.V, &kept))) return st;
             if (kept < nb) return fail(QM_ERR_NUMERIC, "qm_davidson: Ritz vectors lost rank at the FP64 switch");
@@ -516,14 +571,17 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
             k_tpa<<<dim3((npw + 255) / 256 < 64 ? (npw + 255) / 256 : 64, nu), 256, 0, s>>>(w.R, ld, npw, w.sel, w.tk,
                                                                                             kin, w.Dl, ld);
         }
-        if (m + nu > nvx) {  // restart from the Ritz vectors
+        if (m + nu > nvx || need_anchor || deanchor) {  // restart from the Ritz vectors (exact here)
             cudaMemcpyAsync(w.V, w.X, big * nb, cudaMemcpyDeviceToDevice, s);
             cudaMemcpyAsync(w.HV, w.HX, big * nb, cudaMemcpyDeviceToDevice, s);
+            if (run.anchored) cudaMemcpyAsync(Ra, w.R, big * nb, cudaMemcpyDeviceToDevice, s);
             {
                 ProfScope pf(PF_OTHER, s);
                 k_set_diag<<<grid_for((long)nb * nb), 256, 0, s>>>(w.Hs, nsq, nb, w.eps);
             }
             m = nb;
+            need_anchor = false;
+            if (deanchor) run.anchored = false;
         }
         // orthogonalise the corrections against the basis and orthonormalise them
         if ((st = run.expand(m, nu, w.V + (size_t)m * ld, &kept))) return st;
@@ -532,6 +590,7 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
         m0 = m;
         m += kept;
     }
+    if (split_ritz && (st = ritz(true))) return st;  // exact Ritz vectors for the output
     // outputs: Ritz vectors and values
     if ((st = cuda_check(cudaMemcpy2DAsync(psi_inout, (size_t)ld_psi * sizeof(double2), w.X, big,
                                            (size_t)npw * sizeof(double2), nb, cudaMemcpyDeviceToDevice, s),

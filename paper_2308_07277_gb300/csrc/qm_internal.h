@@ -205,9 +205,10 @@ qm_status heev_lowest(double2* A, int lda, int m, int nev, double* evals, double
 size_t heev_work_bytes(int m, int nev);
 // Cholesky-with-dropping orthonormalisation: chol_transform factors S (nd x nd Gram matrix,
 // destroyed) and counts the kept vectors into kept_dev; chol_transform_rows then writes the
-// nd x kept transform W for gemm_tn.  keep, rank: nd ints; X: nd x nd scratch.
+// nd x kept transform W for gemm_tn.  keep, rank: nd ints; X: nd x nd scratch.  fp32: factor
+// in FP32 arithmetic (for Gram matrices that carry FP32 errors anyway).
 qm_status chol_transform(double2* S, int lds, int nd, double drop_rel, int* keep, int* rank, int* kept_dev,
-                         double2* X, double2* W, int ldw_max, cudaStream_t s);
+                         double2* X, double2* W, int ldw_max, cudaStream_t s, bool fp32 = false);
 qm_status chol_transform_rows(const double2* L, int lds, int nd, const int* keep, const int* rank, int kept,
                               double2* X, double2* W, cudaStream_t s);
 

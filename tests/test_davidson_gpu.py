@@ -124,7 +124,7 @@ def test_davidson_not_converged_and_errors(Q):
 @pytest.mark.parametrize("cell", [S.config1(), S.cubic_si8(12.0, nbnd=12, reps=(2, 1, 1))],
                          ids=lambda c: f"{c.name}_{c.ecutwfc_ry:g}Ry_nb{c.nbnd}")
 def test_davidson_mixed_precision_matches_dense(Q, cell):
-    """Precision form: FP32 H psi and FP32-arithmetic subspace products until the residual
+    """Precision form: FP32 H psi and BF16x3 tensor-core subspace products until the residual
     reaches 1e-4, then FP64; eigenvalues still within 1e-9 Ha of brute force."""
     c = make_case(cell, 0)
     ev = np.linalg.eigvalsh(OH.dense_h(c["gs"], c["v"], c["beta"], c["D"]))[: cell.nbnd]
@@ -132,6 +132,23 @@ def test_davidson_mixed_precision_matches_dense(Q, cell):
     assert info["converged"] and info["iterations_mixed"] > 0 and info["band_applies_mixed"] > 0, info
     np.testing.assert_allclose(eig, ev, atol=TOL_EIG)
     check_pairs(c, eig, X, 1e-9)
+
+
+@pytest.mark.parametrize("cell", [S.cubic_si8(12.0, nbnd=12, reps=(2, 1, 1)),
+                                  S.cubic_si8(10.0, nbnd=10, kpts=[[0.25, 0.25, 0.25]])],
+                         ids=lambda c: f"{c.name}_{c.ecutwfc_ry:g}Ry_nb{c.nbnd}")
+def test_davidson_mixed_buffer_bands_matches_dense(Q, cell):
+    """Precision form with buffer bands (its FP64 phase anchored on the Ritz vectors of each
+    restart, tensor-core products for the small remainders): the nconv lowest eigenvalues within
+    1e-9 Ha of brute force, and their residuals, recomputed by the oracle, within tol."""
+    nconv, extra = cell.nbnd, 4
+    c = make_case(cell, 0, nb=nconv + extra)
+    ev = np.linalg.eigvalsh(OH.dense_h(c["gs"], c["v"], c["beta"], c["D"]))[:nconv]
+    eig, X, info = run_gpu(Q, cell, 0, c, tol=1e-9, max_iter=300, prec="mixed", nconv=nconv)
+    assert info["converged"] and info["iterations_mixed"] > 0 and info["iterations"] > info["iterations_mixed"], info
+    np.testing.assert_allclose(eig[:nconv], ev, atol=TOL_EIG)
+    np.testing.assert_allclose(X @ X.conj().T, np.eye(X.shape[0]), atol=1e-12)
+    check_pairs(c, eig[:nconv], X[:nconv], 1e-9)
 
 
 @pytest.mark.parametrize("ik", [1])
