@@ -209,8 +209,8 @@ struct DavidsonRun {
         return zgemm_cn(M, N, npw, A, ld, B, ld, C, ldc, w.Part, zgemm_cn_splits(M, N, npw), s);
     }
     qm_status tn_tc(int M, int K, const double2* A, int lda, const double2* B, double2* C, bool acc,
-                    double alpha = 1.0, double diag = 0.0) {
-        return zgemm_tn_bf16x3(M, npw, K, A, lda, B, ld, C, ld, acc, alpha, diag, sub, sub_bytes, tc_err, s);
+                    double alpha = 1.0) {
+        return zgemm_tn_bf16x3(M, npw, K, A, lda, B, ld, C, ld, acc, alpha, sub, sub_bytes, tc_err, s);
     }
     qm_status tn64(int M, int K, const double2* A, int lda, const double2* B, double2* C, bool acc,
                    double alpha = 1.0) {
@@ -231,29 +231,22 @@ struct DavidsonRun {
     bool exact_second_pass() const { return !tc || !mixed || ortho64; }
 
     // One Cholesky-QR pass with dropping: the n_in rows of src -> *k orthonormal rows of dst.
-    // exact: Gram matrix in FP64; in the precision form an exact pass applies its near-identity
-    // transform W as dst = src + src (W - I), the identity part exact (tensor-core product of
-    // the small remainder).  Pass 0 drops directions whose pivot is below `drop` of their own
-    // norm^2; an exact second pass only drops exact null directions.
+    // exact: Gram matrix and transform in FP64 (the transform of an exact pass can be far from
+    // the identity when the tensor-core pass before it met an ill-conditioned block, so it is
+    // not split into identity + small remainder).  Pass 0 drops directions whose pivot is below
+    // `drop` of their own norm^2; an exact second pass only drops exact null directions.
     qm_status chol_pass(const double2* src, int n_in, double2* dst, bool exact, double drop, int* kout) {
         qm_status st = exact ? cn64(n_in, n_in, src, src, w.G, n_in) : cn_tc(n_in, n_in, src, src, w.G, n_in);
         if (st) return st;
         int k = 0;
-        if ((st = chol_transform(w.G, n_in, n_in, drop, w.sel, w.rank, w.info, w.A, w.Cs, 0, s, !exact)) ||
+        if ((st = chol_transform(w.G, n_in, n_in, drop, w.sel, w.rank, w.info, w.A, w.Cs, 0, s)) ||
             (st = cuda_check(cudaMemcpyAsync(&k, w.info, sizeof(int), cudaMemcpyDeviceToHost, s), "D2H kept")) ||
             (st = cuda_check(cudaStreamSynchronize(s), "stream sync")))
             return st;
         *kout = k;
         if (k == 0) return QM_OK;
         if ((st = chol_transform_rows(w.G, n_in, n_in, w.sel, w.rank, k, w.A, w.Cs, s))) return st;
-        if (!tc || (exact && k < n_in)) return tn64(k, n_in, w.Cs, k, src, dst, false);
-        if (exact) {
-            st = cuda_check(cudaMemcpy2DAsync(dst, (size_t)ld * sizeof(double2), src, (size_t)ld * sizeof(double2),
-                                              (size_t)npw * sizeof(double2), k, cudaMemcpyDeviceToDevice, s),
-                            "copy rows");
-            return st ? st : tn_tc(k, n_in, w.Cs, k, src, dst, true, 1.0, -1.0);
-        }
-        return tn_tc(k, n_in, w.Cs, k, src, dst, false);
+        return (!tc || exact) ? tn64(k, n_in, w.Cs, k, src, dst, false) : tn_tc(k, n_in, w.Cs, k, src, dst, false);
     }
 
     // One classical Gram-Schmidt pass of the nu rows of D against the m basis rows V:
@@ -281,10 +274,11 @@ struct DavidsonRun {
     // The nu correction rows of D (overwritten) -> *kept rows at `out`, orthonormal and
     // orthogonal to the m basis rows.  Plain FP64: two Gram-Schmidt passes, then two
     // Cholesky-QR passes.  Precision form: Gram-Schmidt and Cholesky-QR on the tensor cores,
-    // then an exact Gram-Schmidt pass and an exact Cholesky-QR pass (FP64 coefficients and
-    // Gram matrix, tensor-core products of the small corrections only): the exact passes come
-    // last because a tensor-core transform of O(1) coefficients leaves ~1e-7 components along
-    // the basis, which only an exact pass after it removes.
+    // then a second Gram-Schmidt pass and Cholesky-QR pass, exact in the FP64 phase (and with
+    // mixed_ortho = 1): FP64 coefficients, Gram matrix and transform; only the Gram-Schmidt
+    // correction, whose coefficients are tiny, is applied on the tensor cores.  The exact
+    // passes come last because a tensor-core transform of O(1) coefficients leaves ~1e-7
+    // components along the basis, which only an exact pass after it removes.
     qm_status expand(int m, int nu, double2* out, int* kept) {
         qm_status st;
         *kept = 0;
@@ -451,10 +445,12 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
     // restart, at convergence and at exit they are recomputed entirely in FP64, so anchors and
     // reported residuals stay exact.  Used only with buffer bands (nconv < nb): without them the
     // top band may rotate by O(1) into states outside the block, and its large coefficients on
-    // later directions would carry the FP32-accuracy errors into its residual.
+    // later directions would carry the FP32-accuracy errors into its residual.  An anchored
+    // phase that stops making progress hands over to plain FP64 (deanchor below).
     double2* Ra = w.Tmp;  // free after the initial orthonormalisation
     bool need_anchor = false, split_ritz = false;
-    int it_anchor = 0;
+    int it_anchor = 0, it_halved = 0;
+    double anchor_best = 0.0;
     std::vector<int> unc;
     bool all_conv = true;
     auto ritz = [&](bool exact) -> qm_status {
@@ -519,11 +515,17 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
         if ((st = heev_lowest(w.A, m, m, nb, w.eps, w.Cs, nb, w.heev, s))) return st;
         if ((st = ritz(false))) return st;
         // the anchored products assume that the bands which must converge take only small
-        // coefficients on the later directions; if the residual stops halving over 10 steps,
-        // the rest of the solve runs in plain FP64 from an exact restart
+        // coefficients on the later directions; if the best residual of the anchored phase has
+        // not halved for 12 steps (robust to oscillation), or after 60 anchored steps, the rest
+        // of the solve runs in plain FP64 from an exact restart
         bool deanchor = false;
-        if (run.anchored && it - it_anchor > 11 && hist_all.size() > 10)
-            deanchor = max_res > 0.5 * hist_all[hist_all.size() - 10] && max_res > o.tol;
+        if (run.anchored) {
+            if (max_res < 0.5 * anchor_best) {
+                anchor_best = max_res;
+                it_halved = it;
+            }
+            deanchor = max_res > o.tol && (it - it_halved > 12 || it - it_anchor > 60);
+        }
         if (split_ritz && (all_conv || deanchor || it == o.max_iter || m + (int)unc.size() > nvx) &&
             (st = ritz(true)))
             return st;
@@ -547,7 +549,8 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
             run.mixed = false;
             run.anchored = run.tc && o.nconv < nb;
             need_anchor = run.anchored;
-            it_anchor = it;
+            it_anchor = it_halved = it;
+            anchor_best = max_res;
             it_mixed = it;
             if ((st = run.cholqr(w.X, nb, w.V, &kept))) return st;
             if (kept < nb) return fail(QM_ERR_NUMERIC, "qm_davidson: Ritz vectors lost rank at the FP64 switch");

@@ -14,9 +14,6 @@ namespace {
 // one CTA (right-looking).  A pivot below drop_rel * S_jj(original) marks vector j as
 // linearly dependent on the previous ones: its row and column are zeroed and it is skipped
 // (Cholesky with dropping == Gram-Schmidt that discards near-null directions).
-// R: arithmetic type (FP64, or FP32 for Gram matrices that are only FP32-accurate anyway);
-// the storage stays FP64.
-template <class R>
 __global__ void __launch_bounds__(1024)
 k_chol_drop(double2* __restrict__ S, int lds, int nd, double drop_rel, int* __restrict__ keep) {
     const int tid = threadIdx.x, bs = blockDim.x;
@@ -36,11 +33,10 @@ k_chol_drop(double2* __restrict__ S, int lds, int nd, double drop_rel, int* __re
             __syncthreads();
             continue;
         }
-        const double l = sqrt(piv);
-        const R il = (R)(1.0 / l);
+        const double l = sqrt(piv), il = 1.0 / l;
         for (int i = j + 1 + tid; i < nd; i += bs) {
             double2 v = S[(size_t)i * lds + j];
-            S[(size_t)i * lds + j] = make_double2((R)v.x * il, (R)v.y * il);
+            S[(size_t)i * lds + j] = make_double2(v.x * il, v.y * il);
         }
         if (tid == 0) {
             S[(size_t)j * lds + j] = make_double2(l, 0.0);
@@ -52,12 +48,12 @@ k_chol_drop(double2* __restrict__ S, int lds, int nd, double drop_rel, int* __re
         const int lane = tid & 31, warp = tid >> 5, nwarp = bs >> 5;
         for (int i = j + 1 + warp; i < nd; i += nwarp) {
             const double2 a = S[(size_t)i * lds + j];
-            const R ax = (R)a.x, ay = (R)a.y;
             for (int k = j + 1 + lane; k <= i; k += 32) {
                 const double2 b = S[(size_t)k * lds + j];
-                const double2 v = S[(size_t)i * lds + k];
-                const R bx = (R)b.x, by = (R)b.y;
-                S[(size_t)i * lds + k] = make_double2((R)v.x - (ax * bx + ay * by), (R)v.y - (ay * bx - ax * by));
+                double2 v = S[(size_t)i * lds + k];
+                v.x -= a.x * b.x + a.y * b.y;
+                v.y -= a.y * b.x - a.x * b.y;
+                S[(size_t)i * lds + k] = v;
             }
         }
         __syncthreads();
@@ -120,15 +116,12 @@ __global__ void k_rank(const int* __restrict__ keep, int nd, int* __restrict__ r
 // S = Y Y^H, given in S (lds), destroyed).  keep/rank: nd ints each; X: nd x nd scratch;
 // kept_dev: 1 int.  Asynchronous; the caller reads kept_dev.
 qm_status chol_transform(double2* S, int lds, int nd, double drop_rel, int* keep, int* rank, int* kept_dev,
-                         double2* X, double2* W, int ldw_max, cudaStream_t s, bool fp32) {
+                         double2* X, double2* W, int ldw_max, cudaStream_t s) {
     (void)ldw_max;
     {
         const size_t smem = (size_t)nd * sizeof(double);
         ProfScope pf(PF_CHOL, s);
-        if (fp32)
-            k_chol_drop<float><<<1, 1024, smem, s>>>(S, lds, nd, drop_rel, keep);
-        else
-            k_chol_drop<double><<<1, 1024, smem, s>>>(S, lds, nd, drop_rel, keep);
+        k_chol_drop<<<1, 1024, smem, s>>>(S, lds, nd, drop_rel, keep);
     }
     {
         ProfScope pf(PF_CHOL, s);

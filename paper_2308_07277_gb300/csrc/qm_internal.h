@@ -176,15 +176,13 @@ size_t nonlocal_bf16x3_bytes(int nproj, int nb, int npw);
 // Subspace products of the Davidson FP32 phase on the tensor cores: FP64 storage rounded to
 // FP32 on load, BF16x3 split products accumulated in FP32 per K split, splits summed in FP64.
 //   cn: C[i][j] = sum_k conj(A[i][k]) B[j][k]                (as zgemm_cn)
-//   tn: C[i][n] (+)= sum_k (alpha A[k][i] + diag [k == i]) B[k][n]   (zgemm_tn with d = NULL
-//       when diag = 0; with accumulate and diag = -1, C += B (alpha A - I) applies a near-identity
-//       rotation to rows already copied into C with FP64 accuracy of the identity part)
+//   tn: C[i][n] (+)= alpha sum_k A[k][i] B[k][n]             (as zgemm_tn with d = NULL)
 // work: subspace_bf16x3_bytes(max M, max N) bytes; err: device int set on a timed-out wait
 qm_status zgemm_cn_bf16x3(int M, int N, int K, const double2* A, int lda, const double2* B, int ldb,
                           double2* C, int ldc, void* work, size_t work_bytes, int* err, cudaStream_t s);
 qm_status zgemm_tn_bf16x3(int M, int N, int K, const double2* A, int lda, const double2* B, int ldb,
-                          double2* C, int ldc, bool accumulate, double alpha, double diag, void* work,
-                          size_t work_bytes, int* err, cudaStream_t s);
+                          double2* C, int ldc, bool accumulate, double alpha, void* work, size_t work_bytes,
+                          int* err, cudaStream_t s);
 size_t subspace_bf16x3_bytes(int max_m, int max_n);
 
 // ---- learned preconditioner (mlp.cu) ----
@@ -205,10 +203,9 @@ qm_status heev_lowest(double2* A, int lda, int m, int nev, double* evals, double
 size_t heev_work_bytes(int m, int nev);
 // Cholesky-with-dropping orthonormalisation: chol_transform factors S (nd x nd Gram matrix,
 // destroyed) and counts the kept vectors into kept_dev; chol_transform_rows then writes the
-// nd x kept transform W for gemm_tn.  keep, rank: nd ints; X: nd x nd scratch.  fp32: factor
-// in FP32 arithmetic (for Gram matrices that carry FP32 errors anyway).
+// nd x kept transform W for gemm_tn.  keep, rank: nd ints; X: nd x nd scratch.
 qm_status chol_transform(double2* S, int lds, int nd, double drop_rel, int* keep, int* rank, int* kept_dev,
-                         double2* X, double2* W, int ldw_max, cudaStream_t s, bool fp32 = false);
+                         double2* X, double2* W, int ldw_max, cudaStream_t s);
 qm_status chol_transform_rows(const double2* L, int lds, int nd, const int* keep, const int* rank, int kept,
                               double2* X, double2* W, cudaStream_t s);
 

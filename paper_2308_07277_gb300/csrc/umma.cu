@@ -338,16 +338,14 @@ __global__ void k_reduce_cn(const float* __restrict__ part, int Z, size_t zstrid
     }
 }
 
-// At[i][j] = alpha * A[j][i] + diag * [i == j] in FP32 (the small coefficient matrix of a basis
-// rotation, made K-major for the tensor-core operand; the shift is applied in FP64 first, so
-// a near-identity rotation passes only its small deviation from the identity)
-__global__ void k_coef_t(const double2* __restrict__ A, int lda, int M, int K, double alpha, double diag,
-                         float2* __restrict__ At) {
+// At[i][j] = alpha * A[j][i] in FP32 (the small coefficient matrix of a basis rotation, made
+// K-major for the tensor-core operand)
+__global__ void k_coef_t(const double2* __restrict__ A, int lda, int M, int K, double alpha, float2* __restrict__ At) {
     const size_t total = (size_t)M * K;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
         const int i = (int)(e / K), j = (int)(e % K);
         const double2 a = A[(size_t)j * lda + i];
-        At[e] = make_float2((float)(alpha * a.x + (i == j ? diag : 0.0)), (float)(alpha * a.y));
+        At[e] = make_float2((float)(alpha * a.x), (float)(alpha * a.y));
     }
 }
 
@@ -443,8 +441,8 @@ qm_status zgemm_cn_bf16x3(int M, int N, int K, const double2* A, int lda, const 
 }
 
 qm_status zgemm_tn_bf16x3(int M, int N, int K, const double2* A, int lda, const double2* B, int ldb, double2* C,
-                          int ldc, bool accumulate, double alpha, double diag, void* work, size_t work_bytes,
-                          int* err, cudaStream_t s) {
+                          int ldc, bool accumulate, double alpha, void* work, size_t work_bytes, int* err,
+                          cudaStream_t s) {
     if (M <= 0 || N <= 0) return QM_OK;
     if (K <= 0) {
         if (accumulate) return QM_OK;
@@ -455,7 +453,7 @@ qm_status zgemm_tn_bf16x3(int M, int N, int K, const double2* A, int lda, const 
     float2* at = (float2*)work;
     {
         ProfScope pf(PF_SPLIT, s);
-        k_coef_t<<<grid_for((size_t)M * K), 256, 0, s>>>(A, lda, M, K, alpha, diag, at);
+        k_coef_t<<<grid_for((size_t)M * K), 256, 0, s>>>(A, lda, M, K, alpha, at);
     }
     qm_status st = cuda_check(cudaGetLastError(), "k_coef_t launch");
     if (st) return st;
