@@ -264,11 +264,18 @@ typedef struct {
     int nvecx;           /* maximum basis size, >= 2 nb (clamped to npw); default 4 nb */
     qm_precision prec;   /* QM_FP64: every step in FP64.  QM_MIXED: H psi in FP32 (qm_hpsi
                             QM_MIXED) and the subspace products as BF16x3 tensor-core products
-                            (FP32 accuracy, see mixed_ortho) until the
-                            largest residual falls below mixed_switch; then the Ritz vectors are
-                            re-orthonormalised and H applied to them in FP64, and the iterations
-                            continue in FP64 to tol.  Eigensolves, residual norms and band
-                            energies are FP64 in both. */
+                            (FP32 accuracy, see mixed_ortho) until the largest residual falls
+                            below mixed_switch; then the Ritz vectors are re-orthonormalised and
+                            H applied to them in FP64, and the iterations continue with FP64
+                            H psi to tol.  In that FP64 phase, when nconv < nb, the basis is
+                            anchored on the exact Ritz vectors of each restart: products that
+                            only involve small quantities (couplings through the anchors'
+                            residuals, later directions, small Ritz coefficients) stay on the
+                            tensor cores, the rest is FP64, and restarts, convergence and exit
+                            recompute the Ritz vectors in FP64; an anchored phase whose best
+                            residual stops halving for 12 steps (or lasts 60) continues in plain
+                            FP64.  Eigensolves, residual norms and band energies are FP64 in
+                            every form. */
     int precond;         /* 0 = Teter-Payne-Allan diagonal preconditioner; 1 = learned (the network
                             `mlp`), with TPA taking over for the rest of the call if the largest
                             residual fails to fall below precond_stall x its value 4 steps earlier */
