@@ -2,16 +2,18 @@
 // matrix-free "Davidson with overlap" that only applies H to blocks of trial vectors).
 //
 // Per iteration, on the caller's stream (host loop; two small device->host reads):
-//   Rayleigh-Ritz   H_sub = V^H (H V) (new columns only), Jacobi eigensolve (FP64)
+//   Rayleigh-Ritz   H_sub = V^H (H V) (new columns only), dense Hermitian eigensolve in FP64
+//                   (heev.cu: Householder reduction, multisection, inverse iteration)
 //   Ritz vectors    X = V c, HX = (HV) c for the lowest nb eigenpairs
 //   residuals       r_n = HX_n - eps_n X_n, ||r_n|| and T_n = <X_n|T|X_n> (FP64)
-//   corrections     delta_n = K_TPA(kin / T_n) r_n for the bands with ||r_n|| > tol
+//   corrections     delta_n = K_TPA(kin / T_n) r_n (or the learned K) for the bands with
+//                   ||r_n|| > tol
 //   restart         if the basis would exceed nvecx: V <- X, HV <- HX
-//   orthonormalise  two classical Gram-Schmidt passes against V, then two passes of
+//   orthonormalise  two classical Gram-Schmidt passes against V and two passes of
 //                   Cholesky-QR within the block, near-dependent directions dropped
 //   expand          V <- [V, delta], HV <- [HV, H delta]
 // The basis is kept orthonormal, so the subspace overlap S_sub is the identity to FP64
-// round-off and Rayleigh-Ritz is a standard Hermitian eigenproblem (heev.cu).
+// round-off and Rayleigh-Ritz is a standard Hermitian eigenproblem.
 //
 // Precision form (QM_MIXED): H psi in FP32 and the subspace products as BF16x3 split products
 // on the tensor cores (FP64 storage rounded to FP32 on load, FP32 accumulation per K split,
@@ -19,7 +21,10 @@
 // pass and the second Cholesky-QR pass stay FP64, which keeps the basis orthonormal to FP64
 // round-off; eigensolves, residual norms and band energies in FP64.  Once the largest residual
 // is below mixed_switch (or stops falling), the Ritz vectors are re-orthonormalised, H is
-// applied to them in FP64 (refinement sweep), and the iterations continue entirely in FP64.
+// applied to them in FP64 (refinement sweep), and the iterations continue with FP64 H psi and
+// exact orthogonalisation passes; with buffer bands that FP64 phase is anchored on the Ritz
+// vectors of each restart (see the loop below), which leaves the products of small
+// quantities on the tensor cores.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -179,7 +184,7 @@ struct DavidsonRun {
     cudaStream_t s;
     Ws w;
     long long applies = 0, applies_mixed = 0;
-    bool mixed = false;          // current phase: FP32 H psi and FP32-arithmetic subspace products
+    bool mixed = false;          // current phase: FP32 H psi and tensor-core (FP32-accuracy) subspace products
     float2* psi32 = nullptr;     // [nb][ld] FP32 staging of the vectors H is applied to
     float2* hpsi32 = nullptr;    // [nb][ld]
     float2* beta32 = nullptr;    // [nproj][ld]
