@@ -47,7 +47,7 @@ typedef enum {
     QM_ERR_NOT_CONVERGED = 4,  /* Davidson hit max_iter; outputs still written */
     QM_ERR_NUMERIC = 5,        /* non-finite value or breakdown (e.g. Cholesky) */
     QM_ERR_TIMEOUT = 6,        /* a bounded device-side wait expired */
-    QM_ERR_UNSUPPORTED = 7     /* valid request this build does not implement */
+    QM_ERR_UNSUPPORTED = 7     /* valid request the library does not implement */
 } qm_status;
 
 typedef enum {
