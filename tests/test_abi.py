@@ -110,3 +110,29 @@ def test_argument_errors_are_reported_not_crashed():
     finally:
         Q.qm_gspace_destroy(g)
     lib.qm_gspace_destroy(None)
+
+
+def test_davidson_option_errors_before_device_work():
+    """qm_davidson validates its options (precision, preconditioner, mixed_ortho, nvecx, tol)
+    and reports QM_ERR_ARG before it touches the device: the pointers below are never
+    dereferenced."""
+    import ctypes
+    import paper_2308_07277_gb300 as Q
+    from paper_2308_07277_gb300 import _lib as L
+    lib = _lib()
+    g = Q.qm_gspace_create(np.eye(3) * 10.0, [[0, 0, 0]], 5.0)
+    try:
+        npw = Q.qm_gspace_query(g)["npw"][0]
+        fake = ctypes.c_void_p(1 << 20)  # 16-byte aligned, never read
+        eig = np.zeros(4)
+        cases = [dict(prec=7), dict(precond=3), dict(precond=1), dict(mixed_ortho=2), dict(nvecx=5),
+                 dict(tol=-1.0), dict(max_iter=-2)]
+        msgs = ["unknown precision", "unknown preconditioner", "learned preconditioner without parameters",
+                "mixed_ortho", "nvecx", "tol", "tol"]
+        for kw, msg in zip(cases, msgs):
+            opts = L.DavidsonOpts(**dict(dict(tol=1e-8, max_iter=10), **kw))
+            st = lib.qm_davidson(g, 0, 4, fake, npw, fake, 0, None, 0, None, ctypes.byref(opts),
+                                 eig.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), None, None)
+            assert st == 1 and msg in Q.qm_last_error(), (kw, st, Q.qm_last_error())
+    finally:
+        Q.qm_gspace_destroy(g)
