@@ -369,6 +369,37 @@ qm_status qm_davidson_batched(int njobs, qm_davidson_job* jobs, const qm_davidso
                               int max_concurrent, void* stream);
 
 /*
+ * qm_precond_apply - the residual and correction steps of one Davidson iteration on their
+ * own (Sec. 5, dft module: the correction step of the matrix-free Davidson; the diagonal
+ * Teter-Payne-Allan preconditioner, Phys. Rev. B 40, 12255 (1989), or the learned network),
+ * with the kernels qm_davidson launches for them:
+ *   r_n      = HX_n - eps_n X_n,            rnorm2_n = ||r_n||^2,
+ *   T_n      = sum_G T_G |X_n(G)|^2 / sum_G |X_n(G)|^2,   T_G = |k+G|^2 / 2,
+ *   delta_n  = K_n(G) r_n(G),  K = K_TPA(T_G / T_n) (precond 0) or the network of
+ *              qm_mlp_forward on the features (T_G/T_n, eps_n/T_n, log(max(|r_n(G)| sqrt(npw) /
+ *              ||r_n||, 1e-6))) (precond 1).
+ *
+ *  g, ik      gspace and k-point.
+ *  n          number of bands, 0 <= n <= 65535 (0 is a no-op).
+ *  X, HX      device, n rows of npw(ik) complex double, row stride ld (>= npw): Ritz vectors
+ *             (any non-zero rows; T_n is normalised by the row's own norm) and H applied to them.
+ *  eps        device, n doubles: the Ritz values eps_n.
+ *  precond    0 = TPA, 1 = learned (mlp: device, QM_MLP_NPARAM floats, as qm_mlp_forward).
+ *  R, delta   device, n rows, row stride ld: outputs r_n and delta_n (must not overlap the inputs
+ *             or each other).
+ *  rnorm2     device, n doubles: output ||r_n||^2 (FP64).
+ *  tkin       device, n doubles: output T_n (FP64).
+ *  stream     cudaStream_t.  precond 0 is asynchronous; precond 1 synchronises the stream to
+ *             read the network's error word (the handle's workspace holds it: same one-stream
+ *             rule as qm_hpsi).
+ * Arithmetic: FP64 (TPA); the network in BF16 with FP32 accumulation, K applied in FP64.
+ * Errors: QM_ERR_ARG, QM_ERR_CUDA, QM_ERR_OOM, QM_ERR_TIMEOUT (a bounded wait of the network).
+ */
+qm_status qm_precond_apply(qm_gspace g, int ik, int n, const void* X, const void* HX, int ld, const double* eps,
+                           int precond, const float* mlp, void* R, void* delta, double* rnorm2, double* tkin,
+                           void* stream);
+
+/*
  * qm_eigh_lowest - lowest nev eigenpairs of a complex Hermitian m x m matrix in FP64: the
  * dense eigensolver of the Davidson Rayleigh-Ritz step, exposed on its own.  Householder
  * reduction to real tridiagonal form, multisection on Sturm counts for the wanted

@@ -77,6 +77,11 @@ SIGNATURES["qm_davidson"] = (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctype
 
 SIGNATURES["qm_hpsi_noalloc"] = SIGNATURES["qm_hpsi"]
 
+SIGNATURES["qm_precond_apply"] = (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                                 ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                 ctypes.c_void_p, ctypes.c_void_p])
+
 SIGNATURES["qm_eigh_lowest"] = (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                                ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p])
 

@@ -207,6 +207,27 @@ def qm_hpsi_noalloc(g, ik, psi, vloc, beta, D, out, prec="fp64", stream=None):
     return out
 
 
+def qm_precond_apply(g, ik, X, HX, eps, mlp=None, stream=None):
+    """Residuals and Davidson corrections of the n rows of X (n, >=npw) complex128 CUDA tensor
+    with HX (same shape and stride) and eps (n,) float64 CUDA tensor; TPA when mlp is None,
+    else the network (QM_MLP_NPARAM float32 CUDA tensor).  Returns (R, delta, rnorm2, tkin)."""
+    lib = _lib.load()
+    if X.dim() != 2 or HX.shape != X.shape or HX.stride(0) != X.stride(0):
+        raise ValueError("X and HX must be 2-D with the same shape and row stride")
+    n = int(X.shape[0])
+    R = torch.empty_like(X)
+    delta = torch.empty_like(X)
+    rn2 = torch.empty(n, dtype=torch.float64, device=X.device)
+    tk = torch.empty(n, dtype=torch.float64, device=X.device)
+    _check(lib.qm_precond_apply(g, int(ik), n, _dev_ptr(X, "X", torch.complex128),
+                                _dev_ptr(HX, "HX", torch.complex128), int(X.stride(0)),
+                                _dev_ptr(eps, "eps", torch.float64), 0 if mlp is None else 1,
+                                _dev_ptr(mlp, "mlp", torch.float32), _dev_ptr(R, "R", torch.complex128),
+                                _dev_ptr(delta, "delta", torch.complex128), _dev_ptr(rn2, "rnorm2", torch.float64),
+                                _dev_ptr(tk, "tkin", torch.float64), _stream_ptr(stream)))
+    return R, delta, rn2, tk
+
+
 def qm_eigh_lowest(A, nev, stream=None):
     """Lowest nev eigenpairs of the Hermitian (m, m) complex128 CUDA tensor A.
     Returns (evals (nev,) float64 CUDA tensor, Y (m, nev) complex128 CUDA tensor)."""

@@ -82,7 +82,7 @@ __global__ void k_tpa(const double2* __restrict__ R, int ld, int npw, const int*
                       const double* __restrict__ tkin, const double* __restrict__ kin, double2* __restrict__ out,
                       int ldo) {
     const int j = blockIdx.y;
-    const int n = sel[j];
+    const int n = sel ? sel[j] : j;  // sel == NULL: row j is band j
     const double inv_t = 1.0 / tkin[n];
     const double2* r = R + (size_t)n * ld;
     double2* o = out + (size_t)j * ldo;
@@ -188,6 +188,7 @@ struct DavidsonRun {
     float2* psi32 = nullptr;     // [nb][ld] FP32 staging of the vectors H is applied to
     float2* hpsi32 = nullptr;    // [nb][ld]
     float2* beta32 = nullptr;    // [nproj][ld]
+    void* beta_tc = nullptr;     // the projectors split once into the tensor-core operand layouts
     bool tc = false;             // precision form: tensor-core subspace products available
     bool anchored = false;       // precision form, FP64 phase: basis rows 0..nb-1 are the Ritz
                                  // vectors of the last restart (the anchor), see qm_davidson
@@ -202,7 +203,7 @@ struct DavidsonRun {
         applies_mixed += n;
         qm_status st = convert_rows(in, ld, psi32, ld, n, npw, s);
         if (st) return st;
-        st = qm_hpsi(g, ik, n, psi32, ld, vloc, nproj, beta32, ld, D, hpsi32, ld, QM_MIXED, s);
+        st = hpsi_run(g, ik, n, psi32, ld, vloc, nproj, beta32, ld, beta_tc, D, hpsi32, ld, QM_MIXED, s);
         if (st) return st;
         return convert_rows(hpsi32, ld, out, ld, n, npw, s);
     }
@@ -368,7 +369,8 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
     const size_t big32 = (size_t)ld * sizeof(float2);
     const bool use_mixed = o.prec == QM_MIXED;
     const size_t oP32 = take(use_mixed ? big32 * nb : 0), oH32 = take(use_mixed ? big32 * nb : 0),
-                 oB32 = take(use_mixed ? big32 * std::max(nproj, 1) : 0);
+                 oB32 = take(use_mixed ? big32 * std::max(nproj, 1) : 0),
+                 oBtc = take(use_mixed && nproj > 0 ? nonlocal_tc_beta_bytes(nproj, nb, npw) : 0);
     const size_t sub_bytes = use_mixed ? subspace_bf16x3_bytes(nvx, nb) : 0;
     const size_t oSub = take(sub_bytes);
     const size_t sq = (size_t)nsq * nsq * sizeof(double2);
@@ -393,6 +395,10 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
         run.hpsi32 = (float2*)(base + oH32);
         run.beta32 = (float2*)(base + oB32);
         if (nproj > 0 && (st = convert_rows((const double2*)beta, ld_beta, run.beta32, ld, nproj, npw, s))) return st;
+        if (nproj > 0) {
+            run.beta_tc = base + oBtc;
+            if ((st = nonlocal_tc_prepare(nproj, nb, npw, run.beta32, ld, run.beta_tc, s))) return st;
+        }
         run.mixed = true;
         run.tc = true;
         run.ortho64 = o.mixed_ortho == 1;
@@ -721,5 +727,54 @@ extern "C" qm_status qm_davidson_batched(int njobs, qm_davidson_job* jobs, const
     for (int i = 0; i < njobs; ++i)
         if (jobs[i].status == QM_ERR_NOT_CONVERGED)
             return fail(QM_ERR_NOT_CONVERGED, "qm_davidson_batched: job " + std::to_string(i) + " did not converge");
+    return QM_OK;
+}
+
+// The residual and correction steps of one Davidson iteration on their own (the kernels the
+// loop above launches): r_n = HX_n - eps_n X_n with ||r_n||^2 and T_n, then
+// delta_n = K r_n with the TPA factor or the learned network.
+extern "C" qm_status qm_precond_apply(qm_gspace g, int ik, int n, const void* X, const void* HX, int ld,
+                                      const double* eps, int precond, const float* mlp, void* R, void* delta,
+                                      double* rnorm2, double* tkin, void* stream) {
+    clear_error();
+    if (!g) return fail(QM_ERR_ARG, "qm_precond_apply: NULL gspace");
+    if (ik < 0 || ik >= g->nk) return fail(QM_ERR_ARG, "qm_precond_apply: ik out of range");
+    if (n < 0 || n > 65535) return fail(QM_ERR_ARG, "qm_precond_apply: need 0 <= n <= 65535");
+    if (precond != 0 && precond != 1) return fail(QM_ERR_ARG, "qm_precond_apply: unknown preconditioner");
+    if (precond == 1 && !mlp) return fail(QM_ERR_ARG, "qm_precond_apply: learned preconditioner without parameters");
+    if (n == 0) return QM_OK;
+    const int npw = g->k[ik].npw;
+    if (!X || !HX || !eps || !R || !delta || !rnorm2 || !tkin)
+        return fail(QM_ERR_ARG, "qm_precond_apply: NULL X, HX, eps, R, delta, rnorm2 or tkin");
+    if (ld < npw) return fail(QM_ERR_ARG, "qm_precond_apply: ld < npw");
+    if (((uintptr_t)X | (uintptr_t)HX | (uintptr_t)R | (uintptr_t)delta) % 16)
+        return fail(QM_ERR_ARG, "qm_precond_apply: X, HX, R, delta not 16-byte aligned");
+    qm_status st = ensure_device(g);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const double* kin = g->k[ik].kin;
+    double2* r = (double2*)R;
+    double2* d = (double2*)delta;
+    {
+        ProfScope pf(PF_OTHER, s);
+        k_residual<<<n, 256, 0, s>>>((const double2*)X, (const double2*)HX, ld, npw, eps, kin, r, rnorm2, tkin);
+    }
+    if ((st = cuda_check(cudaGetLastError(), "k_residual launch"))) return st;
+    if (precond == 0) {
+        ProfScope pf(PF_OTHER, s);
+        k_tpa<<<dim3(std::min(64, (npw + 255) / 256), n), 256, 0, s>>>(r, ld, npw, nullptr, tkin, kin, d, ld);
+        return cuda_check(cudaGetLastError(), "k_tpa launch");
+    }
+    // the network's bounded tensor-core waits report through a device word in the workspace
+    if ((st = ensure_workspace(g, 256, s))) return st;
+    int* err = (int*)g->ws.ptr;
+    if ((st = cuda_check(cudaMemsetAsync(err, 0, sizeof(int), s), "reset error word")) ||
+        (st = mlp_precond_apply(mlp, r, ld, npw, nullptr, n, tkin, eps, rnorm2, kin, d, ld, err, s)))
+        return st;
+    int e = 0;
+    if ((st = cuda_check(cudaMemcpyAsync(&e, err, sizeof(int), cudaMemcpyDeviceToHost, s), "D2H error word")) ||
+        (st = cuda_check(cudaStreamSynchronize(s), "stream sync")))
+        return st;
+    if (e) return fail(QM_ERR_TIMEOUT, "qm_precond_apply: a bounded tensor-core wait of the network expired");
     return QM_OK;
 }

@@ -28,7 +28,7 @@ struct HpsiLayout {
     int splits;
 };
 
-static HpsiLayout hpsi_layout(qm_gspace g, int ik, int nb, int nproj, bool fp32) {
+static HpsiLayout hpsi_layout(qm_gspace g, int ik, int nb, int nproj, bool fp32, bool own_beta) {
     HpsiLayout L{};
     const size_t cs = fp32 ? sizeof(float2) : sizeof(double2);
     const size_t rs = fp32 ? sizeof(float) : sizeof(double);
@@ -51,7 +51,7 @@ static HpsiLayout hpsi_layout(qm_gspace g, int ik, int nb, int nproj, bool fp32)
     L.t_bytes = nbc * per_band;
     off = align_up(off + L.t_bytes, 256);
     L.nl_off = off;  // tensor-core split operands (precision form)
-    off = align_up(off + (fp32 && nproj > 0 ? nonlocal_bf16x3_bytes(nproj, nb, npw) : 0), 256);
+    off = align_up(off + (fp32 && nproj > 0 ? nonlocal_tc_bytes(nproj, nb, npw, own_beta) : 0), 256);
     L.err_off = off;
     off = align_up(off + 256, 256);
     L.total = off;
@@ -66,6 +66,13 @@ extern "C" qm_status qm_hpsi(qm_gspace g, int ik, int nb, const void* psi, int l
                              int nproj, const void* beta, int ld_beta, const double* D, void* out, int ld_out,
                              qm_precision prec, void* stream) {
     clear_error();
+    return hpsi_run(g, ik, nb, psi, ld_psi, vloc_r, nproj, beta, ld_beta, nullptr, D, out, ld_out, prec,
+                    (cudaStream_t)stream);
+}
+
+qm_status qm::hpsi_run(qm_gspace g, int ik, int nb, const void* psi, int ld_psi, const double* vloc_r, int nproj,
+                       const void* beta, int ld_beta, const void* beta_prepared, const double* D, void* out,
+                       int ld_out, qm_precision prec, cudaStream_t s) {
     if (!g) return fail(QM_ERR_ARG, "qm_hpsi: NULL gspace");
     if (ik < 0 || ik >= g->nk) return fail(QM_ERR_ARG, "qm_hpsi: ik out of range");
     if (nb < 0 || nproj < 0) return fail(QM_ERR_ARG, "qm_hpsi: negative nb or nproj");
@@ -91,9 +98,8 @@ extern "C" qm_status qm_hpsi(qm_gspace g, int ik, int nb, const void* psi, int l
 
     qm_status st = ensure_device(g);
     if (st) return st;
-    cudaStream_t s = (cudaStream_t)stream;
 
-    const HpsiLayout L = hpsi_layout(g, ik, nb, nproj, fp32);
+    const HpsiLayout L = hpsi_layout(g, ik, nb, nproj, fp32, beta_prepared == nullptr);
     if ((st = ensure_workspace(g, L.total, s))) return st;
     char* ws = (char*)g->ws.ptr;
     void* vt = ws + L.vt_off;
@@ -109,8 +115,8 @@ extern "C" qm_status qm_hpsi(qm_gspace g, int ik, int nb, const void* psi, int l
             (st = cuda_check(cudaStreamWaitEvent(a, g->ev_fork, 0), "fork wait")) ||
             (st = cuda_check(cudaMemsetAsync(err, 0, sizeof(int), a), "reset tensor-core error word")))
             return st;
-        if ((st = nonlocal_bf16x3(nproj, nb, npw, (const float2*)beta, ld_beta, (const float2*)psi, ld_psi, D,
-                                  (float2*)out, ld_out, ws + L.nl_off, err, a, false)))
+        if ((st = nonlocal_tc(nproj, nb, npw, (const float2*)beta, ld_beta, beta_prepared, (const float2*)psi, ld_psi,
+                              D, (float2*)out, ld_out, ws + L.nl_off, err, a, false)))
             return st;
         if ((st = cuda_check(cudaEventRecord(g->ev_join, a), "join event"))) return st;
         if ((st = launch_vt_prepare(g, vloc_r, vt, fp32, s))) return st;

@@ -99,7 +99,7 @@ struct DavidsonCorr {  // out_j(G) = K r_{sel[j]}(G), features from the residual
         const int j = (int)(tile / tpb);
         const int g = (int)(tile - (long)j * tpb) * kMT + tid;
         if (g >= npw) return false;
-        const int n = __ldg(sel + j);
+        const int n = sel ? __ldg(sel + j) : j;  // sel == NULL: row j is band j
         const double t = __ldg(tk + n);
         const double2 r = R[(size_t)n * ld + g];
         mlp_feat(__ldg(kin + g), 1.0 / t, __ldg(eps + n) / t, sqrt(r.x * r.x + r.y * r.y),
@@ -110,7 +110,7 @@ struct DavidsonCorr {  // out_j(G) = K r_{sel[j]}(G), features from the residual
         const long tpb = tiles_per_band();
         const int j = (int)(tile / tpb);
         const int g = (int)(tile - (long)j * tpb) * kMT + tid;
-        const double2 r = R[(size_t)__ldg(sel + j) * ld + g];
+        const double2 r = R[(size_t)(sel ? __ldg(sel + j) : j) * ld + g];
         out[(size_t)j * ldo + g] = make_double2((double)k * r.x, (double)k * r.y);
     }
 };

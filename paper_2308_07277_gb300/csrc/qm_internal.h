@@ -173,6 +173,23 @@ qm_status nonlocal_bf16x3(int nproj, int nb, int npw, const float2* beta, int ld
                           int ld_psi, const double* D, float2* out, int ld_out, void* work, int* err,
                           cudaStream_t s, bool accumulate = true);
 size_t nonlocal_bf16x3_bytes(int nproj, int nb, int npw);
+// The same product with operands pre-split into tile-blocked BF16 planes in global memory and
+// streamed by bulk copies through a warp-specialised tcgen05 pipeline (nonlocal_tc.cu).
+// beta_prepared: NULL (beta is split on every call, in `work`) or the output of
+// nonlocal_tc_prepare (nonlocal_tc_beta_bytes bytes; depends on nproj and npw only).
+// work: nonlocal_tc_bytes(nproj, nb, npw, beta_prepared == NULL) bytes.
+qm_status nonlocal_tc(int nproj, int nb, int npw, const float2* beta, int ld_beta, const void* beta_prepared,
+                      const float2* psi, int ld_psi, const double* D, float2* out, int ld_out, void* work, int* err,
+                      cudaStream_t s, bool accumulate = false);
+size_t nonlocal_tc_bytes(int nproj, int nb, int npw, bool with_beta);
+size_t nonlocal_tc_beta_bytes(int nproj, int nb, int npw);
+qm_status nonlocal_tc_prepare(int nproj, int nb, int npw, const float2* beta, int ld_beta, void* beta_work,
+                              cudaStream_t s);
+// qm_hpsi with the precision form's projectors optionally pre-split (beta_prepared, see
+// nonlocal_tc); qm_hpsi itself passes NULL.
+qm_status hpsi_run(qm_gspace g, int ik, int nb, const void* psi, int ld_psi, const double* vloc_r, int nproj,
+                   const void* beta, int ld_beta, const void* beta_prepared, const double* D, void* out, int ld_out,
+                   qm_precision prec, cudaStream_t s);
 // Subspace products of the Davidson FP32 phase on the tensor cores: FP64 storage rounded to
 // FP32 on load, BF16x3 split products accumulated in FP32 per K split, splits summed in FP64.
 //   cn: C[i][j] = sum_k conj(A[i][k]) B[j][k]                (as zgemm_cn)

@@ -136,3 +136,33 @@ def test_davidson_option_errors_before_device_work():
             assert st == 1 and msg in Q.qm_last_error(), (kw, st, Q.qm_last_error())
     finally:
         Q.qm_gspace_destroy(g)
+
+
+def test_precond_apply_errors_before_device_work():
+    """qm_precond_apply checks its arguments (band count, preconditioner, parameters, NULL
+    buffers, leading dimension, alignment) and reports QM_ERR_ARG before any device work;
+    n = 0 is a no-op."""
+    import ctypes
+    import paper_2308_07277_gb300 as Q
+    lib = _lib()
+    g = Q.qm_gspace_create(np.eye(3) * 10.0, [[0, 0, 0]], 5.0)
+    try:
+        npw = Q.qm_gspace_query(g)["npw"][0]
+        f = ctypes.c_void_p(1 << 20)      # aligned, never read
+        odd = ctypes.c_void_p((1 << 20) + 8)
+        cases = [((0, -1, f, f, npw, f, 0, None, f, f, f, f), "n"),
+                 ((0, 70000, f, f, npw, f, 0, None, f, f, f, f), "n"),
+                 ((3, 2, f, f, npw, f, 0, None, f, f, f, f), "ik"),
+                 ((0, 2, f, f, npw, f, 2, None, f, f, f, f), "unknown preconditioner"),
+                 ((0, 2, f, f, npw, f, 1, None, f, f, f, f), "without parameters"),
+                 ((0, 2, None, f, npw, f, 0, None, f, f, f, f), "NULL"),
+                 ((0, 2, f, f, npw, f, 0, None, f, f, None, f), "NULL"),
+                 ((0, 2, f, f, npw - 1, f, 0, None, f, f, f, f), "ld < npw"),
+                 ((0, 2, f, odd, npw, f, 0, None, f, f, f, f), "aligned")]
+        for args, msg in cases:
+            st = lib.qm_precond_apply(g, *args, None)
+            assert st == 1 and msg in Q.qm_last_error(), (args, st, Q.qm_last_error())
+        assert lib.qm_precond_apply(g, 0, 0, None, None, 0, None, 0, None, None, None, None, None, None) == 0
+        assert lib.qm_precond_apply(None, 0, 1, f, f, npw, f, 0, None, f, f, f, f, None) == 1
+    finally:
+        Q.qm_gspace_destroy(g)

@@ -242,6 +242,33 @@ def test_tpa_closed_forms():
     assert abs(OP.tpa_k(1.0) - 65.0 / 81.0) < 1e-15
 
 
+def test_tpa_apply_closed_form():
+    """tpa_apply against hand-computed values: T_n is the kinetic energy per unit norm of the
+    band's Ritz vector (weights |psi|^2, normalised), not of the residual, and the factor is
+    applied to the residual.  Row 0: |psi|^2 = 1 on a plane wave with T_G = 1 and 3 on one with
+    T_G = 3, so T_0 = (1 + 3*3) / 4 = 5/2; row 1: all weight on T_G = 5, so T_1 = 5.  At
+    T_G = 0, 5/2, 5 the factors of row 0 are K(0) = 1, K(1) = 65/81 and
+    K(2) = (27+36+48+64) / (27+36+48+64+256) = 175/431; row 1 sees x = 0, 1/2, 1, and
+    K(1/2) = (27+9+3+1) / (27+9+3+1+1) = 40/41."""
+    kin = np.array([0.0, 1.0, 3.0, 2.5, 5.0])
+    psi = np.zeros((2, 5), complex)
+    psi[0, 1] = 1.0 * np.exp(0.3j)
+    psi[0, 2] = np.sqrt(3.0) * np.exp(-1.1j)
+    psi[1, 4] = 2.0j                       # T_n must not depend on the norm or phase
+    rng = np.random.default_rng(5)
+    r = rng.normal(size=(2, 5)) + 1j * rng.normal(size=(2, 5))
+    r[:, 1:3] *= 1e3                       # weight of the residual elsewhere than psi's
+    got = OP.tpa_apply(r, psi, kin)
+    k0 = {0: 1.0, 3: 65.0 / 81.0, 4: 175.0 / 431.0}
+    k1 = {0: 1.0, 3: 40.0 / 41.0, 4: 65.0 / 81.0}
+    for g, k in k0.items():
+        assert abs(got[0, g] - k * r[0, g]) <= 1e-15 * abs(r[0, g])
+    for g, k in k1.items():
+        assert abs(got[1, g] - k * r[1, g]) <= 1e-15 * abs(r[1, g])
+    # psi scaled by a complex constant per row: identical result
+    np.testing.assert_allclose(OP.tpa_apply(r, 7.5j * psi, kin), got, rtol=1e-15, atol=0)
+
+
 # ----------------------------------------------------------------- Davidson vs brute force
 @pytest.mark.parametrize("cellf", [S.config1, lambda: S.cubic_si8(10.0, nbnd=8, kpts=[[0.25, 0.25, 0.25]])])
 def test_davidson_matches_dense(cellf):
