@@ -131,6 +131,27 @@ qm_status qm_hpsi(qm_gspace g, int ik, int nb,
                   qm_precision prec, void* stream);
 
 /*
+ * qm_hpsi_prepare - prepare the projectors of k-point ik for the precision form: the
+ * Hamiltonian's projectors are fixed for a k-point (Sec. 2.3, KB form; Sec. 5, the KSHam of a
+ * k-point holds them across all its H psi calls), so their 3-term BF16 split into the two
+ * tensor-core operand layouts of the nonlocal part is done once here instead of on every
+ * qm_hpsi(QM_MIXED) call.
+ *
+ *  g, ik          gspace and k-point.
+ *  nproj, beta, ld_beta   as in qm_hpsi (beta: device, FP32 complex).  nproj = 0 releases the
+ *                 k-point's prepared projectors (beta may be NULL).
+ *  stream         cudaStream_t; the split runs asynchronously on it.
+ * A later qm_hpsi(g, ik, ..., QM_MIXED) whose nproj, beta and ld_beta are the prepared ones
+ * uses the prepared operands (the result is identical: the same split of the same values).  The
+ * caller must not change the contents of beta while it is prepared; call again after changing
+ * it.  Device memory: 12 bytes per projector coefficient (two layouts of three BF16 planes),
+ * owned by the handle (freed by this call with nproj = 0, a larger re-preparation, or
+ * qm_gspace_destroy).  Not for use inside a stream capture (allocates).
+ * Errors: QM_ERR_ARG, QM_ERR_OOM, QM_ERR_CUDA.
+ */
+qm_status qm_hpsi_prepare(qm_gspace g, int ik, int nproj, const void* beta, int ld_beta, void* stream);
+
+/*
  * qm_hpsi_noalloc - the same H psi as qm_hpsi, for callers that cannot allocate device
  * memory.  The paper has no counterpart: this is a deployment variant of qm_hpsi.
  *
@@ -292,6 +313,11 @@ typedef struct {
     const float* mlp;    /* precond = 1: device, QM_MLP_NPARAM floats (see qm_mlp_forward) */
     double precond_stall; /* precond = 1: stall ratio of the fallback rule; 0 -> 0.8, >= 1: never
                              fall back */
+    int plain_restart;   /* 0 (default) = thick restart: when the basis is full it restarts from the
+                            Ritz vectors AND the new directions of the previous step's Ritz vectors
+                            of the unconverged bands (GD+k: Stathopoulos & Saad, ETNA 7, 163 (1998)),
+                            as many as fit beside the next corrections; 1 = plain restart from the
+                            Ritz vectors only */
 } qm_davidson_opts;
 
 /* Counters of one qm_davidson call (the paper's "H-psi calls" are band_applies / nb). */
@@ -305,6 +331,8 @@ typedef struct {
     long long band_applies_mixed;  /* QM_MIXED: H psi applications done in FP32 */
     int precond_fallback;    /* precond = 1: Rayleigh-Ritz step after which TPA replaced the
                                 network (0: the network was used throughout) */
+    int restarts;            /* basis restarts */
+    long long restart_kept;  /* previous-step directions kept over all thick restarts */
 } qm_davidson_stats;
 
 /*

@@ -60,14 +60,15 @@ class DavidsonOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("nvecx", ctypes.c_int),
                 ("prec", ctypes.c_int), ("precond", ctypes.c_int), ("mixed_switch", ctypes.c_double),
                 ("nconv", ctypes.c_int), ("mixed_ortho", ctypes.c_int), ("history", c_double_p),
-                ("mlp", ctypes.c_void_p), ("precond_stall", ctypes.c_double)]
+                ("mlp", ctypes.c_void_p), ("precond_stall", ctypes.c_double), ("plain_restart", ctypes.c_int)]
 
 
 class DavidsonStats(ctypes.Structure):
     """qm_davidson_stats of include/qm.h."""
     _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("band_applies", ctypes.c_longlong),
                 ("max_residual", ctypes.c_double), ("seconds", ctypes.c_double), ("iterations_mixed", ctypes.c_int),
-                ("band_applies_mixed", ctypes.c_longlong), ("precond_fallback", ctypes.c_int)]
+                ("band_applies_mixed", ctypes.c_longlong), ("precond_fallback", ctypes.c_int),
+                ("restarts", ctypes.c_int), ("restart_kept", ctypes.c_longlong)]
 
 
 SIGNATURES["qm_davidson"] = (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
@@ -76,6 +77,8 @@ SIGNATURES["qm_davidson"] = (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctype
                                             ctypes.POINTER(DavidsonStats), ctypes.c_void_p])
 
 SIGNATURES["qm_hpsi_noalloc"] = SIGNATURES["qm_hpsi"]
+SIGNATURES["qm_hpsi_prepare"] = (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                                ctypes.c_void_p])
 
 SIGNATURES["qm_precond_apply"] = (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                                  ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,

@@ -123,8 +123,18 @@ def qm_hpsi(g, ik, psi, vloc, beta, D, out=None, prec="fp64", stream=None):
     return out
 
 
+def qm_hpsi_prepare(g, ik, beta, stream=None):
+    """Prepare the precision form's projectors of k-point ik (beta: (nproj, >=npw) complex64
+    CUDA tensor that stays unchanged while prepared; None releases)."""
+    lib = _lib.load()
+    nproj = 0 if beta is None else int(beta.shape[0])
+    _check(lib.qm_hpsi_prepare(g, int(ik), nproj, _dev_ptr(beta, "beta", torch.complex64),
+                               int(beta.stride(0)) if nproj else 0, _stream_ptr(stream)))
+
+
 def qm_davidson(g, ik, psi, vloc, beta, D, tol=1e-8, max_iter=100, nvecx=0, prec="fp64", stream=None,
-                raise_not_converged=True, mixed_switch=0.0, nconv=0, mlp=None, precond_stall=0.0, mixed_ortho=0):
+                raise_not_converged=True, mixed_switch=0.0, nconv=0, mlp=None, precond_stall=0.0, mixed_ortho=0,
+                plain_restart=0):
     """Lowest nb eigenpairs; psi (nb, >=npw) complex128 CUDA tensor is overwritten by the
     Ritz vectors.  Returns (eigenvalues ndarray (nb,), stats dict)."""
     lib = _lib.load()
@@ -136,7 +146,7 @@ def qm_davidson(g, ik, psi, vloc, beta, D, tol=1e-8, max_iter=100, nvecx=0, prec
     opts = _lib.DavidsonOpts(tol=float(tol), max_iter=int(max_iter), nvecx=int(nvecx), prec=_PREC[prec],
                              precond=0 if mlp is None else 1, mixed_switch=float(mixed_switch), nconv=int(nconv),
                              mixed_ortho=int(mixed_ortho), history=_dp(hist), mlp=_dev_ptr(mlp, "mlp", torch.float32),
-                             precond_stall=float(precond_stall))
+                             precond_stall=float(precond_stall), plain_restart=int(plain_restart))
     stats = _lib.DavidsonStats()
     eig = np.zeros(nb, np.float64)
     st = lib.qm_davidson(g, int(ik), nb, _dev_ptr(psi, "psi", torch.complex128), int(psi.stride(0)),
@@ -147,7 +157,8 @@ def qm_davidson(g, ik, psi, vloc, beta, D, tol=1e-8, max_iter=100, nvecx=0, prec
     info = {"iterations": stats.iterations, "converged": bool(stats.converged),
             "band_applies": stats.band_applies, "max_residual": stats.max_residual, "seconds": stats.seconds,
             "iterations_mixed": stats.iterations_mixed, "band_applies_mixed": stats.band_applies_mixed,
-            "precond_fallback": stats.precond_fallback,
+            "precond_fallback": stats.precond_fallback, "restarts": stats.restarts,
+            "restart_kept": stats.restart_kept,
             "history": hist[: max(0, stats.iterations)].tolist(),
             "status": STATUS.get(st, st)}
     if st != 0 and not (st == 4 and not raise_not_converged):
@@ -367,7 +378,7 @@ def qm_mlp_train(band_off, feats, r2, c, D, theta, steps, lr, W=None, stream=Non
 
 
 def qm_davidson_batched(jobs, tol=1e-8, max_iter=100, nvecx=0, prec="fp64", nconv=0, mixed_switch=0.0, mlp=None,
-                        max_concurrent=0, stream=None, raise_not_converged=True, mixed_ortho=0):
+                        max_concurrent=0, stream=None, raise_not_converged=True, mixed_ortho=0, plain_restart=0):
     """Concurrent Davidson solves.  jobs: list of dicts with keys g, ik, psi (overwritten by
     the Ritz vectors), vloc, beta, D (CUDA tensors as for qm_davidson).  Returns a list of
     (eigenvalues ndarray, info dict) in job order."""
@@ -394,7 +405,8 @@ def qm_davidson_batched(jobs, tol=1e-8, max_iter=100, nvecx=0, prec="fp64", ncon
                                   history=hists[-1].ctypes.data_as(ctypes.c_void_p))
     opts = _lib.DavidsonOpts(tol=float(tol), max_iter=int(max_iter), nvecx=int(nvecx), prec=_PREC[prec],
                              precond=0 if mlp is None else 1, mixed_switch=float(mixed_switch), nconv=int(nconv),
-                             mixed_ortho=int(mixed_ortho), history=None, mlp=_dev_ptr(mlp, "mlp", torch.float32))
+                             mixed_ortho=int(mixed_ortho), history=None, mlp=_dev_ptr(mlp, "mlp", torch.float32),
+                             plain_restart=int(plain_restart))
     st = lib.qm_davidson_batched(n, arr, ctypes.byref(opts), int(max_concurrent), _stream_ptr(stream))
     out = []
     for i in range(n):
@@ -402,7 +414,8 @@ def qm_davidson_batched(jobs, tol=1e-8, max_iter=100, nvecx=0, prec="fp64", ncon
         out.append((eigs[i], {"iterations": s.iterations, "converged": bool(s.converged),
                               "band_applies": s.band_applies, "max_residual": s.max_residual, "seconds": s.seconds,
                               "iterations_mixed": s.iterations_mixed, "band_applies_mixed": s.band_applies_mixed,
-                              "precond_fallback": s.precond_fallback,
+                              "precond_fallback": s.precond_fallback, "restarts": s.restarts,
+                              "restart_kept": s.restart_kept,
                               "history": hists[i][: max(0, s.iterations)].tolist(),
                               "status": STATUS.get(arr[i].status, arr[i].status)}))
     if st != 0 and not (st == 4 and not raise_not_converged):

@@ -134,6 +134,37 @@ __global__ void k_set_diag(double2* __restrict__ H, int ld, int m, const double*
     }
 }
 
+// dst[j][i] = src[i][c(j)] for i < ni, j < nj, c(j) = sel ? sel[j] : j (column gather + transpose)
+__global__ void k_cols_to_rows(const double2* __restrict__ src, int lds, int ni, const int* __restrict__ sel, int nj,
+                               double2* __restrict__ dst, int ldd) {
+    const long total = (long)ni * nj;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+        const int j = (int)(e / ni), i = (int)(e % ni);
+        dst[(size_t)j * ldd + i] = src[(size_t)i * lds + (sel ? sel[j] : j)];
+    }
+}
+
+// zero the rows of X (n rows of length len) whose 2-norm is below thresh: one warp per row
+__global__ void k_zero_small_rows(double2* __restrict__ X, int ld, int n, int len, double thresh) {
+    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (row >= n) return;
+    double2* x = X + (size_t)row * ld;
+    double s2 = 0.0;
+    for (int i = lane; i < len; i += 32) s2 += x[i].x * x[i].x + x[i].y * x[i].y;
+    for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    if (s2 < thresh * thresh)
+        for (int i = lane; i < len; i += 32) x[i] = make_double2(0.0, 0.0);
+}
+
+// C[i][j] = (i == j) for i < rows, j < cols
+__global__ void k_set_identity(double2* __restrict__ C, int ld, int rows, int cols) {
+    const long total = (long)rows * cols;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / cols), j = (int)(e % cols);
+        C[(size_t)i * ld + j] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+    }
+}
+
 template <class D, class S>
 __global__ void k_convert_rows(const S* __restrict__ in, int ldi, D* __restrict__ out, int ldo, int rows, int cols) {
     const long total = (long)rows * cols;
@@ -160,6 +191,8 @@ qm_status convert_rows(const S* in, int ldi, D* out, int ldo, int rows, int cols
 struct Ws {
     double2 *V, *HV, *X, *HX, *R, *Dl, *Tmp;  // [.. rows][ld]
     double2 *Hs, *G, *A, *Z, *Cs, *Part;      // small
+    double2 *Cp, *CT, *PT, *QT;               // previous Ritz coefficients [nvecx+1][nb]; transposed blocks
+    double2 *Y, *HY;                          // [nb][ld]: previous-direction rows kept at a restart
     double *eval, *eps, *rn2, *tk;
     int *sel, *rank, *info;
     void* heev;
@@ -235,6 +268,67 @@ struct DavidsonRun {
     // tensor-core product, either of O(1) coefficients followed by that exact pass, or of tiny
     // coefficients (the exact pass's corrections), whose FP32 relative error is negligible.
     bool exact_second_pass() const { return !tc || !mixed || ortho64; }
+
+    // Thick restart with the previous Ritz vectors (the "+k" of GD+k restarting; Stathopoulos &
+    // Saad, Electron. Trans. Numer. Anal. 7, 163 (1998)).  In coefficient space of the current
+    // orthonormal basis (m rows): C (m x nb, Cs) holds the current Ritz vectors, Cp those of the
+    // previous step (zero in the rows added since).  The previous Ritz vectors of the nu
+    // unconverged bands (sel) are orthogonalised against C twice, rows below 1e-12 dropped,
+    // orthonormalised by two Cholesky-QR passes with dropping, and at most cap of them kept as
+    // Q; the rows Y = V Q and H Y = (H V) Q are written to w.Y, w.HY (*k rows).  The span of
+    // [X, Y] is that of the current and previous Ritz vectors, which is what a plain Ritz
+    // restart throws away.  All small products in FP64; Y in the precision of the phase.
+    qm_status prev_directions(int m, int nu, int cap, int nsq, int* kout) {
+        *kout = 0;
+        if (nu <= 0 || cap <= 0) return QM_OK;
+        qm_status st;
+        {
+            ProfScope pf(PF_OTHER, s);
+            k_cols_to_rows<<<grid_for((long)m * nb), 256, 0, s>>>(w.Cs, nb, m, nullptr, nb, w.CT, nsq);
+            k_cols_to_rows<<<grid_for((long)m * nu), 256, 0, s>>>(w.Cp, nb, m, w.sel, nu, w.PT, nsq);
+        }
+        if ((st = cuda_check(cudaGetLastError(), "k_cols_to_rows launch"))) return st;
+        auto cgs = [&](double2* Pr, int n) -> qm_status {
+            qm_status s2;
+            if ((s2 = zgemm_cn(nb, n, m, w.CT, nsq, Pr, nsq, w.A, n, w.Part, zgemm_cn_splits(nb, n, m), s)) ||
+                (s2 = zgemm_tn(n, m, nb, w.A, n, nullptr, w.CT, nsq, Pr, nsq, true, s, -1.0)))
+                return s2;
+            return QM_OK;
+        };
+        auto cholqr_c = [&](double2* src, int n, double2* dst, double drop, int* k) -> qm_status {
+            qm_status s2;
+            int kk = 0;
+            if ((s2 = zgemm_cn(n, n, m, src, nsq, src, nsq, w.G, n, w.Part, zgemm_cn_splits(n, n, m), s)) ||
+                (s2 = chol_transform(w.G, n, n, drop, w.sel, w.rank, w.info, w.A, w.Z, 0, s)) ||
+                (s2 = cuda_check(cudaMemcpyAsync(&kk, w.info, sizeof(int), cudaMemcpyDeviceToHost, s), "D2H kept")) ||
+                (s2 = cuda_check(cudaStreamSynchronize(s), "stream sync")))
+                return s2;
+            *k = kk;
+            if (kk == 0) return QM_OK;
+            if ((s2 = chol_transform_rows(w.G, n, n, w.sel, w.rank, kk, w.A, w.Z, s))) return s2;
+            return zgemm_tn(kk, m, n, w.Z, kk, nullptr, src, nsq, dst, nsq, false, s);
+        };
+        int k1 = 0, k2 = 0;
+        if ((st = cgs(w.PT, nu)) || (st = cgs(w.PT, nu))) return st;
+        {
+            ProfScope pf(PF_OTHER, s);
+            k_zero_small_rows<<<(nu + 7) / 8, 256, 0, s>>>(w.PT, nsq, nu, m, 1e-12);
+        }
+        if ((st = cholqr_c(w.PT, nu, w.QT, 1e-10, &k1))) return st;
+        if (k1 == 0) return QM_OK;
+        if ((st = cgs(w.QT, k1)) || (st = cholqr_c(w.QT, k1, w.PT, 1e-14, &k2))) return st;
+        const int k = std::min(k2, cap);
+        if (k == 0) return QM_OK;
+        {
+            ProfScope pf(PF_OTHER, s);  // Q [m][k] from its rows
+            k_cols_to_rows<<<grid_for((long)m * k), 256, 0, s>>>(w.PT, nsq, k, nullptr, m, w.QT, k);
+        }
+        if ((st = cuda_check(cudaGetLastError(), "k_cols_to_rows launch")) ||
+            (st = gemm_tn(k, m, w.QT, k, w.V, w.Y, false)) || (st = gemm_tn(k, m, w.QT, k, w.HV, w.HY, false)))
+            return st;
+        *kout = k;
+        return QM_OK;
+    }
 
     // One Cholesky-QR pass with dropping: the n_in rows of src -> *k orthonormal rows of dst.
     // exact: Gram matrix and transform in FP64 (the transform of an exact pass can be far from
@@ -334,6 +428,7 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
     if (o.nconv <= 0 || o.nconv > nb) o.nconv = nb;
     if (o.precond != 0 && o.precond != 1) return fail(QM_ERR_ARG, "qm_davidson: unknown preconditioner");
     if (o.mixed_ortho != 0 && o.mixed_ortho != 1) return fail(QM_ERR_ARG, "qm_davidson: mixed_ortho must be 0 or 1");
+    if (o.plain_restart != 0 && o.plain_restart != 1) return fail(QM_ERR_ARG, "qm_davidson: plain_restart must be 0 or 1");
     if (o.precond == 1 && !o.mlp) return fail(QM_ERR_ARG, "qm_davidson: learned preconditioner without parameters");
 
     qm_status st = ensure_device(g);
@@ -375,6 +470,10 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
     const size_t oSub = take(sub_bytes);
     const size_t sq = (size_t)nsq * nsq * sizeof(double2);
     const size_t oHs = take(sq), oG = take(sq), oA = take(sq), oZ = take(sq), oCs = take(sq);
+    const bool thick = o.plain_restart == 0;
+    const size_t sqb = (size_t)nsq * nb * sizeof(double2);
+    const size_t oCp = take(thick ? sqb : 0), oCT = take(thick ? sqb : 0), oPT = take(thick ? sqb : 0),
+                 oQT = take(thick ? sqb : 0), oY = take(thick ? big * nb : 0), oHY = take(thick ? big * nb : 0);
     const size_t oPart = take(gemm_cn_partial_bytes(false));
     const size_t oEval = take(sizeof(double) * nsq), oEps = take(sizeof(double) * nsq),
                  oRn = take(sizeof(double) * nsq), oTk = take(sizeof(double) * nsq),
@@ -411,6 +510,14 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
     w.Z = (double2*)(base + oZ);
     w.Cs = (double2*)(base + oCs);
     w.Part = (double2*)(base + oPart);
+    if (thick) {
+        w.Cp = (double2*)(base + oCp);
+        w.CT = (double2*)(base + oCT);
+        w.PT = (double2*)(base + oPT);
+        w.QT = (double2*)(base + oQT);
+        w.Y = (double2*)(base + oY);
+        w.HY = (double2*)(base + oHY);
+    }
     w.eval = (double*)(base + oEval);
     w.eps = (double*)(base + oEps);
     w.rn2 = (double*)(base + oRn);
@@ -433,6 +540,14 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
     if (kept < nb) return fail(QM_ERR_NUMERIC, "qm_davidson: initial psi block is rank deficient");
     if ((st = run.hpsi(w.V, w.HV, nb))) return st;
     int m = nb, m0 = 0;
+    // previous Ritz coefficients: after a (re)start the Ritz vectors are the first nb basis rows
+    auto reset_prev = [&]() -> qm_status {
+        if (!thick) return QM_OK;
+        ProfScope pf(PF_OTHER, s);
+        k_set_identity<<<grid_for((long)nsq * nb), 256, 0, s>>>(w.Cp, nb, nsq, nb);
+        return cuda_check(cudaGetLastError(), "k_set_identity launch");
+    };
+    if ((st = reset_prev())) return st;
     bool use_mlp = o.precond == 1;
     const double stall = o.precond_stall > 0.0 ? o.precond_stall : 0.8;
     int fallback_it = 0;
@@ -440,7 +555,8 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
     int* mlp_err = w.info + 2;
     if (use_mlp && (st = cuda_check(cudaMemsetAsync(mlp_err, 0, sizeof(int), s), "reset error word"))) return st;
     std::vector<double> rn2(nb), eps(nb);
-    int it = 0, it_mixed = 0;
+    int it = 0, it_mixed = 0, restarts = 0;
+    long long prev_kept = 0;
     std::vector<double> hist_mixed;
     bool converged = false;
     double max_res = 0.0;
@@ -566,6 +682,7 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
             if ((st = run.cholqr(w.X, nb, w.V, &kept))) return st;
             if (kept < nb) return fail(QM_ERR_NUMERIC, "qm_davidson: Ritz vectors lost rank at the FP64 switch");
             if ((st = run.hpsi(w.V, w.HV, nb))) return st;
+            if ((st = reset_prev())) return st;
             m0 = 0;
             m = nb;
             continue;
@@ -585,23 +702,49 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
             k_tpa<<<dim3((npw + 255) / 256 < 64 ? (npw + 255) / 256 : 64, nu), 256, 0, s>>>(w.R, ld, npw, w.sel, w.tk,
                                                                                             kin, w.Dl, ld);
         }
+        bool restarted = false;
         if (m + nu > nvx || need_anchor || deanchor) {  // restart from the Ritz vectors (exact here)
-            cudaMemcpyAsync(w.V, w.X, big * nb, cudaMemcpyDeviceToDevice, s);
-            cudaMemcpyAsync(w.HV, w.HX, big * nb, cudaMemcpyDeviceToDevice, s);
-            if (run.anchored) cudaMemcpyAsync(Ra, w.R, big * nb, cudaMemcpyDeviceToDevice, s);
+            // thick restart: the previous Ritz vectors' new directions ride along (not on the
+            // restarts that open or close the anchored phase, whose basis must be the Ritz vectors)
+            int kp = 0;
+            if (thick && !need_anchor && !deanchor && (st = run.prev_directions(m, nu, nvx - nb - nu, nsq, &kp)))
+                return st;
+            if ((st = cuda_check(cudaMemcpyAsync(w.V, w.X, big * nb, cudaMemcpyDeviceToDevice, s), "restart copy")) ||
+                (st = cuda_check(cudaMemcpyAsync(w.HV, w.HX, big * nb, cudaMemcpyDeviceToDevice, s), "restart copy")))
+                return st;
+            if (kp > 0 &&
+                ((st = cuda_check(cudaMemcpyAsync(w.V + (size_t)nb * ld, w.Y, big * kp, cudaMemcpyDeviceToDevice, s),
+                                  "restart copy")) ||
+                 (st = cuda_check(cudaMemcpyAsync(w.HV + (size_t)nb * ld, w.HY, big * kp, cudaMemcpyDeviceToDevice, s),
+                                  "restart copy"))))
+                return st;
+            if (run.anchored &&
+                (st = cuda_check(cudaMemcpyAsync(Ra, w.R, big * nb, cudaMemcpyDeviceToDevice, s), "restart copy")))
+                return st;
             {
                 ProfScope pf(PF_OTHER, s);
                 k_set_diag<<<grid_for((long)nb * nb), 256, 0, s>>>(w.Hs, nsq, nb, w.eps);
             }
-            m = nb;
+            m = nb + kp;
+            restarts += 1;
+            prev_kept += kp;
             need_anchor = false;
             if (deanchor) run.anchored = false;
+            restarted = true;
+            if ((st = reset_prev())) return st;
+        } else if (thick) {
+            // this step's Ritz coefficients become the previous ones (rows added later are zero)
+            if ((st = cuda_check(cudaMemcpyAsync(w.Cp, w.Cs, sizeof(double2) * (size_t)m * nb, cudaMemcpyDeviceToDevice, s),
+                                 "copy Ritz coefficients")) ||
+                (st = cuda_check(cudaMemsetAsync(w.Cp + (size_t)m * nb, 0, sizeof(double2) * (size_t)(nsq - m) * nb, s),
+                                 "zero Ritz coefficients")))
+                return st;
         }
         // orthogonalise the corrections against the basis and orthonormalise them
         if ((st = run.expand(m, nu, w.V + (size_t)m * ld, &kept))) return st;
         if (kept == 0) break;  // no new directions: stagnation
         if ((st = run.hpsi(w.V + (size_t)m * ld, w.HV + (size_t)m * ld, kept))) return st;
-        m0 = m;
+        m0 = restarted ? nb : m;  // after a thick restart the kept directions' columns of H_sub are new too
         m += kept;
     }
     if (split_ritz && (st = ritz(true))) return st;  // exact Ritz vectors for the output
@@ -633,6 +776,8 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
         stats->iterations_mixed = run.mixed ? stats->iterations : it_mixed;
         stats->band_applies_mixed = run.applies_mixed;
         stats->precond_fallback = fallback_it;
+        stats->restarts = restarts;
+        stats->restart_kept = prev_kept;
     }
     if (!converged) return fail(QM_ERR_NOT_CONVERGED, "qm_davidson: max_iter reached before tol");
     return QM_OK;

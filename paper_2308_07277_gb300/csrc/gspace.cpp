@@ -200,6 +200,7 @@ qm_status gspace_clone(qm_gspace g, qm_gspace* out) {
     if (!c) return fail(QM_ERR_OOM, "gspace clone: host allocation");
     c->ws = Workspace{};
     c->dws = Workspace{};
+    c->prep.assign(c->nk, NlPrep{});  // prepared projectors belong to the origin
     c->aux = nullptr;
     c->ev_fork = c->ev_join = nullptr;
     c->shared_tables = true;
@@ -419,6 +420,8 @@ extern "C" void qm_gspace_destroy(qm_gspace g) {
         }
         if (g->ws.ptr) cudaFree(g->ws.ptr);
         if (g->dws.ptr) cudaFree(g->dws.ptr);
+        for (auto& p : g->prep)
+            if (p.dev) cudaFree(p.dev);
         if (g->ev_fork) cudaEventDestroy(g->ev_fork);
         if (g->ev_join) cudaEventDestroy(g->ev_join);
         if (g->aux) cudaStreamDestroy(g->aux);

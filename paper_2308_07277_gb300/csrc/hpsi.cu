@@ -98,6 +98,10 @@ qm_status qm::hpsi_run(qm_gspace g, int ik, int nb, const void* psi, int ld_psi,
 
     qm_status st = ensure_device(g);
     if (st) return st;
+    if (fp32 && nproj > 0 && !beta_prepared && ik < (int)g->prep.size()) {
+        const NlPrep& p = g->prep[ik];
+        if (p.dev && p.beta == beta && p.ld == ld_beta && p.nproj == nproj) beta_prepared = p.dev;
+    }
 
     const HpsiLayout L = hpsi_layout(g, ik, nb, nproj, fp32, beta_prepared == nullptr);
     if ((st = ensure_workspace(g, L.total, s))) return st;
@@ -134,6 +138,54 @@ qm_status qm::hpsi_run(qm_gspace g, int ik, int nb, const void* psi, int ld_psi,
         st = zgemm_tn(nb, npw, nproj, (const double2*)P, nb, D, (const double2*)beta, ld_beta, (double2*)out, ld_out,
                       true, s);
         if (st) return st;
+    }
+    return QM_OK;
+}
+
+extern "C" qm_status qm_hpsi_prepare(qm_gspace g, int ik, int nproj, const void* beta, int ld_beta, void* stream) {
+    clear_error();
+    if (!g) return fail(QM_ERR_ARG, "qm_hpsi_prepare: NULL gspace");
+    if (ik < 0 || ik >= g->nk) return fail(QM_ERR_ARG, "qm_hpsi_prepare: ik out of range");
+    if (nproj < 0) return fail(QM_ERR_ARG, "qm_hpsi_prepare: negative nproj");
+    const int npw = g->k[ik].npw;
+    if (nproj > 0) {
+        if (!beta) return fail(QM_ERR_ARG, "qm_hpsi_prepare: NULL beta with nproj > 0");
+        if (ld_beta < npw) return fail(QM_ERR_ARG, "qm_hpsi_prepare: ld_beta < npw");
+        if ((uintptr_t)beta % 8) return fail(QM_ERR_ARG, "qm_hpsi_prepare: beta not 8-byte aligned");
+    }
+    qm_status st = ensure_device(g);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((int)g->prep.size() < g->nk) g->prep.resize(g->nk);
+    NlPrep& p = g->prep[ik];
+    if (nproj == 0) {  // release
+        if (p.dev) {
+            if ((st = cuda_check(cudaStreamSynchronize(s), "qm_hpsi_prepare: sync"))) return st;
+            cudaFree(p.dev);
+        }
+        p = NlPrep{};
+        return QM_OK;
+    }
+    const size_t bytes = nonlocal_tc_beta_bytes(nproj, 1, npw);
+    if (!p.dev || p.bytes < bytes) {
+        if (p.dev) {
+            if ((st = cuda_check(cudaStreamSynchronize(s), "qm_hpsi_prepare: sync"))) return st;
+            cudaFree(p.dev);
+            p = NlPrep{};
+        }
+        if (cudaMalloc(&p.dev, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            p = NlPrep{};
+            return fail(QM_ERR_OOM, "qm_hpsi_prepare: device allocation of the prepared projectors");
+        }
+        p.bytes = bytes;
+    }
+    p.beta = beta;
+    p.ld = ld_beta;
+    p.nproj = nproj;
+    if ((st = nonlocal_tc_prepare(nproj, 1, npw, (const float2*)beta, ld_beta, p.dev, s))) {
+        p.beta = nullptr;  // a failed preparation is never used
+        return st;
     }
     return QM_OK;
 }

@@ -46,6 +46,16 @@ struct Workspace {
     size_t bytes = 0;
 };
 
+// Projectors of one k-point prepared for the precision form's tensor-core nonlocal part
+// (qm_hpsi_prepare): the BF16 planes of beta in both GEMM layouts, for calls that pass the same
+// (beta, ld, nproj).
+struct NlPrep {
+    const void* beta = nullptr;
+    int ld = 0, nproj = 0;
+    void* dev = nullptr;
+    size_t bytes = 0;
+};
+
 }  // namespace qm
 
 struct qm_gspace_s {
@@ -68,6 +78,7 @@ struct qm_gspace_s {
     int* rev[3] = {nullptr, nullptr, nullptr};
     std::vector<double2> h_tw[3];
     std::vector<int> h_rev[3];
+    std::vector<qm::NlPrep> prep;  // per k-point prepared projectors (qm_hpsi_prepare)
     qm::Workspace ws;    // qm_hpsi workspace
     qm::Workspace dws;   // qm_davidson workspace
     // second stream of qm_hpsi(QM_MIXED): the tensor-core nonlocal part runs on it while the

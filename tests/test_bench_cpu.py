@@ -11,15 +11,22 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def test_reference_arm_prints_one_json_line():
-    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                        "--warmup", "0", "--cpu-sample-bands", "8"], capture_output=True, text=True, timeout=600)
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "2",
+                        "--warmup", "0", "--cpu-sample-bands", "1"], capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr
     lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == "band-applies/s"
-    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    import bench
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == bench.host_cores()
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["higher_is_better"] is True
+    # ms_per_step is the measured mean step of what ran: bands per step / value
+    bands = d["config"]["sample_bands_per_step"]
+    assert abs(d["ms_per_step"] - 1e3 * bands / d["value"]) <= 1e-6 * d["ms_per_step"]
+    assert d["config"]["workload"] == bench.WORKLOAD
 
 
 def _worker(rank, world, port, q):

@@ -231,3 +231,28 @@ def test_hpsi_mixed_full_size_sampled_bands(Q, cell, ik):
         assert rel.max() <= TOL_MIXED
     finally:
         Q.qm_gspace_destroy(g)
+
+
+@pytest.mark.parametrize("cellf,ik,nb", [(S.config1, 0, None), (S.config2, 3, 160)], ids=["config1", "config2_k3_full"])
+def test_hpsi_prepared_projectors_identical(Q, cellf, ik, nb):
+    """qm_hpsi_prepare splits the projectors once; qm_hpsi(QM_MIXED) with the prepared beta gives
+    bit-identical results to the call that splits beta itself, and releasing restores the
+    per-call path."""
+    cell = cellf()
+    g = _gspace(Q, cell)
+    try:
+        c = make_case(cell, ik, nb=nb)
+        psi = dev(c["psi"], torch.complex64)
+        beta = dev(c["beta"], torch.complex64)
+        v, D = dev(c["v"]), dev(c["D"])
+        a = Q.qm_hpsi(g, ik, psi, v, beta, D, prec="mixed").clone()
+        Q.qm_hpsi_prepare(g, ik, beta)
+        b = Q.qm_hpsi(g, ik, psi, v, beta, D, prec="mixed").clone()
+        beta2 = beta.clone()                              # another buffer: not the prepared one
+        b2 = Q.qm_hpsi(g, ik, psi, v, beta2, D, prec="mixed").clone()
+        Q.qm_hpsi_prepare(g, ik, None)
+        d = Q.qm_hpsi(g, ik, psi, v, beta, D, prec="mixed").clone()
+        torch.cuda.synchronize()
+        assert torch.equal(a, b) and torch.equal(a, b2) and torch.equal(a, d)
+    finally:
+        Q.qm_gspace_destroy(g)
