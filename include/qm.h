@@ -131,6 +131,14 @@ qm_status qm_hpsi(qm_gspace g, int ik, int nb,
                   qm_precision prec, void* stream);
 
 /*
+ * qm_hpsi_check - synchronise `stream` and read (and clear) the handle's sticky error word:
+ * QM_ERR_TIMEOUT if a bounded device-side wait of a tensor-core kernel launched by an earlier
+ * qm_hpsi(QM_MIXED) or qm_precond_apply call on this handle expired since the last check (the
+ * outputs of such a call are undefined), else QM_OK.  qm_davidson checks it itself.
+ */
+qm_status qm_hpsi_check(qm_gspace g, void* stream);
+
+/*
  * qm_hpsi_prepare - prepare the projectors of k-point ik for the precision form: the
  * Hamiltonian's projectors are fixed for a k-point (Sec. 2.3, KB form; Sec. 5, the KSHam of a
  * k-point holds them across all its H psi calls), so their 3-term BF16 split into the two
@@ -270,6 +278,15 @@ qm_status qm_batch_run(qm_batch b, void* stream);
 /* qm_batch_check - synchronise `stream` and read the batch's device error word:
  * QM_ERR_TIMEOUT if a bounded device-side wait of the last replay expired, else QM_OK. */
 qm_status qm_batch_check(qm_batch b, void* stream);
+
+/* qm_batch_hold - failure-detection test hook of the bounded waits (not part of the method).
+ * job >= 0: from the next replay on, the last-phase work items of that job wait for one more
+ * completion than will ever arrive, so their bounded waits expire, the launch gives up and
+ * qm_batch_check reports QM_ERR_TIMEOUT (the outputs of that replay are undefined); job = -1
+ * restores normal replays.  spin_limit: polls per bounded wait (0 = the library default of
+ * 2^24); a small value makes the expiry quick.  Synchronises the device.  Errors: QM_ERR_ARG,
+ * QM_ERR_CUDA. */
+qm_status qm_batch_hold(qm_batch b, int job, long long spin_limit);
 
 /* qm_batch_query - shape, sizes and tuning result of a batch. */
 qm_status qm_batch_query(qm_batch b, qm_batch_info* info);

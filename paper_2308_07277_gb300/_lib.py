@@ -77,6 +77,7 @@ SIGNATURES["qm_davidson"] = (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctype
                                             ctypes.POINTER(DavidsonStats), ctypes.c_void_p])
 
 SIGNATURES["qm_hpsi_noalloc"] = SIGNATURES["qm_hpsi"]
+SIGNATURES["qm_hpsi_check"] = (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p])
 SIGNATURES["qm_hpsi_prepare"] = (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
                                                 ctypes.c_void_p])
 
@@ -116,6 +117,7 @@ SIGNATURES["qm_batch_create"] = (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(Hps
                                                 ctypes.POINTER(ctypes.c_void_p)])
 SIGNATURES["qm_batch_run"] = (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p])
 SIGNATURES["qm_batch_check"] = (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p])
+SIGNATURES["qm_batch_hold"] = (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong])
 SIGNATURES["qm_batch_query"] = (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(BatchInfo)])
 SIGNATURES["qm_batch_destroy"] = (None, [ctypes.c_void_p])
 

@@ -293,6 +293,11 @@ class Batch:
     def check(self, stream=None):
         _check(_lib.load().qm_batch_check(self.handle, _stream_ptr(stream)))
 
+    def hold(self, job, spin_limit=0):
+        """Failure-detection test hook (qm_batch_hold): job >= 0 withholds one completion from
+        that job's last phase so the bounded waits expire; job = -1 restores."""
+        _check(_lib.load().qm_batch_hold(self.handle, int(job), int(spin_limit)))
+
     def info(self):
         inf = _lib.BatchInfo()
         _check(_lib.load().qm_batch_query(self.handle, ctypes.byref(inf)))

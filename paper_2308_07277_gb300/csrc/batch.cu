@@ -29,6 +29,7 @@ struct qm_batch_s {
     long long band_applies = 0;
     void* dmem = nullptr;
     int* err = nullptr;
+    BatchCtl* ctl = nullptr;  // device controls of the bounded waits
     cudaGraphExec_t exec = nullptr;
     cudaStream_t cap = nullptr;
 };
@@ -144,6 +145,7 @@ qm_status build(qm_batch b, int ctas, int points, size_t group_bytes, bool* infe
 
     // device layout
     Region R;
+    const size_t o_ctl = R.take(sizeof(BatchCtl));
     const size_t o_jobs = R.take(sizeof(BatchJobDev) * nj);
     const size_t o_cells = R.take(sizeof(BatchCellDev) * nc);
     std::vector<int4> items;
@@ -259,6 +261,10 @@ qm_status build(qm_batch b, int ctas, int points, size_t group_bytes, bool* infe
         for (int a = 0; a < 3; ++a) Cl[c].rev[a] = g->rev[a];
         Cl[c].scale = 1.0 / ((double)g->n[0] * g->n[1] * g->n[2]);
     }
+    {
+        const BatchCtl ctl{kBatchSpinLimit, -1, 0};
+        std::memcpy(img.data() + o_ctl, &ctl, sizeof(ctl));
+    }
     std::memcpy(img.data() + o_jobs, J.data(), sizeof(BatchJobDev) * nj);
     std::memcpy(img.data() + o_cells, Cl.data(), sizeof(BatchCellDev) * nc);
     std::memcpy(img.data() + o_items, items.data(), sizeof(int4) * items.size());
@@ -271,6 +277,7 @@ qm_status build(qm_batch b, int ctas, int points, size_t group_bytes, bool* infe
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device);
     BatchLaunch L{};
+    L.ctl = (const BatchCtl*)(base + o_ctl);
     L.jobs = (const BatchJobDev*)(base + o_jobs);
     L.cells = (const BatchCellDev*)(base + o_cells);
     L.items = (const int4*)(base + o_items);
@@ -308,6 +315,7 @@ qm_status build(qm_batch b, int ctas, int points, size_t group_bytes, bool* infe
     b->dmem = dmem;
     b->exec = exec;
     b->err = L.err;
+    b->ctl = (BatchCtl*)(base + o_ctl);
     b->ctas = ctas;
     b->points = points;
     b->group_mb = group_bytes ? (int)(group_bytes >> 20) : -1;
@@ -493,6 +501,17 @@ extern "C" qm_status qm_batch_check(qm_batch b, void* stream) {
     clear_error();
     if (!b || !b->exec) return fail(QM_ERR_ARG, "qm_batch_check: invalid batch");
     return read_err(b, (cudaStream_t)stream);
+}
+
+extern "C" qm_status qm_batch_hold(qm_batch b, int job, long long spin_limit) {
+    clear_error();
+    if (!b || !b->exec || !b->ctl) return fail(QM_ERR_ARG, "qm_batch_hold: invalid batch");
+    if (job < -1 || job >= (int)b->jobs.size()) return fail(QM_ERR_ARG, "qm_batch_hold: job out of range");
+    if (spin_limit < 0) return fail(QM_ERR_ARG, "qm_batch_hold: negative spin_limit");
+    const BatchCtl ctl{spin_limit > 0 ? spin_limit : kBatchSpinLimit, job, job >= 0 ? 1 : 0};
+    qm_status st = cuda_check(cudaDeviceSynchronize(), "qm_batch_hold: synchronize");
+    if (st) return st;
+    return cuda_check(cudaMemcpy(b->ctl, &ctl, sizeof(ctl), cudaMemcpyHostToDevice), "qm_batch_hold: upload");
 }
 
 extern "C" qm_status qm_batch_query(qm_batch b, qm_batch_info* info) {

@@ -74,7 +74,18 @@ struct BatchCellDev {
     double scale;
 };
 
+// Host-written controls of the bounded waits (device memory, read at every item, so that the
+// captured graph need not change): the poll limit of every wait, and a failure-detection test
+// hook that makes the last-phase (K3) items of one job wait for one completion more than will
+// ever arrive.
+struct BatchCtl {
+    long long spin_limit;  // polls per bounded wait
+    int hold_job;          // job whose K3 waits need hold_extra more plane items (-1: none)
+    int hold_extra;
+};
+
 struct BatchLaunch {
+    const BatchCtl* ctl;
     const BatchJobDev* jobs;
     const BatchCellDev* cells;
     const int4* items;
@@ -99,8 +110,8 @@ __device__ __forceinline__ int ld_relaxed_gpu(const int* p) {
 }
 
 // bounded wait for *p >= target; false on expiry (sets *err) or when *err is already set
-__device__ __forceinline__ bool batch_wait(const int* p, int target, int* err) {
-    for (long long it = 0; it < kBatchSpinLimit; ++it) {
+__device__ __forceinline__ bool batch_wait(const int* p, int target, int* err, long long limit) {
+    for (long long it = 0; it < limit; ++it) {
         if (ld_acquire_gpu(p) >= target) return true;
         if (ld_relaxed_gpu(err)) return false;
         __nanosleep(64);
@@ -416,8 +427,8 @@ __device__ void bk_nla(const BatchJobDev& J, int tile, unsigned char* sm, int ti
 // ---------------------------------------------------------------- the persistent kernel
 template <class R>
 __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 3 : 2)  // FP32: 3 CTAs per SM, FP64: 2
-k_batch(const BatchJobDev* __restrict__ jobs, const BatchCellDev* __restrict__ cells, const int4* __restrict__ items,
-        int nitems, int* cnt, int* cell_cnt, int* head, int* err) {
+k_batch(const BatchCtl* __restrict__ ctl, const BatchJobDev* __restrict__ jobs, const BatchCellDev* __restrict__ cells,
+        const int4* __restrict__ items, int nitems, int* cnt, int* cell_cnt, int* head, int* err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(16) BatchJobDev J;
     __shared__ int s_item, s_next, s_go;
@@ -439,16 +450,21 @@ k_batch(const BatchJobDev* __restrict__ jobs, const BatchCellDev* __restrict__ c
         if (tid == 0) {
             bool go = true;
             const int* c = cnt + (size_t)w.y * kBatchCounters;
+            const long long lim = ctl->spin_limit;
             switch (w.x) {
-                case BK_NLR: go = batch_wait(c + BC_NLP, jobs[w.y].nchunk * jobs[w.y].nbblk, err); break;
+                case BK_NLR: go = batch_wait(c + BC_NLP, jobs[w.y].nchunk * jobs[w.y].nbblk, err, lim); break;
                 case BK_K2: {
                     const int cell = jobs[w.y].cell;
-                    go = batch_wait(c + BC_K1, jobs[w.y].nk1, err) &&
-                         batch_wait(cell_cnt + cell, cells[cell].nchunk, err);
+                    go = batch_wait(c + BC_K1, jobs[w.y].nk1, err, lim) &&
+                         batch_wait(cell_cnt + cell, cells[cell].nchunk, err, lim);
                     break;
                 }
-                case BK_K3: go = batch_wait(c + BC_K2, jobs[w.y].nk2, err); break;
-                case BK_NLA: go = batch_wait(c + BC_K3, jobs[w.y].nk1, err) && batch_wait(c + BC_NLR, 1, err); break;
+                case BK_K3:
+                    go = batch_wait(c + BC_K2, jobs[w.y].nk2 + (w.y == ctl->hold_job ? ctl->hold_extra : 0), err, lim);
+                    break;
+                case BK_NLA:
+                    go = batch_wait(c + BC_K3, jobs[w.y].nk1, err, lim) && batch_wait(c + BC_NLR, 1, err, lim);
+                    break;
                 default: break;
             }
             if (go) __threadfence();
@@ -493,7 +509,7 @@ k_batch(const BatchJobDev* __restrict__ jobs, const BatchCellDev* __restrict__ c
 // maximum (the attribute is per function, and graphs of several batches hold different sizes).
 template <class R>
 qm_status batch_launch_impl(const BatchLaunch& L, cudaStream_t s) {
-    k_batch<R><<<L.grid, kThreads, L.smem, s>>>(L.jobs, L.cells, L.items, L.nitems, L.cnt, L.cell_cnt, L.head,
+    k_batch<R><<<L.grid, kThreads, L.smem, s>>>(L.ctl, L.jobs, L.cells, L.items, L.nitems, L.cnt, L.cell_cnt, L.head,
                                                  L.err);
     return cuda_check(cudaGetLastError(), "batched H psi launch");
 }

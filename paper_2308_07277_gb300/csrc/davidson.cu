@@ -178,7 +178,7 @@ __global__ void k_convert_rows(const S* __restrict__ in, int ldi, D* __restrict_
     }
 }
 
-inline int grid_for(long n) { return (int)std::max<long>(1, std::min<long>((n + 255) / 256, 152 * 8)); }
+inline int grid_for(long n) { return grid_stride_blocks((size_t)std::max<long>(n, 1), 256, 8); }
 
 template <class D, class S>
 qm_status convert_rows(const S* in, int ldi, D* out, int ldo, int rows, int cols, cudaStream_t s) {
@@ -766,6 +766,7 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
         if ((st = cuda_check(cudaMemcpy(&e, run.tc_err, sizeof(int), cudaMemcpyDeviceToHost), "D2H error word")))
             return st;
         if (e) return fail(QM_ERR_TIMEOUT, "qm_davidson: a bounded tensor-core wait of a subspace product expired");
+        if ((st = qm_hpsi_check(g, stream))) return st;  // the tensor-core nonlocal part of its H psi
     }
     if (stats) {
         stats->iterations = it > o.max_iter ? o.max_iter : it;
@@ -910,16 +911,9 @@ extern "C" qm_status qm_precond_apply(qm_gspace g, int ik, int n, const void* X,
         k_tpa<<<dim3(std::min(64, (npw + 255) / 256), n), 256, 0, s>>>(r, ld, npw, nullptr, tkin, kin, d, ld);
         return cuda_check(cudaGetLastError(), "k_tpa launch");
     }
-    // the network's bounded tensor-core waits report through a device word in the workspace
-    if ((st = ensure_workspace(g, 256, s))) return st;
-    int* err = (int*)g->ws.ptr;
-    if ((st = cuda_check(cudaMemsetAsync(err, 0, sizeof(int), s), "reset error word")) ||
-        (st = mlp_precond_apply(mlp, r, ld, npw, nullptr, n, tkin, eps, rnorm2, kin, d, ld, err, s)))
+    // the network's bounded tensor-core waits report through the handle's sticky error word
+    if ((st = ensure_workspace(g, kWsHeader, s))) return st;
+    if ((st = mlp_precond_apply(mlp, r, ld, npw, nullptr, n, tkin, eps, rnorm2, kin, d, ld, (int*)g->ws.ptr, s)))
         return st;
-    int e = 0;
-    if ((st = cuda_check(cudaMemcpyAsync(&e, err, sizeof(int), cudaMemcpyDeviceToHost, s), "D2H error word")) ||
-        (st = cuda_check(cudaStreamSynchronize(s), "stream sync")))
-        return st;
-    if (e) return fail(QM_ERR_TIMEOUT, "qm_precond_apply: a bounded tensor-core wait of the network expired");
-    return QM_OK;
+    return qm_hpsi_check(g, stream);
 }

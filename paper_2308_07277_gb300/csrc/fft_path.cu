@@ -21,7 +21,7 @@ size_t stick_buffer_bytes_per_band(qm_gspace g, int ik, bool fp32) {
 qm_status launch_vt_prepare(qm_gspace g, const double* vloc, void* vt, bool fp32, cudaStream_t s) {
     const size_t nr = (size_t)g->n[0] * g->n[1] * g->n[2];
     const double scale = 1.0 / (double)nr;
-    int blocks = (int)std::min<size_t>((nr + 255) / 256, 152 * 8);
+    const int blocks = grid_stride_blocks(nr, 256, 8);
     ProfScope ps(PF_VT, s);
     if (fp32)
         k_vt<float><<<blocks, 256, 0, s>>>(vloc, (float*)vt, g->n[0], g->n[1], g->n[2], g->rev[0], g->rev[1], g->rev[2], scale);
@@ -47,7 +47,7 @@ qm_status launch_local_kinetic(qm_gspace g, int ik, int nb, const void* psi, int
 qm_status launch_vt_prepare_tab(const DevTables& t, const double* vloc, void* vt, bool fp32, cudaStream_t s) {
     const size_t nr = (size_t)t.n[0] * t.n[1] * t.n[2];
     const double scale = 1.0 / (double)nr;
-    int blocks = (int)std::min<size_t>((nr + 255) / 256, 152 * 8);
+    const int blocks = grid_stride_blocks(nr, 256, 8);
     ProfScope ps(PF_VT, s);
     if (fp32)
         k_vt<float><<<blocks, 256, 0, s>>>(vloc, (float*)vt, t.n[0], t.n[1], t.n[2], t.rev[0], t.rev[1], t.rev[2], scale);

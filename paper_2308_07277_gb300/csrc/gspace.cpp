@@ -35,18 +35,25 @@ qm_status cuda_check(cudaError_t e, const char* what) {
                 std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+// Grow-only workspace.  Its first kWsHeader bytes are a header that survives regrowth (the
+// handle's sticky device error word lives there, see qm_hpsi_check); a new workspace starts
+// with a zero header.
 static qm_status grow(Workspace& ws, size_t bytes, cudaStream_t stream) {
+    bytes = std::max(bytes, kWsHeader);
     if (ws.bytes >= bytes) return QM_OK;
-    if (ws.ptr) {
-        qm_status st = cuda_check(cudaStreamSynchronize(stream), "workspace sync");
-        if (st) return st;
-        cudaFree(ws.ptr);
-        ws.ptr = nullptr;
-        ws.bytes = 0;
-    }
     size_t want = align_up(bytes + bytes / 8, 1 << 20);
-    qm_status st = cuda_check(cudaMalloc(&ws.ptr, want), "workspace cudaMalloc");
-    if (st) return st;
+    void* fresh = nullptr;
+    qm_status st;
+    if (ws.ptr && (st = cuda_check(cudaStreamSynchronize(stream), "workspace sync"))) return st;
+    if ((st = cuda_check(cudaMalloc(&fresh, want), "workspace cudaMalloc"))) return st;
+    st = ws.ptr ? cuda_check(cudaMemcpy(fresh, ws.ptr, kWsHeader, cudaMemcpyDeviceToDevice), "workspace header")
+                : cuda_check(cudaMemset(fresh, 0, kWsHeader), "workspace header");
+    if (st) {
+        cudaFree(fresh);
+        return st;
+    }
+    if (ws.ptr) cudaFree(ws.ptr);
+    ws.ptr = fresh;
     ws.bytes = want;
     return QM_OK;
 }
@@ -79,6 +86,20 @@ qm_status allow_dynamic_smem(const void* kernel, size_t need, const char* what) 
     if ((long long)need > (long long)max_dyn)
         return fail(QM_ERR_UNSUPPORTED, std::string(what) + ": needs more shared memory than a CTA can have");
     return QM_OK;
+}
+
+int device_sms() {
+    static std::mutex mu;
+    static std::map<int, int> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(dev);
+    if (it != cache.end()) return it->second;
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+    cache[dev] = n;
+    return n;
 }
 
 qm_status ensure_workspace(qm_gspace g, size_t bytes, cudaStream_t stream) { return grow(g->ws, bytes, stream); }

@@ -10,7 +10,7 @@
 // second stream, concurrently with k_vt, K1 and K2 of every band: it writes
 // out = sum_p beta_p D_p P[p][b], and K3 (which waits for it) adds the local and kinetic
 // parts.  The tensor-core kernels (96 KB of shared memory) share SMs with the FFT kernels.
-// Workspace (owned by the gspace handle): Vt | P | split-K partials | stick buffer | nonlocal | err.
+// Workspace (owned by the gspace handle): error word | Vt | P | split-K partials | stick buffer | nonlocal.
 #include <algorithm>
 #include <cstdint>
 
@@ -35,7 +35,8 @@ static HpsiLayout hpsi_layout(qm_gspace g, int ik, int nb, int nproj, bool fp32,
     const size_t nr = (size_t)g->n[0] * g->n[1] * g->n[2];
     const int npw = g->k[ik].npw;
     L.splits = nproj > 0 ? zgemm_cn_splits(nproj, nb, npw) : 1;
-    size_t off = 0;
+    size_t off = kWsHeader;  // the header holds the handle's sticky error word
+    L.err_off = 0;
     L.vt_off = off;
     off = align_up(off + nr * rs, 256);
     L.p_off = off;
@@ -52,8 +53,6 @@ static HpsiLayout hpsi_layout(qm_gspace g, int ik, int nb, int nproj, bool fp32,
     off = align_up(off + L.t_bytes, 256);
     L.nl_off = off;  // tensor-core split operands (precision form)
     off = align_up(off + (fp32 && nproj > 0 ? nonlocal_tc_bytes(nproj, nb, npw, own_beta) : 0), 256);
-    L.err_off = off;
-    off = align_up(off + 256, 256);
     L.total = off;
     return L;
 }
@@ -116,8 +115,7 @@ qm_status qm::hpsi_run(qm_gspace g, int ik, int nb, const void* psi, int ld_psi,
         int* err = (int*)(ws + L.err_off);
         cudaStream_t a = g->aux;
         if ((st = cuda_check(cudaEventRecord(g->ev_fork, s), "fork event")) ||
-            (st = cuda_check(cudaStreamWaitEvent(a, g->ev_fork, 0), "fork wait")) ||
-            (st = cuda_check(cudaMemsetAsync(err, 0, sizeof(int), a), "reset tensor-core error word")))
+            (st = cuda_check(cudaStreamWaitEvent(a, g->ev_fork, 0), "fork wait")))
             return st;
         if ((st = nonlocal_tc(nproj, nb, npw, (const float2*)beta, ld_beta, beta_prepared, (const float2*)psi, ld_psi,
                               D, (float2*)out, ld_out, ws + L.nl_off, err, a, false)))
@@ -188,4 +186,20 @@ extern "C" qm_status qm_hpsi_prepare(qm_gspace g, int ik, int nproj, const void*
         return st;
     }
     return QM_OK;
+}
+
+extern "C" qm_status qm_hpsi_check(qm_gspace g, void* stream) {
+    clear_error();
+    if (!g) return fail(QM_ERR_ARG, "qm_hpsi_check: NULL gspace");
+    if (!g->ws.ptr) return QM_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    int e = 0;
+    qm_status st;
+    if ((st = cuda_check(cudaStreamSynchronize(s), "qm_hpsi_check: sync")) ||
+        (st = cuda_check(cudaMemcpy(&e, g->ws.ptr, sizeof(int), cudaMemcpyDeviceToHost), "qm_hpsi_check: read")))
+        return st;
+    if (!e) return QM_OK;
+    if ((st = cuda_check(cudaMemset(g->ws.ptr, 0, sizeof(int)), "qm_hpsi_check: clear"))) return st;
+    return fail(QM_ERR_TIMEOUT, "a bounded tensor-core wait of an earlier call on this handle expired (its outputs are "
+                                "undefined)");
 }

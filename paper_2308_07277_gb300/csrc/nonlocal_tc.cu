@@ -84,54 +84,50 @@ __device__ __forceinline__ void put8(unsigned char* blk, int R, int nkt, int r, 
 
 // Rows of complex src (K = 2 ncols interleaved reals) -> blocked split operand.  expand = 0:
 // row r is src row r as stored; expand = 1: rows 2b, 2b+1 are src row b as stored and its
-// rotation (im, -re).  Rows >= nrows_out and K beyond 2 ncols are written as zeros; the array
-// covers rows_pad rows and nkt K tiles.  One thread per (row, 8-value chunk), the 8 rows of a
-// core matrix on consecutive threads (one 128-byte run per plane).
-__global__ void k_split_rows(const float2* __restrict__ src, int ld, int nsrc, int ncols, int expand, int rows_pad,
-                             int R, int nkt, unsigned char* __restrict__ blk) {
-    const int nchunk = nkt * (KT / 8);
-    const long total = (long)rows_pad * nchunk;
-    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
-        const int rlo = (int)(e & 7);
-        const long q = e >> 3;
-        const int ch = (int)(q % nchunk);
-        const int r = (int)(q / nchunk) * 8 + rlo;
-        const int b = expand ? (r >> 1) : r;
-        const int rot = expand ? (r & 1) : 0;
-        const int c0 = ch * 4;  // first complex column of the chunk
-        float v[8];
-        if (b < nsrc && c0 + 3 < ncols) {
-            const float4* s = reinterpret_cast<const float4*>(src + (size_t)b * ld + c0);
-            float4 a, bb;
-            if (((uintptr_t)s & 15) == 0) {
-                a = __ldg(s);
-                bb = __ldg(s + 1);
-            } else {
-                const float2* s2 = src + (size_t)b * ld + c0;
-                const float2 x0 = __ldg(s2), x1 = __ldg(s2 + 1), x2 = __ldg(s2 + 2), x3 = __ldg(s2 + 3);
-                a = make_float4(x0.x, x0.y, x1.x, x1.y);
-                bb = make_float4(x2.x, x2.y, x3.x, x3.y);
-            }
+// rotation (im, -re).  Rows >= nsrc (resp. 2 nsrc) and K beyond 2 ncols are written as zeros.
+// CTA: 8 rows (one core-matrix row group, blockIdx.y) x 32 chunks of 8 K values (blockIdx.x);
+// the 8 rows of a core matrix on consecutive threads (one 128-byte run per plane), the 4
+// chunks of a K tile on consecutive thread octets.
+constexpr int kSplitChunks = 32;
+__global__ void __launch_bounds__(256) k_split_rows(const float2* __restrict__ src, int ld, int nsrc, int ncols,
+                                                    int expand, int R, int nkt, unsigned char* __restrict__ blk) {
+    const int r = blockIdx.y * 8 + (threadIdx.x & 7);
+    const int ch = blockIdx.x * kSplitChunks + (threadIdx.x >> 3);
+    if (ch >= nkt * (KT / 8)) return;
+    const int b = expand ? (r >> 1) : r;
+    const int c0 = ch * 4;  // first complex column of the chunk
+    float v[8];
+    if (b < nsrc && c0 + 3 < ncols) {
+        const float2* s2 = src + (size_t)b * ld + c0;
+        if (((uintptr_t)s2 & 15) == 0) {
+            const float4 a = __ldg(reinterpret_cast<const float4*>(s2)), bb = __ldg(reinterpret_cast<const float4*>(s2) + 1);
             v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = bb.x; v[5] = bb.y; v[6] = bb.z; v[7] = bb.w;
         } else {
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                float2 x = make_float2(0.f, 0.f);
-                if (b < nsrc && c0 + j < ncols) x = __ldg(src + (size_t)b * ld + c0 + j);
+                const float2 x = __ldg(s2 + j);
                 v[2 * j] = x.x;
                 v[2 * j + 1] = x.y;
             }
         }
-        if (rot) {
+    } else {
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const float re = v[2 * j], im = v[2 * j + 1];
-                v[2 * j] = im;
-                v[2 * j + 1] = -re;
-            }
+        for (int j = 0; j < 4; ++j) {
+            float2 x = make_float2(0.f, 0.f);
+            if (b < nsrc && c0 + j < ncols) x = __ldg(src + (size_t)b * ld + c0 + j);
+            v[2 * j] = x.x;
+            v[2 * j + 1] = x.y;
         }
-        put8(blk, R, nkt, r, ch * 8, v);
     }
+    if (expand && (r & 1)) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float re = v[2 * j], im = v[2 * j + 1];
+            v[2 * j] = im;
+            v[2 * j + 1] = -re;
+        }
+    }
+    put8(blk, R, nkt, r, ch * 8, v);
 }
 
 // beta [P][G] (complex, ld) -> blocked split betaT: row g, K = (p, u) (u = re/im of beta[p][g]).
@@ -385,14 +381,6 @@ k_nl_gemm(const unsigned char* __restrict__ A, const unsigned char* __restrict__
 
 inline size_t rup(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-int sm_count() {
-    int dev = 0, n = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        n <= 0)
-        n = 148;
-    return n;
-}
-
 // N tile of the projection: the 2 nb columns in the fewest tiles of at most 256, rounded to 16
 int proj_bn(int nb) {
     const int n = 2 * nb;
@@ -419,7 +407,7 @@ NlLayout nl_layout(int nproj, int nb, int npw, bool with_beta) {
     L.ntile_a = (npw + kAppBN - 1) / kAppBN;
     L.nkt_a = (int)(rup(2 * (size_t)nproj, KT) / KT);
     const int tiles = L.ntile_p * L.mtile_p;
-    L.splits = std::max(1, std::min(std::min(kMaxUmmaSplits, L.nkt_p), sm_count() / std::max(1, tiles)));
+    L.splits = std::max(1, std::min(std::min(kMaxUmmaSplits, L.nkt_p), device_sms() / std::max(1, tiles)));
     L.zstride = (size_t)L.mtile_p * TM * L.ntile_p * L.bn_p;
     size_t off = 0;
     auto take = [&](size_t b) {
@@ -436,14 +424,14 @@ NlLayout nl_layout(int nproj, int nb, int npw, bool with_beta) {
     return L;
 }
 
-inline int grid_for(long n, int per = 256) { return (int)std::max<long>(1, std::min<long>((n + per - 1) / per, 152L * 16)); }
+inline int grid_for(long n, int per = 256) { return grid_stride_blocks((size_t)std::max<long>(n, 1), per, 16); }
 
 qm_status split_beta(int nproj, int npw, const float2* beta, int ld_beta, const NlLayout& L, unsigned char* betaK,
                      unsigned char* betaT, cudaStream_t s) {
     {
         ProfScope pf(PF_SPLIT, s);
-        const long n = (long)L.mtile_p * TM * L.nkt_p * (KT / 8);
-        k_split_rows<<<grid_for(n), 256, 0, s>>>(beta, ld_beta, nproj, npw, 0, L.mtile_p * TM, TM, L.nkt_p, betaK);
+        const dim3 grid((unsigned)((L.nkt_p * (KT / 8) + kSplitChunks - 1) / kSplitChunks), (unsigned)(L.mtile_p * TM / 8));
+        k_split_rows<<<grid, 256, 0, s>>>(beta, ld_beta, nproj, npw, 0, TM, L.nkt_p, betaK);
     }
     qm_status st = cuda_check(cudaGetLastError(), "k_split_rows launch");
     if (st) return st;
@@ -512,8 +500,8 @@ qm_status nonlocal_tc(int nproj, int nb, int npw, const float2* beta, int ld_bet
     unsigned char* E = w + L.e_off;
     {
         ProfScope pf(PF_SPLIT, s);
-        const long n = (long)L.ntile_p * L.bn_p * L.nkt_p * (KT / 8);
-        k_split_rows<<<grid_for(n), 256, 0, s>>>(psi, ld_psi, nb, npw, 1, L.ntile_p * L.bn_p, L.bn_p, L.nkt_p, psiX);
+        const dim3 grid((unsigned)((L.nkt_p * (KT / 8) + kSplitChunks - 1) / kSplitChunks), (unsigned)(L.ntile_p * L.bn_p / 8));
+        k_split_rows<<<grid, 256, 0, s>>>(psi, ld_psi, nb, npw, 1, L.bn_p, L.nkt_p, psiX);
     }
     if ((st = cuda_check(cudaGetLastError(), "k_split_rows launch"))) return st;
     // projection C[p][2b + t] = <beta_p | psi_b>, split over K

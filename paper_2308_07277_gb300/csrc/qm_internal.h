@@ -103,11 +103,24 @@ qm_status ensure_device(qm_gspace g);
 // (free with qm_gspace_destroy; destroy it before g)
 qm_status gspace_clone(qm_gspace g, qm_gspace* out);
 
-// grow-only workspace owned by a gspace handle; synchronises `stream` before regrowing
+// grow-only workspace owned by a gspace handle; synchronises `stream` before regrowing.  The
+// first kWsHeader bytes of the qm_hpsi workspace hold the handle's sticky error word (an int
+// set by a tensor-core kernel whose bounded wait expired; read and cleared by qm_hpsi_check).
+constexpr size_t kWsHeader = 256;
 qm_status ensure_workspace(qm_gspace g, size_t bytes, cudaStream_t stream);
 qm_status ensure_dav_workspace(qm_gspace g, size_t bytes, cudaStream_t stream);
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// multiprocessor count of the current device (queried once per device)
+int device_sms();
+// grid for a grid-stride loop over n elements: enough CTAs of `per` threads, at most `waves`
+// CTAs per multiprocessor
+inline int grid_stride_blocks(size_t n, int per, int waves) {
+    const size_t want = (n + per - 1) / per;
+    const size_t cap = (size_t)device_sms() * waves;
+    return (int)(want < 1 ? 1 : (want < cap ? want : cap));
+}
 
 // Allow `kernel` the device's per-CTA opt-in maximum of dynamic shared memory (minus its
 // static shared memory), once per (kernel, device), and check `need` against it.  The
@@ -176,14 +189,10 @@ qm_status zgemm_tn(int M, int N, int K, const double2* A, int lda, const double*
                    const double2* B, int ldb, double2* C, int ldc, bool accumulate,
                    cudaStream_t s, double alpha = 1.0);
 int zgemm_cn_splits(int M, int N, int K);
-// ---- tensor-core nonlocal step of the precision form (umma.cu) ----
+// ---- tensor-core nonlocal step of the precision form (nonlocal_tc.cu) ----
 constexpr int kMaxUmmaSplits = 64;
 // out[b][g] (+)= sum_p beta[p][g] D_p <beta_p|psi_b> (FP32 complex in/out) as BF16x3 split
-// tcgen05 products; work: nonlocal_bf16x3_bytes(); err: device int set on a timed-out wait
-qm_status nonlocal_bf16x3(int nproj, int nb, int npw, const float2* beta, int ld_beta, const float2* psi,
-                          int ld_psi, const double* D, float2* out, int ld_out, void* work, int* err,
-                          cudaStream_t s, bool accumulate = true);
-size_t nonlocal_bf16x3_bytes(int nproj, int nb, int npw);
+// tcgen05 products; err: device int set on a timed-out wait.
 // The same product with operands pre-split into tile-blocked BF16 planes in global memory and
 // streamed by bulk copies through a warp-specialised tcgen05 pipeline (nonlocal_tc.cu).
 // beta_prepared: NULL (beta is split on every call, in `work`) or the output of

@@ -1,6 +1,6 @@
-// Tensor-core (tcgen05) GEMMs of the precision form: the nonlocal projection P = beta^H psi
-// and application beta D P of the Kleinman-Bylander term (Sec. 2.3) as 3-term BF16 split
-// products accumulated in FP32.
+// Tensor-core (tcgen05) subspace products of the precision form's Davidson (the overlaps of
+// Sec. 5's Davidson: H_sub, Gram matrices, basis rotations) as 3-term BF16 split products
+// accumulated in FP32, with operands split on the fly from FP64 storage.
 //
 // Splitting: an FP32 value x is written x = x0 + x1 + x2 with x0 = bf16(x),
 // x1 = bf16(x - x0), x2 = bf16(x - x0 - x1); a product a*b keeps the six terms a_i b_j with
@@ -301,26 +301,6 @@ k_umma_split(LA la, LB lb, int M, int N, int ktiles_per_split, int ktiles_total,
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(UN));
 }
 
-// sum the split-K partials of the projection C'[p][2b + t] and write the application's A
-// operand P'[b][p] = D_p * P[p][b] (FP32 complex, ld nproj)
-__global__ void k_reduce_proj(const float* __restrict__ part, int Z, size_t zstride, int ldc, int nproj, int nb,
-                              const double* __restrict__ D, float2* __restrict__ Pd) {
-    const size_t total = (size_t)nb * nproj;
-    // consecutive threads take consecutive bands: the (re, im) pairs of one partial row are
-    // contiguous, so every load of the split loop is coalesced
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-        const int p = (int)(e / nb), b = (int)(e % nb);
-        float sr = 0.f, si = 0.f;
-        for (int z = 0; z < Z; ++z) {
-            const float2 q = __ldg(reinterpret_cast<const float2*>(part + (size_t)z * zstride + (size_t)p * ldc) + b);
-            sr += q.x;
-            si += q.y;
-        }
-        const float d = (float)D[p];
-        Pd[(size_t)b * nproj + p] = make_float2(d * sr, d * si);
-    }
-}
-
 // sum the split-K partials C'[z][i][2j + t] of a subspace product in FP64 and write the complex
 // result C[i][j] (FP64, row stride ldc)
 __global__ void k_reduce_cn(const float* __restrict__ part, int Z, size_t zstride, int ldp, int M, int N,
@@ -350,7 +330,7 @@ __global__ void k_coef_t(const double2* __restrict__ A, int lda, int M, int K, d
 }
 
 inline size_t rup(size_t x, size_t a) { return (x + a - 1) / a * a; }
-inline int grid_for(size_t n) { return (int)std::max<size_t>(1, std::min<size_t>((n + 255) / 256, 152 * 16)); }
+inline int grid_for(size_t n) { return grid_stride_blocks(std::max<size_t>(n, 1), 256, 16); }
 
 template <class LA, class LB, class Out>
 qm_status umma_launch(const LA& la, const LB& lb, int M, int N, int kreal, int splits, Out* C, size_t ldc,
@@ -372,47 +352,12 @@ qm_status umma_launch(const LA& la, const LB& lb, int M, int N, int kreal, int s
 
 }  // namespace
 
-size_t nonlocal_bf16x3_bytes(int nproj, int nb, int npw) {
-    (void)npw;
-    const size_t rP = rup(nproj, UM), r2B = rup(2 * (size_t)nb, UN);
-    return rup((size_t)kMaxUmmaSplits * rP * r2B * 4, 256) + rup((size_t)nb * nproj * sizeof(float2), 256);
-}
-
-// out[b][g] (+)= sum_p beta[p][g] D_p sum_g' conj(beta[p][g']) psi[b][g']   (FP32 complex in/out)
-qm_status nonlocal_bf16x3(int nproj, int nb, int npw, const float2* beta, int ld_beta, const float2* psi, int ld_psi,
-                          const double* D, float2* out, int ld_out, void* work, int* err, cudaStream_t s,
-                          bool accumulate) {
-    if (nproj <= 0 || nb <= 0) return QM_OK;
-    const size_t rP = rup(nproj, UM), r2B = rup(2 * (size_t)nb, UN);
-    float* part = (float*)work;
-    float2* Pd = (float2*)((char*)work + rup((size_t)kMaxUmmaSplits * rP * r2B * 4, 256));
-    // projection: C'[p][2b + t] = <beta_p | psi_b>, split over K (2 npw real columns)
-    const int tiles = (int)((rP / UM) * (r2B / UN));
-    const int splits = std::max(1, std::min(kMaxUmmaSplits, 2 * 152 / std::max(1, tiles)));  // 2 CTAs per SM
-    const size_t zstride = rP * r2B;
-    PlainRows<float2> la{beta, ld_beta, nproj, npw};
-    ExpandRows<float2> lb{psi, ld_psi, nb, npw, 1};
-    int Z = 1;
-    qm_status st = umma_launch(la, lb, nproj, 2 * nb, 2 * npw, splits, part, r2B, zstride, false, err, s, &Z);
-    if (st) return st;
-    {
-        ProfScope pf(PF_SPLIT, s);
-        k_reduce_proj<<<grid_for((size_t)nb * nproj), 256, 0, s>>>(part, Z, zstride, (int)r2B, nproj, nb, D, Pd);
-    }
-    if ((st = cuda_check(cudaGetLastError(), "k_reduce_proj launch"))) return st;
-    // application: out'[b][2g + t] += sum_p (D P)[b][p] beta[p][g]
-    PlainRows<float2> la2{Pd, nproj, nb, nproj};
-    ExpandTRows<float2> lb2{beta, ld_beta, nproj, npw};
-    return umma_launch(la2, lb2, nb, 2 * npw, 2 * nproj, 1, (float*)out, 2 * (size_t)ld_out, 0, accumulate, err, s,
-                       nullptr);
-}
-
 // ---- subspace products of the Davidson FP32 phase (FP64 storage, BF16x3 tensor-core products) ----
 
 size_t subspace_bf16x3_bytes(int max_m, int max_n) {
-    // the cn split-K partials: splits x tiles <= 2 x 152 + tiles (see zgemm_cn_bf16x3)
+    // the cn split-K partials: splits x tiles <= 2 x SMs + tiles (see zgemm_cn_bf16x3)
     const size_t tiles = (rup((size_t)max_m, UM) / UM) * (rup(2 * (size_t)max_n, UN) / UN);
-    const size_t part = rup((2 * 152 + tiles) * UM * UN * sizeof(float), 256);
+    const size_t part = rup((2 * (size_t)device_sms() + tiles) * UM * UN * sizeof(float), 256);
     // the tn coefficient operand: M x K FP32 complex.  Calls on one stream reuse the buffer.
     const size_t coef = rup((size_t)max_m * max_m * sizeof(float2), 256);
     return std::max(part, coef);
@@ -426,7 +371,7 @@ qm_status zgemm_cn_bf16x3(int M, int N, int K, const double2* A, int lda, const 
     const size_t zstride = rM * r2N;
     const int cap = (int)std::min<size_t>(kMaxUmmaSplits, work_bytes / (zstride * sizeof(float)));
     if (cap < 1) return fail(QM_ERR_ARG, "zgemm_cn_bf16x3: workspace too small");
-    const int splits = std::max(1, std::min(cap, (2 * 152 + tiles - 1) / tiles));  // 2 CTAs per SM
+    const int splits = std::max(1, std::min(cap, (2 * device_sms() + tiles - 1) / tiles));  // 2 CTAs per SM
     PlainRows<double2> la{A, lda, M, K};
     ExpandRows<double2> lb{B, ldb, N, K, 1};
     int Z = 1;

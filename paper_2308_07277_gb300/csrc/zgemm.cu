@@ -287,7 +287,7 @@ qm_status cn_launch(int M, int N, int K, const C* A, int lda, const C* B, int ld
             k_gemm_cn<C, W, TM, TN><<<grid, NTH, 0, s>>>(M, N, K, A, lda, B, ldb, partial, N, kchunk);
         }
         size_t total = (size_t)M * N;
-        int blocks = (int)std::min<size_t>((total + 255) / 256, 152 * 8);
+        const int blocks = grid_stride_blocks(total, 256, 8);
         ProfScope pf(PF_REDUCE, s);
         k_reduce_splits<C><<<blocks, 256, 0, s>>>(M, N, partial, splits, Cm, ldc);
     }

@@ -166,3 +166,24 @@ def test_precond_apply_errors_before_device_work():
         assert lib.qm_precond_apply(None, 0, 1, f, f, npw, f, 0, None, f, f, f, f, None) == 1
     finally:
         Q.qm_gspace_destroy(g)
+
+
+def test_prepare_check_hold_argument_errors():
+    """qm_hpsi_prepare, qm_hpsi_check and qm_batch_hold reject bad arguments with QM_ERR_ARG
+    before any device work."""
+    import ctypes
+    import paper_2308_07277_gb300 as Q
+    lib = _lib()
+    g = Q.qm_gspace_create(np.eye(3) * 10.0, [[0, 0, 0]], 5.0)
+    try:
+        npw = Q.qm_gspace_query(g)["npw"][0]
+        f = ctypes.c_void_p(1 << 20)
+        for args, msg in [((g, 1, 4, f, npw, None), "ik"), ((g, 0, -1, f, npw, None), "negative"),
+                          ((g, 0, 4, None, npw, None), "NULL beta"), ((g, 0, 4, f, npw - 1, None), "ld_beta"),
+                          ((None, 0, 4, f, npw, None), "NULL gspace")]:
+            assert lib.qm_hpsi_prepare(*args) == 1 and msg in Q.qm_last_error(), (args, Q.qm_last_error())
+        assert lib.qm_hpsi_check(None, None) == 1
+        assert lib.qm_hpsi_check(g, None) == 0           # no workspace yet: nothing to report
+    finally:
+        Q.qm_gspace_destroy(g)
+    assert lib.qm_batch_hold(None, 0, 0) == 1

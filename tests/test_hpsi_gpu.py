@@ -1,9 +1,13 @@
 """Parity of the CUDA H-psi (qm_hpsi through the C ABI) with the FP64 oracle.
 
 Tolerance: FP64 path, per band ||Hpsi_gpu - Hpsi_oracle|| / ||Hpsi_oracle|| <= 1e-11 and
-element-wise |diff| <= 1e-11 * max|Hpsi_oracle(band)|.  The mixed path (FP32 FFTs and
-GEMMs) is held to 2e-5 relative per band: FP32 round-off (2^-24 = 6e-8) grown by
-log2(N_r) ~ 20 FFT stages and by sqrt(npw) ~ 1.4e2 in the FP32 projector sums.
+element-wise |diff| <= 1e-11 * max|Hpsi_oracle(band)|.  The mixed path (FP32 FFTs, BF16x3
+tensor-core GEMMs accumulated in FP32) is held per band and element-wise: FP32 round-off
+(2^-24 = 6e-8) grows by ~log2(N_r) ~ 20 FFT stages and by sqrt(K) in the FP32 sums of the
+projections over K = 2 npw terms.  Measured maxima: per band 5e-8 .. 3e-7 and element-wise
+(relative to the band's largest element) 8e-8 .. 1.3e-6 on the cells up to 72^3 and 18k plane
+waves; 3.5e-6 / 2.4e-5 and 5.5e-6 / 2.4e-5 on the 255- and 216-atom cells (96k and 44k plane
+waves).  Bars: 1e-6 per band and 5e-6 element-wise up to 72^3, 1e-5 and 5e-5 beyond.
 """
 import numpy as np
 import pytest
@@ -17,7 +21,19 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TOL64 = 1e-11
-TOL_MIXED = 2e-5
+TOL_MIXED = 1e-6          # per band, cells up to 72^3
+TOL_MIXED_ELEM = 5e-6     # element-wise, relative to the band's largest element
+TOL_MIXED_LARGE = 1e-5    # per band, the 216- and 255-atom cells
+TOL_MIXED_LARGE_ELEM = 5e-5
+
+
+def check_mixed(got, want, large=False):
+    rel = band_rel_err(got, want)
+    scale = np.abs(want).max(axis=1, keepdims=True)
+    el = (np.abs(got - want) / scale).max()
+    tb, te = (TOL_MIXED_LARGE, TOL_MIXED_LARGE_ELEM) if large else (TOL_MIXED, TOL_MIXED_ELEM)
+    assert rel.max() <= tb and el <= te, (rel.max(), el)
+    return rel.max(), el
 
 
 @pytest.fixture(scope="module")
@@ -163,9 +179,8 @@ def test_hpsi_mixed_precision_error(Q, cell, ik, nb):
         c = make_case(cell, ik, nb=nb)
         want = OH.hpsi_fft(c["psi"], c["gs"], c["v"], c["beta"], c["D"])
         got = gpu_hpsi(Q, g, ik, c, prec="mixed")
-        rel = band_rel_err(got, want)
-        print(f"mixed H-psi max per-band relative error {rel.max():.3e}")
-        assert rel.max() <= TOL_MIXED
+        rel, el = check_mixed(got, want)
+        print(f"mixed H-psi max per-band relative error {rel:.3e}, element-wise {el:.3e}")
     finally:
         Q.qm_gspace_destroy(g)
 
@@ -193,7 +208,7 @@ def test_hpsi_mixed_small_cells(Q, cell):
     try:
         c = make_case(cell, 0)
         want = OH.hpsi_fft(c["psi"], c["gs"], c["v"], c["beta"], c["D"])
-        assert band_rel_err(gpu_hpsi(Q, g, 0, c, prec="mixed"), want).max() <= TOL_MIXED
+        check_mixed(gpu_hpsi(Q, g, 0, c, prec="mixed"), want)
     finally:
         Q.qm_gspace_destroy(g)
 
@@ -205,11 +220,11 @@ def test_hpsi_mixed_padded_rows_local_only_and_repeatable(Q):
         c = make_case(cell, 0)
         want = OH.hpsi_fft(c["psi"], c["gs"], c["v"], c["beta"], c["D"])
         a = gpu_hpsi(Q, g, 0, c, prec="mixed", ld_pad=5)
-        assert band_rel_err(a, want).max() <= TOL_MIXED
+        check_mixed(a, want)
         b = gpu_hpsi(Q, g, 0, c, prec="mixed", ld_pad=5)
         np.testing.assert_array_equal(a, b)             # the two streams give a fixed result
         want_loc = OH.hpsi_fft(c["psi"], c["gs"], c["v"], None, None)
-        assert band_rel_err(gpu_hpsi(Q, g, 0, c, prec="mixed", with_nl=False, ld_pad=3), want_loc).max() <= TOL_MIXED
+        check_mixed(gpu_hpsi(Q, g, 0, c, prec="mixed", with_nl=False, ld_pad=3), want_loc)
     finally:
         Q.qm_gspace_destroy(g)
 
@@ -226,9 +241,8 @@ def test_hpsi_mixed_full_size_sampled_bands(Q, cell, ik):
         nb = cell.nbnd
         sample = sorted({0, 1, nb // 2, nb - 2, nb - 1})
         want = OH.hpsi_fft(c["psi"][sample], c["gs"], c["v"], c["beta"], c["D"])
-        rel = band_rel_err(got[sample], want)
-        print(f"{cell.name} k{ik}: mixed max sampled band rel err {rel.max():.2e}")
-        assert rel.max() <= TOL_MIXED
+        rel, el = check_mixed(got[sample], want, large=cell.nat > 64)
+        print(f"{cell.name} k{ik}: mixed max sampled band rel err {rel:.2e}, element-wise {el:.2e}")
     finally:
         Q.qm_gspace_destroy(g)
 
