@@ -160,7 +160,7 @@ qm_status qm_hpsi_check(qm_gspace g, void* stream);
 qm_status qm_hpsi_prepare(qm_gspace g, int ik, int nproj, const void* beta, int ld_beta, void* stream);
 
 /*
- * qm_hpsi_noalloc - the same H psi as qm_hpsi, for callers that cannot allocate device
+ * qm_hpsi_noalloc - the H psi operator of qm_hpsi for callers that cannot allocate device
  * memory.  The paper has no counterpart: this is a deployment variant of qm_hpsi.
  *
  * Who needs it: code running under an allocator that owns the whole device heap (for
@@ -169,19 +169,29 @@ qm_status qm_hpsi_prepare(qm_gspace g, int ik, int nproj, const void* beta, int 
  * device or could fail for lack of free memory.  This call allocates nothing: it calls
  * no cudaMalloc, cudaFree or other allocating routine, not even on first use of a handle.
  * The caller still passes every input and output (same arguments and meaning as qm_hpsi).
- * All scratch - a copy of the k-point's gspace tables, V(r) in the FFT layout, the
- * projections, the split-K partial sums and the FFT stick buffer - lives in one fixed
+ * All scratch - V(r) in the FFT layout, the projections, the split-K partial sums, the FFT
+ * stick buffer and, when needed, a copy of the k-point's gspace tables - lives in one fixed
  * device array of QM_HPSI_NOALLOC_SCRATCH_BYTES inside the library; every GPU that loads
  * the library holds it until the process exits (the driver makes it resident when the
  * library's device code and data are loaded on that GPU, which with CUDA's lazy loading
  * can be the first call of this entry point).
  *
- *  - The first call on each device looks up the array's device address once; make that
- *    first call before any CUDA stream capture.
+ *  - Every call looks up the array's device address (cudaGetSymbolAddress); the first call
+ *    on a device may load the library's device code there, so make that first call before
+ *    any CUDA stream capture.
  *  - Every call shares the one array and leaves its contents behind.  Calls whose GPU work
  *    overlaps (different streams, or different threads without ordering) race on it:
  *    issue them on one stream.  No scratch byte needs to start at zero; each call writes
  *    everything it reads.
+ *  - The k-point's FFT tables: when the handle already holds them on the device (any earlier
+ *    qm_hpsi, qm_hpsi_prepare or qm_davidson call with the handle uploaded them), they are
+ *    read in place and the call only queues work on `stream`.  Otherwise every call copies
+ *    them from the handle's host copies into the array; that source is pageable host memory,
+ *    so the host waits until the stream's earlier work is done before each copy.
+ *  - Numerics: QM_FP64 is the FP64 path of qm_hpsi.  QM_MIXED runs the FP32 FFT path of
+ *    qm_hpsi but its nonlocal projection and application as FP32 SIMT products (qm_hpsi uses
+ *    BF16x3 tensor-core products, whose operand planes would need scratch of their own); both
+ *    are FP32-accurate (measured against the FP64 oracle: about 1e-7 per band on small cells).
  *  - A problem whose scratch exceeds the array is rejected with QM_ERR_ARG and a message
  *    giving the bytes it needs (tables + N1*N2*N3 reals + nproj*nb complex + one band of
  *    the stick buffer); use qm_hpsi for those.

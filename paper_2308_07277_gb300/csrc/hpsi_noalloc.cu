@@ -10,19 +10,27 @@
 // until the process exits.
 //
 // Rules of use:
-//  - the first call on each device resolves the array's device address
-//    (cudaGetSymbolAddress) once; make that first call outside any stream capture;
+//  - every call resolves the array's device address (cudaGetSymbolAddress, no allocation);
+//    the first call on a device may load the library's device code there, so make that first
+//    call outside any stream capture;
 //  - every call, from any handle or thread, shares the one array: calls whose work
 //    overlaps on the GPU (different streams, or different threads without ordering)
 //    race on it; order them on one stream;
 //  - nothing in the array has to start at zero: each call writes every scratch byte it
 //    reads (tables are copied in, the stick buffer and partial sums are fully written);
+//  - the k-point's FFT tables: if the handle already holds them on the device (an earlier
+//    qm_hpsi or qm_davidson call with the handle uploaded them), they are read in place and the
+//    call only queues work on the stream; otherwise they are copied on every call from the
+//    handle's host copies into the scratch array (pageable host memory, so the host waits
+//    until the stream's earlier work is done before each copy);
+//  - QM_MIXED: the FFT path is the FP32 one of qm_hpsi; the nonlocal projection and
+//    application are FP32 SIMT products (not the tensor-core BF16x3 split of qm_hpsi, whose
+//    operand planes would need scratch of their own);
 //  - problems whose scratch exceeds QM_HPSI_NOALLOC_SCRATCH_BYTES are rejected with
 //    QM_ERR_ARG and a message giving the bytes needed.
 // No cudaMalloc, cudaFree or other allocating routine is called on this path.
 #include <algorithm>
 #include <cstring>
-#include <mutex>
 
 #include "qm_internal.h"
 
@@ -31,24 +39,13 @@ namespace {
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[QM_HPSI_NOALLOC_SCRATCH_BYTES];
 
-constexpr int kMaxDev = 64;
-std::mutex g_mu;
-void* g_ptr[kMaxDev] = {};
-
-// device address of the scratch array on the current device (resolved once per device)
+// device address of the scratch array on the current device, resolved on every call (a
+// cached address could outlive a module reload after the context is torn down)
 qm_status scratch_address(void** out) {
-    int dev = 0;
-    qm_status st = cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+    void* p = nullptr;
+    qm_status st = cuda_check(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress(noalloc scratch)");
     if (st) return st;
-    if (dev < 0 || dev >= kMaxDev) return fail(QM_ERR_UNSUPPORTED, "qm_hpsi_noalloc: device index >= 64");
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_ptr[dev]) {
-        void* p = nullptr;
-        st = cuda_check(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress(noalloc scratch)");
-        if (st) return st;
-        g_ptr[dev] = p;
-    }
-    *out = g_ptr[dev];
+    *out = p;
     return QM_OK;
 }
 
@@ -101,19 +98,24 @@ extern "C" qm_status qm_hpsi_noalloc(qm_gspace g, int ik, int nb, const void* ps
     const size_t nr = (size_t)N1 * N2 * N3;
     const size_t per_band = (size_t)N1 * kt.nstick_pad * cs;
 
-    // scratch layout: tables | Vt | P | stick buffer (>= 1 band) | split-K partials (what is left)
+    // the handle's device tables, when an earlier call uploaded them to this device
+    int cur_dev = -1;
+    if (cudaGetDevice(&cur_dev) != cudaSuccess) return fail(QM_ERR_CUDA, "qm_hpsi_noalloc: cudaGetDevice");
+    const bool in_place = g->uploaded && g->device == cur_dev;
+    // scratch layout: tables (unless in place) | Vt | P | stick buffer (>= 1 band) | split-K partials (what is left)
     Carve c;
-    const size_t o_g0 = c.take(sizeof(int) * kt.h_g0.size());
-    const size_t o_plane = c.take(sizeof(int) * kt.h_plane.size());
-    const size_t o_rows = c.take(sizeof(int) * kt.h_rows.size());
-    const size_t o_code = c.take(sizeof(int2) * kt.h_code.size());
-    const size_t o_kin64 = c.take(sizeof(double) * npw);
-    const size_t o_kin32 = c.take(fp32 ? sizeof(float) * npw : 0);
+    const bool copy = !in_place;
+    const size_t o_g0 = c.take(copy ? sizeof(int) * kt.h_g0.size() : 0);
+    const size_t o_plane = c.take(copy ? sizeof(int) * kt.h_plane.size() : 0);
+    const size_t o_rows = c.take(copy ? sizeof(int) * kt.h_rows.size() : 0);
+    const size_t o_code = c.take(copy ? sizeof(int2) * kt.h_code.size() : 0);
+    const size_t o_kin64 = c.take(copy ? sizeof(double) * npw : 0);
+    const size_t o_kin32 = c.take(copy && fp32 ? sizeof(float) * npw : 0);
     size_t o_tw64[3], o_tw32[3], o_rev[3];
     for (int d = 0; d < 3; ++d) {
-        o_tw64[d] = c.take(sizeof(double2) * g->n[d]);
-        o_tw32[d] = c.take(fp32 ? sizeof(float2) * g->n[d] : 0);
-        o_rev[d] = c.take(sizeof(int) * g->n[d]);
+        o_tw64[d] = c.take(copy ? sizeof(double2) * g->n[d] : 0);
+        o_tw32[d] = c.take(copy && fp32 ? sizeof(float2) * g->n[d] : 0);
+        o_rev[d] = c.take(copy ? sizeof(int) * g->n[d] : 0);
     }
     const size_t o_vt = c.take(nr * rs);
     const size_t o_p = c.take((size_t)nproj * nb * cs);
@@ -150,41 +152,56 @@ extern "C" qm_status qm_hpsi_noalloc(qm_gspace g, int ik, int nb, const void* ps
         if (bytes == 0) return QM_OK;
         return cuda_check(cudaMemcpyAsync(base + off, src, bytes, cudaMemcpyHostToDevice, s), "noalloc table copy");
     };
-    if ((st = up(o_g0, kt.h_g0.data(), sizeof(int) * kt.h_g0.size())) ||
+    DevTables t;
+    if (in_place) {
+        for (int d = 0; d < 3; ++d) {
+            t.tw[d] = fp32 ? (const void*)g->tw32[d] : (const void*)g->tw64[d];
+            t.rev[d] = g->rev[d];
+        }
+        t.stick_g0 = kt.stick_g0;
+        t.stick_plane = kt.stick_plane;
+        t.rows = kt.rows;
+        t.g_code = kt.g_code;
+        t.kin = fp32 ? (const void*)kt.kin_f : (const void*)kt.kin;
+    } else if ((st = up(o_g0, kt.h_g0.data(), sizeof(int) * kt.h_g0.size())) ||
         (st = up(o_plane, kt.h_plane.data(), sizeof(int) * kt.h_plane.size())) ||
         (st = up(o_rows, kt.h_rows.data(), sizeof(int) * kt.h_rows.size())) ||
         (st = up(o_code, kt.h_code.data(), sizeof(int2) * kt.h_code.size())) ||
-        (st = up(o_kin64, kt.h_kin.data(), sizeof(double) * npw)))
+        (st = up(o_kin64, kt.h_kin.data(), sizeof(double) * npw))) {
         return st;
-    for (int d = 0; d < 3; ++d)
-        if ((st = up(o_tw64[d], g->h_tw[d].data(), sizeof(double2) * g->n[d])) ||
-            (st = up(o_rev[d], g->h_rev[d].data(), sizeof(int) * g->n[d])))
-            return st;
-    if (fp32) {
-        k_to_float<<<(npw + 255) / 256, 256, 0, s>>>((const double*)(base + o_kin64), (float*)(base + o_kin32), npw);
-        count_launch(1);
-        for (int d = 0; d < 3; ++d) {
-            k_to_float<<<1, 256, 0, s>>>((const double*)(base + o_tw64[d]), (float*)(base + o_tw32[d]), 2 * g->n[d]);
-            count_launch(1);
-        }
     }
-    DevTables t;
+    if (copy) {
+        for (int d = 0; d < 3; ++d)
+            if ((st = up(o_tw64[d], g->h_tw[d].data(), sizeof(double2) * g->n[d])) ||
+                (st = up(o_rev[d], g->h_rev[d].data(), sizeof(int) * g->n[d])))
+                return st;
+        if (fp32) {
+            k_to_float<<<(npw + 255) / 256, 256, 0, s>>>((const double*)(base + o_kin64), (float*)(base + o_kin32), npw);
+            count_launch(1);
+            for (int d = 0; d < 3; ++d) {
+                k_to_float<<<1, 256, 0, s>>>((const double*)(base + o_tw64[d]), (float*)(base + o_tw32[d]), 2 * g->n[d]);
+                count_launch(1);
+            }
+        }
+        for (int d = 0; d < 3; ++d) {
+            t.tw[d] = base + (fp32 ? o_tw32[d] : o_tw64[d]);
+            t.rev[d] = (const int*)(base + o_rev[d]);
+        }
+        t.stick_g0 = (const int*)(base + o_g0);
+        t.stick_plane = (const int*)(base + o_plane);
+        t.rows = (const int*)(base + o_rows);
+        t.g_code = (const int2*)(base + o_code);
+        t.kin = base + (fp32 ? o_kin32 : o_kin64);
+    }
     for (int d = 0; d < 3; ++d) {
         t.n[d] = g->n[d];
         t.plan[d] = g->plan[d];
-        t.tw[d] = base + (fp32 ? o_tw32[d] : o_tw64[d]);
-        t.rev[d] = (const int*)(base + o_rev[d]);
     }
     t.ldx = g->ldx;
     t.ldy = g->ldy;
     t.nstick = kt.nstick;
     t.nstick_pad = kt.nstick_pad;
     t.nrow = kt.nrow;
-    t.stick_g0 = (const int*)(base + o_g0);
-    t.stick_plane = (const int*)(base + o_plane);
-    t.rows = (const int*)(base + o_rows);
-    t.g_code = (const int2*)(base + o_code);
-    t.kin = base + (fp32 ? o_kin32 : o_kin64);
 
     void* vt = base + o_vt;
     void* P = base + o_p;

@@ -219,7 +219,10 @@ k_nl_gemm(const unsigned char* __restrict__ A, const unsigned char* __restrict__
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag, s_used, s_issued;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int nt = blockIdx.x, mt = blockIdx.y;
+    // projection: N tiles fastest (the few N tiles of one M tile share its beta tiles in L2);
+    // application: M tiles fastest (the M tiles of one N tile share its betaT tiles, which are
+    // then read from HBM once instead of once per M tile)
+    const int nt = EPI == 0 ? blockIdx.x : blockIdx.y, mt = EPI == 0 ? blockIdx.y : blockIdx.x;
     const int kt0 = blockIdx.z * kt_per_split;
     const int kt1 = min(nkt, kt0 + kt_per_split);
     const int nk = max(0, kt1 - kt0);
@@ -452,8 +455,8 @@ qm_status gemm_launch(const unsigned char* A, const unsigned char* B, int nkt, i
     qm_status st = allow_dynamic_smem((const void*)k_nl_gemm<EPI>, smem, "tensor-core nonlocal GEMM shared memory");
     if (st) return st;
     ProfScope pf(PF_UMMA, s);
-    k_nl_gemm<EPI><<<dim3(ntl, mt, splits), kGemmThreads, smem, s>>>(A, B, nkt, BN, M, N, per, C, ldc, zstride,
-                                                                      accumulate ? 1 : 0, err);
+    const dim3 grid = EPI == 0 ? dim3(ntl, mt, splits) : dim3(mt, ntl, splits);
+    k_nl_gemm<EPI><<<grid, kGemmThreads, smem, s>>>(A, B, nkt, BN, M, N, per, C, ldc, zstride, accumulate ? 1 : 0, err);
     return cuda_check(cudaGetLastError(), "k_nl_gemm launch");
 }
 

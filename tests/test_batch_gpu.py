@@ -1,9 +1,11 @@
 """Batched H psi (qm_batch_*: every band x k-point x cell in one persistent launch replayed
 from a CUDA graph) against the FP64 oracle.
 
-Bars: FP64 1e-11 relative per band, QM_MIXED 2e-5 relative per band (the FP32 bar of the
-single-call tests); the batch equals the per-cell qm_hpsi loop to 1e-13 (FP64: same FFT
-arithmetic, nonlocal sums in another order); results do not depend on the launch shape.
+Bars: FP64 1e-11 relative per band; QM_MIXED 1e-6 relative per band (measured up to 1.1e-7 on
+these cells: FP32 FFTs and FP32 nonlocal sums over at most ~9,000 plane waves); the batch
+equals the per-cell qm_hpsi loop to 1e-13 (FP64: same FFT arithmetic, nonlocal sums in
+another order) and to 1e-6 in QM_MIXED (the single call's nonlocal part is the BF16x3
+tensor-core product); results do not depend on the launch shape.
 """
 import numpy as np
 import pytest
@@ -18,7 +20,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TOL64 = 1e-11
-TOL_MIXED = 2e-5
+TOL_MIXED = 1e-6
 
 
 @pytest.fixture(scope="module")
@@ -148,7 +150,7 @@ def test_batch_uneven_cells_full_size(Q, prec, tol):
         got = jobs[jj]["out"][bands].cpu().numpy().astype(np.complex128)
         err = band_rel_err(got, want).max()
         assert err <= tol, (cell.name, ik, err)
-    loop_tol = 1e-13 if prec == "fp64" else 1e-5
+    loop_tol = 1e-13 if prec == "fp64" else 1e-6
     for j in jobs:
         ref = Q.qm_hpsi(j["g"], j["ik"], j["psi"], j["vloc"], j["beta"], j["D"], prec=prec)
         torch.cuda.synchronize()

@@ -1,12 +1,15 @@
 """qm_hpsi_noalloc, the allocation-free variant of qm_hpsi for callers that cannot
 allocate device memory (e.g. under an allocator that owns the device heap), checked
 against qm_hpsi through the C ABI on two calls in a row that share the library's fixed
-scratch array.  Collected last on purpose: if it fails, a run stopping at the first
-failure has already run every other test."""
+scratch array, and against the FP64 oracle (padded rows, no projectors, a non-default
+stream, a handle whose tables were never uploaded and one that already holds them).
+Collected last on purpose: if it fails, a run stopping at the first failure has already run
+every other test."""
 import numpy as np
 import pytest
 
 import qm_synth as S
+from oracle import hamiltonian as OH
 
 from cases import band_rel_err, make_case
 
@@ -14,7 +17,12 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TOL64 = 1e-11       # the FP64 H-psi parity tolerance of the other tests
-TOL_MIXED = 2e-5
+# QM_MIXED: the no-allocation path runs its nonlocal part as FP32 SIMT products, the single
+# call as BF16x3 tensor-core products; both are FP32-accurate, so they agree to about the
+# FP32 H-psi error (measured up to 3e-7 per band on the 64-atom cell)
+TOL_MIXED = 2e-6
+TOL_MIXED_NOALLOC = 1e-6         # against the FP64 oracle, per band
+TOL_MIXED_NOALLOC_ELEM = 5e-6    # element-wise, relative to the band's largest element
 
 
 @pytest.fixture(scope="module")
@@ -79,5 +87,41 @@ def test_noalloc_rejects_problems_larger_than_its_scratch(Q):
         with pytest.raises(Q.QMError) as e:
             Q.qm_hpsi_noalloc(g, 0, psi, v, None, None, out)
         assert e.value.status == 1 and "scratch" in str(e.value)
+    finally:
+        Q.qm_gspace_destroy(g)
+
+
+def test_noalloc_matches_oracle_padded_local_only_side_stream(Q):
+    """Against the oracle: rows padded beyond npw, with and without projectors, on a side
+    stream; first on a handle whose tables only exist on the host (copied into the scratch
+    array), then on the same handle after qm_hpsi has uploaded them (read in place)."""
+    cell = S.cubic_si8(12.0, nbnd=7, reps=(2, 1, 1), kpts=[[0.25, 0.25, -0.25]])
+    c = make_case(cell, 0)
+    want = OH.hpsi_fft(c["psi"], c["gs"], c["v"], c["beta"], c["D"])
+    want_loc = OH.hpsi_fft(c["psi"], c["gs"], c["v"], None, None)
+    npw = c["psi"].shape[1]
+    g = Q.qm_gspace_create(cell.lattice, cell.kpts, cell.ecut_ha, cell.grid)
+    side = torch.cuda.Stream()
+    try:
+        for phase in ("host tables", "device tables"):
+            for prec, tb, te in (("fp64", TOL64, TOL64), ("mixed", TOL_MIXED_NOALLOC, TOL_MIXED_NOALLOC_ELEM)):
+                dt = torch.complex128 if prec == "fp64" else torch.complex64
+                psi = torch.zeros((c["psi"].shape[0], npw + 5), dtype=dt, device="cuda")
+                psi[:, :npw] = dev(c["psi"], dt)
+                v, beta, D = dev(c["v"], torch.float64), dev(c["beta"], dt), dev(c["D"], torch.float64)
+                for with_nl, ref in ((True, want), (False, want_loc)):
+                    out = torch.full((psi.shape[0], npw + 3), float("nan"), dtype=dt, device="cuda")
+                    torch.cuda.synchronize()
+                    with torch.cuda.stream(side):
+                        Q.qm_hpsi_noalloc(g, 0, psi, v, beta if with_nl else None, D if with_nl else None, out,
+                                          prec=prec, stream=side)
+                    side.synchronize()
+                    got = out[:, :npw].cpu().numpy().astype(np.complex128)
+                    rel = band_rel_err(got, ref).max()
+                    el = (np.abs(got - ref) / np.abs(ref).max(axis=1, keepdims=True)).max()
+                    assert rel <= tb and el <= te, (phase, prec, with_nl, rel, el)
+            if phase == "host tables":
+                Q.qm_hpsi(g, 0, dev(c["psi"], torch.complex128), dev(c["v"], torch.float64), None, None)
+                torch.cuda.synchronize()
     finally:
         Q.qm_gspace_destroy(g)
