@@ -431,15 +431,16 @@ qm_status qm_davidson_batched(int njobs, qm_davidson_job* jobs, const qm_davidso
  *   r_n      = HX_n - eps_n X_n,            rnorm2_n = ||r_n||^2,
  *   T_n      = sum_G T_G |X_n(G)|^2 / sum_G |X_n(G)|^2,   T_G = |k+G|^2 / 2,
  *   delta_n  = K_n(G) r_n(G),  K = K_TPA(T_G / T_n) (precond 0) or the network of
- *              qm_mlp_forward on the features (T_G/T_n, eps_n/T_n, log(max(|r_n(G)| sqrt(npw) /
- *              ||r_n||, 1e-6))) (precond 1).
+ *              qm_mlp_forward on the features (T_G/T_n, eps_n/T_n, (H_GG - eps_n)/T_n)
+ *              (precond 1; H_GG from qm_hamiltonian_diag).
  *
  *  g, ik      gspace and k-point.
  *  n          number of bands, 0 <= n <= 65535 (0 is a no-op).
  *  X, HX      device, n rows of npw(ik) complex double, row stride ld (>= npw): Ritz vectors
  *             (any non-zero rows; T_n is normalised by the row's own norm) and H applied to them.
  *  eps        device, n doubles: the Ritz values eps_n.
- *  precond    0 = TPA, 1 = learned (mlp: device, QM_MLP_NPARAM floats, as qm_mlp_forward).
+ *  precond    0 = TPA, 1 = learned (mlp: device, QM_MLP_NPARAM floats, as qm_mlp_forward;
+ *             hdiag: device, npw doubles, the diagonal of H(k); both may be NULL for TPA).
  *  R, delta   device, n rows, row stride ld: outputs r_n and delta_n (must not overlap the inputs
  *             or each other).
  *  rnorm2     device, n doubles: output ||r_n||^2 (FP64).
@@ -451,8 +452,20 @@ qm_status qm_davidson_batched(int njobs, qm_davidson_job* jobs, const qm_davidso
  * Errors: QM_ERR_ARG, QM_ERR_CUDA, QM_ERR_OOM, QM_ERR_TIMEOUT (a bounded wait of the network).
  */
 qm_status qm_precond_apply(qm_gspace g, int ik, int n, const void* X, const void* HX, int ld, const double* eps,
-                           int precond, const float* mlp, void* R, void* delta, double* rnorm2, double* tkin,
-                           void* stream);
+                           int precond, const float* mlp, const double* hdiag, void* R, void* delta, double* rnorm2,
+                           double* tkin, void* stream);
+
+/*
+ * qm_hamiltonian_diag - the diagonal of H(k) in the plane-wave basis (Eq. KSHamMat with the KB
+ * term of Sec. 2.3):  hdiag[G] = |k+G|^2/2 + Vt(0) + sum_p D_p |beta_p(G)|^2, Vt(0) = the mean
+ * of V(r) over the grid.  The learned preconditioner's third feature is (hdiag - eps_n) / T_n.
+ *  vloc_r, nproj, beta, ld_beta, D   as in qm_hpsi, FP64 (beta may be NULL when nproj == 0).
+ *  hdiag      device, npw(ik) doubles (output).
+ * FP64, asynchronous on stream (partial sums of V in the handle's workspace: same one-stream
+ * rule as qm_hpsi).  Errors: QM_ERR_ARG, QM_ERR_OOM, QM_ERR_CUDA.
+ */
+qm_status qm_hamiltonian_diag(qm_gspace g, int ik, const double* vloc_r, int nproj, const void* beta, int ld_beta,
+                              const double* D, double* hdiag, void* stream);
 
 /*
  * qm_eigh_lowest - lowest nev eigenpairs of a complex Hermitian m x m matrix in FP64: the
@@ -483,8 +496,9 @@ qm_status qm_eigh_lowest(int m, int nev, const void* A, int lda, double* evals, 
  * | w3 (64) | b3 (1).  Arithmetic: BF16 weights, features and hidden activations, FP32
  * accumulation (the 64 x 64 layer of inference on the tensor cores, tcgen05).
  * Features of plane wave G of band n (scale-free): x = T_G / T_n with T_G = |k+G|^2/2 and T_n
- * the band's kinetic energy per unit norm; e = eps_n / T_n (Ritz value); l =
- * log(max(|r_n(G)| sqrt(npw) / ||r_n||, 1e-6)).
+ * the band's kinetic energy per unit norm; e = eps_n / T_n (Ritz value); d = (H_GG - eps_n) / T_n
+ * with H_GG the diagonal of H(k) (qm_hamiltonian_diag).  None depends on the residual, so the
+ * correction K r_n is linear in r_n.
  * Training target: the exact correction delta*_n = P_c psi_n / (psi_n^H P_c psi_n) - psi_n,
  * P_c the projector on the exact eigenspace of eigenvalue n (with its degenerate partners); loss: the mean over bands of
  * 1 - cos^2 between K.r_n and delta*_n (only the direction matters to Davidson), weighted by
@@ -501,6 +515,7 @@ qm_status qm_mlp_forward(long long n, const float* feats, const float* theta, fl
 /* qm_mlp_pairs - training samples of n Ritz pairs of k-point ik from exact eigenpairs.
  *  psi, hpsi   device, n rows (ld_psi, ld_hpsi >= npw) complex double: Ritz vectors and H psi.
  *  eps         device, n Ritz values.
+ *  hdiag       device, npw doubles: the diagonal of H(k) (qm_hamiltonian_diag).
  *  U, lam      device: nu exact unit eigenvectors (rows, ld_u >= npw) and eigenvalues, ascending.
  *  cluster_tol band n (the n-th lowest Ritz pair) targets eigenvalue n and its partners within
  *              cluster_tol; a band whose cluster reaches lam[nu-1] (or n >= nu) gets D = 0.
@@ -509,7 +524,7 @@ qm_status qm_mlp_forward(long long n, const float* feats, const float* theta, fl
  *              D_n = 0): Davidson stops on its largest residual, so the bands that carry it weigh most.
  * Synchronous (allocates temporaries with cudaMallocAsync). */
 qm_status qm_mlp_pairs(qm_gspace g, int ik, int n, const void* psi, int ld_psi, const void* hpsi, int ld_hpsi,
-                       const double* eps, int nu, const void* U, int ld_u, const double* lam,
+                       const double* eps, const double* hdiag, int nu, const void* U, int ld_u, const double* lam,
                        double cluster_tol, float* feats, float* r2, float* c, float* D, float* W, void* stream);
 
 /* qm_mlp_loss_grad - loss (host double) and its gradient (device, QM_MLP_NPARAM floats) over

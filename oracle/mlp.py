@@ -23,7 +23,12 @@ Parameters, one flat vector of NPARAM (the layout the library uses):
 Features of plane wave G of band n (scale-free):
     x  = T_G / T_n                 T_G = |k+G|^2 / 2,  T_n = sum_G T_G |psi_n(G)|^2 / sum_G |psi_n(G)|^2
     e  = eps_n / T_n               eps_n: the band's Ritz value
-    l  = log(max(|r_n(G)| sqrt(npw) / ||r_n||, 1e-6))
+    d  = (H_GG - eps_n) / T_n      H_GG: the diagonal of H(k) in the plane-wave basis,
+                                   H_GG = T_G + Vt(0) + sum_p D_p |beta_p(G)|^2 (Eq. KSHamMat with the
+                                   KB term; Vt(0) = mean of V(r))
+Reading: the correction step's features carry the Hamiltonian's own diagonal, the quantity the
+classic Davidson correction (H_GG - eps_n)^-1 r_n(G) divides by, of which TPA keeps only the
+kinetic part; none of them depends on the residual, so K r_n stays linear in r_n.
 
 Exact correction (the training target).  Reading: the correction that would turn the Ritz
 vector psi_n into its component in the exact eigenspace it converges to,
@@ -55,7 +60,6 @@ from .precond import tpa_k
 HIDDEN = 64
 NIN = 3
 NPARAM = HIDDEN * NIN + HIDDEN + HIDDEN * HIDDEN + HIDDEN + HIDDEN + 1  # 4481
-FEAT_LOG_FLOOR = 1e-6
 
 
 def unpack(theta):
@@ -110,17 +114,24 @@ def forward(theta, F):
     return tpa_k(F[:, 0]) * softplus(z3) / math.log(2.0), (F, z1, h1, z2, h2, z3)
 
 
-def features(kin, psi, res, eps):
-    """(nb*npw, 3) feature rows, band-major, for Ritz vectors psi, residuals res, values eps."""
+def hamiltonian_diagonal(kin, vloc, beta, D):
+    """H_GG = T_G + Vt(0) + sum_p D_p |beta_p(G)|^2: the diagonal of Eq. KSHamMat with the KB term
+    (Vt(0) = (1/N_r) sum_j V(r_j), the G = G' coefficient of the local potential)."""
+    h = np.asarray(kin, float) + float(np.mean(vloc))
+    if beta is not None and beta.shape[0]:
+        h = h + (np.asarray(D, float)[:, None] * np.abs(beta) ** 2).sum(axis=0)
+    return h
+
+
+def features(kin, psi, eps, hdiag):
+    """(nb*npw, 3) feature rows (x, e, d), band-major, for Ritz vectors psi with Ritz values eps
+    and the Hamiltonian's diagonal hdiag."""
     w = np.abs(psi) ** 2
     tn = (w * kin[None, :]).sum(axis=1) / w.sum(axis=1)
-    npw = psi.shape[1]
-    rn = np.linalg.norm(res, axis=1)
     x = kin[None, :] / tn[:, None]
     e = np.broadcast_to((eps / tn)[:, None], x.shape)
-    ratio = np.abs(res) * math.sqrt(npw) / rn[:, None]
-    l = np.log(np.maximum(ratio, FEAT_LOG_FLOOR))
-    return np.stack([x, e, l], axis=-1).reshape(-1, 3)
+    d = (hdiag[None, :] - eps[:, None]) / tn[:, None]
+    return np.stack([x, e, d], axis=-1).reshape(-1, 3)
 
 
 def exact_corrections(psi, lam, U, cluster_tol):
@@ -142,9 +153,9 @@ def exact_corrections(psi, lam, U, cluster_tol):
     return out
 
 
-def samples(kin, psi, res, eps, dstar):
+def samples(kin, psi, res, eps, dstar, hdiag):
     """Training samples: features (nb*npw, 3), |r|^2 (nb*npw,), c (nb*npw,), D (nb,), W (nb,)."""
-    F = features(kin, psi, res, eps)
+    F = features(kin, psi, eps, hdiag)
     r2 = (np.abs(res) ** 2).reshape(-1)
     c = np.real(np.conj(res) * dstar).reshape(-1)
     D = (np.abs(dstar) ** 2).sum(axis=1)

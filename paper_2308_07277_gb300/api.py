@@ -218,10 +218,11 @@ def qm_hpsi_noalloc(g, ik, psi, vloc, beta, D, out, prec="fp64", stream=None):
     return out
 
 
-def qm_precond_apply(g, ik, X, HX, eps, mlp=None, stream=None):
+def qm_precond_apply(g, ik, X, HX, eps, mlp=None, hdiag=None, stream=None):
     """Residuals and Davidson corrections of the n rows of X (n, >=npw) complex128 CUDA tensor
     with HX (same shape and stride) and eps (n,) float64 CUDA tensor; TPA when mlp is None,
-    else the network (QM_MLP_NPARAM float32 CUDA tensor).  Returns (R, delta, rnorm2, tkin)."""
+    else the network (QM_MLP_NPARAM float32 CUDA tensor) with hdiag (npw,) float64, the
+    diagonal of H.  Returns (R, delta, rnorm2, tkin)."""
     lib = _lib.load()
     if X.dim() != 2 or HX.shape != X.shape or HX.stride(0) != X.stride(0):
         raise ValueError("X and HX must be 2-D with the same shape and row stride")
@@ -233,7 +234,8 @@ def qm_precond_apply(g, ik, X, HX, eps, mlp=None, stream=None):
     _check(lib.qm_precond_apply(g, int(ik), n, _dev_ptr(X, "X", torch.complex128),
                                 _dev_ptr(HX, "HX", torch.complex128), int(X.stride(0)),
                                 _dev_ptr(eps, "eps", torch.float64), 0 if mlp is None else 1,
-                                _dev_ptr(mlp, "mlp", torch.float32), _dev_ptr(R, "R", torch.complex128),
+                                _dev_ptr(mlp, "mlp", torch.float32), _dev_ptr(hdiag, "hdiag", torch.float64),
+                                _dev_ptr(R, "R", torch.complex128),
                                 _dev_ptr(delta, "delta", torch.complex128), _dev_ptr(rn2, "rnorm2", torch.float64),
                                 _dev_ptr(tk, "tkin", torch.float64), _stream_ptr(stream)))
     return R, delta, rn2, tk
@@ -334,9 +336,24 @@ def qm_mlp_forward(feats, theta, stream=None):
     return K
 
 
-def qm_mlp_pairs(g, ik, psi, hpsi, eps, U, lam, cluster_tol=1e-6, stream=None):
+def qm_hamiltonian_diag(g, ik, vloc, beta, D, stream=None):
+    """The diagonal of H(k) in the plane-wave basis, (npw,) float64 CUDA tensor (beta, D:
+    complex128 / float64 CUDA tensors or None)."""
+    info = qm_gspace_query(g)
+    npw = info["npw"][ik]
+    out = torch.empty(npw, dtype=torch.float64, device=vloc.device)
+    nproj = 0 if beta is None else int(beta.shape[0])
+    _check(_lib.load().qm_hamiltonian_diag(g, int(ik), _dev_ptr(vloc, "vloc", torch.float64), nproj,
+                                           _dev_ptr(beta, "beta", torch.complex128), int(beta.stride(0)) if nproj else 0,
+                                           _dev_ptr(D, "D", torch.float64) if nproj else None,
+                                           _dev_ptr(out, "hdiag", torch.float64), _stream_ptr(stream)))
+    return out
+
+
+def qm_mlp_pairs(g, ik, psi, hpsi, eps, hdiag, U, lam, cluster_tol=1e-6, stream=None):
     """Training samples of the Ritz pairs (psi, eps) with H psi = hpsi against the exact
-    eigenpairs (U rows, lam ascending); all complex128/float64 CUDA tensors.
+    eigenpairs (U rows, lam ascending), hdiag the diagonal of H (qm_hamiltonian_diag); all
+    complex128/float64 CUDA tensors.
     Returns (feats (n*npw, 3), r2 (n*npw,), c (n*npw,), D (n,), W (n,)) float32 CUDA tensors."""
     n, npw = int(psi.shape[0]), None
     info = qm_gspace_query(g)
@@ -349,7 +366,8 @@ def qm_mlp_pairs(g, ik, psi, hpsi, eps, U, lam, cluster_tol=1e-6, stream=None):
     W = torch.empty(n, dtype=torch.float32, device=dev)
     _check(_lib.load().qm_mlp_pairs(g, int(ik), n, _dev_ptr(psi, "psi", torch.complex128), int(psi.stride(0)),
                                     _dev_ptr(hpsi, "hpsi", torch.complex128), int(hpsi.stride(0)),
-                                    _dev_ptr(eps, "eps", torch.float64), int(U.shape[0]),
+                                    _dev_ptr(eps, "eps", torch.float64), _dev_ptr(hdiag, "hdiag", torch.float64),
+                                    int(U.shape[0]),
                                     _dev_ptr(U, "U", torch.complex128), int(U.stride(0)),
                                     _dev_ptr(lam, "lam", torch.float64), float(cluster_tol),
                                     _dev_ptr(feats, "feats"), _dev_ptr(r2, "r2"), _dev_ptr(c, "c"), _dev_ptr(D, "D"),

@@ -95,6 +95,42 @@ __global__ void k_tpa(const double2* __restrict__ R, int ld, int npw, const int*
     }
 }
 
+// partial sums of V(r) over a grid stride (one per block, fixed order: deterministic)
+__global__ void __launch_bounds__(256) k_vsum(const double* __restrict__ V, size_t nr, double* __restrict__ part) {
+    __shared__ double sh[256];
+    double a = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nr; i += (size_t)gridDim.x * blockDim.x) a += V[i];
+    sh[threadIdx.x] = a;
+    __syncthreads();
+    for (int st = 128; st > 0; st >>= 1) {
+        if (threadIdx.x < st) sh[threadIdx.x] += sh[threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+// hdiag[G] = kin[G] + mean(V) + sum_p D_p |beta_p(G)|^2: the diagonal of H(k) (Eq. KSHamMat with
+// the KB term of Sec. 2.3; the G = G' coefficient of the local part is the mean of V(r))
+__global__ void __launch_bounds__(256) k_hdiag(const double* __restrict__ kin, int npw, const double* __restrict__ part,
+                                               int npart, double inv_nr, const double2* __restrict__ beta, int ld,
+                                               int nproj, const double* __restrict__ D, double* __restrict__ hdiag) {
+    __shared__ double vmean;
+    if (threadIdx.x == 0) {
+        double a = 0.0;
+        for (int b = 0; b < npart; ++b) a += part[b];
+        vmean = a * inv_nr;
+    }
+    __syncthreads();
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= npw) return;
+    double nl = 0.0;
+    for (int p = 0; p < nproj; ++p) {
+        const double2 b = beta[(size_t)p * ld + g];
+        nl += D[p] * (b.x * b.x + b.y * b.y);
+    }
+    hdiag[g] = kin[g] + vmean + nl;
+}
+
 // Hermitian completion after new columns [m0, m) of H were computed for rows [0, m):
 // H[j][i] = conj(H[i][j]) for i < m0 <= j; the new diagonal block is symmetrised.
 __global__ void k_herm_fill(double2* __restrict__ H, int ld, int m0, int m) {
@@ -188,12 +224,32 @@ qm_status convert_rows(const S* in, int ldi, D* out, int ldo, int rows, int cols
     return cuda_check(cudaGetLastError(), "k_convert_rows launch");
 }
 
+}  // namespace
+
+qm_status hamiltonian_diag(qm_gspace g, int ik, const double* vloc, int nproj, const double2* beta, int ld_beta,
+                           const double* D, double* hdiag, double* work, cudaStream_t s) {
+    const size_t nr = (size_t)g->n[0] * g->n[1] * g->n[2];
+    const int npw = g->k[ik].npw;
+    {
+        ProfScope pf(PF_OTHER, s);
+        k_vsum<<<kVmeanBlocks, 256, 0, s>>>(vloc, nr, work);
+    }
+    {
+        ProfScope pf(PF_OTHER, s);
+        k_hdiag<<<(npw + 255) / 256, 256, 0, s>>>(g->k[ik].kin, npw, work, kVmeanBlocks, 1.0 / (double)nr, beta,
+                                                   ld_beta, nproj, D, hdiag);
+    }
+    return cuda_check(cudaGetLastError(), "hamiltonian diagonal launch");
+}
+
+namespace {
+
 struct Ws {
     double2 *V, *HV, *X, *HX, *R, *Dl, *Tmp;  // [.. rows][ld]
     double2 *Hs, *G, *A, *Z, *Cs, *Part;      // small
     double2 *Cp, *CT, *PT, *QT;               // previous Ritz coefficients [nvecx+1][nb]; transposed blocks
     double2 *Y, *HY;                          // [nb][ld]: previous-direction rows kept at a restart
-    double *eval, *eps, *rn2, *tk;
+    double *eval, *eps, *rn2, *tk, *hdiag, *vpart;
     int *sel, *rank, *info;
     void* heev;
 };
@@ -479,6 +535,8 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
                  oRn = take(sizeof(double) * nsq), oTk = take(sizeof(double) * nsq),
                  oSel = take(sizeof(int) * nsq), oRank = take(sizeof(int) * nsq), oInfo = take(sizeof(int) * 4),
                  oHeev = take(heev_work_bytes(nsq, nsq));
+    const size_t oHd = take(o.precond == 1 ? sizeof(double) * npw : 0),
+                 oVp = take(o.precond == 1 ? sizeof(double) * kVmeanBlocks : 0);
     if ((st = ensure_dav_workspace(g, off, s))) return st;
     char* base = (char*)g->dws.ptr;
     Ws& w = run.w;
@@ -526,6 +584,8 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
     w.rank = (int*)(base + oRank);
     w.info = (int*)(base + oInfo);
     w.heev = base + oHeev;
+    w.hdiag = (double*)(base + oHd);
+    w.vpart = (double*)(base + oVp);
     run.tc_err = w.info + 3;
     if (use_mixed && (st = cuda_check(cudaMemsetAsync(run.tc_err, 0, sizeof(int), s), "reset error word"))) return st;
     const double* kin = g->k[ik].kin;
@@ -554,6 +614,9 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
     std::vector<double> hist_all;
     int* mlp_err = w.info + 2;
     if (use_mlp && (st = cuda_check(cudaMemsetAsync(mlp_err, 0, sizeof(int), s), "reset error word"))) return st;
+    // the network's features need the Hamiltonian's diagonal (once per solve)
+    if (use_mlp && (st = hamiltonian_diag(g, ik, vloc_r, nproj, (const double2*)beta, ld_beta, D, w.hdiag, w.vpart, s)))
+        return st;
     std::vector<double> rn2(nb), eps(nb);
     int it = 0, it_mixed = 0, restarts = 0;
     long long prev_kept = 0;
@@ -695,7 +758,7 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
         const int nu = (int)unc.size();
         cudaMemcpyAsync(w.sel, unc.data(), sizeof(int) * nu, cudaMemcpyHostToDevice, s);
         if (use_mlp) {
-            if ((st = mlp_precond_apply(o.mlp, w.R, ld, npw, w.sel, nu, w.tk, w.eps, w.rn2, kin, w.Dl, ld, mlp_err, s)))
+            if ((st = mlp_precond_apply(o.mlp, w.R, ld, npw, w.sel, nu, w.tk, w.eps, w.hdiag, kin, w.Dl, ld, mlp_err, s)))
                 return st;
         } else {
             ProfScope pf(PF_OTHER, s);
@@ -880,14 +943,15 @@ extern "C" qm_status qm_davidson_batched(int njobs, qm_davidson_job* jobs, const
 // loop above launches): r_n = HX_n - eps_n X_n with ||r_n||^2 and T_n, then
 // delta_n = K r_n with the TPA factor or the learned network.
 extern "C" qm_status qm_precond_apply(qm_gspace g, int ik, int n, const void* X, const void* HX, int ld,
-                                      const double* eps, int precond, const float* mlp, void* R, void* delta,
-                                      double* rnorm2, double* tkin, void* stream) {
+                                      const double* eps, int precond, const float* mlp, const double* hdiag, void* R,
+                                      void* delta, double* rnorm2, double* tkin, void* stream) {
     clear_error();
     if (!g) return fail(QM_ERR_ARG, "qm_precond_apply: NULL gspace");
     if (ik < 0 || ik >= g->nk) return fail(QM_ERR_ARG, "qm_precond_apply: ik out of range");
     if (n < 0 || n > 65535) return fail(QM_ERR_ARG, "qm_precond_apply: need 0 <= n <= 65535");
     if (precond != 0 && precond != 1) return fail(QM_ERR_ARG, "qm_precond_apply: unknown preconditioner");
-    if (precond == 1 && !mlp) return fail(QM_ERR_ARG, "qm_precond_apply: learned preconditioner without parameters");
+    if (precond == 1 && (!mlp || !hdiag))
+        return fail(QM_ERR_ARG, "qm_precond_apply: learned preconditioner without parameters or H diagonal");
     if (n == 0) return QM_OK;
     const int npw = g->k[ik].npw;
     if (!X || !HX || !eps || !R || !delta || !rnorm2 || !tkin)
@@ -913,7 +977,26 @@ extern "C" qm_status qm_precond_apply(qm_gspace g, int ik, int n, const void* X,
     }
     // the network's bounded tensor-core waits report through the handle's sticky error word
     if ((st = ensure_workspace(g, kWsHeader, s))) return st;
-    if ((st = mlp_precond_apply(mlp, r, ld, npw, nullptr, n, tkin, eps, rnorm2, kin, d, ld, (int*)g->ws.ptr, s)))
+    if ((st = mlp_precond_apply(mlp, r, ld, npw, nullptr, n, tkin, eps, hdiag, kin, d, ld, (int*)g->ws.ptr, s)))
         return st;
     return qm_hpsi_check(g, stream);
+}
+
+extern "C" qm_status qm_hamiltonian_diag(qm_gspace g, int ik, const double* vloc_r, int nproj, const void* beta,
+                                         int ld_beta, const double* D, double* hdiag, void* stream) {
+    clear_error();
+    if (!g) return fail(QM_ERR_ARG, "qm_hamiltonian_diag: NULL gspace");
+    if (ik < 0 || ik >= g->nk) return fail(QM_ERR_ARG, "qm_hamiltonian_diag: ik out of range");
+    if (nproj < 0 || !vloc_r || !hdiag || (nproj > 0 && (!beta || !D)))
+        return fail(QM_ERR_ARG, "qm_hamiltonian_diag: NULL argument or negative nproj");
+    const int npw = g->k[ik].npw;
+    if (nproj > 0 && ld_beta < npw) return fail(QM_ERR_ARG, "qm_hamiltonian_diag: ld_beta < npw");
+    if (nproj > 0 && (uintptr_t)beta % 16) return fail(QM_ERR_ARG, "qm_hamiltonian_diag: beta not 16-byte aligned");
+    qm_status st = ensure_device(g);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    // the partial sums of V live in the handle's workspace, after its error-word header
+    if ((st = ensure_workspace(g, kWsHeader + sizeof(double) * kVmeanBlocks, s))) return st;
+    return hamiltonian_diag(g, ik, vloc_r, nproj, (const double2*)beta, ld_beta, D, hdiag,
+                            (double*)((char*)g->ws.ptr + kWsHeader), s);
 }

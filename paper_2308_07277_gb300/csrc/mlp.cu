@@ -54,12 +54,12 @@ __device__ __forceinline__ float tpa(float x) {
     return num / (num + 16.f * x2 * x2);
 }
 
-// features of one plane wave (shared by the sample generator and the Davidson correction)
-__device__ __forceinline__ void mlp_feat(double kin, double inv_t, double e_over_t, double rabs, double r_scale,
-                                         float f[3]) {
+// features of one plane wave (shared by the sample generator and the Davidson correction):
+// x = T_G / T_n, e = eps_n / T_n, d = (H_GG - eps_n) / T_n with H_GG the Hamiltonian's diagonal
+__device__ __forceinline__ void mlp_feat(double kin, double inv_t, double eps, double hdiag, float f[3]) {
     f[0] = (float)(kin * inv_t);
-    f[1] = (float)e_over_t;
-    f[2] = logf(fmaxf((float)(rabs * r_scale), 1e-6f));
+    f[1] = (float)(eps * inv_t);
+    f[2] = (float)((hdiag - eps) * inv_t);
 }
 
 // ---------------------------------------------------------------- inference (tensor cores)
@@ -89,7 +89,7 @@ struct DavidsonCorr {  // out_j(G) = K r_{sel[j]}(G), features from the residual
     const double2* R;
     int ld, npw, nu;
     const int* sel;
-    const double *tk, *eps, *rn2, *kin;
+    const double *tk, *eps, *hdiag, *kin;
     double2* out;
     int ldo;
     __device__ __forceinline__ long tiles_per_band() const { return (npw + kMT - 1) / kMT; }
@@ -101,9 +101,7 @@ struct DavidsonCorr {  // out_j(G) = K r_{sel[j]}(G), features from the residual
         if (g >= npw) return false;
         const int n = sel ? __ldg(sel + j) : j;  // sel == NULL: row j is band j
         const double t = __ldg(tk + n);
-        const double2 r = R[(size_t)n * ld + g];
-        mlp_feat(__ldg(kin + g), 1.0 / t, __ldg(eps + n) / t, sqrt(r.x * r.x + r.y * r.y),
-                 sqrt((double)npw / __ldg(rn2 + n)), f);
+        mlp_feat(__ldg(kin + g), 1.0 / t, __ldg(eps + n), __ldg(hdiag + g), f);
         return true;
     }
     __device__ __forceinline__ void store(long tile, int tid, float k) const {
@@ -521,8 +519,8 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double (*sh)[256]) {
 __global__ void __launch_bounds__(256)
 k_mlp_pairs(const double2* __restrict__ psi, int ldp, const double2* __restrict__ hpsi, int ldh,
             const double* __restrict__ eps, const double2* __restrict__ P, const int* __restrict__ ok,
-            const double* __restrict__ kin, int npw, float* __restrict__ feats, float* __restrict__ r2,
-            float* __restrict__ cc, float* __restrict__ D, float* __restrict__ W) {
+            const double* __restrict__ kin, const double* __restrict__ hdiag, int npw, float* __restrict__ feats,
+            float* __restrict__ r2, float* __restrict__ cc, float* __restrict__ D, float* __restrict__ W) {
     __shared__ double sh[4][256];
     const int n = blockIdx.x;
     const double e = eps[n];
@@ -540,7 +538,7 @@ k_mlp_pairs(const double2* __restrict__ psi, int ldp, const double2* __restrict_
         v[3] += a.x * q.x + a.y * q.y;
     }
     block_sum<4>(v, sh);
-    const double inv_t = v[0] / v[1], e_t = e * inv_t, rs = sqrt((double)npw / v[2]), is = 1.0 / v[3];
+    const double inv_t = v[0] / v[1], is = 1.0 / v[3];
     double d[1] = {0.0};
     const bool keep = ok[n] != 0;  // an incomplete cluster: no target (delta* = 0)
     for (int g = threadIdx.x; g < npw; g += blockDim.x) {
@@ -549,7 +547,7 @@ k_mlp_pairs(const double2* __restrict__ psi, int ldp, const double2* __restrict_
         const double dx = keep ? q.x * is - a.x : 0.0, dy = keep ? q.y * is - a.y : 0.0;
         const size_t s = (size_t)n * npw + g;
         float f[3];
-        mlp_feat(kin[g], inv_t, e_t, sqrt(rx * rx + ry * ry), rs, f);
+        mlp_feat(kin[g], inv_t, e, hdiag[g], f);
         feats[3 * s] = f[0];
         feats[3 * s + 1] = f[1];
         feats[3 * s + 2] = f[2];
@@ -567,9 +565,9 @@ k_mlp_pairs(const double2* __restrict__ psi, int ldp, const double2* __restrict_
 }  // namespace
 
 qm_status mlp_precond_apply(const float* theta, const double2* R, int ld, int npw, const int* sel, int nu,
-                            const double* tk, const double* eps, const double* rn2, const double* kin, double2* out,
+                            const double* tk, const double* eps, const double* hdiag, const double* kin, double2* out,
                             int ldo, int* err, cudaStream_t s) {
-    DavidsonCorr src{R, ld, npw, nu, sel, tk, eps, rn2, kin, out, ldo};
+    DavidsonCorr src{R, ld, npw, nu, sel, tk, eps, hdiag, kin, out, ldo};
     const long nt = (long)((npw + kMT - 1) / kMT) * nu;
     ProfScope pf(PF_MLP, s);
     k_mlp_infer<DavidsonCorr><<<infer_grid(nt), kMT, 0, s>>>(src, theta, err);
@@ -667,13 +665,13 @@ extern "C" qm_status qm_mlp_forward(long long n, const float* feats, const float
 }
 
 extern "C" qm_status qm_mlp_pairs(qm_gspace g, int ik, int n, const void* psi, int ld_psi, const void* hpsi,
-                                  int ld_hpsi, const double* eps, int nu, const void* U, int ld_u, const double* lam,
-                                  double cluster_tol, float* feats, float* r2, float* c, float* D, float* W,
-                                  void* stream) {
+                                  int ld_hpsi, const double* eps, const double* hdiag, int nu, const void* U, int ld_u,
+                                  const double* lam, double cluster_tol, float* feats, float* r2, float* c, float* D,
+                                  float* W, void* stream) {
     clear_error();
     if (!g || ik < 0 || ik >= g->nk) return fail(QM_ERR_ARG, "qm_mlp_pairs: bad gspace or ik");
     const int npw = g->k[ik].npw;
-    if (n < 1 || nu < 1 || !psi || !hpsi || !eps || !U || !lam || !feats || !r2 || !c || !D || !W)
+    if (n < 1 || nu < 1 || !psi || !hpsi || !eps || !hdiag || !U || !lam || !feats || !r2 || !c || !D || !W)
         return fail(QM_ERR_ARG, "qm_mlp_pairs: bad arguments");
     if (ld_psi < npw || ld_hpsi < npw || ld_u < npw) return fail(QM_ERR_ARG, "qm_mlp_pairs: leading dimension < npw");
     if (!(cluster_tol >= 0.0)) return fail(QM_ERR_ARG, "qm_mlp_pairs: cluster_tol < 0");
@@ -698,7 +696,8 @@ extern "C" qm_status qm_mlp_pairs(qm_gspace g, int ik, int n, const void* psi, i
     {
         ProfScope pf(PF_MLP, s);
         k_mlp_pairs<<<n, 256, 0, s>>>((const double2*)psi, ld_psi, (const double2*)hpsi, ld_hpsi, eps,
-                                      (const double2*)P.p, (const int*)ok.p, g->k[ik].kin, npw, feats, r2, c, D, W);
+                                      (const double2*)P.p, (const int*)ok.p, g->k[ik].kin, hdiag, npw, feats, r2, c,
+                                      D, W);
     }
     {
         ProfScope pf(PF_MLP, s);

@@ -224,10 +224,15 @@ size_t subspace_bf16x3_bytes(int max_m, int max_n);
 
 // ---- learned preconditioner (mlp.cu) ----
 // out_j(G) = K(f) R[sel[j]](G) for j < nu: the network's correction of the Davidson step;
-// tk, eps, rn2: per band T_n, Ritz value, ||r_n||^2 (device); err: device int set on a timed-out wait
+// tk, eps: per band T_n and Ritz value; hdiag: the Hamiltonian's diagonal per plane wave (device);
+// err: device int set on a timed-out wait
 qm_status mlp_precond_apply(const float* theta, const double2* R, int ld, int npw, const int* sel, int nu,
-                            const double* tk, const double* eps, const double* rn2, const double* kin, double2* out,
+                            const double* tk, const double* eps, const double* hdiag, const double* kin, double2* out,
                             int ldo, int* err, cudaStream_t s);
+// hdiag[G] = T_G + mean(V) + sum_p D_p |beta_p(G)|^2 (FP64; work: kVmeanBlocks doubles)
+constexpr int kVmeanBlocks = 256;
+qm_status hamiltonian_diag(qm_gspace g, int ik, const double* vloc, int nproj, const double2* beta, int ld_beta,
+                           const double* D, double* hdiag, double* work, cudaStream_t s);
 
 // upper bound of the split-K partial buffer any gemm_cn call needs
 size_t gemm_cn_partial_bytes(bool fp32);

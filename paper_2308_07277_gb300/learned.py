@@ -2,7 +2,8 @@
 
 For a cell's k-point: the exact lowest eigenpairs come from a tightly converged Davidson run
 (qm_davidson, FP64); Ritz pairs come from Davidson runs stopped after a few Rayleigh-Ritz steps;
-qm_mlp_pairs turns each Ritz pair into training samples (features, |r|^2, Re(conj(r) delta*))
+qm_mlp_pairs turns each Ritz pair into training samples (features x = T_G/T_n, e = eps_n/T_n,
+d = (H_GG - eps_n)/T_n with the Hamiltonian's diagonal from qm_hamiltonian_diag; |r|^2; Re(conj(r) delta*))
 against the exact correction delta*; qm_mlp_train fits the network with the library's BF16
 forward and backward kernels (full-batch Adam).  Every arithmetic step runs in libqm.so; this
 module sequences the calls and concatenates device buffers.
@@ -35,6 +36,7 @@ def collect(g, ik, vloc, beta, D, psi0, nb, snapshots=(1, 2, 3, 5, 8, 12, 18, 26
     seed the exact run (extra rows buffer the clusters at the top), the first nb rows the
     truncated runs.  Returns a list of (feats, r2, c, D, W) per snapshot."""
     dev = psi0.device
+    hd = A.qm_hamiltonian_diag(g, ik, vloc, beta, D, stream=stream)
     U = psi0.clone()
     lam, _ = A.qm_davidson(g, ik, U, vloc, beta, D, tol=exact_tol, max_iter=1000, stream=stream)
     lam_d = torch.from_numpy(lam).to(dev)
@@ -44,7 +46,7 @@ def collect(g, ik, vloc, beta, D, psi0, nb, snapshots=(1, 2, 3, 5, 8, 12, 18, 26
         eps, _ = A.qm_davidson(g, ik, X, vloc, beta, D, tol=1e-14, max_iter=int(t), raise_not_converged=False,
                                stream=stream)
         HX = A.qm_hpsi(g, ik, X, vloc, beta, D, stream=stream)
-        out.append(A.qm_mlp_pairs(g, ik, X, HX, torch.from_numpy(eps).to(dev), U, lam_d, cluster_tol,
+        out.append(A.qm_mlp_pairs(g, ik, X, HX, torch.from_numpy(eps).to(dev), hd, U, lam_d, cluster_tol,
                                   stream=stream))
     return out
 
@@ -65,24 +67,8 @@ def assemble(parts):
     return torch.from_numpy(off).to(feats.device), feats, r2, c, D, W
 
 
-# weights of the third input (log |r_G| feature) in W1[j][k], k = 2
-_W1_RESIDUAL_INPUT = slice(2, 192, 3)
-
-
-def train(dataset, theta, steps=1500, lr=1e-3, residual_feature=False, stream=None):
+def train(dataset, theta, steps=1500, lr=1e-3, stream=None):
     """Adam on theta (in place) over the whole training set (residual-share band weights);
-    returns the loss history.
-
-    residual_feature=False (default) trains without the log |r_G| input: its column of the
-    samples is zeroed and its input weights are zero afterwards.  With that input the
-    correction K(f(r)) r is a nonlinear map of the residual; measured on held-out cells, such
-    networks fit the exact corrections better sample by sample but make block Davidson
-    stagnate, while the (x, e) networks converge like TPA."""
+    returns the loss history."""
     off, feats, r2, c, D, W = dataset
-    if not residual_feature:
-        feats = feats.clone()
-        feats[:, 2] = 0.0
-    hist = A.qm_mlp_train(off, feats, r2, c, D, theta, steps, lr, W=W, stream=stream)
-    if not residual_feature:
-        theta[_W1_RESIDUAL_INPUT] = 0.0
-    return hist
+    return A.qm_mlp_train(off, feats, r2, c, D, theta, steps, lr, W=W, stream=stream)

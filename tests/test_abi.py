@@ -150,20 +150,24 @@ def test_precond_apply_errors_before_device_work():
         npw = Q.qm_gspace_query(g)["npw"][0]
         f = ctypes.c_void_p(1 << 20)      # aligned, never read
         odd = ctypes.c_void_p((1 << 20) + 8)
-        cases = [((0, -1, f, f, npw, f, 0, None, f, f, f, f), "n"),
-                 ((0, 70000, f, f, npw, f, 0, None, f, f, f, f), "n"),
-                 ((3, 2, f, f, npw, f, 0, None, f, f, f, f), "ik"),
-                 ((0, 2, f, f, npw, f, 2, None, f, f, f, f), "unknown preconditioner"),
-                 ((0, 2, f, f, npw, f, 1, None, f, f, f, f), "without parameters"),
-                 ((0, 2, None, f, npw, f, 0, None, f, f, f, f), "NULL"),
-                 ((0, 2, f, f, npw, f, 0, None, f, f, None, f), "NULL"),
-                 ((0, 2, f, f, npw - 1, f, 0, None, f, f, f, f), "ld < npw"),
-                 ((0, 2, f, odd, npw, f, 0, None, f, f, f, f), "aligned")]
+        cases = [((0, -1, f, f, npw, f, 0, None, None, f, f, f, f), "n"),
+                 ((0, 70000, f, f, npw, f, 0, None, None, f, f, f, f), "n"),
+                 ((3, 2, f, f, npw, f, 0, None, None, f, f, f, f), "ik"),
+                 ((0, 2, f, f, npw, f, 2, None, None, f, f, f, f), "unknown preconditioner"),
+                 ((0, 2, f, f, npw, f, 1, None, f, f, f, f, f), "without parameters"),
+                 ((0, 2, f, f, npw, f, 1, f, None, f, f, f, f), "H diagonal"),
+                 ((0, 2, None, f, npw, f, 0, None, None, f, f, f, f), "NULL"),
+                 ((0, 2, f, f, npw, f, 0, None, None, f, f, None, f), "NULL"),
+                 ((0, 2, f, f, npw - 1, f, 0, None, None, f, f, f, f), "ld < npw"),
+                 ((0, 2, f, odd, npw, f, 0, None, None, f, f, f, f), "aligned")]
         for args, msg in cases:
             st = lib.qm_precond_apply(g, *args, None)
             assert st == 1 and msg in Q.qm_last_error(), (args, st, Q.qm_last_error())
-        assert lib.qm_precond_apply(g, 0, 0, None, None, 0, None, 0, None, None, None, None, None, None) == 0
-        assert lib.qm_precond_apply(None, 0, 1, f, f, npw, f, 0, None, f, f, f, f, None) == 1
+        assert lib.qm_precond_apply(g, 0, 0, None, None, 0, None, 0, None, None, None, None, None, None, None) == 0
+        assert lib.qm_precond_apply(None, 0, 1, f, f, npw, f, 0, None, None, f, f, f, f, None) == 1
+        for args, msg in [((g, 3, f, 0, None, 0, None, f, None), "ik"), ((g, 0, None, 0, None, 0, None, f, None), "NULL"),
+                          ((g, 0, f, 4, None, npw, f, f, None), "NULL"), ((g, 0, f, 4, f, npw - 1, f, f, None), "ld_beta")]:
+            assert lib.qm_hamiltonian_diag(*args) == 1 and msg in Q.qm_last_error(), (args, Q.qm_last_error())
     finally:
         Q.qm_gspace_destroy(g)
 

@@ -97,7 +97,7 @@ def test_snapshot_weights_are_residual_shares():
     res[1] *= 3.0
     dstar = rng.normal(size=(nb, npw)) + 1j * rng.normal(size=(nb, npw))
     dstar[3] = 0.0                                        # dropped band: no weight
-    *_, D, W = M.samples(kin, psi, res, rng.normal(size=nb), dstar)
+    *_, D, W = M.samples(kin, psi, res, rng.normal(size=nb), dstar, kin + 0.3)
     rn2 = (np.abs(res) ** 2).sum(axis=1)
     assert W[3] == 0.0 and abs(W.sum() - 1.0) < 1e-15
     assert np.allclose(W[:3], rn2[:3] / rn2[:3].sum(), rtol=1e-15)
@@ -123,18 +123,34 @@ def test_features_are_scale_free_and_x_is_one_on_a_single_wave():
     rng = np.random.default_rng(5)
     nb, npw = 2, 30
     kin = rng.uniform(0, 5, npw)
+    hd = kin + rng.uniform(-1, 2, npw)
     psi = rng.normal(size=(nb, npw)) + 1j * rng.normal(size=(nb, npw))
-    res = rng.normal(size=(nb, npw)) + 1j * rng.normal(size=(nb, npw))
-    res[0, 3] = 0.0
     eps = np.array([-0.3, 0.4])
-    F = M.features(kin, psi, res, eps)
-    F2 = M.features(kin, 3.0 * psi, (2 - 1j) * res, eps)
+    F = M.features(kin, psi, eps, hd)
+    F2 = M.features(kin, (3.0 - 2j) * psi, eps, hd)
     assert np.allclose(F, F2, rtol=1e-13, atol=1e-13)
-    assert F[3, 2] == math.log(M.FEAT_LOG_FLOOR)         # zero residual component: floored log
     one = np.zeros((1, npw), complex)
     one[0, 7] = 2.0
-    Fo = M.features(kin, one, res[:1], eps[:1])
+    Fo = M.features(kin, one, eps[:1], hd)
+    # a single plane wave: T_n = T_7, so x = 1 there, e = eps / T_7, d = (H_GG - eps) / T_7
     assert abs(Fo[7, 0] - 1.0) < 1e-15 and abs(Fo[0, 1] - eps[0] / kin[7]) < 1e-15
+    assert np.allclose(Fo[:, 2], (hd - eps[0]) / kin[7], rtol=1e-15, atol=0)
+
+
+def test_hamiltonian_diagonal_is_the_dense_diagonal():
+    """H_GG of the feature equals the diagonal of the brute-force H_GG' (Eq. KSHamMat with the
+    KB term), with and without projectors, and a constant V0 shifts it by V0."""
+    cell = S.cubic_si8(10.0, nbnd=4, kpts=[[0.25, -0.25, 0.25]])
+    c = make_case(cell, 0)
+    H = OH.dense_h(c["gs"], c["v"], c["beta"], c["D"])
+    hd = M.hamiltonian_diagonal(c["gs"]["kin"], c["v"], c["beta"], c["D"])
+    np.testing.assert_allclose(hd, np.diag(H).real, rtol=0, atol=1e-12 * np.abs(hd).max())
+    assert np.abs(np.diag(H).imag).max() < 1e-14
+    H0 = OH.dense_h(c["gs"], c["v"], None, None)
+    np.testing.assert_allclose(M.hamiltonian_diagonal(c["gs"]["kin"], c["v"], None, None), np.diag(H0).real,
+                               rtol=0, atol=1e-12 * np.abs(hd).max())
+    np.testing.assert_allclose(M.hamiltonian_diagonal(c["gs"]["kin"], c["v"] + 0.7, None, None),
+                               np.diag(H0).real + 0.7, rtol=0, atol=1e-12 * np.abs(hd).max())
 
 
 def test_exact_correction_lands_in_the_eigenspace():

@@ -43,7 +43,7 @@ def oracle_inputs(cell, ik, nb):
     return c, X, HX, eps
 
 
-def run_gpu(Q, cell, ik, X, HX, eps, mlp=None, ld_pad=0):
+def run_gpu(Q, cell, ik, X, HX, eps, mlp=None, ld_pad=0, hdiag=None):
     g = Q.qm_gspace_create(cell.lattice, cell.kpts, cell.ecut_ha, cell.grid)
     try:
         n, npw = X.shape
@@ -52,7 +52,8 @@ def run_gpu(Q, cell, ik, X, HX, eps, mlp=None, ld_pad=0):
         Xd[:, :npw] = torch.from_numpy(X).cuda()
         HXd[:, :npw] = torch.from_numpy(HX).cuda()
         th = None if mlp is None else torch.from_numpy(np.asarray(mlp, np.float32)).cuda()
-        R, d, rn2, tk = Q.qm_precond_apply(g, ik, Xd, HXd, torch.from_numpy(eps).cuda(), mlp=th)
+        hd = None if hdiag is None else torch.from_numpy(hdiag).cuda()
+        R, d, rn2, tk = Q.qm_precond_apply(g, ik, Xd, HXd, torch.from_numpy(eps).cuda(), mlp=th, hdiag=hd)
         torch.cuda.synchronize()
         return (R[:, :npw].cpu().numpy(), d[:, :npw].cpu().numpy(), rn2.cpu().numpy(), tk.cpu().numpy())
     finally:
@@ -91,10 +92,11 @@ def test_learned_correction_matches_oracle(Q, cellf, ik, nb):
     cell = cellf()
     c, X, HX, eps = oracle_inputs(cell, ik, nb)
     th = rand_theta(7)
-    R, d, rn2, tk = run_gpu(Q, cell, ik, X, HX, eps, mlp=th)
     kin = c["gs"]["kin"]
+    hd = M.hamiltonian_diagonal(kin, c["v"], c["beta"], c["D"])
+    R, d, rn2, tk = run_gpu(Q, cell, ik, X, HX, eps, mlp=th, hdiag=hd)
     r_o = HX - eps[:, None] * X
-    F = M.features(kin, X, r_o, eps)
+    F = M.features(kin, X, eps, hd)
     Ke = forward_bf16(th, F).reshape(r_o.shape)
     Ko = M.forward(th, F)[0].reshape(r_o.shape)
     nz = np.abs(r_o) > 0
@@ -113,5 +115,23 @@ def test_zero_bands_is_a_noop(Q):
         e = torch.zeros((0, 411), dtype=torch.complex128, device="cuda")
         R, d, rn2, tk = Q.qm_precond_apply(g, 0, e, e, torch.zeros(0, dtype=torch.float64, device="cuda"))
         assert R.shape == (0, 411) and d.shape == (0, 411)
+    finally:
+        Q.qm_gspace_destroy(g)
+
+
+@pytest.mark.parametrize("cellf,ik", [(S.config1, 0), (S.config2, 1)], ids=["cfg1", "cfg2_k1"])
+def test_hamiltonian_diagonal_matches_oracle(Q, cellf, ik):
+    """qm_hamiltonian_diag (the third feature's H_GG) against the oracle's diagonal, which is
+    pinned to the brute-force H_GG'; with and without projectors."""
+    cell = cellf()
+    c = make_case(cell, ik, nb=1)
+    kin = c["gs"]["kin"]
+    g = Q.qm_gspace_create(cell.lattice, cell.kpts, cell.ecut_ha, cell.grid)
+    try:
+        v, beta, D = (torch.from_numpy(a).cuda() for a in (c["v"], c["beta"], c["D"]))
+        for b, dd in ((beta, D), (None, None)):
+            got = Q.qm_hamiltonian_diag(g, ik, v, b, dd).cpu().numpy()
+            want = M.hamiltonian_diagonal(kin, c["v"], None if b is None else c["beta"], None if b is None else c["D"])
+            np.testing.assert_allclose(got, want, rtol=1e-13, atol=1e-13 * np.abs(want).max())
     finally:
         Q.qm_gspace_destroy(g)
