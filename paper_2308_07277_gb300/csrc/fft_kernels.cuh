@@ -413,6 +413,284 @@ __device__ void fft_z_vmul(C* buf, int ldy, int ncol, const int* cmap, int nv, c
     fft_lines<C, -1, false, true>(buf, ldy, 1, ncol, cmap, pz, tw, tid, nt);
 }
 
+// ---------------------------------------------------------------- two register passes per 1D FFT
+// The stages of a compile-time plan are split after stage K: stages [0, K) act on strided groups
+// of a line (the thread with offset n < MB holds x[n + m MB], m < N/MB, MB = L[K] = the block
+// length of stage K) and stages [K, nst) on contiguous sub-blocks of MB elements.  Each group is
+// loaded into registers once, all its stages run there, and it is stored once: two passes
+// through shared memory per 1D transform instead of one per stage.  The butterflies, twiddles
+// and their order are those of the one-stage-per-pass code above, so the results are identical
+// (DIF: natural order in, digit-reversed out; DIT the reverse).  K minimises the larger group.
+constexpr int fused_split(int n) {
+    CPlan p = make_cplan(n);
+    int best = p.nst, bestv = n;
+    for (int k = 1; k <= p.nst; ++k) {
+        const int mb = k < p.nst ? p.L[k] : 1;
+        const int v = (n / mb > mb) ? n / mb : mb;
+        if (v < bestv) {
+            bestv = v;
+            best = k;
+        }
+    }
+    return best;
+}
+template <int N> struct Fused {
+    static constexpr CPlan P = make_cplan(N);
+    static constexpr int K = fused_split(N);
+    static constexpr int MB = K < P.nst ? P.L[K] : 1;  // contiguous sub-block length
+    static constexpr int NA = N / MB;                   // elements of a strided group
+    static constexpr bool ok = (NA > MB ? NA : MB) <= 18;  // register budget of a group
+};
+
+// stage S on a strided group u[m] = x[n + m MB] (S < K)
+template <class C, int SG, bool DIF, int N, int S>
+__device__ __forceinline__ void stage_strided(C* u, int n, const C* tw) {
+    constexpr CPlan P = make_cplan(N);
+    constexpr int MB = Fused<N>::MB;
+    constexpr int R = P.r[S], L = P.L[S], M = L / R, STEP = N / L;
+#pragma unroll
+    for (int blk = 0; blk < N / L; ++blk) {
+#pragma unroll
+        for (int q = 0; q < M / MB; ++q) {
+            C v[R];
+#pragma unroll
+            for (int j = 0; j < R; ++j) v[j] = u[blk * (L / MB) + q + j * (M / MB)];
+            const int n1 = n + q * MB;
+            if (DIF) {
+                Dft<C, SG, R>::run(v);
+                if constexpr (M > 1) {
+#pragma unroll
+                    for (int k2 = 1; k2 < R; ++k2) v[k2] = cmul(v[k2], twid<C, SG>(tw, n1 * k2 * STEP));
+                }
+            } else {
+                if constexpr (M > 1) {
+#pragma unroll
+                    for (int k2 = 1; k2 < R; ++k2) v[k2] = cmul(v[k2], twid<C, SG>(tw, n1 * k2 * STEP));
+                }
+                Dft<C, SG, R>::run(v);
+            }
+#pragma unroll
+            for (int j = 0; j < R; ++j) u[blk * (L / MB) + q + j * (M / MB)] = v[j];
+        }
+    }
+}
+
+// stage S on a contiguous sub-block u[i] = x[b MB + i] (S >= K): every index is a constant
+template <class C, int SG, bool DIF, int N, int S>
+__device__ __forceinline__ void stage_block(C* u, const C* tw) {
+    constexpr CPlan P = make_cplan(N);
+    constexpr int MB = Fused<N>::MB;
+    constexpr int R = P.r[S], L = P.L[S], M = L / R, STEP = N / L;
+#pragma unroll
+    for (int blk = 0; blk < MB / L; ++blk) {
+#pragma unroll
+        for (int n1 = 0; n1 < M; ++n1) {
+            C v[R];
+#pragma unroll
+            for (int j = 0; j < R; ++j) v[j] = u[blk * L + n1 + j * M];
+            if (DIF) {
+                Dft<C, SG, R>::run(v);
+                if constexpr (M > 1) {
+#pragma unroll
+                    for (int k2 = 1; k2 < R; ++k2) v[k2] = cmul(v[k2], twid<C, SG>(tw, n1 * k2 * STEP));
+                }
+            } else {
+                if constexpr (M > 1) {
+#pragma unroll
+                    for (int k2 = 1; k2 < R; ++k2) v[k2] = cmul(v[k2], twid<C, SG>(tw, n1 * k2 * STEP));
+                }
+                Dft<C, SG, R>::run(v);
+            }
+#pragma unroll
+            for (int j = 0; j < R; ++j) u[blk * L + n1 + j * M] = v[j];
+        }
+    }
+}
+
+// stages of a group in plan order: DIF S = S0, S0+1, ..., S1-1; DIT S = S1-1, ..., S0
+template <class C, int SG, bool DIF, int N, int S, int S1>
+__device__ __forceinline__ void strided_stages(C* u, int n, const C* tw) {
+    if constexpr (S < S1) {
+        if constexpr (DIF) {
+            stage_strided<C, SG, true, N, S>(u, n, tw);
+            strided_stages<C, SG, true, N, S + 1, S1>(u, n, tw);
+        } else {
+            strided_stages<C, SG, false, N, S + 1, S1>(u, n, tw);
+            stage_strided<C, SG, false, N, S>(u, n, tw);
+        }
+    }
+}
+template <class C, int SG, bool DIF, int N, int S, int S1>
+__device__ __forceinline__ void block_stages(C* u, const C* tw) {
+    if constexpr (S < S1) {
+        if constexpr (DIF) {
+            stage_block<C, SG, true, N, S>(u, tw);
+            block_stages<C, SG, true, N, S + 1, S1>(u, tw);
+        } else {
+            block_stages<C, SG, false, N, S + 1, S1>(u, tw);
+            stage_block<C, SG, false, N, S>(u, tw);
+        }
+    }
+}
+
+// item t of a pass over nlines lines with G groups each -> (line, group): column passes
+// (LINE_FAST) put consecutive lines on consecutive threads, row passes consecutive groups
+template <bool LINE_FAST>
+__device__ __forceinline__ void item_of(int t, int nlines, int G, RDiv dl, int& line, int& grp) {
+    if (LINE_FAST) {
+        grp = dl.div(t);
+        line = t - grp * nlines;
+    } else {
+        line = t / G;
+        grp = t - line * G;
+    }
+}
+
+// pass over the strided groups of nlines lines (stages [0, K)); ends with __syncthreads()
+template <class C, int SG, bool DIF, bool LINE_FAST, int N>
+__device__ __forceinline__ void pass_strided(C* buf, int es, int ls, int nlines, const int* lmap, const C* tw, int tid,
+                                             int nt) {
+    using F = Fused<N>;
+    RDiv dl{nlines, 1.0f / (float)nlines};
+    for (int t = tid; t < nlines * F::MB; t += nt) {
+        int line, n;
+        item_of<LINE_FAST>(t, nlines, F::MB, dl, line, n);
+        C* p = buf + (lmap ? lmap[line] : line) * ls + n * es;
+        C u[F::NA];
+#pragma unroll
+        for (int m = 0; m < F::NA; ++m) u[m] = p[m * F::MB * es];
+        strided_stages<C, SG, DIF, N, 0, F::K>(u, n, tw);
+#pragma unroll
+        for (int m = 0; m < F::NA; ++m) p[m * F::MB * es] = u[m];
+    }
+    __syncthreads();
+}
+
+// pass over the contiguous sub-blocks of nlines lines (stages [K, nst)); ends with __syncthreads()
+template <class C, int SG, bool DIF, bool LINE_FAST, int N>
+__device__ __forceinline__ void pass_block(C* buf, int es, int ls, int nlines, const int* lmap, const C* tw, int tid,
+                                           int nt) {
+    using F = Fused<N>;
+    if constexpr (F::K < F::P.nst) {
+        RDiv dl{nlines, 1.0f / (float)nlines};
+        for (int t = tid; t < nlines * F::NA; t += nt) {
+            int line, b;
+            item_of<LINE_FAST>(t, nlines, F::NA, dl, line, b);
+            C* p = buf + (lmap ? lmap[line] : line) * ls + b * F::MB * es;
+            C u[F::MB];
+#pragma unroll
+            for (int i = 0; i < F::MB; ++i) u[i] = p[i * es];
+            block_stages<C, SG, DIF, N, F::K, F::P.nst>(u, tw);
+#pragma unroll
+            for (int i = 0; i < F::MB; ++i) p[i * es] = u[i];
+        }
+        __syncthreads();
+    }
+}
+
+// full 1D transform of nlines lines in two register passes; ends with __syncthreads()
+template <class C, int SG, bool DIF, bool LINE_FAST, int N>
+__device__ __forceinline__ void fft2_lines_ct(C* buf, int es, int ls, int nlines, const int* lmap, const C* tw,
+                                              int tid, int nt) {
+    if (DIF) {
+        pass_strided<C, SG, true, LINE_FAST, N>(buf, es, ls, nlines, lmap, tw, tid, nt);
+        pass_block<C, SG, true, LINE_FAST, N>(buf, es, ls, nlines, lmap, tw, tid, nt);
+    } else {
+        pass_block<C, SG, false, LINE_FAST, N>(buf, es, ls, nlines, lmap, tw, tid, nt);
+        pass_strided<C, SG, false, LINE_FAST, N>(buf, es, ls, nlines, lmap, tw, tid, nt);
+    }
+}
+
+// z transforms of the ncol columns of one plane (natural column order, column l at buf + l,
+// element z at z * ldy) with the V multiply between the inverse and forward transforms:
+// inverse strided pass, one register pass of [inverse inner stages, x V(z), forward inner
+// stages] per sub-block, forward strided pass (a single register pass when the plan has no
+// sub-blocks).  V of (z position p, column l) is v[p * ldv + l], read through L2.
+template <class C, class R, int N>
+__device__ __forceinline__ void fft2_z_vmul_ct(C* buf, int ldy, int ncol, const R* __restrict__ v, int ldv,
+                                               const C* tw, int tid, int nt) {
+    using F = Fused<N>;
+    RDiv dl{ncol, 1.0f / (float)ncol};
+    if constexpr (F::K < F::P.nst) {
+        pass_strided<C, +1, true, true, N>(buf, ldy, 1, ncol, nullptr, tw, tid, nt);
+        for (int t = tid; t < ncol * F::NA; t += nt) {
+            int col, b;
+            item_of<true>(t, ncol, F::NA, dl, col, b);
+            C* p = buf + col + b * F::MB * ldy;
+            const R* vv = v + col + b * F::MB * ldv;
+            C u[F::MB];
+#pragma unroll
+            for (int i = 0; i < F::MB; ++i) u[i] = p[i * ldy];
+            block_stages<C, +1, true, N, F::K, F::P.nst>(u, tw);
+#pragma unroll
+            for (int i = 0; i < F::MB; ++i) {
+                const R sc = __ldcg(vv + i * ldv);
+                u[i] = mk<C>(u[i].x * sc, u[i].y * sc);
+            }
+            block_stages<C, -1, false, N, F::K, F::P.nst>(u, tw);
+#pragma unroll
+            for (int i = 0; i < F::MB; ++i) p[i * ldy] = u[i];
+        }
+        __syncthreads();
+        pass_strided<C, -1, false, true, N>(buf, ldy, 1, ncol, nullptr, tw, tid, nt);
+    } else {  // one group holds the whole column
+        for (int col = tid; col < ncol; col += nt) {
+            C* p = buf + col;
+            C u[N];
+#pragma unroll
+            for (int m = 0; m < N; ++m) u[m] = p[m * ldy];
+            strided_stages<C, +1, true, N, 0, F::K>(u, 0, tw);
+#pragma unroll
+            for (int m = 0; m < N; ++m) {
+                const R sc = __ldcg(v + col + m * ldv);
+                u[m] = mk<C>(u[m].x * sc, u[m].y * sc);
+            }
+            strided_stages<C, -1, false, N, 0, F::K>(u, 0, tw);
+#pragma unroll
+            for (int m = 0; m < N; ++m) p[m * ldy] = u[m];
+        }
+        __syncthreads();
+    }
+}
+
+// dispatch: two-pass register transforms for the lengths whose groups fit the register
+// budget, the stage-per-pass code otherwise (both end with __syncthreads())
+template <class C, int SG, bool DIF, bool LINE_FAST>
+__device__ void fft2_lines(C* buf, int es, int ls, int nlines, const int* lmap, const AxisPlan& pl, const C* tw,
+                           int tid, int nt) {
+    switch (pl.n) {
+#define QM_CASE(n)                                                                                \
+    case n:                                                                                       \
+        if constexpr (Fused<n>::ok) {                                                             \
+            fft2_lines_ct<C, SG, DIF, LINE_FAST, n>(buf, es, ls, nlines, lmap, tw, tid, nt);      \
+            return;                                                                               \
+        }                                                                                         \
+        break;
+        QM_FFT_LENGTHS(QM_CASE)
+#undef QM_CASE
+        default: break;
+    }
+    fft_lines<C, SG, DIF, LINE_FAST>(buf, es, ls, nlines, lmap, pl, tw, tid, nt);
+}
+
+template <class C, class R>
+__device__ void fft2_z_vmul(C* buf, int ldy, int ncol, const R* __restrict__ v, int ldv, const AxisPlan& pz,
+                            const C* tw, int tid, int nt) {
+    switch (pz.n) {
+#define QM_CASE(n)                                                       \
+    case n:                                                              \
+        if constexpr (Fused<n>::ok) {                                    \
+            fft2_z_vmul_ct<C, R, n>(buf, ldy, ncol, v, ldv, tw, tid, nt); \
+            return;                                                      \
+        }                                                                \
+        break;
+        QM_FFT_LENGTHS(QM_CASE)
+#undef QM_CASE
+        default: break;
+    }
+    fft_z_vmul<C, R>(buf, ldy, ncol, nullptr, ncol, v, ldv, pz, tw, tid, nt);
+}
+
 // x sticks per CTA of the stick kernels: 64 in FP32 (19 KB of lines), 32 in FP64
 template <class R> constexpr int sticks_per_cta() { return sizeof(R) == 4 ? 64 : 32; }
 constexpr int kThreads = 256;
@@ -442,7 +720,7 @@ k_stick_inverse(const typename Cx<R>::T* __restrict__ psi, int ld_psi, const int
         lines[(c.x - s0) * ldx + c.y] = src[g];
     }
     __syncthreads();
-    fft_lines<C, +1, true, false>(lines, 1, ldx, ns, nullptr, px, tw, tid, nt);
+    fft2_lines<C, +1, true, false>(lines, 1, ldx, ns, nullptr, px, tw, tid, nt);
     C* dst = T + (size_t)b * N1 * nstick_pad + s0;
     for (int i = tid; i < N1 * ns; i += nt) {
         int p = i / ns, l = i - p * ns;
@@ -452,7 +730,7 @@ k_stick_inverse(const typename Cx<R>::T* __restrict__ psi, int ld_psi, const int
 
 // ---------------------------------------------------------------- K2
 template <class R>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 3)
 k_plane(typename Cx<R>::T* __restrict__ T, int nstick, int nstick_pad, const int* __restrict__ stick_plane,
         const int* __restrict__ rows, int nrow, AxisPlan py, AxisPlan pz,
         const typename Cx<R>::T* __restrict__ tw_y, const typename Cx<R>::T* __restrict__ tw_z, int ldy,
@@ -474,9 +752,9 @@ k_plane(typename Cx<R>::T* __restrict__ T, int nstick, int nstick_pad, const int
     __syncthreads();
     // inverse y on the active rows; z on every column: inverse, V(r)/N_r (in the permuted,
     // digit-reversed order of all three axes), forward; forward y on the active rows
-    fft_lines<C, +1, true, false>(plane, 1, ldy, nrow, rows, py, twy, tid, nt);
-    fft_z_vmul<C, R>(plane, ldy, N2, nullptr, N2, Vt + (size_t)p1 * N3 * N2, N2, pz, twz, tid, nt);
-    fft_lines<C, -1, false, false>(plane, 1, ldy, nrow, rows, py, twy, tid, nt);
+    fft2_lines<C, +1, true, false>(plane, 1, ldy, nrow, rows, py, twy, tid, nt);
+    fft2_z_vmul<C, R>(plane, ldy, N2, Vt + (size_t)p1 * N3 * N2, N2, pz, twz, tid, nt);
+    fft2_lines<C, -1, false, false>(plane, 1, ldy, nrow, rows, py, twy, tid, nt);
     for (int s = tid; s < nstick; s += nt) Tp[s] = plane[__ldg(stick_plane + s)];
 }
 
@@ -504,7 +782,7 @@ k_stick_forward(const typename Cx<R>::T* __restrict__ T, int nstick, int nstick_
         lines[l * ldx + p] = srcT[(size_t)p * nstick_pad + l];
     }
     __syncthreads();
-    fft_lines<C, -1, false, false>(lines, 1, ldx, ns, nullptr, px, tw, tid, nt);
+    fft2_lines<C, -1, false, false>(lines, 1, ldx, ns, nullptr, px, tw, tid, nt);
     const int gb = __ldg(stick_g0 + s0), ge = __ldg(stick_g0 + s0 + ns);
     const C* ps = psi + (size_t)b * ld_psi;
     C* po = out + (size_t)b * ld_out;
