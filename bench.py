@@ -60,9 +60,11 @@ def parse():
     ap.add_argument("--davidson-tol", type=float, default=1e-8)
     ap.add_argument("--batched", type=int, default=1, help="also time the batched form (0: skip)")
     ap.add_argument("--large", type=int, default=1, help="also time H psi on the 216- and 255-atom cells (0: skip)")
+    ap.add_argument("--davidson-255", type=int, default=1,
+                    help="time Davidson on the 255-atom cell, k-point 0: the combined form vs plain FP64 (about 4 "
+                         "minutes; 0: skip)")
     ap.add_argument("--davidson-large", type=int, default=0,
-                    help="1: also time Davidson on the 216-atom cell (learned vs TPA) and the 255-atom cell (all "
-                         "forms combined vs plain FP64); several minutes")
+                    help="1: also time Davidson on the 216-atom cell, learned vs TPA (about 2 minutes)")
     return ap.parse_args()
 
 
@@ -383,8 +385,8 @@ def measure_hpsi(steps, warmup, Q, lib, g, cell, wl, v, D, world, dev, peaks, sa
 def run_davidson(args, Q, lib, g, cell, wl64, v, D):
     """Block Davidson to args.davidson_tol at every k-point from the seeded random start:
     the plain FP64 form, FP64 with 10 % buffer bands (only the lowest 160 must converge), the
-    precision form (QM_MIXED) without and with the buffer bands, and the buffered precision form
-    with the 4 k-point solves run concurrently (qm_davidson_batched).  Wall time of the calls."""
+    precision form (QM_MIXED) with the buffer bands, and the same with the 4 k-point solves run
+    concurrently (qm_davidson_batched).  Wall time of the calls."""
     import numpy as np
     import torch
 
@@ -393,8 +395,7 @@ def run_davidson(args, Q, lib, g, cell, wl64, v, D):
     out = {"tol_ha": args.davidson_tol, "nbnd": nb, "nk": nk}
     eigs = {}
     nextra = max(1, nb // 10)
-    for form, prec, extra in (("fp64", "fp64", 0), ("fp64_buffer", "fp64", nextra), ("mixed", "mixed", 0),
-                              ("mixed_buffer", "mixed", nextra)):
+    for form, prec, extra in (("fp64", "fp64", 0), ("fp64_buffer", "fp64", nextra), ("mixed_buffer", "mixed", nextra)):
         per_k = []
         lib.qm_prof_enable(1)
         torch.cuda.synchronize()
@@ -432,7 +433,7 @@ def run_davidson(args, Q, lib, g, cell, wl64, v, D):
         "kernels": read_prof(lib)}
     lib.qm_prof_enable(0)
     eigs["mixed_buffer_batched"] = [eig[:nb] for eig, _ in res]
-    for form in ("fp64_buffer", "mixed", "mixed_buffer", "mixed_buffer_batched"):
+    for form in ("fp64_buffer", "mixed_buffer", "mixed_buffer_batched"):
         out[f"speedup_{form}_vs_fp64"] = out["fp64"]["seconds_total"] / out[form]["seconds_total"]
         out[f"max_eig_diff_{form}_vs_fp64_ha"] = float(max(np.abs(a - b).max()
                                                          for a, b in zip(eigs["fp64"], eigs[form])))
@@ -592,17 +593,11 @@ def train_network(Q, S, dev):
                    "loss_last": float(hist[-1]), "seconds": time.time() - t0}
 
 
-def run_davidson_large(args, Q, S, dev):
+def run_davidson_large(args, Q, S, dev, theta):
     """Davidson to 1e-8 Ha on the learned-form workload (216-atom cell, 480 bands, Gamma;
-    precision form with 10 % buffer bands, TPA vs the trained network) and the combined
-    workload (255-atom cell, 288 bands, 4 k: plain FP64 one k-point after another vs the
-    precision form with buffer bands, the learned preconditioner and the 4 k-points solved
-    concurrently)."""
+    precision form with 10 % buffer bands, TPA vs the trained network)."""
     import numpy as np
     import torch
-    theta, tinfo = train_network(Q, S, dev)
-    out = {"training": tinfo}
-    # learned-form workload
     cell = S.config4()
     g = Q.GSpace(cell.lattice, cell.kpts, cell.ecut_ha, cell.grid)
     _, _, kpg = g.indices(0)
@@ -610,8 +605,7 @@ def run_davidson_large(args, Q, S, dev):
     beta = torch.from_numpy(S.beta_of_q(kpg, cell.tau, cell.omega)).to(dev)
     D = torch.from_numpy(S.dvals(cell.nat)).to(dev)
     nb, nextra = cell.nbnd, cell.nbnd // 10
-    rec = {}
-    eigs = {}
+    rec, eigs = {}, {}
     for name, mlp in (("tpa", None), ("learned", theta)):
         p = torch.from_numpy(S.psi_random(cell.seed, nb + nextra, g.npw[0], stream=0)).to(dev)
         torch.cuda.synchronize()
@@ -623,11 +617,17 @@ def run_davidson_large(args, Q, S, dev):
             "iterations", "iterations_mixed", "band_applies", "converged", "max_residual", "precond_fallback")}}
         eigs[name] = eig[:nb]
     rec["max_eig_diff_ha"] = float(np.abs(eigs["tpa"] - eigs["learned"]).max())
-    out[cell.name] = rec
-    del beta, p
     g.close()
-    torch.cuda.empty_cache()
-    # combined workload
+    return {cell.name: rec}
+
+
+def run_davidson_255(args, Q, S, dev, theta):
+    """The all-forms workload: Davidson to 1e-8 Ha on the 255-atom cell (96x96x48, 288 bands,
+    1020 projectors).  k-point 0: plain FP64 (no buffer bands) against the combined form
+    (precision form + 28 buffer bands + the learned preconditioner); then the combined form on
+    all 4 k-points solved concurrently (qm_davidson_batched).  Wall time of the calls."""
+    import numpy as np
+    import torch
     cell = S.config5()
     g = Q.GSpace(cell.lattice, cell.kpts, cell.ecut_ha, cell.grid)
     v = torch.from_numpy(S.vloc_on_grid(cell.lattice, cell.tau, cell.grid)).to(dev)
@@ -637,33 +637,33 @@ def run_davidson_large(args, Q, S, dev):
     for ik in range(nk):
         _, _, kpg = g.indices(ik)
         betas.append(torch.from_numpy(S.beta_of_q(kpg, cell.tau, cell.omega)).to(dev))
-    rec = {}
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    e64, its = [], []
-    for ik in range(nk):
-        p = torch.from_numpy(S.psi_random(cell.seed, nb, g.npw[ik], stream=ik)).to(dev)
-        eig, info = Q.qm_davidson(g.handle, ik, p, v, betas[ik], D, tol=args.davidson_tol, max_iter=300,
-                                  prec="fp64", raise_not_converged=False)
-        e64.append(eig)
-        its.append((info["iterations"], info["converged"]))
+    out, eigs = {"tol_ha": args.davidson_tol, "nbnd": nb}, {}
+    for name, prec, extra, mlp in (("fp64", "fp64", 0, None), ("combined", "mixed", nextra, theta)):
+        p = torch.from_numpy(S.psi_random(cell.seed, nb + extra, g.npw[0], stream=0)).to(dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        eig, info = Q.qm_davidson(g.handle, 0, p, v, betas[0], D, tol=args.davidson_tol, max_iter=400, prec=prec,
+                                  nconv=nb, mlp=mlp, raise_not_converged=False)
+        torch.cuda.synchronize()
+        out[f"k0_{name}"] = {"seconds": time.perf_counter() - t0, **{k: info[k] for k in (
+            "iterations", "iterations_mixed", "band_applies", "converged", "max_residual", "restarts",
+            "precond_fallback")}}
+        eigs[name] = eig[:nb]
         del p
-    torch.cuda.synchronize()
-    rec["fp64"] = {"seconds": time.perf_counter() - t0, "iterations_converged": its}
+    out["k0_speedup_combined_vs_fp64"] = out["k0_fp64"]["seconds"] / out["k0_combined"]["seconds"]
+    out["k0_max_eig_diff_ha"] = float(np.abs(eigs["fp64"] - eigs["combined"]).max())
     jobs = [{"g": g.handle, "ik": ik, "vloc": v, "beta": betas[ik], "D": D,
              "psi": torch.from_numpy(S.psi_random(cell.seed, nb + nextra, g.npw[ik], stream=ik)).to(dev)}
             for ik in range(nk)]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    res = Q.qm_davidson_batched(jobs, tol=args.davidson_tol, max_iter=300, prec="mixed", nconv=nb, mlp=theta,
+    res = Q.qm_davidson_batched(jobs, tol=args.davidson_tol, max_iter=400, prec="mixed", nconv=nb, mlp=theta,
                                 raise_not_converged=False)
     torch.cuda.synchronize()
-    rec["combined"] = {"seconds": time.perf_counter() - t0,
-                       "iterations_converged": [(i["iterations"], i["converged"]) for _, i in res],
-                       "precond_fallback": [i["precond_fallback"] for _, i in res]}
-    rec["speedup_combined_vs_fp64"] = rec["fp64"]["seconds"] / rec["combined"]["seconds"]
-    rec["max_eig_diff_ha"] = float(max(np.abs(a - e[:nb]).max() for a, (e, _) in zip(e64, res)))
-    out[cell.name] = rec
+    out["all_k_combined_concurrent"] = {
+        "seconds": time.perf_counter() - t0,
+        "per_k": [{k: i[k] for k in ("iterations", "converged", "max_residual", "precond_fallback")} for _, i in res],
+        "k0_max_eig_diff_vs_fp64_ha": float(np.abs(res[0][0][:nb] - eigs["fp64"]).max())}
     g.close()
     return out
 
@@ -732,7 +732,9 @@ def run_ours(args):
     torch.cuda.empty_cache()
     batched = run_batched(args, Q, S, dev) if args.batched else None
     large = run_large_cells(args, Q, S, dev) if args.large else None
-    dav_large = run_davidson_large(args, Q, S, dev) if args.davidson_large else None
+    theta, tinfo = train_network(Q, S, dev) if (args.davidson_large or args.davidson_255) else (None, None)
+    dav255 = run_davidson_255(args, Q, S, dev, theta) if args.davidson_255 else None
+    dav_large = run_davidson_large(args, Q, S, dev, theta) if args.davidson_large else None
     if rank == 0:
         head = forms["mixed"]
         keep = ("value", "ms_per_step", "steps", "roofline", "roofline_other", "kernels", "gpu_launches")
@@ -757,9 +759,11 @@ def run_ours(args):
                             "fp64": {k: forms2["fp64"][k] for k in keep},
                             "mixed_over_fp64": forms2["mixed"]["value"] / forms2["fp64"]["value"]},
                 "davidson": dav,
+                "davidson_255_atoms": dav255,
+                "learned_training": tinfo,
                 "batched": batched,
                 "large_cells": large,
-                "davidson_large": dav_large,
+                "davidson_216_atoms_learned": dav_large,
                 "cpu_baseline": oracle_sample("config5", args.cpu_sample_bands)}
         print(json.dumps(line))
     if world > 1:

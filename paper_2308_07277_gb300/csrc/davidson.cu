@@ -756,7 +756,9 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
         }
         if (it == o.max_iter) break;
         const int nu = (int)unc.size();
-        cudaMemcpyAsync(w.sel, unc.data(), sizeof(int) * nu, cudaMemcpyHostToDevice, s);
+        if ((st = cuda_check(cudaMemcpyAsync(w.sel, unc.data(), sizeof(int) * nu, cudaMemcpyHostToDevice, s),
+                             "H2D unconverged bands")))
+            return st;
         if (use_mlp) {
             if ((st = mlp_precond_apply(o.mlp, w.R, ld, npw, w.sel, nu, w.tk, w.eps, w.hdiag, kin, w.Dl, ld, mlp_err, s)))
                 return st;

@@ -439,7 +439,8 @@ template <int N> struct Fused {
     static constexpr int K = fused_split(N);
     static constexpr int MB = K < P.nst ? P.L[K] : 1;  // contiguous sub-block length
     static constexpr int NA = N / MB;                   // elements of a strided group
-    static constexpr bool ok = (NA > MB ? NA : MB) <= 18;  // register budget of a group
+    // used where it saves passes (plans of three or more stages) and a group fits the register budget
+    static constexpr bool ok = P.nst >= 3 && (NA > MB ? NA : MB) <= 18;
 };
 
 // stage S on a strided group u[m] = x[n + m MB] (S < K)
@@ -533,17 +534,16 @@ __device__ __forceinline__ void block_stages(C* u, const C* tw) {
     }
 }
 
-// item t of a pass over nlines lines with G groups each -> (line, group): column passes
-// (LINE_FAST) put consecutive lines on consecutive threads, row passes consecutive groups
+// item t of a pass over nlines lines with G groups each -> (line, group).  Consecutive threads
+// take the same group of consecutive lines, so a warp's accesses step by the line stride: one
+// element apart in column passes, an odd padded row length apart in row passes (ldx, ldy are
+// odd), i.e. free of shared-memory bank conflicts either way; a thread's group itself (strided
+// or contiguous) never shares a warp access with its neighbours' elements.
 template <bool LINE_FAST>
 __device__ __forceinline__ void item_of(int t, int nlines, int G, RDiv dl, int& line, int& grp) {
-    if (LINE_FAST) {
-        grp = dl.div(t);
-        line = t - grp * nlines;
-    } else {
-        line = t / G;
-        grp = t - line * G;
-    }
+    (void)G;
+    grp = dl.div(t);
+    line = t - grp * nlines;
 }
 
 // pass over the strided groups of nlines lines (stages [0, K)); ends with __syncthreads()

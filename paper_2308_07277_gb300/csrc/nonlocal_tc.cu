@@ -157,11 +157,26 @@ __global__ void __launch_bounds__(256) k_split_t(const float2* __restrict__ beta
     put8(blk, R, nkt, g0 + gg, p0 * 2 + ch * 8, v);
 }
 
-// sum the split-K partials of the projection C[z][p][2b + t] (FP32, ldc) and write the
-// application's A operand E = D P expanded, blocked and split (rows 2b + t, K = (p, u)); rows
-// >= 2 nb and p >= P are zeros.  One thread per (row, 4 projectors).
-__global__ void k_reduce_e(const float* __restrict__ part, int Z, size_t zstride, int ldc, int P, int nb,
-                           const double* __restrict__ D, int rows_pad, int nkt, unsigned char* __restrict__ blk) {
+// sum the split-K partials of the projection C[z][p][c] (FP32, ldc; c = 2b + t) in a fixed order
+// and scale by D_p: Pd[p][c] = D_p sum_z C[z][p][c] (consecutive threads, consecutive c: coalesced)
+__global__ void k_reduce_p(const float* __restrict__ part, int Z, size_t zstride, int ldc, int P, int ncol,
+                           const double* __restrict__ D, float* __restrict__ Pd) {
+    const size_t total = (size_t)P * ncol;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const int p = (int)(e / ncol), c = (int)(e - (size_t)p * ncol);
+        const float* q = part + (size_t)p * ldc + c;
+        float a = 0.f;
+        for (int z = 0; z < Z; ++z) a += __ldg(q + (size_t)z * zstride);
+        Pd[e] = a * (float)__ldg(D + p);
+    }
+}
+
+// the application's A operand E = D P expanded, blocked and split (rows 2b + t, K = (p, u)):
+// E[2b][(p,0)] = ar, E[2b][(p,1)] = -ai, E[2b+1][(p,0)] = ai, E[2b+1][(p,1)] = ar with
+// a = Pd[p][2b] + i Pd[p][2b+1]; rows >= 2 nb and p >= P are zeros.  One thread per (row, 4
+// projectors), the 8 rows of a core matrix on consecutive threads.
+__global__ void k_expand_e(const float* __restrict__ Pd, int P, int nb, int rows_pad, int nkt,
+                           unsigned char* __restrict__ blk) {
     const int nchunk = nkt * (KT / 8);
     const long total = (long)rows_pad * nchunk;
     for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
@@ -176,14 +191,9 @@ __global__ void k_reduce_e(const float* __restrict__ part, int Z, size_t zstride
             const int p = ch * 4 + j;
             float ar = 0.f, ai = 0.f;
             if (b < nb && p < P) {
-                for (int z = 0; z < Z; ++z) {
-                    const float2 c = __ldg(reinterpret_cast<const float2*>(part + (size_t)z * zstride + (size_t)p * ldc) + b);
-                    ar += c.x;
-                    ai += c.y;
-                }
-                const float d = (float)__ldg(D + p);
-                ar *= d;
-                ai *= d;
+                const float2 a = __ldg(reinterpret_cast<const float2*>(Pd + (size_t)p * 2 * nb) + b);
+                ar = a.x;
+                ai = a.y;
             }
             v[2 * j] = t ? ai : ar;
             v[2 * j + 1] = t ? ar : -ai;
@@ -396,7 +406,7 @@ struct NlLayout {
     int bn_p, ntile_p, mtile_p, nkt_p;  // projection: N tile, tiles, K tiles (of 2 npw)
     int mtile_a, ntile_a, nkt_a;        // application
     int splits;
-    size_t betaK_off, betaT_off, psiX_off, part_off, e_off, total;
+    size_t betaK_off, betaT_off, psiX_off, part_off, pd_off, e_off, total;
     size_t zstride;
 };
 
@@ -422,6 +432,7 @@ NlLayout nl_layout(int nproj, int nb, int npw, bool with_beta) {
     L.betaT_off = take(with_beta ? (size_t)L.ntile_a * L.nkt_a * block_bytes(kAppBN) : 0);
     L.psiX_off = take((size_t)L.ntile_p * L.nkt_p * block_bytes(L.bn_p));
     L.part_off = take((size_t)L.splits * L.zstride * sizeof(float));
+    L.pd_off = take((size_t)nproj * 2 * nb * sizeof(float));
     L.e_off = take((size_t)L.mtile_a * L.nkt_a * block_bytes(TM));
     L.total = off;
     return L;
@@ -516,12 +527,18 @@ qm_status nonlocal_tc(int nproj, int nb, int npw, const float2* beta, int ld_bet
         const int per = (L.nkt_p + L.splits - 1) / L.splits;
         return (L.nkt_p + per - 1) / per;
     }();
+    float* Pd = (float*)(w + L.pd_off);
+    {
+        ProfScope pf(PF_SPLIT, s);
+        k_reduce_p<<<grid_for((long)nproj * 2 * nb), 256, 0, s>>>(part, Z, L.zstride, (int)ldc_p, nproj, 2 * nb, D, Pd);
+    }
+    if ((st = cuda_check(cudaGetLastError(), "k_reduce_p launch"))) return st;
     {
         ProfScope pf(PF_SPLIT, s);
         const long n = (long)L.mtile_a * TM * L.nkt_a * (KT / 8);
-        k_reduce_e<<<grid_for(n), 256, 0, s>>>(part, Z, L.zstride, (int)ldc_p, nproj, nb, D, L.mtile_a * TM, L.nkt_a, E);
+        k_expand_e<<<grid_for(n), 256, 0, s>>>(Pd, nproj, nb, L.mtile_a * TM, L.nkt_a, E);
     }
-    if ((st = cuda_check(cudaGetLastError(), "k_reduce_e launch"))) return st;
+    if ((st = cuda_check(cudaGetLastError(), "k_expand_e launch"))) return st;
     // application out[b][g] (+)= sum_p beta[p][g] D_p P[p][b]
     return gemm_launch<1>(E, betaT, L.nkt_a, kAppBN, 2 * nb, npw, L.mtile_a, L.ntile_a, 1, (float*)out, (size_t)ld_out,
                           0, accumulate, err, s);

@@ -150,6 +150,12 @@ def cell_inputs(Q, cell):
 
 
 def test_training_lowers_the_loss_and_davidson_converges_with_it(Q):
+    """What the trained network gains over TPA, measured: on the training samples and on the
+    samples of a held-out cell its weighted correction-direction loss is below TPA's (the gain
+    the network is trained for), and block Davidson with it reaches the brute-force eigenvalues
+    of the held-out cell.  The iteration counts of the two are printed, not asserted as a gain:
+    on these Hamiltonians a diagonal network preconditioner converges like TPA (measured: within
+    a few iterations either way), so the test bounds the learned run's iterations instead."""
     from paper_2308_07277_gb300 import learned
     parts, gs = [], []
     for cell in small_training_cells():
@@ -166,23 +172,30 @@ def test_training_lowers_the_loss_and_davidson_converges_with_it(Q):
     L_tpa = M.cosine_loss_of_k(tpa_k(F[:, 0]), r2, cc, D, off, W)
     L_best = M.cosine_loss_of_k(cc / np.maximum(r2, 1e-300), r2, cc, D, off, W)
     print(f"training loss {hist[0]:.4f} -> {hist[-1]:.4f}; TPA {L_tpa:.4f}; best diagonal {L_best:.4f}")
-    assert L_best <= hist[-1] + 1e-3
-    # Davidson with the trained network on a held-out cell: brute-force eigenvalues
+    assert L_best <= hist[-1] + 1e-3 and hist[-1] < L_tpa
+    # a held-out cell: its own samples, and Davidson with the trained network
     lat, tau = S.fcc_supercell(1, 1, 1)
     cell = S.Cell("heldout", lat, tau, 16.0, None, nbnd=8, kpts=np.array([[0.25, -0.25, 0.25]]), seed=77)
-    c = make_case(cell, 0)
-    ev = np.linalg.eigvalsh(OH.dense_h(c["gs"], c["v"], c["beta"], c["D"]))[: cell.nbnd]
+    c = make_case(cell, 0, nb=cell.nbnd + 8)
     g = Q.qm_gspace_create(cell.lattice, cell.kpts, cell.ecut_ha, c["grid"])
     gs.append(g)
     t = {k: torch.from_numpy(c[k]).cuda() for k in ("v", "beta", "D", "psi")}
+    hold = learned.assemble(learned.collect(g, 0, t["v"], t["beta"], t["D"], t["psi"], cell.nbnd))
+    L_net, _ = Q.qm_mlp_loss_grad(hold[0], hold[1], hold[2], hold[3], hold[4], theta, W=hold[5])
+    offh, Fh, r2h, cch, Dh, Wh = (a.cpu().numpy().astype(np.float64) for a in hold)
+    L_tpa_h = M.cosine_loss_of_k(tpa_k(Fh[:, 0]), r2h, cch, Dh, offh.astype(np.int64), Wh)
+    print(f"held-out loss: network {L_net:.4f}, TPA {L_tpa_h:.4f}")
+    assert L_net < L_tpa_h
+    ev = np.linalg.eigvalsh(OH.dense_h(c["gs"], c["v"], c["beta"], c["D"]))[: cell.nbnd]
     its = {}
     for name, mlp in [("tpa", None), ("mlp", theta)]:
-        X = t["psi"].clone()
+        X = t["psi"][: cell.nbnd].clone()
         eig, info = Q.qm_davidson(g, 0, X, t["v"], t["beta"], t["D"], tol=1e-9, max_iter=300, mlp=mlp)
         assert info["converged"]
         np.testing.assert_allclose(eig, ev, atol=1e-9)
         its[name] = (info["iterations"], info["precond_fallback"])
     print("Davidson iterations (tpa, mlp):", its)
+    assert its["mlp"][0] <= 1.5 * its["tpa"][0] + 5
     for g in gs:
         Q.qm_gspace_destroy(g)
 
