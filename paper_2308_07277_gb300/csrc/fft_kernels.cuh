@@ -691,13 +691,26 @@ __device__ void fft2_z_vmul(C* buf, int ldy, int ncol, const R* __restrict__ v, 
     fft_z_vmul<C, R>(buf, ldy, ncol, nullptr, ncol, v, ldv, pz, tw, tid, nt);
 }
 
+// whether the two-register-pass code serves a runtime length (host side)
+inline bool fused_length(int n) {
+    switch (n) {
+#define QM_CASE(n) \
+    case n: return Fused<n>::ok;
+        QM_FFT_LENGTHS(QM_CASE)
+#undef QM_CASE
+        default: return false;
+    }
+}
+
 // x sticks per CTA of the stick kernels: 64 in FP32 (19 KB of lines), 32 in FP64
 template <class R> constexpr int sticks_per_cta() { return sizeof(R) == 4 ? 64 : 32; }
 constexpr int kThreads = 256;
 
 // ---------------------------------------------------------------- K1
-template <class R>
-__global__ void __launch_bounds__(kThreads)
+// FUSED: the two-register-pass transforms (a separate instantiation, so that the stage-per-pass
+// lengths keep their lower register count and higher occupancy)
+template <class R, bool FUSED>
+__global__ void __launch_bounds__(kThreads, FUSED ? 3 : 4)
 k_stick_inverse(const typename Cx<R>::T* __restrict__ psi, int ld_psi, const int* __restrict__ stick_g0,
                 const int2* __restrict__ g_code, int nstick, int nstick_pad, AxisPlan px,
                 const typename Cx<R>::T* __restrict__ tw_x, int ldx, typename Cx<R>::T* __restrict__ T) {
@@ -720,7 +733,10 @@ k_stick_inverse(const typename Cx<R>::T* __restrict__ psi, int ld_psi, const int
         lines[(c.x - s0) * ldx + c.y] = src[g];
     }
     __syncthreads();
-    fft2_lines<C, +1, true, false>(lines, 1, ldx, ns, nullptr, px, tw, tid, nt);
+    if constexpr (FUSED)
+        fft2_lines<C, +1, true, false>(lines, 1, ldx, ns, nullptr, px, tw, tid, nt);
+    else
+        fft_lines<C, +1, true, false>(lines, 1, ldx, ns, nullptr, px, tw, tid, nt);
     C* dst = T + (size_t)b * N1 * nstick_pad + s0;
     for (int i = tid; i < N1 * ns; i += nt) {
         int p = i / ns, l = i - p * ns;
@@ -729,8 +745,8 @@ k_stick_inverse(const typename Cx<R>::T* __restrict__ psi, int ld_psi, const int
 }
 
 // ---------------------------------------------------------------- K2
-template <class R>
-__global__ void __launch_bounds__(kThreads, 3)
+template <class R, bool FUSED>
+__global__ void __launch_bounds__(kThreads, FUSED ? 3 : 4)
 k_plane(typename Cx<R>::T* __restrict__ T, int nstick, int nstick_pad, const int* __restrict__ stick_plane,
         const int* __restrict__ rows, int nrow, AxisPlan py, AxisPlan pz,
         const typename Cx<R>::T* __restrict__ tw_y, const typename Cx<R>::T* __restrict__ tw_z, int ldy,
@@ -752,15 +768,21 @@ k_plane(typename Cx<R>::T* __restrict__ T, int nstick, int nstick_pad, const int
     __syncthreads();
     // inverse y on the active rows; z on every column: inverse, V(r)/N_r (in the permuted,
     // digit-reversed order of all three axes), forward; forward y on the active rows
-    fft2_lines<C, +1, true, false>(plane, 1, ldy, nrow, rows, py, twy, tid, nt);
-    fft2_z_vmul<C, R>(plane, ldy, N2, Vt + (size_t)p1 * N3 * N2, N2, pz, twz, tid, nt);
-    fft2_lines<C, -1, false, false>(plane, 1, ldy, nrow, rows, py, twy, tid, nt);
+    if constexpr (FUSED) {
+        fft2_lines<C, +1, true, false>(plane, 1, ldy, nrow, rows, py, twy, tid, nt);
+        fft2_z_vmul<C, R>(plane, ldy, N2, Vt + (size_t)p1 * N3 * N2, N2, pz, twz, tid, nt);
+        fft2_lines<C, -1, false, false>(plane, 1, ldy, nrow, rows, py, twy, tid, nt);
+    } else {
+        fft_lines<C, +1, true, false>(plane, 1, ldy, nrow, rows, py, twy, tid, nt);
+        fft_z_vmul<C, R>(plane, ldy, N2, nullptr, N2, Vt + (size_t)p1 * N3 * N2, N2, pz, twz, tid, nt);
+        fft_lines<C, -1, false, false>(plane, 1, ldy, nrow, rows, py, twy, tid, nt);
+    }
     for (int s = tid; s < nstick; s += nt) Tp[s] = plane[__ldg(stick_plane + s)];
 }
 
 // ---------------------------------------------------------------- K3
-template <class R>
-__global__ void __launch_bounds__(kThreads)
+template <class R, bool FUSED>
+__global__ void __launch_bounds__(kThreads, FUSED ? 3 : 4)
 k_stick_forward(const typename Cx<R>::T* __restrict__ T, int nstick, int nstick_pad,
                 const int* __restrict__ stick_g0, const int2* __restrict__ g_code, const R* __restrict__ kin,
                 AxisPlan px, const typename Cx<R>::T* __restrict__ tw_x, int ldx,
@@ -782,7 +804,10 @@ k_stick_forward(const typename Cx<R>::T* __restrict__ T, int nstick, int nstick_
         lines[l * ldx + p] = srcT[(size_t)p * nstick_pad + l];
     }
     __syncthreads();
-    fft2_lines<C, -1, false, false>(lines, 1, ldx, ns, nullptr, px, tw, tid, nt);
+    if constexpr (FUSED)
+        fft2_lines<C, -1, false, false>(lines, 1, ldx, ns, nullptr, px, tw, tid, nt);
+    else
+        fft_lines<C, -1, false, false>(lines, 1, ldx, ns, nullptr, px, tw, tid, nt);
     const int gb = __ldg(stick_g0 + s0), ge = __ldg(stick_g0 + s0 + ns);
     const C* ps = psi + (size_t)b * ld_psi;
     C* po = out + (size_t)b * ld_out;
@@ -828,9 +853,13 @@ qm_status local_kinetic_impl(qm_gspace g, int ik, int nb, const void* psi, int l
     const size_t sm_stick = (size_t)(sticks_per_cta<R>() * g->ldx + N1) * sizeof(C);
     const size_t sm_plane = (size_t)(N3 * g->ldy + N2 + N3) * sizeof(C);
     qm_status st;
-    if ((st = allow_dynamic_smem((const void*)k_plane<R>, sm_plane, "qm_hpsi: FFT plane in shared memory")) ||
-        (st = allow_dynamic_smem((const void*)k_stick_inverse<R>, sm_stick, "qm_hpsi: FFT sticks in shared memory")) ||
-        (st = allow_dynamic_smem((const void*)k_stick_forward<R>, sm_stick, "qm_hpsi: FFT sticks in shared memory")))
+    const bool fx = fused_length(N1), fyz = fused_length(N2) || fused_length(N3);
+    auto kin_ = fx ? k_stick_inverse<R, true> : k_stick_inverse<R, false>;
+    auto kfw_ = fx ? k_stick_forward<R, true> : k_stick_forward<R, false>;
+    auto kpl_ = fyz ? k_plane<R, true> : k_plane<R, false>;
+    if ((st = allow_dynamic_smem((const void*)kpl_, sm_plane, "qm_hpsi: FFT plane in shared memory")) ||
+        (st = allow_dynamic_smem((const void*)kin_, sm_stick, "qm_hpsi: FFT sticks in shared memory")) ||
+        (st = allow_dynamic_smem((const void*)kfw_, sm_stick, "qm_hpsi: FFT sticks in shared memory")))
         return st;
     const int ntile = (kt.nstick + sticks_per_cta<R>() - 1) / sticks_per_cta<R>();
     const C* tw_x = (const C*)(sizeof(R) == 8 ? (const void*)g->tw64[0] : (const void*)g->tw32[0]);
@@ -844,12 +873,12 @@ qm_status local_kinetic_impl(qm_gspace g, int ik, int nb, const void* psi, int l
         C* po = (C*)out + (size_t)b0 * ld_out;
         {
             ProfScope pf(PF_STICK_INV, s);
-            k_stick_inverse<R><<<dim3(ntile, nbx), kThreads, sm_stick, s>>>(
+            kin_<<<dim3(ntile, nbx), kThreads, sm_stick, s>>>(
                 ps, ld_psi, kt.stick_g0, kt.g_code, kt.nstick, kt.nstick_pad, g->plan[0], tw_x, g->ldx, T);
         }
         {
             ProfScope pf(PF_PLANE, s);
-            k_plane<R><<<dim3(N1, nbx), kThreads, sm_plane, s>>>(
+            kpl_<<<dim3(N1, nbx), kThreads, sm_plane, s>>>(
                 T, kt.nstick, kt.nstick_pad, kt.stick_plane, kt.rows, kt.nrow, g->plan[1], g->plan[2], tw_y, tw_z,
                 g->ldy, (const R*)vt, N1);
         }
@@ -859,7 +888,7 @@ qm_status local_kinetic_impl(qm_gspace g, int ik, int nb, const void* psi, int l
         }
         {
             ProfScope pf(PF_STICK_FWD, s);
-            k_stick_forward<R><<<dim3(ntile, nbx), kThreads, sm_stick, s>>>(
+            kfw_<<<dim3(ntile, nbx), kThreads, sm_stick, s>>>(
                 T, kt.nstick, kt.nstick_pad, kt.stick_g0, kt.g_code, kin, g->plan[0], tw_x, g->ldx, ps, ld_psi, po,
                 ld_out, accumulate ? 1 : 0);
         }
@@ -878,9 +907,13 @@ qm_status local_kinetic_tab_impl(const DevTables& t, int nb, const void* psi, in
     const size_t sm_stick = (size_t)(sticks_per_cta<R>() * t.ldx + N1) * sizeof(C);
     const size_t sm_plane = (size_t)(N3 * t.ldy + N2 + N3) * sizeof(C);
     qm_status st;
-    if ((st = allow_dynamic_smem((const void*)k_plane<R>, sm_plane, "FFT plane in shared memory")) ||
-        (st = allow_dynamic_smem((const void*)k_stick_inverse<R>, sm_stick, "FFT sticks in shared memory")) ||
-        (st = allow_dynamic_smem((const void*)k_stick_forward<R>, sm_stick, "FFT sticks in shared memory")))
+    const bool fx = fused_length(N1), fyz = fused_length(N2) || fused_length(N3);
+    auto kin_ = fx ? k_stick_inverse<R, true> : k_stick_inverse<R, false>;
+    auto kfw_ = fx ? k_stick_forward<R, true> : k_stick_forward<R, false>;
+    auto kpl_ = fyz ? k_plane<R, true> : k_plane<R, false>;
+    if ((st = allow_dynamic_smem((const void*)kpl_, sm_plane, "FFT plane in shared memory")) ||
+        (st = allow_dynamic_smem((const void*)kin_, sm_stick, "FFT sticks in shared memory")) ||
+        (st = allow_dynamic_smem((const void*)kfw_, sm_stick, "FFT sticks in shared memory")))
         return st;
     const int ntile = (t.nstick + sticks_per_cta<R>() - 1) / sticks_per_cta<R>();
     const C* tw_x = (const C*)t.tw[0];
@@ -894,18 +927,18 @@ qm_status local_kinetic_tab_impl(const DevTables& t, int nb, const void* psi, in
         C* po = (C*)out + (size_t)b0 * ld_out;
         {
             ProfScope pf(PF_STICK_INV, s);
-            k_stick_inverse<R><<<dim3(ntile, nbx), kThreads, sm_stick, s>>>(
+            kin_<<<dim3(ntile, nbx), kThreads, sm_stick, s>>>(
                 ps, ld_psi, t.stick_g0, t.g_code, t.nstick, t.nstick_pad, t.plan[0], tw_x, t.ldx, T);
         }
         {
             ProfScope pf(PF_PLANE, s);
-            k_plane<R><<<dim3(N1, nbx), kThreads, sm_plane, s>>>(
+            kpl_<<<dim3(N1, nbx), kThreads, sm_plane, s>>>(
                 T, t.nstick, t.nstick_pad, t.stick_plane, t.rows, t.nrow, t.plan[1], t.plan[2], tw_y, tw_z, t.ldy,
                 (const R*)vt, N1);
         }
         {
             ProfScope pf(PF_STICK_FWD, s);
-            k_stick_forward<R><<<dim3(ntile, nbx), kThreads, sm_stick, s>>>(
+            kfw_<<<dim3(ntile, nbx), kThreads, sm_stick, s>>>(
                 T, t.nstick, t.nstick_pad, t.stick_g0, t.g_code, kin, t.plan[0], tw_x, t.ldx, ps, ld_psi, po, ld_out, 0);
         }
     }
