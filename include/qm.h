@@ -223,10 +223,12 @@ qm_status qm_hpsi_noalloc(qm_gspace g, int ik, int nb,
  * the phases of consecutive groups interleaved as a software pipeline, so the intermediate
  * data of a group is still in L2 when its next phase reads it.  The shape of the launch
  * (resident CTAs per SM; grid points per FFT work item, from which the lines per x-stick item
- * and the bands per yz-plane item follow; the group size) is either given or picked by the
- * autotuner, which times three replays of each candidate (after one warm-up) with CUDA events
- * on `stream`: every feasible (CTAs per SM, points per item) pair at 24 MB groups, then the
- * other group sizes (48 MB, one group) at the best pair; the fastest is kept.
+ * and the bands per yz-plane item follow; the group size; the radix order of the FFT plans) is
+ * either given or picked by the autotuner, which times three replays of each candidate (after
+ * one warm-up) with CUDA events on `stream`: every feasible (CTAs per SM, points per item) pair
+ * at 24 MB groups and radix order 1, then the other group sizes (48 MB, one group) at the best
+ * pair, then radix order 2 at the best shape; the fastest is kept.  The radix order changes the
+ * rounding, not the operator: both orders give the same H psi to FFT round-off.
  */
 typedef struct {
     qm_gspace g;            /* gspace of the job's cell (device tables on the current device) */
@@ -250,6 +252,8 @@ typedef struct {
     int item_points;   /* target grid points per FFT work item, 256..65536; 0 = autotune */
     int group_mb;      /* stick-buffer megabytes per pipelined group of jobs, 1..4096; -1 = one
                           group (the work items of each phase of all jobs together); 0 = autotune */
+    int fft_order;     /* radix order of the FFT plans: 1 = large radices first (8s, 4, 2, 9s, 3,
+                          5s, the single-call order), 2 = the same radices reversed; 0 = autotune */
 } qm_batch_shape;
 
 typedef struct {
@@ -263,6 +267,7 @@ typedef struct {
     long long smem_bytes;          /* dynamic shared memory per CTA */
     long long device_bytes;        /* device memory owned by the batch */
     double tuned_ms;               /* autotuner's best median time per replay (ms; 0 if not tuned) */
+    int fft_order;                 /* radix order in use: 0 = large radices first, 1 = reversed */
 } qm_batch_info;
 
 /*

@@ -103,7 +103,8 @@ class HpsiJob(ctypes.Structure):
 
 class BatchShape(ctypes.Structure):
     """qm_batch_shape of include/qm.h."""
-    _fields_ = [("ctas_per_sm", ctypes.c_int), ("item_points", ctypes.c_int), ("group_mb", ctypes.c_int)]
+    _fields_ = [("ctas_per_sm", ctypes.c_int), ("item_points", ctypes.c_int), ("group_mb", ctypes.c_int),
+                ("fft_order", ctypes.c_int)]
 
 
 class BatchInfo(ctypes.Structure):
@@ -112,7 +113,7 @@ class BatchInfo(ctypes.Structure):
                 ("grid", ctypes.c_int),
                 ("items", ctypes.c_int), ("cells", ctypes.c_int), ("candidates", ctypes.c_int),
                 ("band_applies", ctypes.c_longlong), ("smem_bytes", ctypes.c_longlong),
-                ("device_bytes", ctypes.c_longlong), ("tuned_ms", ctypes.c_double)]
+                ("device_bytes", ctypes.c_longlong), ("tuned_ms", ctypes.c_double), ("fft_order", ctypes.c_int)]
 
 
 SIGNATURES["qm_batch_create"] = (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(HpsiJob), ctypes.c_int,

@@ -263,7 +263,7 @@ class Batch:
     tensors as for qm_hpsi; beta/D may be None).  The tensors are referenced by the plan
     and must stay alive and in place while it exists."""
 
-    def __init__(self, jobs, prec="fp64", ctas_per_sm=0, item_points=0, group_mb=0, stream=None):
+    def __init__(self, jobs, prec="fp64", ctas_per_sm=0, item_points=0, group_mb=0, stream=None, fft_order=None):
         lib = _lib.load()
         self.prec = _PREC[prec]
         cdt = torch.complex128 if self.prec == QM_FP64 else torch.complex64
@@ -283,7 +283,9 @@ class Batch:
                                   D=_dev_ptr(j["D"], "D", torch.float64) if nproj else None,
                                   out=_dev_ptr(out, "out", cdt))
             self._keep.append((psi, out, beta, j["vloc"], j.get("D")))
-        shape = _lib.BatchShape(int(ctas_per_sm), int(item_points), int(group_mb))
+        if fft_order is None:   # a fully given launch shape keeps the default radix order
+            fft_order = 1 if (ctas_per_sm and item_points and group_mb) else 0
+        shape = _lib.BatchShape(int(ctas_per_sm), int(item_points), int(group_mb), int(fft_order))
         h = ctypes.c_void_p()
         _check(lib.qm_batch_create(len(jobs), arr, self.prec, ctypes.byref(shape), _stream_ptr(stream),
                                    ctypes.byref(h)))
@@ -317,9 +319,9 @@ class Batch:
             pass
 
 
-def qm_batch_create(jobs, prec="fp64", ctas_per_sm=0, item_points=0, group_mb=0, stream=None):
+def qm_batch_create(jobs, prec="fp64", ctas_per_sm=0, item_points=0, group_mb=0, stream=None, fft_order=None):
     return Batch(jobs, prec=prec, ctas_per_sm=ctas_per_sm, item_points=item_points, group_mb=group_mb,
-                 stream=stream)
+                 stream=stream, fft_order=fft_order)
 
 
 QM_MLP_NPARAM = 4481   # include/qm.h

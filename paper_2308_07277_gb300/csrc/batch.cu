@@ -13,8 +13,8 @@
 namespace qm {
 qm_status batch_launch_f32(const BatchLaunch& L, cudaStream_t s);
 qm_status batch_launch_f64(const BatchLaunch& L, cudaStream_t s);
-int batch_occupancy_f32(size_t smem);
-int batch_occupancy_f64(size_t smem);
+int batch_occupancy_f32(size_t smem, int order);
+int batch_occupancy_f64(size_t smem, int order);
 }  // namespace qm
 
 using namespace qm;
@@ -24,6 +24,7 @@ struct qm_batch_s {
     qm_precision prec = QM_FP64;
     std::vector<qm_hpsi_job> jobs;
     int ctas = 0, points = 0, group_mb = 0, grid = 0, nitems = 0, ncells = 0, candidates = 0;
+    int order = 0;  // FFT radix order of the built plan
     size_t smem = 0, dbytes = 0;
     double tuned_ms = 0.0;
     long long band_applies = 0;
@@ -59,7 +60,7 @@ void release(qm_batch b) {
 
 // Build the work lists and device data for one shape and capture the launch in a graph.
 // `infeasible` is set (and QM_OK returned) when the shape does not fit the SM.
-qm_status build(qm_batch b, int ctas, int points, size_t group_bytes, bool* infeasible) {
+qm_status build(qm_batch b, int ctas, int points, size_t group_bytes, int radix_order, bool* infeasible) {
     *infeasible = false;
     const bool fp32 = b->prec == QM_MIXED;
     const size_t cs = fp32 ? sizeof(float2) : sizeof(double2);
@@ -83,6 +84,16 @@ qm_status build(qm_batch b, int ctas, int points, size_t group_bytes, bool* infe
 
     std::vector<BatchJobDev> J(nj);
     std::vector<BatchCellDev> Cl(nc);
+    // the FFT plans (and digit-reversal tables) of every length in the chosen radix order
+    std::map<int, std::pair<AxisPlan, std::vector<int>>> plans;
+    auto plan_of = [&](int n) -> const std::pair<AxisPlan, std::vector<int>>& {
+        auto it = plans.find(n);
+        if (it == plans.end()) {
+            it = plans.emplace(n, std::make_pair(AxisPlan{}, std::vector<int>())).first;
+            fft_plan(n, radix_order, it->second.first, it->second.second);
+        }
+        return it->second;
+    };
     size_t smem = (size_t)kBatchAB * kBatchAP * cs;  // application staging
     for (int j = 0; j < nj; ++j) {
         const qm_hpsi_job& q = b->jobs[j];
@@ -118,9 +129,9 @@ qm_status build(qm_batch b, int ctas, int points, size_t group_bytes, bool* infe
         d.ld_psi = q.ld_psi;
         d.ld_out = q.ld_out;
         d.ld_beta = q.ld_beta;
-        d.px = g->plan[0];
-        d.py = g->plan[1];
-        d.pz = g->plan[2];
+        d.px = plan_of(g->n[0]).first;
+        d.py = plan_of(g->n[1]).first;
+        d.pz = plan_of(g->n[2]).first;
         d.stick_g0 = kt.stick_g0;
         d.stick_plane = kt.stick_plane;
         d.g_code = kt.g_code;
@@ -137,7 +148,7 @@ qm_status build(qm_batch b, int ctas, int points, size_t group_bytes, bool* infe
         *infeasible = true;
         return QM_OK;
     }
-    const int occ = fp32 ? batch_occupancy_f32(smem) : batch_occupancy_f64(smem);
+    const int occ = fp32 ? batch_occupancy_f32(smem, radix_order) : batch_occupancy_f64(smem, radix_order);
     if (occ < ctas) {
         *infeasible = true;
         return QM_OK;
@@ -220,6 +231,14 @@ qm_status build(qm_batch b, int ctas, int points, size_t group_bytes, bool* infe
         o_rows[j] = R.take(sizeof(int) * (size_t)J[j].bpp * J[j].nrow);
         o_cols[j] = R.take(sizeof(int) * (size_t)J[j].bpp * J[j].n2);
     }
+    // digit-reversal tables of the radix order 1 plans (order 0 uses the gspace's own)
+    std::map<int, size_t> o_rev;
+    if (radix_order)
+        for (int c = 0; c < nc; ++c)
+            for (int a = 0; a < 3; ++a) {
+                const int n = cell_job[c]->g->n[a];
+                if (!o_rev.count(n)) o_rev[n] = R.take(sizeof(int) * (size_t)n);
+            }
     const size_t table_end = R.off;
     for (int c = 0; c < nc; ++c) {
         const qm_gspace g = cell_job[c]->g;
@@ -258,12 +277,17 @@ qm_status build(qm_batch b, int ctas, int points, size_t group_bytes, bool* infe
         Cl[c].n1 = g->n[0];
         Cl[c].n2 = g->n[1];
         Cl[c].n3 = g->n[2];
-        for (int a = 0; a < 3; ++a) Cl[c].rev[a] = g->rev[a];
+        for (int a = 0; a < 3; ++a)
+            Cl[c].rev[a] = radix_order ? (const int*)(base + o_rev[g->n[a]]) : g->rev[a];
         Cl[c].scale = 1.0 / ((double)g->n[0] * g->n[1] * g->n[2]);
     }
     {
         const BatchCtl ctl{kBatchSpinLimit, -1, 0};
         std::memcpy(img.data() + o_ctl, &ctl, sizeof(ctl));
+    }
+    for (const auto& kv : o_rev) {
+        const std::vector<int>& rv = plan_of(kv.first).second;
+        std::memcpy(img.data() + kv.second, rv.data(), sizeof(int) * rv.size());
     }
     std::memcpy(img.data() + o_jobs, J.data(), sizeof(BatchJobDev) * nj);
     std::memcpy(img.data() + o_cells, Cl.data(), sizeof(BatchCellDev) * nc);
@@ -286,6 +310,7 @@ qm_status build(qm_batch b, int ctas, int points, size_t group_bytes, bool* infe
     L.cell_cnt = L.cnt + (size_t)nj * kBatchCounters;
     L.head = L.cell_cnt + nc;
     L.err = L.head + 1;
+    L.order = radix_order;
     L.grid = std::max(1, std::min(ctas * nsm, L.nitems));
     L.smem = smem;
 
@@ -324,6 +349,7 @@ qm_status build(qm_batch b, int ctas, int points, size_t group_bytes, bool* infe
     b->ncells = nc;
     b->smem = smem;
     b->dbytes = total;
+    b->order = radix_order;
     return QM_OK;
 }
 
@@ -399,8 +425,9 @@ extern "C" qm_status qm_batch_create(int njobs, const qm_hpsi_job* jobs, qm_prec
     const bool fp32 = prec == QM_MIXED;
     int ctas = shape ? shape->ctas_per_sm : 0, points = shape ? shape->item_points : 0;
     int gmb = shape ? shape->group_mb : 0;
+    const int ford = shape ? shape->fft_order : 0;  // 0: autotune; 1, 2: radix order 0, 1
     if (ctas < 0 || ctas > 8 || points < 0 || (points > 0 && (points < 256 || points > 65536)) || gmb < -1 ||
-        gmb > 4096)
+        gmb > 4096 || ford < 0 || ford > 2)
         return fail(QM_ERR_ARG, "qm_batch_create: shape out of range");
     auto gbytes = [](int mb) { return mb > 0 ? (size_t)mb << 20 : (size_t)0; };
     qm_status st;
@@ -434,17 +461,20 @@ extern "C" qm_status qm_batch_create(int njobs, const qm_hpsi_job* jobs, qm_prec
         }
     cudaStream_t s = (cudaStream_t)stream;
     bool infeasible = false;
-    if (ctas > 0 && points > 0 && gmb != 0) {
-        st = build(b, ctas, points, gbytes(gmb), &infeasible);
+    if (ctas > 0 && points > 0 && gmb != 0 && ford != 0) {
+        st = build(b, ctas, points, gbytes(gmb), ford - 1, &infeasible);
         if (!st && infeasible) st = fail(QM_ERR_UNSUPPORTED, "qm_batch_create: shape does not fit the SM");
     } else {
         // autotune (each timed run executes the whole batch): every feasible (CTAs per SM,
-        // points per item) at the first group size, then the group sizes at the best of those
+        // points per item) at the first group size and radix order 0, then the group sizes at
+        // the best of those, then the other radix order at the best shape
         double best = 1e300;
         int bc = 0, bp = 0, bg = gmb != 0 ? gmb : kCandGroupMb[0];
+        const int o0 = ford ? ford - 1 : 0;
+        int bo = o0;
         st = QM_OK;
-        auto try_shape = [&](int c, int p, int g) -> qm_status {
-            qm_status s2 = build(b, c, p, gbytes(g), &infeasible);
+        auto try_shape = [&](int c, int p, int g, int o) -> qm_status {
+            qm_status s2 = build(b, c, p, gbytes(g), o, &infeasible);
             if (s2 || infeasible) return s2;
             double ms = 0.0;
             s2 = time_runs(b, s, 3, &ms);
@@ -456,6 +486,7 @@ extern "C" qm_status qm_batch_create(int njobs, const qm_hpsi_job* jobs, qm_prec
                 bc = c;
                 bp = p;
                 bg = g;
+                bo = o;
             }
             return QM_OK;
         };
@@ -464,19 +495,20 @@ extern "C" qm_status qm_batch_create(int njobs, const qm_hpsi_job* jobs, qm_prec
             if (ctas > 0 && c != ctas) continue;
             for (int p : kCandPoints) {
                 if (points > 0 && p != points) continue;
-                if ((st = try_shape(c, p, g0))) break;
+                if ((st = try_shape(c, p, g0, o0))) break;
             }
             if (st) break;
         }
         if (!st && bc != 0 && gmb == 0) {
             const int c = bc, p = bp;
             for (int g : kCandGroupMb)
-                if (g != g0 && (st = try_shape(c, p, g))) break;
+                if (g != g0 && (st = try_shape(c, p, g, o0))) break;
         }
+        if (!st && bc != 0 && ford == 0) st = try_shape(bc, bp, bg, 1 - o0);
         if (!st && bc == 0) st = fail(QM_ERR_UNSUPPORTED, "qm_batch_create: no shape fits the SM");
         if (!st) {
             const int cands = b->candidates;
-            st = build(b, bc, bp, gbytes(bg), &infeasible);
+            st = build(b, bc, bp, gbytes(bg), bo, &infeasible);
             b->candidates = cands;
             b->tuned_ms = best;
         }
@@ -528,6 +560,7 @@ extern "C" qm_status qm_batch_query(qm_batch b, qm_batch_info* info) {
     info->smem_bytes = (long long)b->smem;
     info->device_bytes = (long long)b->dbytes;
     info->tuned_ms = b->tuned_ms;
+    info->fft_order = b->order;
     return QM_OK;
 }
 

@@ -94,6 +94,7 @@ struct BatchLaunch {
     int* cell_cnt;  // [ncells]
     int* head;      // ticket counter
     int* err;       // error word
+    int order;      // radix order of the FFT plans (0 or 1)
     int grid;
     size_t smem;
 };
@@ -129,12 +130,14 @@ template <> __device__ __forceinline__ double ldcg(const double* p) { return __l
 // The FFT lengths of the batched workload get compile-time plans; others take the runtime plan.
 #define QM_FFT_LENGTHS_BATCH(X) X(18) X(20) X(24) X(25) X(27) X(30) X(32) X(36) X(40) X(45) X(48) X(50) X(54) X(60) X(64)
 
-template <class C, int SG, bool DIF, bool LINE_FAST>
+// ORD: radix order of the compile-time plans (0: large radices first, 1: reversed); the
+// job's runtime AxisPlans and the cells' digit-reversal tables follow the same order.
+template <class C, int SG, bool DIF, bool LINE_FAST, int ORD>
 __device__ void fft_lines_b(C* buf, int es, int ls, int nlines, const int* lmap, const AxisPlan& pl, const C* tw,
                             int tid, int nt) {
     switch (pl.n) {
 #define QM_CASE(n) \
-    case n: fft_lines_ct<C, SG, DIF, LINE_FAST, n>(buf, es, ls, nlines, lmap, tw, tid, nt); return;
+    case n: fft_lines_ct<C, SG, DIF, LINE_FAST, n, ORD>(buf, es, ls, nlines, lmap, tw, tid, nt); return;
         QM_FFT_LENGTHS_BATCH(QM_CASE)
 #undef QM_CASE
         default: break;
@@ -150,6 +153,29 @@ __device__ void fft_lines_b(C* buf, int es, int ls, int nlines, const int* lmap,
             __syncthreads();
         }
     }
+}
+
+// z transforms of stacked planes with the V multiply between them (see fft_z_vmul_ct)
+template <class C, class R, int ORD>
+__device__ void fft_z_vmul_b(C* buf, int ldy, int ncol, const int* cmap, int nv, const R* __restrict__ v, int ldv,
+                             const AxisPlan& pz, const C* tw, int tid, int nt) {
+    switch (pz.n) {
+#define QM_CASE(n) \
+    case n: fft_z_vmul_ct<C, R, n, ORD>(buf, ldy, ncol, cmap, nv, v, ldv, tw, tid, nt); return;
+        QM_FFT_LENGTHS_BATCH(QM_CASE)
+#undef QM_CASE
+        default: break;
+    }
+    fft_lines_b<C, +1, true, true, ORD>(buf, ldy, 1, ncol, cmap, pz, tw, tid, nt);
+    for (int i = tid; i < pz.n * ncol; i += nt) {
+        const int r = i / ncol, l = i - r * ncol;
+        const R sc = __ldcg(v + r * ldv + l % nv);
+        C* x = buf + (cmap ? cmap[l] : l) + r * ldy;
+        const C y = *x;
+        *x = mk<C>(y.x * sc, y.y * sc);
+    }
+    __syncthreads();
+    fft_lines_b<C, -1, false, true, ORD>(buf, ldy, 1, ncol, cmap, pz, tw, tid, nt);
 }
 
 // ---------------------------------------------------------------- item bodies
@@ -172,7 +198,7 @@ __device__ void bk_vt(const BatchCellDev& c, int chunk, int tid, int nt) {
 }
 
 // K1: lines [L0, L1) of the job's (band, stick) list, line L = b * nstick + s
-template <class R>
+template <class R, int ORD>
 __device__ void bk_k1(const BatchJobDev& J, int tile, unsigned char* sm, int tid, int nt) {
     using C = typename Cx<R>::T;
     const int N1 = J.n1, ldx = J.ldx, nst = J.nstick;
@@ -199,7 +225,7 @@ __device__ void bk_k1(const BatchJobDev& J, int tile, unsigned char* sm, int tid
         L += sb - sa;
     }
     __syncthreads();
-    fft_lines_b<C, +1, true, false>(lines, 1, ldx, nlines, nullptr, J.px, tw, tid, nt);
+    fft_lines_b<C, +1, true, false, ORD>(lines, 1, ldx, nlines, nullptr, J.px, tw, tid, nt);
     C* T = (C*)J.T;
     const RDiv dl{nlines, 1.0f / (float)nlines};
     for (int i = tid; i < N1 * nlines; i += nt) {
@@ -210,7 +236,7 @@ __device__ void bk_k1(const BatchJobDev& J, int tile, unsigned char* sm, int tid
 }
 
 // K2: plane p1 of bands [b0, b0 + nbp), the planes stacked in shared memory
-template <class R>
+template <class R, int ORD>
 __device__ void bk_k2(const BatchJobDev& J, const R* vt, int grp, int p1, unsigned char* sm, int tid, int nt) {
     using C = typename Cx<R>::T;
     const int N1 = J.n1, N2 = J.n2, N3 = J.n3, ldy = J.ldy, nst = J.nstick;
@@ -233,10 +259,10 @@ __device__ void bk_k2(const BatchJobDev& J, const R* vt, int grp, int p1, unsign
         plane[bi * ps + __ldg(J.stick_plane + s)] = ldcg(T + ((size_t)(b0 + bi) * N1 + p1) * J.nstick_pad + s);
     }
     __syncthreads();
-    fft_lines_b<C, +1, true, false>(plane, 1, ldy, nbp * J.nrow, J.rows2, J.py, twy, tid, nt);
+    fft_lines_b<C, +1, true, false, ORD>(plane, 1, ldy, nbp * J.nrow, J.rows2, J.py, twy, tid, nt);
     // z: inverse, V(r)/N_r, forward (one fused pass for the compile-time lengths)
-    fft_z_vmul<C, R>(plane, ldy, nbp * N2, J.cols2, N2, vt + (size_t)p1 * N3 * N2, N2, J.pz, twz, tid, nt);
-    fft_lines_b<C, -1, false, false>(plane, 1, ldy, nbp * J.nrow, J.rows2, J.py, twy, tid, nt);
+    fft_z_vmul_b<C, R, ORD>(plane, ldy, nbp * N2, J.cols2, N2, vt + (size_t)p1 * N3 * N2, N2, J.pz, twz, tid, nt);
+    fft_lines_b<C, -1, false, false, ORD>(plane, 1, ldy, nbp * J.nrow, J.rows2, J.py, twy, tid, nt);
     for (int i = tid; i < nbp * nst; i += nt) {
         const int bi = ds.div(i), s = i - bi * nst;
         T[((size_t)(b0 + bi) * N1 + p1) * J.nstick_pad + s] = plane[bi * ps + __ldg(J.stick_plane + s)];
@@ -244,7 +270,7 @@ __device__ void bk_k2(const BatchJobDev& J, const R* vt, int grp, int p1, unsign
 }
 
 // K3: forward x transform of lines [L0, L1), gather the sphere, add the kinetic term
-template <class R>
+template <class R, int ORD>
 __device__ void bk_k3(const BatchJobDev& J, int tile, unsigned char* sm, int tid, int nt) {
     using C = typename Cx<R>::T;
     const int N1 = J.n1, ldx = J.ldx, nst = J.nstick;
@@ -263,7 +289,7 @@ __device__ void bk_k3(const BatchJobDev& J, int tile, unsigned char* sm, int tid
         lines[l * ldx + p] = ldcg(T + ((size_t)b * N1 + p) * J.nstick_pad + s);
     }
     __syncthreads();
-    fft_lines_b<C, -1, false, false>(lines, 1, ldx, nlines, nullptr, J.px, tw, tid, nt);
+    fft_lines_b<C, -1, false, false, ORD>(lines, 1, ldx, nlines, nullptr, J.px, tw, tid, nt);
     const C* psi = (const C*)J.psi;
     C* out = (C*)J.out;
     const R* kin = (const R*)J.kin;
@@ -425,7 +451,7 @@ __device__ void bk_nla(const BatchJobDev& J, int tile, unsigned char* sm, int ti
 }
 
 // ---------------------------------------------------------------- the persistent kernel
-template <class R>
+template <class R, int ORD>
 __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 3 : 2)  // FP32: 3 CTAs per SM, FP64: 2
 k_batch(const BatchCtl* __restrict__ ctl, const BatchJobDev* __restrict__ jobs, const BatchCellDev* __restrict__ cells,
         const int4* __restrict__ items, int nitems, int* cnt, int* cell_cnt, int* head, int* err) {
@@ -475,10 +501,10 @@ k_batch(const BatchCtl* __restrict__ ctl, const BatchJobDev* __restrict__ jobs, 
             switch (w.x) {
                 case BK_VT: bk_vt<R>(cells[w.y], w.z, tid, nt); break;
                 case BK_NLP: bk_nlp<R>(J, w.z, w.w, smem_raw, tid, nt); break;
-                case BK_K1: bk_k1<R>(J, w.z, smem_raw, tid, nt); break;
+                case BK_K1: bk_k1<R, ORD>(J, w.z, smem_raw, tid, nt); break;
                 case BK_NLR: bk_nlr<R>(J, tid, nt); break;
-                case BK_K2: bk_k2<R>(J, (const R*)cells[J.cell].vt, w.z, w.w, smem_raw, tid, nt); break;
-                case BK_K3: bk_k3<R>(J, w.z, smem_raw, tid, nt); break;
+                case BK_K2: bk_k2<R, ORD>(J, (const R*)cells[J.cell].vt, w.z, w.w, smem_raw, tid, nt); break;
+                case BK_K3: bk_k3<R, ORD>(J, w.z, smem_raw, tid, nt); break;
                 case BK_NLA: bk_nla<R>(J, w.z, smem_raw, tid, nt); break;
                 default: break;
             }
@@ -509,27 +535,35 @@ k_batch(const BatchCtl* __restrict__ ctl, const BatchJobDev* __restrict__ jobs, 
 // maximum (the attribute is per function, and graphs of several batches hold different sizes).
 template <class R>
 qm_status batch_launch_impl(const BatchLaunch& L, cudaStream_t s) {
-    k_batch<R><<<L.grid, kThreads, L.smem, s>>>(L.ctl, L.jobs, L.cells, L.items, L.nitems, L.cnt, L.cell_cnt, L.head,
-                                                 L.err);
+    if (L.order)
+        k_batch<R, 1><<<L.grid, kThreads, L.smem, s>>>(L.ctl, L.jobs, L.cells, L.items, L.nitems, L.cnt, L.cell_cnt,
+                                                       L.head, L.err);
+    else
+        k_batch<R, 0><<<L.grid, kThreads, L.smem, s>>>(L.ctl, L.jobs, L.cells, L.items, L.nitems, L.cnt, L.cell_cnt,
+                                                       L.head, L.err);
     return cuda_check(cudaGetLastError(), "batched H psi launch");
 }
 
 // resident CTAs per SM at `smem` bytes of dynamic shared memory (0 if it does not fit)
-template <class R>
-int batch_occupancy_impl(size_t smem) {
+template <class R, int ORD>
+int batch_occupancy_ord(size_t smem) {
     int dev = 0, optin = 0;
     cudaFuncAttributes fa{};
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
-        cudaFuncGetAttributes(&fa, k_batch<R>) != cudaSuccess)
+        cudaFuncGetAttributes(&fa, k_batch<R, ORD>) != cudaSuccess)
         return 0;
     const int max_dyn = optin - (int)fa.sharedSizeBytes;
     if ((long long)smem > max_dyn) return 0;
-    if (cudaFuncSetAttribute(k_batch<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_batch<R, ORD>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn) != cudaSuccess)
         return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<R>, kThreads, smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<R, ORD>, kThreads, smem) != cudaSuccess) return 0;
     return n;
+}
+template <class R>
+int batch_occupancy_impl(size_t smem, int order) {
+    return order ? batch_occupancy_ord<R, 1>(smem) : batch_occupancy_ord<R, 0>(smem);
 }
 
 }  // namespace qm

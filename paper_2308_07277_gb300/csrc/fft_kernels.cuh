@@ -216,22 +216,25 @@ struct CPlan {
     int r[kMaxStages];
     int L[kMaxStages];
 };
-constexpr CPlan make_cplan(int n) {
+// ord = 0: that radix sequence; ord = 1: the same radices in reverse order (small radices first;
+// the batched form's autotuner chooses between the two, see fft_plan in gspace.cpp)
+constexpr CPlan make_cplan(int n, int ord = 0) {
+    int rs[kMaxStages] = {}, nr = 0, m = n;
+    while (m % 8 == 0) { rs[nr++] = 8; m /= 8; }
+    if (m % 4 == 0) { rs[nr++] = 4; m /= 4; }
+    if (m % 2 == 0) { rs[nr++] = 2; m /= 2; }
+    while (m % 9 == 0) { rs[nr++] = 9; m /= 9; }
+    if (m % 3 == 0) { rs[nr++] = 3; m /= 3; }
+    while (m % 5 == 0) { rs[nr++] = 5; m /= 5; }
     CPlan p{};
-    int m = n, L = n;
-    auto push = [&](int r) {
+    int L = n;
+    for (int i = 0; i < nr; ++i) {
+        const int r = ord ? rs[nr - 1 - i] : rs[i];
         p.r[p.nst] = r;
         p.L[p.nst] = L;
         ++p.nst;
         L /= r;
-        m /= r;
-    };
-    while (m % 8 == 0) push(8);
-    if (m % 4 == 0) push(4);
-    if (m % 2 == 0) push(2);
-    while (m % 9 == 0) push(9);
-    if (m % 3 == 0) push(3);
-    while (m % 5 == 0) push(5);
+    }
     return p;
 }
 
@@ -291,26 +294,26 @@ __device__ __forceinline__ void fft_stage_ct(C* buf, int es, int ls, int nlines,
 }
 
 // stage S of the plan of N (DIF order), then the rest (DIF: S+1 .. ; DIT: S-1 .. 0)
-template <class C, int SG, bool DIF, bool LINE_FAST, int N, int S>
+template <class C, int SG, bool DIF, bool LINE_FAST, int N, int S, int ORD = 0>
 __device__ __forceinline__ void fft_stages_ct(C* buf, int es, int ls, int nlines, RDiv ld, const int* lmap,
                                               const C* tw, int tid, int nt) {
-    constexpr CPlan P = make_cplan(N);
+    constexpr CPlan P = make_cplan(N, ORD);
     if constexpr (S >= 0 && S < P.nst) {
         fft_stage_ct<C, SG, P.r[S], P.L[S], N, DIF, LINE_FAST>(buf, es, ls, nlines, ld, lmap, tw, tid, nt);
         __syncthreads();
-        fft_stages_ct<C, SG, DIF, LINE_FAST, N, DIF ? S + 1 : S - 1>(buf, es, ls, nlines, ld, lmap, tw, tid, nt);
+        fft_stages_ct<C, SG, DIF, LINE_FAST, N, DIF ? S + 1 : S - 1, ORD>(buf, es, ls, nlines, ld, lmap, tw, tid, nt);
     }
 }
 
 // stages S, S+1, ..., END-1 of the plan of N in DIF order
-template <class C, int SG, bool LINE_FAST, int N, int S, int END>
+template <class C, int SG, bool LINE_FAST, int N, int S, int END, int ORD = 0>
 __device__ __forceinline__ void fft_stages_ct_to(C* buf, int es, int ls, int nlines, RDiv ld, const int* lmap,
                                                  const C* tw, int tid, int nt) {
-    constexpr CPlan P = make_cplan(N);
+    constexpr CPlan P = make_cplan(N, ORD);
     if constexpr (S < END) {
         fft_stage_ct<C, SG, P.r[S], P.L[S], N, true, LINE_FAST>(buf, es, ls, nlines, ld, lmap, tw, tid, nt);
         __syncthreads();
-        fft_stages_ct_to<C, SG, LINE_FAST, N, S + 1, END>(buf, es, ls, nlines, ld, lmap, tw, tid, nt);
+        fft_stages_ct_to<C, SG, LINE_FAST, N, S + 1, END, ORD>(buf, es, ls, nlines, ld, lmap, tw, tid, nt);
     }
 }
 
@@ -321,15 +324,15 @@ __device__ __forceinline__ void fft_stages_ct_to(C* buf, int es, int ls, int nli
 // pass in registers (bitwise the same result as three passes).  V of element (z, column l) is
 // v[z * ldv + l % nv] (nv = columns of one plane), read through L2 (it may have been written
 // by the same launch).
-template <class C, class R, int N>
+template <class C, class R, int N, int ORD = 0>
 __device__ __forceinline__ void fft_z_vmul_ct(C* buf, int ldy, int ncol, const int* cmap, int nv,
                                               const R* __restrict__ v, int ldv, const C* tw, int tid, int nt) {
-    constexpr CPlan P = make_cplan(N);
+    constexpr CPlan P = make_cplan(N, ORD);
     constexpr int RL = P.r[P.nst - 1];
     constexpr int NBLK = N / RL;
     RDiv ld{ncol, 1.0f / (float)ncol};
     RDiv dv{nv, 1.0f / (float)nv};
-    fft_stages_ct_to<C, +1, true, N, 0, P.nst - 1>(buf, ldy, 1, ncol, ld, cmap, tw, tid, nt);
+    fft_stages_ct_to<C, +1, true, N, 0, P.nst - 1, ORD>(buf, ldy, 1, ncol, ld, cmap, tw, tid, nt);
     for (int t = tid; t < ncol * NBLK; t += nt) {
         const int blk = ld.div(t);
         const int col = t - blk * ncol;
@@ -350,15 +353,15 @@ __device__ __forceinline__ void fft_z_vmul_ct(C* buf, int ldy, int ncol, const i
         for (int j = 0; j < RL; ++j) p[j * ldy] = u[j];
     }
     __syncthreads();
-    fft_stages_ct<C, -1, false, true, N, P.nst - 2>(buf, ldy, 1, ncol, ld, cmap, tw, tid, nt);
+    fft_stages_ct<C, -1, false, true, N, P.nst - 2, ORD>(buf, ldy, 1, ncol, ld, cmap, tw, tid, nt);
 }
 
-template <class C, int SG, bool DIF, bool LINE_FAST, int N>
+template <class C, int SG, bool DIF, bool LINE_FAST, int N, int ORD = 0>
 __device__ __forceinline__ void fft_lines_ct(C* buf, int es, int ls, int nlines, const int* lmap, const C* tw,
                                              int tid, int nt) {
-    constexpr CPlan P = make_cplan(N);
+    constexpr CPlan P = make_cplan(N, ORD);
     RDiv ld{nlines, 1.0f / (float)nlines};
-    fft_stages_ct<C, SG, DIF, LINE_FAST, N, DIF ? 0 : P.nst - 1>(buf, es, ls, nlines, ld, lmap, tw, tid, nt);
+    fft_stages_ct<C, SG, DIF, LINE_FAST, N, DIF ? 0 : P.nst - 1, ORD>(buf, es, ls, nlines, ld, lmap, tw, tid, nt);
 }
 
 #define QM_FFT_LENGTHS(X) \

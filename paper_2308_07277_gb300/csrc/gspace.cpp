@@ -130,12 +130,12 @@ static void inv3_transpose_2pi(const double a[9], double b[9]) {
     for (int i = 0; i < 9; ++i) b[i] = twopi * c[i] / det;
 }
 
-static void make_plan(int n, AxisPlan& p, std::vector<int>& rev) {
+void fft_plan(int n, int order, AxisPlan& p, std::vector<int>& rev) {
     p.n = n;
     p.nst = 0;
     int m = n;
-    // radix order: 8s, at most one 4 and one 2, 9s, at most one 3, 5s (must match the
-    // compile-time plans of the FFT kernels)
+    // radix order 0: 8s, at most one 4 and one 2, 9s, at most one 3, 5s; order 1: the same
+    // radices reversed (must match the compile-time plans of the FFT kernels, make_cplan)
     std::vector<int> rs;
     while (m % 8 == 0) { rs.push_back(8); m /= 8; }
     if (m % 4 == 0) { rs.push_back(4); m /= 4; }
@@ -143,6 +143,7 @@ static void make_plan(int n, AxisPlan& p, std::vector<int>& rev) {
     while (m % 9 == 0) { rs.push_back(9); m /= 9; }
     if (m % 3 == 0) { rs.push_back(3); m /= 3; }
     while (m % 5 == 0) { rs.push_back(5); m /= 5; }
+    if (order) std::reverse(rs.begin(), rs.end());
     int L = n;
     for (int r : rs) {
         p.r[p.nst] = r;
@@ -296,7 +297,7 @@ extern "C" qm_status qm_gspace_create(const double lattice[9], int nk, const dou
     qm_status st = QM_OK;
     // FFT plans, twiddles exp(+2 pi i t / N) (quarter turns exact), digit-reversal tables
     for (int d = 0; d < 3; ++d) {
-        make_plan(g->n[d], g->plan[d], g->h_rev[d]);
+        fft_plan(g->n[d], 0, g->plan[d], g->h_rev[d]);
         int N = g->n[d];
         g->h_tw[d].resize(N);
         for (int t = 0; t < N; ++t) {

@@ -148,6 +148,11 @@ class ProfScope {
     bool active_ = false;
 };
 
+// Mixed-radix plan of an FFT length and the digit-reversal table of its in-place DIF passes:
+// rev[position] = natural index.  order 0 = the radix sequence of the single-call kernels,
+// order 1 = the same radices reversed (an alternative for the batched form's autotuner).
+void fft_plan(int n, int order, AxisPlan& p, std::vector<int>& rev);
+
 // ---- FFT path (fft_path.cu) ----
 // Vt[p1][p3][p2] = V(rev1[p1], rev2[p2], rev3[p3]) / N_r   (real type R)
 qm_status launch_vt_prepare(qm_gspace g, const double* vloc, void* vt, bool fp32, cudaStream_t s);

@@ -104,11 +104,16 @@ def test_batch_matches_oracle_small(Q, prec, tol):
 
 
 def test_batch_equals_per_cell_loop_and_is_shape_independent(Q):
+    """Launch shapes change only the schedule: bitwise the same result; the reversed FFT radix
+    order changes the rounding: the same H psi to FP64 round-off (1e-13 against the loop)."""
     cells = small_batch_cells()
     gss, jobs, cases = make_batch(Q, cells, "fp64", drop_proj=(2,))
     outs = []
-    for shape in [(1, 1024, -1), (2, 4096, 1), (1, 8192, 2)]:   # FP64 fits at most 2 CTAs per SM
-        b = Q.Batch(jobs, prec="fp64", ctas_per_sm=shape[0], item_points=shape[1], group_mb=shape[2])
+    shapes = [(1, 1024, -1, 1), (2, 4096, 1, 1), (1, 8192, 2, 1), (2, 2048, -1, 2)]   # FP64: at most 2 CTAs per SM
+    for shape in shapes:
+        b = Q.Batch(jobs, prec="fp64", ctas_per_sm=shape[0], item_points=shape[1], group_mb=shape[2],
+                    fft_order=shape[3])
+        assert b.info()["fft_order"] == shape[3] - 1
         b.run()
         b.check()
         outs.append([j["out"].clone() for j in jobs])
@@ -117,14 +122,16 @@ def test_batch_equals_per_cell_loop_and_is_shape_independent(Q):
         for a, j in zip(outs[-1], jobs):
             assert torch.equal(a, j["out"])
         b.close()
-    for o in outs[1:]:
-        for a, c in zip(outs[0], o):
-            assert torch.equal(a, c)
-    for j, a in zip(jobs, outs[0]):
+    for o, shape in zip(outs[1:], shapes[1:]):
+        if shape[3] == 1:
+            for a, c in zip(outs[0], o):
+                assert torch.equal(a, c)
+    for j, a, a2 in zip(jobs, outs[0], outs[-1]):
         ref = Q.qm_hpsi(j["g"], j["ik"], j["psi"], j["vloc"], j["beta"], j["D"])
         torch.cuda.synchronize()
-        rel = (torch.linalg.vector_norm(a - ref, dim=1) / torch.linalg.vector_norm(ref, dim=1)).max().item()
-        assert rel <= 1e-13, rel
+        for x in (a, a2):
+            rel = (torch.linalg.vector_norm(x - ref, dim=1) / torch.linalg.vector_norm(ref, dim=1)).max().item()
+            assert rel <= 1e-13, rel
 
 
 @pytest.mark.parametrize("prec,tol", [("fp64", TOL64), ("mixed", TOL_MIXED)])
@@ -135,7 +142,7 @@ def test_batch_uneven_cells_full_size(Q, prec, tol):
     gss, jobs, cases = make_batch(Q, cells, prec)
     b = Q.Batch(jobs, prec=prec)
     info = b.info()
-    assert info["candidates"] >= 6 and info["ctas_per_sm"] >= 1 and info["cells"] == 256
+    assert info["candidates"] >= 7 and info["ctas_per_sm"] >= 1 and info["cells"] == 256 and info["fft_order"] in (0, 1)
     b.run()
     b.check()
     njob = len(jobs)
