@@ -60,9 +60,18 @@ def parse():
     ap.add_argument("--davidson-tol", type=float, default=1e-8)
     ap.add_argument("--batched", type=int, default=1, help="also time the batched form (0: skip)")
     ap.add_argument("--large", type=int, default=1, help="also time H psi on the 216- and 255-atom cells (0: skip)")
+    ap.add_argument("--profile", default="",
+                    help="profiling run: only the precision form's H psi steps (projectors prepared) on the named "
+                         "cell (config2, config4, config5) for --warmup + --steps steps, for ncu command lines")
+    ap.add_argument("--profile-k", type=int, default=0, help="--profile: k-points to use (0: all)")
+    ap.add_argument("--profile-batched", default="", help="profiling run of the batched form: mixed or fp64 "
+                    "(the 256 uneven cells, the tuned shape of the benchmark, --warmup + --steps replays)")
     ap.add_argument("--davidson-255", type=int, default=1,
                     help="time Davidson on the 255-atom cell, k-point 0: the combined form vs plain FP64 (about 4 "
                          "minutes; 0: skip)")
+    ap.add_argument("--davidson-255-all", type=int, default=0,
+                    help="1: also solve all 4 k-points of the 255-atom cell concurrently in the combined form "
+                         "(about 3 minutes)")
     ap.add_argument("--davidson-large", type=int, default=0,
                     help="1: also time Davidson on the 216-atom cell, learned vs TPA (about 2 minutes)")
     return ap.parse_args()
@@ -624,8 +633,9 @@ def run_davidson_large(args, Q, S, dev, theta):
 def run_davidson_255(args, Q, S, dev, theta):
     """The all-forms workload: Davidson to 1e-8 Ha on the 255-atom cell (96x96x48, 288 bands,
     1020 projectors).  k-point 0: plain FP64 (no buffer bands) against the combined form
-    (precision form + 28 buffer bands + the learned preconditioner); then the combined form on
-    all 4 k-points solved concurrently (qm_davidson_batched).  Wall time of the calls."""
+    (precision form + 28 buffer bands + the learned preconditioner); with --davidson-255-all 1
+    also the combined form on all 4 k-points solved concurrently (qm_davidson_batched).  Wall
+    time of the calls."""
     import numpy as np
     import torch
     cell = S.config5()
@@ -652,6 +662,9 @@ def run_davidson_255(args, Q, S, dev, theta):
         del p
     out["k0_speedup_combined_vs_fp64"] = out["k0_fp64"]["seconds"] / out["k0_combined"]["seconds"]
     out["k0_max_eig_diff_ha"] = float(np.abs(eigs["fp64"] - eigs["combined"]).max())
+    if not args.davidson_255_all:
+        g.close()
+        return out
     jobs = [{"g": g.handle, "ik": ik, "vloc": v, "beta": betas[ik], "D": D,
              "psi": torch.from_numpy(S.psi_random(cell.seed, nb + nextra, g.npw[ik], stream=ik)).to(dev)}
             for ik in range(nk)]
@@ -770,10 +783,66 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_profile(args):
+    """Only the kernels a profiler should see: the precision form's H psi steps on one cell (all
+    k-points or the first --profile-k), projectors prepared, or replays of the batched form."""
+    import torch
+
+    import paper_2308_07277_gb300 as Q
+    import qm_synth as S
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if args.profile_batched:
+        prec = args.profile_batched
+        cells = S.config3_cells(lambda c: product_grid(Q, c))
+        cdt = torch.complex128 if prec == "fp64" else torch.complex64
+        gss, jobs = [], []
+        for cell in cells:
+            g = Q.GSpace(cell.lattice, cell.kpts, cell.ecut_ha, cell.grid)
+            gss.append(g)
+            v = torch.from_numpy(S.vloc_on_grid(cell.lattice, cell.tau, cell.grid, cell.depth, cell.width,
+                                                ortho_period=cell.ortho_period)).to(dev)
+            D = torch.from_numpy(S.dvals(cell.nat)).to(dev)
+            for ik in range(len(cell.kpts)):
+                _, _, kpg = g.indices(ik)
+                psi = torch.from_numpy(S.psi_random(cell.seed, cell.nbnd, g.npw[ik], stream=ik)).to(cdt).to(dev)
+                beta = torch.from_numpy(S.beta_of_q(kpg, cell.tau, cell.omega, cell.rc)).to(cdt).to(dev)
+                jobs.append({"g": g.handle, "ik": ik, "psi": psi, "vloc": v, "beta": beta, "D": D,
+                             "out": torch.empty_like(psi)})
+        shape = dict(ctas_per_sm=3, item_points=8192, group_mb=-1) if prec == "mixed" else \
+            dict(ctas_per_sm=1, item_points=8192, group_mb=-1)
+        b = Q.Batch(jobs, prec=prec, **shape)
+        for _ in range(args.warmup + args.steps):
+            b.run()
+        b.check()
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": "batched", "prec": prec, "replays": args.warmup + args.steps, **b.info()}))
+        return
+    cell = getattr(S, args.profile)()
+    nk = args.profile_k or len(cell.kpts)
+    g = Q.GSpace(cell.lattice, cell.kpts[:nk], cell.ecut_ha, cell.grid)
+    v = torch.from_numpy(S.vloc_on_grid(cell.lattice, cell.tau, cell.grid)).to(dev)
+    D = torch.from_numpy(S.dvals(cell.nat)).to(dev)
+    psi, beta, out = [], [], []
+    for ik in range(nk):
+        _, _, kpg = g.indices(ik)
+        psi.append(torch.from_numpy(S.psi_random(cell.seed, cell.nbnd, g.npw[ik], stream=ik)).to(torch.complex64).to(dev))
+        beta.append(torch.from_numpy(S.beta_of_q(kpg, cell.tau, cell.omega)).to(torch.complex64).to(dev))
+        out.append(torch.empty_like(psi[-1]))
+        Q.qm_hpsi_prepare(g.handle, ik, beta[-1])
+    for _ in range(args.warmup + args.steps):
+        for ik in range(nk):
+            Q.qm_hpsi(g.handle, ik, psi[ik], v, beta[ik], D, out=out[ik], prec="mixed")
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": cell.name, "k_points": nk, "steps": args.warmup + args.steps}))
+    g.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.profile or args.profile_batched:
+        run_profile(args)
     else:
         run_ours(args)
 
