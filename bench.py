@@ -64,6 +64,7 @@ def parse():
                     help="profiling run: only the precision form's H psi steps (projectors prepared) on the named "
                          "cell (config2, config4, config5) for --warmup + --steps steps, for ncu command lines")
     ap.add_argument("--profile-k", type=int, default=0, help="--profile: k-points to use (0: all)")
+    ap.add_argument("--profile-prec", default="mixed", choices=["mixed", "fp64"], help="--profile: precision form")
     ap.add_argument("--profile-batched", default="", help="profiling run of the batched form: mixed or fp64 "
                     "(the 256 uneven cells, the tuned shape of the benchmark, --warmup + --steps replays)")
     ap.add_argument("--davidson-255", type=int, default=1,
@@ -819,21 +820,24 @@ def run_profile(args):
         return
     cell = getattr(S, args.profile)()
     nk = args.profile_k or len(cell.kpts)
+    prec = args.profile_prec
+    cdt = torch.complex64 if prec == "mixed" else torch.complex128
     g = Q.GSpace(cell.lattice, cell.kpts[:nk], cell.ecut_ha, cell.grid)
     v = torch.from_numpy(S.vloc_on_grid(cell.lattice, cell.tau, cell.grid)).to(dev)
     D = torch.from_numpy(S.dvals(cell.nat)).to(dev)
     psi, beta, out = [], [], []
     for ik in range(nk):
         _, _, kpg = g.indices(ik)
-        psi.append(torch.from_numpy(S.psi_random(cell.seed, cell.nbnd, g.npw[ik], stream=ik)).to(torch.complex64).to(dev))
-        beta.append(torch.from_numpy(S.beta_of_q(kpg, cell.tau, cell.omega)).to(torch.complex64).to(dev))
+        psi.append(torch.from_numpy(S.psi_random(cell.seed, cell.nbnd, g.npw[ik], stream=ik)).to(cdt).to(dev))
+        beta.append(torch.from_numpy(S.beta_of_q(kpg, cell.tau, cell.omega)).to(cdt).to(dev))
         out.append(torch.empty_like(psi[-1]))
-        Q.qm_hpsi_prepare(g.handle, ik, beta[-1])
+        if prec == "mixed":
+            Q.qm_hpsi_prepare(g.handle, ik, beta[-1])
     for _ in range(args.warmup + args.steps):
         for ik in range(nk):
-            Q.qm_hpsi(g.handle, ik, psi[ik], v, beta[ik], D, out=out[ik], prec="mixed")
+            Q.qm_hpsi(g.handle, ik, psi[ik], v, beta[ik], D, out=out[ik], prec=prec)
     torch.cuda.synchronize()
-    print(json.dumps({"profile": cell.name, "k_points": nk, "steps": args.warmup + args.steps}))
+    print(json.dumps({"profile": cell.name, "precision": prec, "k_points": nk, "steps": args.warmup + args.steps}))
     g.close()
 
 
