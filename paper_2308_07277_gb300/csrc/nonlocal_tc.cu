@@ -438,6 +438,14 @@ NlLayout nl_layout(int nproj, int nb, int npw, bool with_beta) {
     return L;
 }
 
+// grid-dimension limits of the split and GEMM launches (y and z of a grid are below 65536)
+qm_status check_limits(const NlLayout& L) {
+    if ((long)L.mtile_p * TM / 8 > 65535 || (long)L.ntile_p * L.bn_p / 8 > 65535 || L.nkt_a > 65535 ||
+        L.ntile_a > 65535 || L.mtile_p > 65535)
+        return fail(QM_ERR_UNSUPPORTED, "tensor-core nonlocal part: too many bands, projectors or plane waves");
+    return QM_OK;
+}
+
 inline int grid_for(long n, int per = 256) { return grid_stride_blocks((size_t)std::max<long>(n, 1), per, 16); }
 
 qm_status split_beta(int nproj, int npw, const float2* beta, int ld_beta, const NlLayout& L, unsigned char* betaK,
@@ -486,6 +494,7 @@ qm_status nonlocal_tc_prepare(int nproj, int nb, int npw, const float2* beta, in
                               cudaStream_t s) {
     if (nproj <= 0) return QM_OK;
     const NlLayout L = nl_layout(nproj, nb, npw, true);
+    if (qm_status st0 = check_limits(L)) return st0;
     unsigned char* w = (unsigned char*)beta_work;
     return split_beta(nproj, npw, beta, ld_beta, L, w + L.betaK_off, w + L.betaT_off, s);
 }
@@ -496,6 +505,7 @@ qm_status nonlocal_tc(int nproj, int nb, int npw, const float2* beta, int ld_bet
     if (nproj <= 0 || nb <= 0) return QM_OK;
     const bool own_beta = beta_prepared == nullptr;
     const NlLayout L = nl_layout(nproj, nb, npw, own_beta);
+    if (qm_status st0 = check_limits(L)) return st0;
     unsigned char* w = (unsigned char*)work;
     const unsigned char* betaK;
     const unsigned char* betaT;
