@@ -708,14 +708,18 @@ inline bool fused_length(int n) {
 // x sticks per CTA of the stick kernels: 64 in FP32 (19 KB of lines), 32 in FP64
 template <class R> constexpr int sticks_per_cta() { return sizeof(R) == 4 ? 64 : 32; }
 constexpr int kThreads = 256;
+// resident CTAs the register budget is sized for: FP32 4 (stage-per-pass) or 3 (two register
+// passes, groups of up to 18 complex values); FP64 2, which the shared memory of an FP64
+// plane or stick tile allows at most anyway (fewer would force spills of the 64-bit values)
+template <class R, bool FUSED> constexpr int fft_min_ctas() { return sizeof(R) == 8 ? 2 : (FUSED ? 3 : 4); }
 
 // ---------------------------------------------------------------- K1
 // FUSED: the two-register-pass transforms (a separate instantiation, so that the stage-per-pass
 // lengths keep their lower register count and higher occupancy)
 template <class R, bool FUSED>
-__global__ void __launch_bounds__(kThreads, FUSED ? 3 : 4)
+__global__ void __launch_bounds__(kThreads, fft_min_ctas<R, FUSED>())
 k_stick_inverse(const typename Cx<R>::T* __restrict__ psi, int ld_psi, const int* __restrict__ stick_g0,
-                const int2* __restrict__ g_code, int nstick, int nstick_pad, AxisPlan px,
+                const int2* __restrict__ g_code, int nstick, int nstick_pad, const __grid_constant__ AxisPlan px,
                 const typename Cx<R>::T* __restrict__ tw_x, int ldx, typename Cx<R>::T* __restrict__ T) {
     using C = typename Cx<R>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -749,9 +753,9 @@ k_stick_inverse(const typename Cx<R>::T* __restrict__ psi, int ld_psi, const int
 
 // ---------------------------------------------------------------- K2
 template <class R, bool FUSED>
-__global__ void __launch_bounds__(kThreads, FUSED ? 3 : 4)
+__global__ void __launch_bounds__(kThreads, fft_min_ctas<R, FUSED>())
 k_plane(typename Cx<R>::T* __restrict__ T, int nstick, int nstick_pad, const int* __restrict__ stick_plane,
-        const int* __restrict__ rows, int nrow, AxisPlan py, AxisPlan pz,
+        const int* __restrict__ rows, int nrow, const __grid_constant__ AxisPlan py, const __grid_constant__ AxisPlan pz,
         const typename Cx<R>::T* __restrict__ tw_y, const typename Cx<R>::T* __restrict__ tw_z, int ldy,
         const R* __restrict__ Vt, int N1) {
     using C = typename Cx<R>::T;
@@ -785,10 +789,10 @@ k_plane(typename Cx<R>::T* __restrict__ T, int nstick, int nstick_pad, const int
 
 // ---------------------------------------------------------------- K3
 template <class R, bool FUSED>
-__global__ void __launch_bounds__(kThreads, FUSED ? 3 : 4)
+__global__ void __launch_bounds__(kThreads, fft_min_ctas<R, FUSED>())
 k_stick_forward(const typename Cx<R>::T* __restrict__ T, int nstick, int nstick_pad,
                 const int* __restrict__ stick_g0, const int2* __restrict__ g_code, const R* __restrict__ kin,
-                AxisPlan px, const typename Cx<R>::T* __restrict__ tw_x, int ldx,
+                const __grid_constant__ AxisPlan px, const typename Cx<R>::T* __restrict__ tw_x, int ldx,
                 const typename Cx<R>::T* __restrict__ psi, int ld_psi, typename Cx<R>::T* __restrict__ out,
                 int ld_out, int accumulate) {
     using C = typename Cx<R>::T;
