@@ -4,9 +4,11 @@
 // Network: z1 = W1 f + b1, h1 = silu(z1), z2 = W2 h1 + b2, h2 = silu(z2), z3 = w3.h2 + b3,
 // K = K_TPA(x) softplus(z3) / log 2: a positive factor on the TPA curve of the plane wave
 // (z3 = 0 gives TPA exactly); parameters one flat FP32 vector (layout in include/qm.h).  Arithmetic is
-// BF16 x BF16 with FP32 accumulation: weights, features and hidden activations are rounded to
-// BF16 before every product; sums, activation functions and the loss are FP32.
-// Features (scale-free): x = T_G / T_n, e = eps_n / T_n, l = log(max(|r_G| sqrt(npw)/||r_n||, 1e-6)).
+// BF16 x BF16 with FP32 accumulation: weights, features, hidden activations and the backward
+// pass's deltas are rounded to BF16 before every product; sums, activation functions and the
+// loss are FP32.
+// Features (scale-free): x = T_G / T_n, e = eps_n / T_n, d = (H_GG - eps_n) / T_n (H_GG the
+// diagonal of H(k) in the plane-wave basis).
 //
 // Kernels
 //   k_mlp_infer   inference with the 64 x 64 layer on the tensor cores: a CTA of 4 warps takes
@@ -15,8 +17,10 @@
 //                 tcgen05.mma (M = 128, N = 64, K = 4 x 16) against W2 (B operand, resident in
 //                 shared memory) into a 64-column FP32 accumulator in tensor memory, and every
 //                 thread reads its sample's row back with tcgen05.ld for the output layer
-//   k_mlp_tile    training tiles of 64 samples (forward, and forward + backward), SIMT with the
-//                 same BF16 rounding; per-CTA gradients are reduced in a fixed order
+//   k_mlp_grad    training: forward and backward of 128-sample tiles with the three 64 x 64
+//                 contractions (z2, dz1 and the weight gradient, which also carries the bias and
+//                 first-layer gradients) as tcgen05 products; per-CTA gradient partials are
+//                 reduced in a fixed order
 //   k_mlp_pairs   training samples from Ritz pairs and exact corrections
 //   k_mlp_adam    Adam update (Kingma & Ba, ICLR 2015)
 #include <cuda_bf16.h>
@@ -234,146 +238,274 @@ int infer_grid(long ntiles) {
     return (int)std::max<long>(1, std::min<long>(ntiles, (long)nsm * 8));
 }
 
-// ---------------------------------------------------------------- training tiles (SIMT)
-constexpr int kTS = 64;   // samples per tile
-constexpr int kTT = 256;  // threads
-constexpr int kW2S = 65;  // padded row stride of W2 in shared memory
-constexpr int kOwn = (kNP + kTT - 1) / kTT;  // gradient entries owned per thread (18)
-constexpr size_t kTileSmem =
-    sizeof(float) * (kH * 3 + kH + kH * kW2S + kH + kH + 1 + kTS * 3 + 4 * kTS * kH + 2 * kTS);
+// ---------------------------------------------------------------- training (tensor cores)
+// Forward and backward pass of a tile of 128 samples (one per thread, one per TMEM lane) with
+// the three 64 x 64 contractions on the tensor cores (BF16 operands, FP32 accumulators):
+//   MMA1  z2 - b2 = h1 W2^T      M = 128 samples, N = 64, K = 64   (A = h1,  B = W2)
+//   MMA2  dz1 / silu'(z1) = dz2 W2                                  (A = dz2, B = W2^T)
+//   MMA3  G += Amat Bmat^T over the tile's samples, accumulated in tensor memory across tiles:
+//         Amat rows 0..63 = dz2^T, rows 64..127 = dz1^T (K = 128 samples);
+//         Bmat rows 0..63 = h1^T, row 64 = ones, rows 65..67 = f^T, rows 68..79 zero (N = 80), so
+//         G[j][i] = dW2[j][i], G[j][64] = db2[j], G[64+j][64] = db1[j], G[64+j][65+k] = dW1[j][k].
+// dw3 and db3 are per-tile column sums on the CUDA cores.  dz2 and dz1 are rounded to BF16
+// before their products, like every other operand.
+constexpr int kGN3 = 80;                             // N of MMA3
+constexpr int kGStride = kH + 1;                     // padded row of h2 (floats, odd: no bank conflicts)
+constexpr uint32_t kIdesc3 = tc::idesc_bf16(128, kGN3);
+constexpr size_t kGradSmem = 2 * 16384 + 2 * 8192 + 32768 + 20480 + sizeof(float) * (kMT * kGStride + kMT + kH * 3 +
+                                                                                    3 * kH + 4);
 
-// MODE 0: K per sample.  MODE 1: forward + backward of the cosine loss given per-band
-// coefficients; per-CTA gradient partials to gpart[blockIdx.x][kNP].
-template <int MODE>
-__global__ void __launch_bounds__(kTT)
-k_mlp_tile(long n, const float* __restrict__ feats, const float* __restrict__ theta, float* __restrict__ Kout,
-           const int* __restrict__ band_of, const float* __restrict__ r2, const float* __restrict__ cc,
-           const float* __restrict__ coef, const float* __restrict__ ratio, float* __restrict__ gpart) {
-    extern __shared__ float sm[];
-    float* W1 = sm;
-    float* b1 = W1 + kH * 3;
-    float* W2 = b1 + kH;
-    float* b2 = W2 + kH * kW2S;
-    float* w3 = b2 + kH;
-    float* b3 = w3 + kH;
-    float* F = b3 + 1;
-    float* H1 = F + kTS * 3;
-    float* S1 = H1 + kTS * kH;  // silu'(z1), later reused
-    float* H2 = S1 + kTS * kH;  // h2, then dz2
-    float* S2 = H2 + kTS * kH;  // silu'(z2), then dz1
-    float* Z3 = S2 + kTS * kH;
-    float* DZ3 = Z3 + kTS;
-    const int tid = threadIdx.x;
-    for (int i = tid; i < kH * 3; i += kTT) W1[i] = bf16r(theta[kOffW1 + i]);
-    for (int i = tid; i < kH; i += kTT) {
-        b1[i] = bf16r(theta[kOffB1 + i]);
-        b2[i] = bf16r(theta[kOffB2 + i]);
-        w3[i] = bf16r(theta[kOffW3 + i]);
+// byte offset of element (row, k) of a K-major no-swizzle operand with 128 K columns
+__device__ __forceinline__ int cm_off128(int row, int k) {
+    return (row >> 3) * 2048 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
+}
+__device__ __forceinline__ void put_bf16(unsigned char* base, int off, float v) {
+    *reinterpret_cast<__nv_bfloat16*>(base + off) = __float2bfloat16_rn(v);
+}
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+    return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(a)) |
+           ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(b)) << 16);
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t v[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15}, [%16];\n"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+          "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+// one thread issues nks K-steps of 16 (operands K-major, 8-row groups sbo bytes apart) and
+// commits them to the mbarrier
+__device__ __forceinline__ void mma_issue(uint32_t d, uint32_t a, uint32_t b, uint32_t sbo, int nks, uint32_t idesc,
+                                          bool accumulate, uint32_t mbar) {
+    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    for (int ks = 0; ks < nks; ++ks) {
+        const uint64_t da = tc::sdesc(a + ks * 256, 128, sbo);
+        const uint64_t db = tc::sdesc(b + ks * 256, 128, sbo);
+        const uint32_t acc = (accumulate || ks > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+            "l"(da), "l"(db), "r"(idesc), "r"(acc));
     }
-    for (int e = tid; e < kH * kH; e += kTT) W2[(e >> 6) * kW2S + (e & 63)] = bf16r(theta[kOffW2 + e]);
-    if (tid == 0) *b3 = bf16r(theta[kOffB3]);
-    float acc[kOwn];
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar));
+}
+// shared-memory writes by the threads -> visible to the tensor core, then one thread issues
+__device__ __forceinline__ void to_async_proxy_and_sync() {
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
+}
+
+// Cosine-loss gradient of every tile of the CTA (grid-stride), given per-band coefficients:
+// per-CTA partials to gpart[blockIdx.x][kNP].  128 threads; a bounded wait that expires sets
+// *err and ends the CTA (its partials are then not written).
+__global__ void __launch_bounds__(kMT, 1)
+k_mlp_grad(long n, const float* __restrict__ feats, const float* __restrict__ theta, const int* __restrict__ band_of,
+           const float* __restrict__ r2, const float* __restrict__ cc, const float* __restrict__ coef,
+           const float* __restrict__ ratio, float* __restrict__ gpart, int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char dsm[];
+    unsigned char* sA1 = dsm;              // h1, 128 x 64
+    unsigned char* sA2 = sA1 + 16384;      // dz2, 128 x 64
+    unsigned char* sW2 = sA2 + 16384;      // W2 as the B operand of MMA1 (rows j, K = i)
+    unsigned char* sW2t = sW2 + 8192;      // W2^T as the B operand of MMA2 (rows i, K = j)
+    unsigned char* sA3 = sW2t + 8192;      // Amat of MMA3, 128 x 128
+    unsigned char* sB3 = sA3 + 32768;      // Bmat of MMA3, 80 x 128
+    float* sH2 = reinterpret_cast<float*>(sB3 + 20480);  // h2 [sample][kGStride]
+    float* sDz3 = sH2 + kMT * kGStride;
+    float* sW1 = sDz3 + kMT;
+    float* sb1 = sW1 + kH * 3;
+    float* sb2 = sb1 + kH;
+    float* sw3 = sb2 + kH;
+    float* sb3 = sw3 + kH;
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                         tc::smem_u32(&tmem_base)),
+                     "r"(256));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(tc::smem_u32(&mbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;\n");
+        *sb3 = bf16r(theta[kOffB3]);
+    }
+    for (int i = tid; i < kH * 3; i += kMT) sW1[i] = bf16r(theta[kOffW1 + i]);
+    for (int i = tid; i < kH; i += kMT) {
+        sb1[i] = bf16r(theta[kOffB1 + i]);
+        sb2[i] = bf16r(theta[kOffB2 + i]);
+        sw3[i] = bf16r(theta[kOffW3 + i]);
+    }
+    for (int e = tid; e < kH * kH; e += kMT) {
+        const int j = e >> 6, i = e & 63;
+        const float w = theta[kOffW2 + e];
+        put_bf16(sW2, cm_off(j, i), w);
+        put_bf16(sW2t, cm_off(i, j), w);
+    }
+    for (int r = 64; r < kGN3; ++r) put_bf16(sB3, cm_off128(r, tid), r == 64 ? 1.f : 0.f);  // ones, f (per tile), zeros
+    to_async_proxy_and_sync();
+    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    const uint32_t tmem = tmem_base;
+    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+    const uint32_t mb = tc::smem_u32(&mbar);
+    uint32_t phase = 0;
+    float gw3 = 0.f;  // thread j < 64: dw3[j]; thread 64: db3
+    bool aborted = false;
+    int tiles = 0;
+    const long nt = (n + kMT - 1) / kMT;
+    for (long tile = blockIdx.x; tile < nt; tile += gridDim.x, ++tiles) {
+        const long s = tile * kMT + tid;
+        const bool valid = s < n;
+        float f[3] = {0.f, 0.f, 0.f};
+        if (valid) {
+            f[0] = feats[3 * s];
+            f[1] = feats[3 * s + 1];
+            f[2] = feats[3 * s + 2];
+        }
+        const float t = valid ? tpa(f[0]) * kInvLog2 : 0.f;  // unrounded x
+        f[0] = bf16r(f[0]);
+        f[1] = bf16r(f[1]);
+        f[2] = bf16r(f[2]);
+        // layer 1: h1 row of this sample into MMA1's A operand and column `tid` of Bmat
 #pragma unroll
-    for (int q = 0; q < kOwn; ++q) acc[q] = 0.f;
-    const int jt = tid & 63, sg = tid >> 6;  // thread -> (column j, sample group)
-    const long ntile = (n + kTS - 1) / kTS;
-    for (long tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
-        const long s0 = tile * kTS;
-        const int ns = (int)min((long)kTS, n - s0);
-        __syncthreads();
-        for (int i = tid; i < kTS * 3; i += kTT) F[i] = (i / 3) < ns ? bf16r(feats[s0 * 3 + i]) : 0.f;
-        __syncthreads();
-        for (int s = sg; s < kTS; s += 4) {  // layer 1
-            const float z = b1[jt] + W1[3 * jt] * F[3 * s] + W1[3 * jt + 1] * F[3 * s + 1] + W1[3 * jt + 2] * F[3 * s + 2];
-            H1[s * kH + jt] = bf16r(silu(z));
-            S1[s * kH + jt] = silu_d(z);
+        for (int kc = 0; kc < kH / 8; ++kc) {
+            float h[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int j = kc * 8 + q;
+                h[q] = bf16r(silu(sb1[j] + sW1[3 * j] * f[0] + sW1[3 * j + 1] * f[1] + sW1[3 * j + 2] * f[2]));
+                put_bf16(sB3, cm_off128(j, tid), h[q]);
+            }
+            *reinterpret_cast<uint4*>(sA1 + cm_off(tid, kc * 8)) =
+                make_uint4(pack_bf16(h[0], h[1]), pack_bf16(h[2], h[3]), pack_bf16(h[4], h[5]), pack_bf16(h[6], h[7]));
         }
-        __syncthreads();
-        for (int s = sg; s < kTS; s += 4) {  // layer 2
-            float z = b2[jt];
-            const float* h = H1 + s * kH;
-            const float* wr = W2 + jt * kW2S;
-#pragma unroll 16
-            for (int i = 0; i < kH; ++i) z += wr[i] * h[i];
-            H2[s * kH + jt] = bf16r(silu(z));
-            S2[s * kH + jt] = silu_d(z);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) put_bf16(sB3, cm_off128(65 + k, tid), f[k]);
+        to_async_proxy_and_sync();
+        if (tid == 0) mma_issue(tmem, tc::smem_u32(sA1), tc::smem_u32(sW2), 1024, kH / 16, kIdesc, false, mb);
+        bool ok = tc::mbar_wait(mb, phase, kSpin);
+        phase ^= 1u;
+        if (!__syncthreads_and(ok)) {
+            aborted = true;
+            break;
         }
-        __syncthreads();
-        if (tid < kTS) {  // output layer
-            float z = *b3;
-            const float* h = H2 + tid * kH;
-#pragma unroll 16
-            for (int j = 0; j < kH; ++j) z += w3[j] * h[j];
-            const float t = tid < ns ? tpa(feats[(s0 + tid) * 3]) * kInvLog2 : 0.f;  // unrounded x
-            const float K = t * softplus(z);
-            if (MODE == 0) {
-                if (tid < ns) Kout[s0 + tid] = K;
-            } else {
-                float d = 0.f;
-                if (tid < ns) {
-                    const long s = s0 + tid;
-                    const int b = band_of[s];
-                    d = coef[b] * (ratio[b] * K * r2[s] - cc[s]) * t * sigm(z);
-                }
-                DZ3[tid] = d;
+        asm volatile("tcgen05.fence::after_thread_sync;\n");
+        // layer 2 and output from z2 - b2 (tensor memory columns 0..63)
+        float z3 = *sb3;
+#pragma unroll
+        for (int c0 = 0; c0 < kH; c0 += 16) {
+            uint32_t v[16];
+            tmem_ld16(tmem + lane_off + (uint32_t)c0, v);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const float h2 = bf16r(silu(__uint_as_float(v[q]) + sb2[c0 + q]));
+                sH2[tid * kGStride + c0 + q] = h2;
+                z3 += sw3[c0 + q] * h2;
             }
         }
-        if (MODE == 0) continue;
-        __syncthreads();
-        // gradients of w3 and b3 (need h2 before it is overwritten)
-#pragma unroll
-        for (int q = 0; q < kOwn; ++q) {
-            const int e = tid + q * kTT;
-            if (e >= kOffW3 && e < kNP) {
-                float a = 0.f;
-                if (e == kOffB3) {
-                    for (int s = 0; s < kTS; ++s) a += DZ3[s];
-                } else {
-                    const int j = e - kOffW3;
-                    for (int s = 0; s < kTS; ++s) a += DZ3[s] * H2[s * kH + j];
-                }
-                acc[q] += a;
-            }
+        float dz3 = 0.f;
+        if (valid) {
+            const int b = band_of[s];
+            const float K = t * softplus(z3);
+            dz3 = coef[b] * (ratio[b] * K * r2[s] - cc[s]) * t * sigm(z3);
         }
-        __syncthreads();
-        for (int s = sg; s < kTS; s += 4) H2[s * kH + jt] = DZ3[s] * w3[jt] * S2[s * kH + jt];  // dz2
-        __syncthreads();
-        for (int s = sg; s < kTS; s += 4) {  // dz1 = (W2^T dz2) silu'(z1)
+        sDz3[tid] = dz3;
+        // dz2 = dz3 w3 silu'(z2): A operand of MMA2 (row tid) and rows 0..63 of Amat (column tid)
+#pragma unroll
+        for (int c0 = 0; c0 < kH; c0 += 16) {
+            uint32_t v[16];
+            tmem_ld16(tmem + lane_off + (uint32_t)c0, v);
+            float d[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                d[q] = bf16r(dz3 * sw3[c0 + q] * silu_d(__uint_as_float(v[q]) + sb2[c0 + q]));
+                put_bf16(sA3, cm_off128(c0 + q, tid), d[q]);
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                *reinterpret_cast<uint4*>(sA2 + cm_off(tid, c0 + 8 * h)) =
+                    make_uint4(pack_bf16(d[8 * h], d[8 * h + 1]), pack_bf16(d[8 * h + 2], d[8 * h + 3]),
+                               pack_bf16(d[8 * h + 4], d[8 * h + 5]), pack_bf16(d[8 * h + 6], d[8 * h + 7]));
+        }
+        to_async_proxy_and_sync();
+        if (tid == 0) mma_issue(tmem + 64, tc::smem_u32(sA2), tc::smem_u32(sW2t), 1024, kH / 16, kIdesc, false, mb);
+        // dw3, db3 of this tile while the tensor core works (h2 and dz3 are complete)
+        if (tid < kH) {
             float a = 0.f;
-            const float* d2 = H2 + s * kH;
-#pragma unroll 16
-            for (int j = 0; j < kH; ++j) a += W2[j * kW2S + jt] * d2[j];
-            S2[s * kH + jt] = a * S1[s * kH + jt];
-        }
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < kOwn; ++q) {
-            const int e = tid + q * kTT;
-            if (e >= kOffW3) continue;
+            for (int q = 0; q < kMT; ++q) a += sDz3[q] * sH2[q * kGStride + tid];
+            gw3 += a;
+        } else if (tid == kH) {
             float a = 0.f;
-            if (e < kOffB1) {  // W1[j][k]
-                const int j = e / 3, k = e - 3 * (e / 3);
-                for (int s = 0; s < kTS; ++s) a += S2[s * kH + j] * F[3 * s + k];
-            } else if (e < kOffW2) {  // b1[j]
-                const int j = e - kOffB1;
-                for (int s = 0; s < kTS; ++s) a += S2[s * kH + j];
-            } else if (e < kOffB2) {  // W2[j][i]
-                const int j = (e - kOffW2) >> 6, i = (e - kOffW2) & 63;
-                for (int s = 0; s < kTS; ++s) a += H2[s * kH + j] * H1[s * kH + i];
-            } else {  // b2[j]
-                const int j = e - kOffB2;
-                for (int s = 0; s < kTS; ++s) a += H2[s * kH + j];
-            }
-            acc[q] += a;
+            for (int q = 0; q < kMT; ++q) a += sDz3[q];
+            gw3 += a;
         }
-    }
-    if (MODE == 1) {
+        ok = tc::mbar_wait(mb, phase, kSpin);
+        phase ^= 1u;
+        if (!__syncthreads_and(ok)) {
+            aborted = true;
+            break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;\n");
+        // dz1 = (dz2 W2) silu'(z1): rows 64..127 of Amat (column tid)
 #pragma unroll
-        for (int q = 0; q < kOwn; ++q) {
-            const int e = tid + q * kTT;
-            if (e < kNP) gpart[(size_t)blockIdx.x * kNP + e] = acc[q];
+        for (int c0 = 0; c0 < kH; c0 += 16) {
+            uint32_t v[16];
+            tmem_ld16(tmem + lane_off + 64u + (uint32_t)c0, v);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const int i = c0 + q;
+                const float z1 = sb1[i] + sW1[3 * i] * f[0] + sW1[3 * i + 1] * f[1] + sW1[3 * i + 2] * f[2];
+                put_bf16(sA3, cm_off128(64 + i, tid), __uint_as_float(v[q]) * silu_d(z1));
+            }
+        }
+        to_async_proxy_and_sync();
+        if (tid == 0)
+            mma_issue(tmem + 128, tc::smem_u32(sA3), tc::smem_u32(sB3), 2048, kMT / 16, kIdesc3, tiles > 0, mb);
+        // the next tile overwrites the operands: wait for MMA3 here
+        ok = tc::mbar_wait(mb, phase, kSpin);
+        phase ^= 1u;
+        if (!__syncthreads_and(ok)) {
+            aborted = true;
+            break;
         }
     }
+    if (aborted) {
+        if (tid == 0) atomicExch(err, 1);
+    } else {
+        asm volatile("tcgen05.fence::after_thread_sync;\n");
+        float* g = gpart + (size_t)blockIdx.x * kNP;
+        if (tiles == 0) {
+            for (int e = tid; e < kNP; e += kMT) g[e] = 0.f;
+        } else {
+            // row tid of G: dW2 row j (tid < 64) with db2[j]; db1 and dW1 row j (tid = 64 + j)
+#pragma unroll 1
+            for (int c0 = 0; c0 < kGN3; c0 += 16) {
+                uint32_t v[16];
+                tmem_ld16(tmem + lane_off + 128u + (uint32_t)c0, v);
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const int col = c0 + q;
+                    const float x = __uint_as_float(v[q]);
+                    if (tid < kH) {
+                        if (col < kH) g[kOffW2 + tid * kH + col] = x;
+                        else if (col == kH) g[kOffB2 + tid] = x;
+                    } else {
+                        const int j = tid - kH;
+                        if (col == kH) g[kOffB1 + j] = x;
+                        else if (col > kH && col <= kH + 3) g[kOffW1 + 3 * j + (col - kH - 1)] = x;
+                    }
+                }
+            }
+            if (tid < kH) g[kOffW3 + tid] = gw3;
+            if (tid == kH) g[kOffB3] = gw3;
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(256));
 }
 
 // per band: A = sum K^2 r2, B = sum K c over its samples (FP64 sums in a fixed order)
@@ -592,26 +724,24 @@ struct DevBuf {
     }
 };
 
-int train_grid() {
+int train_grid() {  // one gradient CTA per SM (its shared memory allows one)
     int dev = 0, nsm = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    return 2 * nsm;
+    return nsm;
 }
 
 // loss (device) and gradient (device) for one parameter vector
 qm_status loss_grad_dev(int nband, const long long* off, const int* band_of, long n, const float* feats, const float* r2,
                         const float* cc, const float* D, const float* W, const float* theta, float* K, double* A, double* B,
-                        float* coef, float* ratio, double* loss_dev, float* gpart, int nblk, float* grad,
+                        float* coef, float* ratio, double* loss_dev, float* gpart, int nblk, float* grad, int* err,
                         cudaStream_t s) {
-    qm_status st0;
-    if ((st0 = allow_dynamic_smem((const void*)k_mlp_tile<0>, kTileSmem, "network training shared memory")) ||
-        (st0 = allow_dynamic_smem((const void*)k_mlp_tile<1>, kTileSmem, "network training shared memory")))
-        return st0;
+    qm_status st0 = allow_dynamic_smem((const void*)k_mlp_grad, kGradSmem, "network training shared memory");
+    if (st0) return st0;
     {
         ProfScope pf(PF_MLP, s);
-        k_mlp_tile<0><<<nblk, kTT, kTileSmem, s>>>(n, feats, theta, K, nullptr, nullptr, nullptr, nullptr, nullptr,
-                                                   nullptr);
+        FeatArray src{feats, K, n};
+        k_mlp_infer<FeatArray><<<infer_grid((n + kMT - 1) / kMT), kMT, 0, s>>>(src, theta, err);
     }
     {
         ProfScope pf(PF_MLP, s);
@@ -623,13 +753,23 @@ qm_status loss_grad_dev(int nband, const long long* off, const int* band_of, lon
     }
     {
         ProfScope pf(PF_MLP, s);
-        k_mlp_tile<1><<<nblk, kTT, kTileSmem, s>>>(n, feats, theta, nullptr, band_of, r2, cc, coef, ratio, gpart);
+        k_mlp_grad<<<nblk, kMT, kGradSmem, s>>>(n, feats, theta, band_of, r2, cc, coef, ratio, gpart, err);
     }
     {
         ProfScope pf(PF_MLP, s);
         k_mlp_reduce_grad<<<(kNP + 255) / 256, 256, 0, s>>>(gpart, nblk, grad);
     }
     return cuda_check(cudaGetLastError(), "learned preconditioner training launch");
+}
+
+// the error word of the bounded tensor-core waits, read after the stream has drained
+qm_status check_err_word(const int* err, cudaStream_t s, const char* what) {
+    int e = 0;
+    qm_status st;
+    if ((st = cuda_check(cudaMemcpyAsync(&e, err, sizeof(int), cudaMemcpyDeviceToHost, s), "D2H error word")) ||
+        (st = cuda_check(cudaStreamSynchronize(s), "stream sync")))
+        return st;
+    return e ? fail(QM_ERR_TIMEOUT, what) : QM_OK;
 }
 
 qm_status check_samples(int nband, const long long* band_off, long nsamples, const void* feats, const void* r2,
@@ -722,23 +862,24 @@ extern "C" qm_status qm_mlp_loss_grad(int nband, const long long* band_off, cons
     const long n = (long)last;
     if (n < 1) return fail(QM_ERR_ARG, "qm_mlp_loss_grad: no samples");
     const int nblk = train_grid();
-    DevBuf K(s), bo(s), A(s), B(s), co(s), ra(s), ld(s), gp(s);
+    DevBuf K(s), bo(s), A(s), B(s), co(s), ra(s), ld(s), gp(s), er(s);
     if ((st = K.get(sizeof(float) * n)) || (st = bo.get(sizeof(int) * n)) || (st = A.get(sizeof(double) * nband)) ||
         (st = B.get(sizeof(double) * nband)) || (st = co.get(sizeof(float) * nband)) ||
         (st = ra.get(sizeof(float) * nband)) || (st = ld.get(sizeof(double))) ||
-        (st = gp.get(sizeof(float) * (size_t)nblk * kNP)))
+        (st = gp.get(sizeof(float) * (size_t)nblk * kNP)) || (st = er.get(sizeof(int))))
         return st;
+    if ((st = cuda_check(cudaMemsetAsync(er.p, 0, sizeof(int), s), "memset"))) return st;
     {
         ProfScope pf(PF_MLP, s);
         k_mlp_band_of<<<nband, 256, 0, s>>>(band_off, nband, (int*)bo.p);
     }
     if ((st = loss_grad_dev(nband, band_off, (const int*)bo.p, n, feats, r2, c, D, W, theta, (float*)K.p,
                             (double*)A.p, (double*)B.p, (float*)co.p, (float*)ra.p, (double*)ld.p, (float*)gp.p, nblk,
-                            grad, s)))
+                            grad, (int*)er.p, s)))
         return st;
     if ((st = cuda_check(cudaMemcpyAsync(loss, ld.p, sizeof(double), cudaMemcpyDeviceToHost, s), "D2H loss")))
         return st;
-    return cuda_check(cudaStreamSynchronize(s), "stream sync");
+    return check_err_word((const int*)er.p, s, "qm_mlp_loss_grad: a bounded tensor-core wait expired");
 }
 
 extern "C" qm_status qm_mlp_train(int nband, const long long* band_off, const float* feats, const float* r2,
@@ -755,15 +896,16 @@ extern "C" qm_status qm_mlp_train(int nband, const long long* band_off, const fl
     const long n = (long)last;
     if (n < 1) return fail(QM_ERR_ARG, "qm_mlp_train: no samples");
     const int nblk = train_grid();
-    DevBuf K(s), bo(s), A(s), B(s), co(s), ra(s), lh(s), gp(s), gr(s), m(s), v(s);
+    DevBuf K(s), bo(s), A(s), B(s), co(s), ra(s), lh(s), gp(s), gr(s), m(s), v(s), er(s);
     if ((st = K.get(sizeof(float) * n)) || (st = bo.get(sizeof(int) * n)) || (st = A.get(sizeof(double) * nband)) ||
         (st = B.get(sizeof(double) * nband)) || (st = co.get(sizeof(float) * nband)) ||
         (st = ra.get(sizeof(float) * nband)) || (st = lh.get(sizeof(double) * (steps + 1))) ||
         (st = gp.get(sizeof(float) * (size_t)nblk * kNP)) || (st = gr.get(sizeof(float) * kNP)) ||
-        (st = m.get(sizeof(float) * kNP)) || (st = v.get(sizeof(float) * kNP)))
+        (st = m.get(sizeof(float) * kNP)) || (st = v.get(sizeof(float) * kNP)) || (st = er.get(sizeof(int))))
         return st;
     if ((st = cuda_check(cudaMemsetAsync(m.p, 0, sizeof(float) * kNP, s), "memset")) ||
-        (st = cuda_check(cudaMemsetAsync(v.p, 0, sizeof(float) * kNP, s), "memset")))
+        (st = cuda_check(cudaMemsetAsync(v.p, 0, sizeof(float) * kNP, s), "memset")) ||
+        (st = cuda_check(cudaMemsetAsync(er.p, 0, sizeof(int), s), "memset")))
         return st;
     {
         ProfScope pf(PF_MLP, s);
@@ -774,7 +916,7 @@ extern "C" qm_status qm_mlp_train(int nband, const long long* band_off, const fl
         // step t: loss and gradient at the current parameters (the last pass only records the loss)
         if ((st = loss_grad_dev(nband, band_off, (const int*)bo.p, n, feats, r2, c, D, W, theta, (float*)K.p,
                                 (double*)A.p, (double*)B.p, (float*)co.p, (float*)ra.p, (double*)lh.p + (t - 1),
-                                (float*)gp.p, nblk, (float*)gr.p, s)))
+                                (float*)gp.p, nblk, (float*)gr.p, (int*)er.p, s)))
             return st;
         if (t > steps) break;
         const double lr_t = lr * std::sqrt(1.0 - std::pow((double)b2, t)) / (1.0 - std::pow((double)b1, t));
@@ -788,5 +930,5 @@ extern "C" qm_status qm_mlp_train(int nband, const long long* band_off, const fl
         (st = cuda_check(cudaMemcpyAsync(loss_history, lh.p, sizeof(double) * (steps + 1), cudaMemcpyDeviceToHost, s),
                          "D2H loss history")))
         return st;
-    return cuda_check(cudaStreamSynchronize(s), "stream sync");
+    return check_err_word((const int*)er.p, s, "qm_mlp_train: a bounded tensor-core wait expired");
 }
