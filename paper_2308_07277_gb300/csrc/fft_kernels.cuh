@@ -764,10 +764,12 @@ k_plane(typename Cx<R>::T* __restrict__ T, int nstick, int nstick_pad, const int
     C* plane = reinterpret_cast<C*>(smem_raw);
     C* twy = plane + N3 * ldy;
     C* twz = twy + N2;
+    int* srow = reinterpret_cast<int*>(twz + N3);  // the active rows (read in every row pass)
     const int tid = threadIdx.x, nt = blockDim.x;
     const int p1 = blockIdx.x, b = blockIdx.y;
     for (int i = tid; i < N2; i += nt) twy[i] = tw_y[i];
     for (int i = tid; i < N3; i += nt) twz[i] = tw_z[i];
+    for (int i = tid; i < nrow; i += nt) srow[i] = __ldg(rows + i);
     for (int i = tid; i < N3 * ldy; i += nt) plane[i] = mk<C>(0, 0);
     __syncthreads();
     C* Tp = T + ((size_t)b * N1 + p1) * nstick_pad;
@@ -776,13 +778,13 @@ k_plane(typename Cx<R>::T* __restrict__ T, int nstick, int nstick_pad, const int
     // inverse y on the active rows; z on every column: inverse, V(r)/N_r (in the permuted,
     // digit-reversed order of all three axes), forward; forward y on the active rows
     if constexpr (FUSED) {
-        fft2_lines<C, +1, true, false>(plane, 1, ldy, nrow, rows, py, twy, tid, nt);
+        fft2_lines<C, +1, true, false>(plane, 1, ldy, nrow, srow, py, twy, tid, nt);
         fft2_z_vmul<C, R>(plane, ldy, N2, Vt + (size_t)p1 * N3 * N2, N2, pz, twz, tid, nt);
-        fft2_lines<C, -1, false, false>(plane, 1, ldy, nrow, rows, py, twy, tid, nt);
+        fft2_lines<C, -1, false, false>(plane, 1, ldy, nrow, srow, py, twy, tid, nt);
     } else {
-        fft_lines<C, +1, true, false>(plane, 1, ldy, nrow, rows, py, twy, tid, nt);
+        fft_lines<C, +1, true, false>(plane, 1, ldy, nrow, srow, py, twy, tid, nt);
         fft_z_vmul<C, R>(plane, ldy, N2, nullptr, N2, Vt + (size_t)p1 * N3 * N2, N2, pz, twz, tid, nt);
-        fft_lines<C, -1, false, false>(plane, 1, ldy, nrow, rows, py, twy, tid, nt);
+        fft_lines<C, -1, false, false>(plane, 1, ldy, nrow, srow, py, twy, tid, nt);
     }
     for (int s = tid; s < nstick; s += nt) Tp[s] = plane[__ldg(stick_plane + s)];
 }
@@ -845,6 +847,20 @@ __global__ void k_vt(const double* __restrict__ V, R* __restrict__ Vt, int N1, i
     }
 }
 
+// Threads of a k_plane CTA: 192 where that keeps at least 90 % of the resident threads of
+// 256-thread CTAs (more, smaller CTAs per SM: each barrier of a pass waits for fewer warps;
+// measured 4-6 % faster on the 72^3 and 96x96x48 grids), else 256 (e.g. the 90^3 plane, whose
+// shared memory allows only three CTAs per SM).  The transforms do not depend on the choice.
+inline int plane_threads(const void* kernel, size_t smem) {
+    int o256 = 0, o192 = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o256, kernel, 256, smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o192, kernel, 192, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return kThreads;
+    }
+    return 192 * o192 * 10 >= 256 * o256 * 9 ? 192 : 256;
+}
+
 // ---------------------------------------------------------------- per-precision launch sequences
 // wait_k3: event the stream waits for before the first x-forward pass (the nonlocal part
 // running concurrently on another stream); accumulate: the x-forward pass adds to `out`.
@@ -858,7 +874,7 @@ qm_status local_kinetic_impl(qm_gspace g, int ik, int nb, const void* psi, int l
     const size_t per_band = (size_t)N1 * kt.nstick_pad * sizeof(C);
     const int nbc = (int)std::max<size_t>(1, std::min<size_t>((size_t)nb, tbuf_bytes / per_band));
     const size_t sm_stick = (size_t)(sticks_per_cta<R>() * g->ldx + N1) * sizeof(C);
-    const size_t sm_plane = (size_t)(N3 * g->ldy + N2 + N3) * sizeof(C);
+    const size_t sm_plane = (size_t)(N3 * g->ldy + N2 + N3) * sizeof(C) + (size_t)N3 * sizeof(int);
     qm_status st;
     const bool fx = fused_length(N1), fyz = fused_length(N2) || fused_length(N3);
     auto kin_ = fx ? k_stick_inverse<R, true> : k_stick_inverse<R, false>;
@@ -868,6 +884,7 @@ qm_status local_kinetic_impl(qm_gspace g, int ik, int nb, const void* psi, int l
         (st = allow_dynamic_smem((const void*)kin_, sm_stick, "qm_hpsi: FFT sticks in shared memory")) ||
         (st = allow_dynamic_smem((const void*)kfw_, sm_stick, "qm_hpsi: FFT sticks in shared memory")))
         return st;
+    const int nt_plane = plane_threads((const void*)kpl_, sm_plane);
     const int ntile = (kt.nstick + sticks_per_cta<R>() - 1) / sticks_per_cta<R>();
     const C* tw_x = (const C*)(sizeof(R) == 8 ? (const void*)g->tw64[0] : (const void*)g->tw32[0]);
     const C* tw_y = (const C*)(sizeof(R) == 8 ? (const void*)g->tw64[1] : (const void*)g->tw32[1]);
@@ -885,7 +902,7 @@ qm_status local_kinetic_impl(qm_gspace g, int ik, int nb, const void* psi, int l
         }
         {
             ProfScope pf(PF_PLANE, s);
-            kpl_<<<dim3(N1, nbx), kThreads, sm_plane, s>>>(
+            kpl_<<<dim3(N1, nbx), nt_plane, sm_plane, s>>>(
                 T, kt.nstick, kt.nstick_pad, kt.stick_plane, kt.rows, kt.nrow, g->plan[1], g->plan[2], tw_y, tw_z,
                 g->ldy, (const R*)vt, N1);
         }
@@ -912,7 +929,7 @@ qm_status local_kinetic_tab_impl(const DevTables& t, int nb, const void* psi, in
     if (tbuf_bytes < per_band) return fail(QM_ERR_ARG, "stick buffer smaller than one band");
     const int nbc = (int)std::max<size_t>(1, std::min<size_t>((size_t)nb, tbuf_bytes / per_band));
     const size_t sm_stick = (size_t)(sticks_per_cta<R>() * t.ldx + N1) * sizeof(C);
-    const size_t sm_plane = (size_t)(N3 * t.ldy + N2 + N3) * sizeof(C);
+    const size_t sm_plane = (size_t)(N3 * t.ldy + N2 + N3) * sizeof(C) + (size_t)N3 * sizeof(int);
     qm_status st;
     const bool fx = fused_length(N1), fyz = fused_length(N2) || fused_length(N3);
     auto kin_ = fx ? k_stick_inverse<R, true> : k_stick_inverse<R, false>;
@@ -922,6 +939,7 @@ qm_status local_kinetic_tab_impl(const DevTables& t, int nb, const void* psi, in
         (st = allow_dynamic_smem((const void*)kin_, sm_stick, "FFT sticks in shared memory")) ||
         (st = allow_dynamic_smem((const void*)kfw_, sm_stick, "FFT sticks in shared memory")))
         return st;
+    const int nt_plane = plane_threads((const void*)kpl_, sm_plane);
     const int ntile = (t.nstick + sticks_per_cta<R>() - 1) / sticks_per_cta<R>();
     const C* tw_x = (const C*)t.tw[0];
     const C* tw_y = (const C*)t.tw[1];
@@ -939,7 +957,7 @@ qm_status local_kinetic_tab_impl(const DevTables& t, int nb, const void* psi, in
         }
         {
             ProfScope pf(PF_PLANE, s);
-            kpl_<<<dim3(N1, nbx), kThreads, sm_plane, s>>>(
+            kpl_<<<dim3(N1, nbx), nt_plane, sm_plane, s>>>(
                 T, t.nstick, t.nstick_pad, t.stick_plane, t.rows, t.nrow, t.plan[1], t.plan[2], tw_y, tw_z, t.ldy,
                 (const R*)vt, N1);
         }
