@@ -350,6 +350,13 @@ typedef struct {
                             of the unconverged bands (GD+k: Stathopoulos & Saad, ETNA 7, 163 (1998)),
                             as many as fit beside the next corrections; 1 = plain restart from the
                             Ritz vectors only */
+    int fp64_exact;      /* QM_MIXED, FP64 phase: 0 (default) = its plane-wave-length products (H_sub
+                            columns, Ritz vectors, orthogonalisation passes, and the nonlocal
+                            GEMMs of its H psi) in double-FP32 arithmetic: FP64 operands split into
+                            two FP32 halves, products and sums by error-free transformations on the
+                            FP32 pipe, per-tile sums in FP64 (about 2^-47 relative accuracy, 48-bit
+                            rather than 53-bit); 1 = those products in FP64 arithmetic.  QM_FP64
+                            is FP64 arithmetic throughout, whatever this field says */
 } qm_davidson_opts;
 
 /* Counters of one qm_davidson call (the paper's "H-psi calls" are band_applies / nb). */
@@ -489,6 +496,22 @@ qm_status qm_hamiltonian_diag(qm_gspace g, int ik, const double* vloc_r, int npr
  */
 qm_status qm_eigh_lowest(int m, int nev, const void* A, int lda, double* evals, void* Y, int ldy,
                          void* stream);
+
+/*
+ * qm_zgemm - the plane-wave-length complex products of the Davidson step (the Gram-Schmidt
+ * and H_sub products, Sec. 5 dft module) and of the nonlocal term (Sec. 2.3), exposed on their
+ * own so that their arithmetic can be checked:
+ *   op 0 (cn): C[m][n] = sum_k conj(A[m][k]) B[n][k]     A: M x K, B: N x K (k contiguous)
+ *   op 1 (tn): C[m][n] = sum_k A[k][m] B[k][n]           A: K x M, B: K x N (m, n contiguous)
+ *  arith   0 = FP64 arithmetic; 1 = double-FP32 (the precision form's FP64 phase, see
+ *          qm_davidson_opts.fp64_exact): operands split into two FP32 halves, error-free
+ *          products and sums on the FP32 pipe, per-tile sums in FP64.
+ *  A, B, C device, complex double, row-major with the leading dimensions given; C is written.
+ *  stream  cudaStream_t.  op 0 allocates its split-K partial sums with cudaMallocAsync.
+ * M, N, K >= 1.  Errors: QM_ERR_ARG, QM_ERR_CUDA, QM_ERR_OOM.
+ */
+qm_status qm_zgemm(int op, int arith, int M, int N, int K, const void* A, int lda, const void* B, int ldb, void* C,
+                   int ldc, void* stream);
 
 /*
  * Learned preconditioner (the learned form): a network K(f) > 0 on per-plane-wave features

@@ -60,7 +60,8 @@ class DavidsonOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("nvecx", ctypes.c_int),
                 ("prec", ctypes.c_int), ("precond", ctypes.c_int), ("mixed_switch", ctypes.c_double),
                 ("nconv", ctypes.c_int), ("mixed_ortho", ctypes.c_int), ("history", c_double_p),
-                ("mlp", ctypes.c_void_p), ("precond_stall", ctypes.c_double), ("plain_restart", ctypes.c_int)]
+                ("mlp", ctypes.c_void_p), ("precond_stall", ctypes.c_double), ("plain_restart", ctypes.c_int),
+                ("fp64_exact", ctypes.c_int)]
 
 
 class DavidsonStats(ctypes.Structure):
@@ -91,6 +92,9 @@ SIGNATURES["qm_hamiltonian_diag"] = (ctypes.c_int, [ctypes.c_void_p, ctypes.c_in
 
 SIGNATURES["qm_eigh_lowest"] = (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                                ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p])
+SIGNATURES["qm_zgemm"] = (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                         ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p])
 
 
 class HpsiJob(ctypes.Structure):

@@ -134,7 +134,7 @@ def qm_hpsi_prepare(g, ik, beta, stream=None):
 
 def qm_davidson(g, ik, psi, vloc, beta, D, tol=1e-8, max_iter=100, nvecx=0, prec="fp64", stream=None,
                 raise_not_converged=True, mixed_switch=0.0, nconv=0, mlp=None, precond_stall=0.0, mixed_ortho=0,
-                plain_restart=0):
+                plain_restart=0, fp64_exact=0):
     """Lowest nb eigenpairs; psi (nb, >=npw) complex128 CUDA tensor is overwritten by the
     Ritz vectors.  Returns (eigenvalues ndarray (nb,), stats dict)."""
     lib = _lib.load()
@@ -146,7 +146,8 @@ def qm_davidson(g, ik, psi, vloc, beta, D, tol=1e-8, max_iter=100, nvecx=0, prec
     opts = _lib.DavidsonOpts(tol=float(tol), max_iter=int(max_iter), nvecx=int(nvecx), prec=_PREC[prec],
                              precond=0 if mlp is None else 1, mixed_switch=float(mixed_switch), nconv=int(nconv),
                              mixed_ortho=int(mixed_ortho), history=_dp(hist), mlp=_dev_ptr(mlp, "mlp", torch.float32),
-                             precond_stall=float(precond_stall), plain_restart=int(plain_restart))
+                             precond_stall=float(precond_stall), plain_restart=int(plain_restart),
+                             fp64_exact=int(fp64_exact))
     stats = _lib.DavidsonStats()
     eig = np.zeros(nb, np.float64)
     st = lib.qm_davidson(g, int(ik), nb, _dev_ptr(psi, "psi", torch.complex128), int(psi.stride(0)),
@@ -254,6 +255,27 @@ def qm_eigh_lowest(A, nev, stream=None):
                               _dev_ptr(ev, "evals", torch.float64), _dev_ptr(Y, "Y", torch.complex128),
                               int(Y.stride(0)), _stream_ptr(stream)))
     return ev, Y
+
+
+def qm_zgemm(op, A, B, arith=0, stream=None):
+    """op "cn": C = conj(A) B^T for A (M, K), B (N, K); op "tn": C = A^T B for A (K, M), B (K, N).
+    complex128 CUDA tensors; arith 0 = FP64, 1 = double-FP32.  Returns C (M, N)."""
+    lib = _lib.load()
+    if op == "cn":
+        (M, K), N = A.shape, int(B.shape[0])
+        if int(B.shape[1]) != K:
+            raise ValueError("A and B must have the same K")
+    elif op == "tn":
+        (K, M), N = A.shape, int(B.shape[1])
+        if int(B.shape[0]) != K:
+            raise ValueError("A and B must have the same K")
+    else:
+        raise ValueError("op must be 'cn' or 'tn'")
+    C = torch.empty((int(M), N), dtype=torch.complex128, device=A.device)
+    _check(lib.qm_zgemm(0 if op == "cn" else 1, int(arith), int(M), N, int(K), _dev_ptr(A, "A", torch.complex128),
+                        int(A.stride(0)), _dev_ptr(B, "B", torch.complex128), int(B.stride(0)),
+                        _dev_ptr(C, "C", torch.complex128), int(C.stride(0)), _stream_ptr(stream)))
+    return C
 
 
 class Batch:
@@ -403,7 +425,8 @@ def qm_mlp_train(band_off, feats, r2, c, D, theta, steps, lr, W=None, stream=Non
 
 
 def qm_davidson_batched(jobs, tol=1e-8, max_iter=100, nvecx=0, prec="fp64", nconv=0, mixed_switch=0.0, mlp=None,
-                        max_concurrent=0, stream=None, raise_not_converged=True, mixed_ortho=0, plain_restart=0):
+                        max_concurrent=0, stream=None, raise_not_converged=True, mixed_ortho=0, plain_restart=0,
+                        fp64_exact=0):
     """Concurrent Davidson solves.  jobs: list of dicts with keys g, ik, psi (overwritten by
     the Ritz vectors), vloc, beta, D (CUDA tensors as for qm_davidson).  Returns a list of
     (eigenvalues ndarray, info dict) in job order."""
@@ -431,7 +454,7 @@ def qm_davidson_batched(jobs, tol=1e-8, max_iter=100, nvecx=0, prec="fp64", ncon
     opts = _lib.DavidsonOpts(tol=float(tol), max_iter=int(max_iter), nvecx=int(nvecx), prec=_PREC[prec],
                              precond=0 if mlp is None else 1, mixed_switch=float(mixed_switch), nconv=int(nconv),
                              mixed_ortho=int(mixed_ortho), history=None, mlp=_dev_ptr(mlp, "mlp", torch.float32),
-                             plain_restart=int(plain_restart))
+                             plain_restart=int(plain_restart), fp64_exact=int(fp64_exact))
     st = lib.qm_davidson_batched(n, arr, ctypes.byref(opts), int(max_concurrent), _stream_ptr(stream))
     out = []
     for i in range(n):

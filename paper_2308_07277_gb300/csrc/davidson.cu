@@ -286,9 +286,10 @@ struct DavidsonRun {
     size_t sub_bytes = 0;
     int* tc_err = nullptr;       // device error word of the tensor-core waits
 
+    bool ds = false;             // precision form: the FP64 phase's long products in double-FP32
     qm_status hpsi(const double2* in, double2* out, int n) {
         applies += n;
-        if (!mixed) return qm_hpsi(g, ik, n, in, ld, vloc, nproj, beta, ldb, D, out, ld, QM_FP64, s);
+        if (!mixed) return hpsi_run(g, ik, n, in, ld, vloc, nproj, beta, ldb, nullptr, D, out, ld, QM_FP64, s, ds);
         applies_mixed += n;
         qm_status st = convert_rows(in, ld, psi32, ld, n, npw, s);
         if (st) return st;
@@ -301,7 +302,7 @@ struct DavidsonRun {
         return zgemm_cn_bf16x3(M, N, npw, A, ld, B, ld, C, ldc, sub, sub_bytes, tc_err, s);
     }
     qm_status cn64(int M, int N, const double2* A, const double2* B, double2* C, int ldc) {
-        return zgemm_cn(M, N, npw, A, ld, B, ld, C, ldc, w.Part, zgemm_cn_splits(M, N, npw), s);
+        return (ds ? zgemm_cn_ds : zgemm_cn)(M, N, npw, A, ld, B, ld, C, ldc, w.Part, zgemm_cn_splits(M, N, npw), s);
     }
     qm_status tn_tc(int M, int K, const double2* A, int lda, const double2* B, double2* C, bool acc,
                     double alpha = 1.0) {
@@ -309,7 +310,7 @@ struct DavidsonRun {
     }
     qm_status tn64(int M, int K, const double2* A, int lda, const double2* B, double2* C, bool acc,
                    double alpha = 1.0) {
-        return zgemm_tn(M, npw, K, A, lda, nullptr, B, ld, C, ld, acc, s, alpha);
+        return (ds ? zgemm_tn_ds : zgemm_tn)(M, npw, K, A, lda, nullptr, B, ld, C, ld, acc, s, alpha);
     }
     // products whose precision follows the phase: H_sub columns and the Ritz vectors
     qm_status gemm_cn(int M, int N, const double2* A, const double2* B, double2* C, int ldc) {
@@ -485,6 +486,7 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
     if (o.precond != 0 && o.precond != 1) return fail(QM_ERR_ARG, "qm_davidson: unknown preconditioner");
     if (o.mixed_ortho != 0 && o.mixed_ortho != 1) return fail(QM_ERR_ARG, "qm_davidson: mixed_ortho must be 0 or 1");
     if (o.plain_restart != 0 && o.plain_restart != 1) return fail(QM_ERR_ARG, "qm_davidson: plain_restart must be 0 or 1");
+    if (o.fp64_exact != 0 && o.fp64_exact != 1) return fail(QM_ERR_ARG, "qm_davidson: fp64_exact must be 0 or 1");
     if (o.precond == 1 && !o.mlp) return fail(QM_ERR_ARG, "qm_davidson: learned preconditioner without parameters");
 
     qm_status st = ensure_device(g);
@@ -558,6 +560,7 @@ extern "C" qm_status qm_davidson(qm_gspace g, int ik, int nb, void* psi_inout, i
         }
         run.mixed = true;
         run.tc = true;
+        run.ds = o.fp64_exact == 0;
         run.ortho64 = o.mixed_ortho == 1;
         run.sub = base + oSub;
         run.sub_bytes = sub_bytes;

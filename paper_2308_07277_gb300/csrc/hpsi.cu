@@ -71,7 +71,7 @@ extern "C" qm_status qm_hpsi(qm_gspace g, int ik, int nb, const void* psi, int l
 
 qm_status qm::hpsi_run(qm_gspace g, int ik, int nb, const void* psi, int ld_psi, const double* vloc_r, int nproj,
                        const void* beta, int ld_beta, const void* beta_prepared, const double* D, void* out,
-                       int ld_out, qm_precision prec, cudaStream_t s) {
+                       int ld_out, qm_precision prec, cudaStream_t s, bool ds_nonlocal) {
     if (!g) return fail(QM_ERR_ARG, "qm_hpsi: NULL gspace");
     if (ik < 0 || ik >= g->nk) return fail(QM_ERR_ARG, "qm_hpsi: ik out of range");
     if (nb < 0 || nproj < 0) return fail(QM_ERR_ARG, "qm_hpsi: negative nb or nproj");
@@ -127,14 +127,15 @@ qm_status qm::hpsi_run(qm_gspace g, int ik, int nb, const void* psi, int ld_psi,
     }
     if ((st = launch_vt_prepare(g, vloc_r, vt, fp32, s))) return st;
     if (nproj > 0 && !fp32) {
-        st = zgemm_cn(nproj, nb, npw, (const double2*)beta, ld_beta, (const double2*)psi, ld_psi, (double2*)P, nb,
-                      (double2*)part, L.splits, s);
+        st = (ds_nonlocal ? zgemm_cn_ds : zgemm_cn)(nproj, nb, npw, (const double2*)beta, ld_beta,
+                                                    (const double2*)psi, ld_psi, (double2*)P, nb, (double2*)part,
+                                                    L.splits, s);
         if (st) return st;
     }
     if ((st = launch_local_kinetic(g, ik, nb, psi, ld_psi, vt, out, ld_out, T, L.t_bytes, fp32, s))) return st;
     if (nproj > 0 && !fp32) {
-        st = zgemm_tn(nb, npw, nproj, (const double2*)P, nb, D, (const double2*)beta, ld_beta, (double2*)out, ld_out,
-                      true, s);
+        st = (ds_nonlocal ? zgemm_tn_ds : zgemm_tn)(nb, npw, nproj, (const double2*)P, nb, D, (const double2*)beta,
+                                                    ld_beta, (double2*)out, ld_out, true, s, 1.0);
         if (st) return st;
     }
     return QM_OK;

@@ -194,6 +194,14 @@ qm_status zgemm_tn(int M, int N, int K, const double2* A, int lda, const double*
                    const double2* B, int ldb, double2* C, int ldc, bool accumulate,
                    cudaStream_t s, double alpha = 1.0);
 int zgemm_cn_splits(int M, int N, int K);
+// the same two products in double-FP32 arithmetic (FP64 in and out, products and sums on the
+// FP32 pipe with error-free transformations, ~2^-47 relative accuracy): the precision form's
+// FP64 phase
+qm_status zgemm_cn_ds(int M, int N, int K, const double2* A, int lda, const double2* B, int ldb,
+                      double2* C, int ldc, double2* partial, int splits, cudaStream_t s);
+qm_status zgemm_tn_ds(int M, int N, int K, const double2* A, int lda, const double* d,
+                      const double2* B, int ldb, double2* C, int ldc, bool accumulate,
+                      cudaStream_t s, double alpha = 1.0);
 // ---- tensor-core nonlocal step of the precision form (nonlocal_tc.cu) ----
 constexpr int kMaxUmmaSplits = 64;
 // out[b][g] (+)= sum_p beta[p][g] D_p <beta_p|psi_b> (FP32 complex in/out) as BF16x3 split
@@ -211,10 +219,11 @@ size_t nonlocal_tc_beta_bytes(int nproj, int nb, int npw);
 qm_status nonlocal_tc_prepare(int nproj, int nb, int npw, const float2* beta, int ld_beta, void* beta_work,
                               cudaStream_t s);
 // qm_hpsi with the precision form's projectors optionally pre-split (beta_prepared, see
-// nonlocal_tc); qm_hpsi itself passes NULL.
+// nonlocal_tc); qm_hpsi itself passes NULL.  ds_nonlocal (QM_FP64 only): the nonlocal GEMMs in
+// double-FP32 arithmetic (zgemm_cn_ds / zgemm_tn_ds), for the precision form's FP64 phase.
 qm_status hpsi_run(qm_gspace g, int ik, int nb, const void* psi, int ld_psi, const double* vloc_r, int nproj,
                    const void* beta, int ld_beta, const void* beta_prepared, const double* D, void* out, int ld_out,
-                   qm_precision prec, cudaStream_t s);
+                   qm_precision prec, cudaStream_t s, bool ds_nonlocal = false);
 // Subspace products of the Davidson FP32 phase on the tensor cores: FP64 storage rounded to
 // FP32 on load, BF16x3 split products accumulated in FP32 per K split, splits summed in FP64.
 //   cn: C[i][j] = sum_k conj(A[i][k]) B[j][k]                (as zgemm_cn)

@@ -25,6 +25,34 @@ template <class C> struct Real;
 template <> struct Real<double2> { using T = double; };
 template <> struct Real<float2> { using T = float; };
 
+// Double-FP32 ("double-single") complex arithmetic type: a double value v is held as
+// hi = fl32(v), lo = fl32(v - hi), 48 significant bits.  A product a b accumulates into a
+// (hi, lo) pair by error-free transformations on the FP32 pipe (Dekker's exact product via an
+// FMA, Knuth's TwoSum): p = fl(a_h b_h) with its exact error e = fma(a_h, b_h, -p), the cross
+// terms a_h b_l + a_l b_h added to e (a_l b_l < 2^-48 |a b| is dropped), then
+// (hi, lo) += p + e with the rounding error of hi + p kept exactly.  About 12 FP32 operations
+// per real multiply-add against one FP64 FMA, on a pipe 64 times wider on this GPU; the per-tile
+// sums go to FP64 accumulators, so the result keeps ~2^-47 relative accuracy per product and
+// no error growth with K.  The _rn intrinsics keep the compiler from fusing the steps.
+struct ds2 {
+    float xh, xl, yh, yl;
+};
+template <> struct Real<ds2> { using T = float; };
+template <class W> constexpr bool is_ds = false;
+template <> constexpr bool is_ds<ds2> = true;
+
+__device__ __forceinline__ void ds_mac(float& hi, float& lo, float ah, float al, float bh, float bl) {
+    const float p = __fmul_rn(ah, bh);
+    float e = __fmaf_rn(ah, bh, -p);
+    e = __fmaf_rn(ah, bl, e);
+    e = __fmaf_rn(al, bh, e);
+    const float t = __fadd_rn(hi, p);
+    const float v = __fsub_rn(t, hi);
+    const float w = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, v)), __fsub_rn(p, v));
+    hi = t;
+    lo = __fadd_rn(lo, __fadd_rn(w, e));
+}
+
 constexpr int BK = 16, NTH = 256;
 
 template <class C>
@@ -37,15 +65,26 @@ __device__ __forceinline__ C czero() {
 
 template <class D, class S>
 __device__ __forceinline__ D cvt(S a) {
-    D r;
-    r.x = (decltype(r.x))a.x;
-    r.y = (decltype(r.y))a.y;
-    return r;
+    if constexpr (is_ds<D>) {
+        D r;
+        r.xh = __double2float_rn(a.x);
+        r.xl = __double2float_rn(a.x - (double)r.xh);
+        r.yh = __double2float_rn(a.y);
+        r.yl = __double2float_rn(a.y - (double)r.yh);
+        return r;
+    } else {
+        D r;
+        r.x = (decltype(r.x))a.x;
+        r.y = (decltype(r.y))a.y;
+        return r;
+    }
 }
+template <> __device__ __forceinline__ ds2 czero<ds2>() { return ds2{0.f, 0.f, 0.f, 0.f}; }
 
-// FP32 arithmetic: move the FP32 sum of one K tile into the FP64 sums (nothing in FP64)
-template <class R, int TM, int TN>
-__device__ __forceinline__ void flush_tile(R (&acc)[TM][TN][2], double (&hi)[TM][TN][2]) {
+// FP32 and double-FP32 arithmetic: move the sum of one K tile into the FP64 sums (nothing in
+// FP64 arithmetic)
+template <class W, class R, int TM, int TN>
+__device__ __forceinline__ void flush_tile(R (&acc)[TM][TN][2], float (&lo)[TM][TN][2], double (&hi)[TM][TN][2]) {
     if constexpr (sizeof(R) == 4) {
 #pragma unroll
         for (int i = 0; i < TM; ++i)
@@ -55,24 +94,44 @@ __device__ __forceinline__ void flush_tile(R (&acc)[TM][TN][2], double (&hi)[TM]
                 for (int c = 0; c < 2; ++c) {
                     hi[i][j][c] += (double)acc[i][j][c];
                     acc[i][j][c] = 0;
+                    if constexpr (is_ds<W>) {
+                        hi[i][j][c] += (double)lo[i][j][c];
+                        lo[i][j][c] = 0.f;
+                    }
                 }
     }
 }
 
-// FP32 arithmetic: the result is the FP64 sum, rounded on output by the caller
+// the finished sum of output (i, j), component c: the FP64 sums for FP32 and double-FP32
+// arithmetic (rounded on output by the caller), the accumulator itself in FP64
 template <class R, int TM, int TN>
-__device__ __forceinline__ void finish_tiles(R (&acc)[TM][TN][2], const double (&hi)[TM][TN][2]) {
-    if constexpr (sizeof(R) == 4) {
-#pragma unroll
-        for (int i = 0; i < TM; ++i)
-#pragma unroll
-            for (int j = 0; j < TN; ++j)
-#pragma unroll
-                for (int c = 0; c < 2; ++c) acc[i][j][c] = (R)hi[i][j][c];
+__device__ __forceinline__ double result(const R (&acc)[TM][TN][2], const double (&hi)[TM][TN][2], int i, int j,
+                                         int c) {
+    if constexpr (sizeof(R) == 4)
+        return hi[i][j][c];
+    else
+        return acc[i][j][c];
+}
+
+// one complex multiply-add of the K loop: cn: acc += conj(a) b; tn: acc += a b
+template <class W, bool CONJ, class R>
+__device__ __forceinline__ void cmac(R (&acc)[2], float (&lo)[2], const W& a, const W& b) {
+    if constexpr (is_ds<W>) {
+        const float s = CONJ ? 1.f : -1.f;  // sign of the a_im b_im term of the real part
+        ds_mac(acc[0], lo[0], a.xh, a.xl, b.xh, b.xl);
+        ds_mac(acc[0], lo[0], s * a.yh, s * a.yl, b.yh, b.yl);
+        ds_mac(acc[1], lo[1], a.xh, a.xl, b.yh, b.yl);
+        ds_mac(acc[1], lo[1], -s * a.yh, -s * a.yl, b.xh, b.xl);
+    } else if constexpr (CONJ) {
+        acc[0] = fma(a.x, b.x, fma(a.y, b.y, acc[0]));
+        acc[1] = fma(a.x, b.y, fma(-a.y, b.x, acc[1]));
+    } else {
+        acc[0] = fma(a.x, b.x, fma(-a.y, b.y, acc[0]));
+        acc[1] = fma(a.x, b.y, fma(a.y, b.x, acc[1]));
     }
 }
 
-// C: storage type of A, B and the output; W: arithmetic type (FP64 or FP32 complex)
+// C: storage type of A, B and the output; W: arithmetic type (FP64, FP32 or double-FP32 complex)
 template <class C, class W, int TM, int TN>
 __global__ void __launch_bounds__(NTH)
 k_gemm_cn(int M, int N, int K, const C* __restrict__ A, int lda, const C* __restrict__ B, int ldb,
@@ -87,11 +146,13 @@ k_gemm_cn(int M, int N, int K, const C* __restrict__ A, int lda, const C* __rest
     const int kb = blockIdx.z * kchunk;
     const int ke = min(K, kb + kchunk);
     R acc[TM][TN][2];
-    double hi[TM][TN][2];  // FP32 arithmetic: sums of the per-tile FP32 partial sums
+    float lo[TM][TN][2];   // double-FP32 arithmetic: the low parts
+    double hi[TM][TN][2];  // FP32 / double-FP32 arithmetic: sums of the per-tile partial sums
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < TN; ++j) acc[i][j][0] = acc[i][j][1] = 0, hi[i][j][0] = hi[i][j][1] = 0.0;
+        for (int j = 0; j < TN; ++j)
+            acc[i][j][0] = acc[i][j][1] = 0, lo[i][j][0] = lo[i][j][1] = 0.f, hi[i][j][0] = hi[i][j][1] = 0.0;
     for (int k0 = kb; k0 < ke; k0 += BK) {
         for (int e = tid; e < BM * BK; e += NTH) {
             int row = e / BK, kk = e % BK;
@@ -114,16 +175,11 @@ k_gemm_cn(int M, int N, int K, const C* __restrict__ A, int lda, const C* __rest
 #pragma unroll
             for (int i = 0; i < TM; ++i)
 #pragma unroll
-                for (int j = 0; j < TN; ++j) {
-                    // conj(a) * b
-                    acc[i][j][0] = fma(a[i].x, b[j].x, fma(a[i].y, b[j].y, acc[i][j][0]));
-                    acc[i][j][1] = fma(a[i].x, b[j].y, fma(-a[i].y, b[j].x, acc[i][j][1]));
-                }
+                for (int j = 0; j < TN; ++j) cmac<W, true>(acc[i][j], lo[i][j], a[i], b[j]);  // conj(a) * b
         }
-        flush_tile<R, TM, TN>(acc, hi);
+        flush_tile<W, R, TM, TN>(acc, lo, hi);
         __syncthreads();
     }
-    finish_tiles<R, TM, TN>(acc, hi);
     C* o = out + (size_t)blockIdx.z * M * ldo;
 #pragma unroll
     for (int i = 0; i < TM; ++i) {
@@ -134,8 +190,8 @@ k_gemm_cn(int M, int N, int K, const C* __restrict__ A, int lda, const C* __rest
             int gn = n0 + tx + 16 * j;
             if (gn < N) {
                 C v;
-                v.x = (decltype(v.x))acc[i][j][0];
-                v.y = (decltype(v.y))acc[i][j][1];
+                v.x = (decltype(v.x))result(acc, hi, i, j, 0);
+                v.y = (decltype(v.y))result(acc, hi, i, j, 1);
                 o[(size_t)gm * ldo + gn] = v;
             }
         }
@@ -169,21 +225,24 @@ k_gemm_tn(int M, int N, int K, const C* __restrict__ A, int lda, const double* _
     const int tx = tid & 15, ty = tid >> 4;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     R acc[TM][TN][2];
-    double hi[TM][TN][2];  // FP32 arithmetic: sums of the per-tile FP32 partial sums
+    float lo[TM][TN][2];   // double-FP32 arithmetic: the low parts
+    double hi[TM][TN][2];  // FP32 / double-FP32 arithmetic: sums of the per-tile partial sums
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < TN; ++j) acc[i][j][0] = acc[i][j][1] = 0, hi[i][j][0] = hi[i][j][1] = 0.0;
+        for (int j = 0; j < TN; ++j)
+            acc[i][j][0] = acc[i][j][1] = 0, lo[i][j][0] = lo[i][j][1] = 0.f, hi[i][j][0] = hi[i][j][1] = 0.0;
     for (int k0 = 0; k0 < K; k0 += BK) {
         for (int e = tid; e < BM * BK; e += NTH) {
             int kk = e / BM, col = e % BM;
             int gk = k0 + kk, gm = m0 + col;
             W av = czero<W>();
             if (gk < K && gm < M) {
-                av = cvt<W>(A[(size_t)gk * lda + gm]);
-                R s = (R)(d ? alpha * d[gk] : alpha);
-                av.x *= s;
-                av.y *= s;
+                C v = A[(size_t)gk * lda + gm];
+                const auto sc = (decltype(v.x))(d ? alpha * d[gk] : alpha);
+                v.x *= sc;
+                v.y *= sc;
+                av = cvt<W>(v);
             }
             As[kk][col] = av;
         }
@@ -203,15 +262,11 @@ k_gemm_tn(int M, int N, int K, const C* __restrict__ A, int lda, const double* _
 #pragma unroll
             for (int i = 0; i < TM; ++i)
 #pragma unroll
-                for (int j = 0; j < TN; ++j) {
-                    acc[i][j][0] = fma(a[i].x, b[j].x, fma(-a[i].y, b[j].y, acc[i][j][0]));
-                    acc[i][j][1] = fma(a[i].x, b[j].y, fma(a[i].y, b[j].x, acc[i][j][1]));
-                }
+                for (int j = 0; j < TN; ++j) cmac<W, false>(acc[i][j], lo[i][j], a[i], b[j]);
         }
-        flush_tile<R, TM, TN>(acc, hi);
+        flush_tile<W, R, TM, TN>(acc, lo, hi);
         __syncthreads();
     }
-    finish_tiles<R, TM, TN>(acc, hi);
 #pragma unroll
     for (int i = 0; i < TM; ++i) {
         int gm = m0 + ty + 16 * i;
@@ -222,8 +277,8 @@ k_gemm_tn(int M, int N, int K, const C* __restrict__ A, int lda, const double* _
             if (gn < N) {
                 C* p = Cm + (size_t)gm * ldc + gn;
                 C v;
-                v.x = (decltype(v.x))acc[i][j][0];
-                v.y = (decltype(v.y))acc[i][j][1];
+                v.x = (decltype(v.x))result(acc, hi, i, j, 0);
+                v.y = (decltype(v.y))result(acc, hi, i, j, 1);
                 if (accumulate) {
                     C o = *p;
                     v.x += o.x;
@@ -298,12 +353,19 @@ template <class C, class W>
 qm_status gemm_cn_impl(int M, int N, int K, const C* A, int lda, const C* B, int ldb, C* Cm, int ldc,
                        C* partial, int max_splits, cudaStream_t s) {
     if (M <= 0 || N <= 0) return QM_OK;
-    const int tm = pick_t(M), tn = pick_t(N);
+    if constexpr (is_ds<W>) {
+        // double-FP32: two FP32 accumulators and an FP64 sum per output; 8 outputs per thread
+        // (about 120 registers, two CTAs per SM)
+        if (M >= N) return cn_launch<C, W, 4, 2>(M, N, K, A, lda, B, ldb, Cm, ldc, partial, max_splits, s);
+        return cn_launch<C, W, 2, 4>(M, N, K, A, lda, B, ldb, Cm, ldc, partial, max_splits, s);
+    } else {
+        const int tm = pick_t(M), tn = pick_t(N);
 #define QM_CN(a, b) \
     if (tm == a && tn == b) return cn_launch<C, W, a, b>(M, N, K, A, lda, B, ldb, Cm, ldc, partial, max_splits, s);
-    QM_CN(5, 5) QM_CN(5, 4) QM_CN(4, 5) QM_CN(4, 4) QM_CN(2, 4) QM_CN(4, 2) QM_CN(2, 5) QM_CN(5, 2) QM_CN(2, 2)
+        QM_CN(5, 5) QM_CN(5, 4) QM_CN(4, 5) QM_CN(4, 4) QM_CN(2, 4) QM_CN(4, 2) QM_CN(2, 5) QM_CN(5, 2) QM_CN(2, 2)
 #undef QM_CN
-    return fail(QM_ERR_UNSUPPORTED, "gemm_cn: no tile");
+        return fail(QM_ERR_UNSUPPORTED, "gemm_cn: no tile");
+    }
 }
 
 template <class C, class W, int TM, int TN>
@@ -320,13 +382,17 @@ template <class C, class W>
 qm_status gemm_tn_impl(int M, int N, int K, const C* A, int lda, const double* d, double alpha, const C* B,
                        int ldb, C* Cm, int ldc, bool accumulate, cudaStream_t s) {
     if (M <= 0 || N <= 0) return QM_OK;
-    const int tm = pick_t(M);
-    // the N dimension (plane waves) is long: TN = 4 keeps 256-wide rows of whole tiles
+    if constexpr (is_ds<W>) {  // double-FP32: 8 outputs per thread, as in gemm_cn_impl
+        return tn_launch<C, W, 2, 4>(M, N, K, A, lda, d, alpha, B, ldb, Cm, ldc, accumulate, s);
+    } else {
+        const int tm = pick_t(M);
+        // the N dimension (plane waves) is long: TN = 4 keeps 256-wide rows of whole tiles
 #define QM_TN(a) \
     if (tm == a) return tn_launch<C, W, a, 4>(M, N, K, A, lda, d, alpha, B, ldb, Cm, ldc, accumulate, s);
-    QM_TN(5) QM_TN(4) QM_TN(2)
+        QM_TN(5) QM_TN(4) QM_TN(2)
 #undef QM_TN
-    return fail(QM_ERR_UNSUPPORTED, "gemm_tn: no tile");
+        return fail(QM_ERR_UNSUPPORTED, "gemm_tn: no tile");
+    }
 }
 
 }  // namespace
@@ -346,6 +412,14 @@ qm_status zgemm_cn(int M, int N, int K, const double2* A, int lda, const double2
                    int ldc, double2* partial, int splits, cudaStream_t s) {
     return gemm_cn_impl<double2, double2>(M, N, K, A, lda, B, ldb, C, ldc, partial, splits, s);
 }
+qm_status zgemm_cn_ds(int M, int N, int K, const double2* A, int lda, const double2* B, int ldb, double2* C,
+                      int ldc, double2* partial, int splits, cudaStream_t s) {
+    return gemm_cn_impl<double2, ds2>(M, N, K, A, lda, B, ldb, C, ldc, partial, splits, s);
+}
+qm_status zgemm_tn_ds(int M, int N, int K, const double2* A, int lda, const double* d, const double2* B, int ldb,
+                      double2* C, int ldc, bool accumulate, cudaStream_t s, double alpha) {
+    return gemm_tn_impl<double2, ds2>(M, N, K, A, lda, d, alpha, B, ldb, C, ldc, accumulate, s);
+}
 qm_status cgemm_cn(int M, int N, int K, const float2* A, int lda, const float2* B, int ldb, float2* C, int ldc,
                    float2* partial, int splits, cudaStream_t s) {
     return gemm_cn_impl<float2, float2>(M, N, K, A, lda, B, ldb, C, ldc, partial, splits, s);
@@ -360,3 +434,30 @@ qm_status cgemm_tn(int M, int N, int K, const float2* A, int lda, const double* 
 }
 
 }  // namespace qm
+
+using namespace qm;
+
+extern "C" qm_status qm_zgemm(int op, int arith, int M, int N, int K, const void* A, int lda, const void* B, int ldb,
+                              void* C, int ldc, void* stream) {
+    clear_error();
+    if ((op != 0 && op != 1) || (arith != 0 && arith != 1)) return fail(QM_ERR_ARG, "qm_zgemm: op or arith not 0/1");
+    if (M < 1 || N < 1 || K < 1 || !A || !B || !C) return fail(QM_ERR_ARG, "qm_zgemm: bad sizes or NULL operand");
+    if (op == 0 ? (lda < K || ldb < K || ldc < N) : (lda < M || ldb < N || ldc < N))
+        return fail(QM_ERR_ARG, "qm_zgemm: leading dimension too small");
+    cudaStream_t s = (cudaStream_t)stream;
+    const double2* a = (const double2*)A;
+    const double2* b = (const double2*)B;
+    double2* c = (double2*)C;
+    if (op == 1)
+        return (arith ? zgemm_tn_ds : zgemm_tn)(M, N, K, a, lda, nullptr, b, ldb, c, ldc, false, s, 1.0);
+    void* part = nullptr;
+    const int splits = zgemm_cn_splits(M, N, K);
+    const size_t bytes = std::min((size_t)splits * M * N * sizeof(double2), gemm_cn_partial_bytes(false));
+    if (cudaMallocAsync(&part, bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(QM_ERR_OOM, "qm_zgemm: split-K partial sums");
+    }
+    qm_status st = (arith ? zgemm_cn_ds : zgemm_cn)(M, N, K, a, lda, b, ldb, c, ldc, (double2*)part, splits, s);
+    cudaFreeAsync(part, s);
+    return st;
+}

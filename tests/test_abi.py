@@ -126,9 +126,9 @@ def test_davidson_option_errors_before_device_work():
         fake = ctypes.c_void_p(1 << 20)  # 16-byte aligned, never read
         eig = np.zeros(4)
         cases = [dict(prec=7), dict(precond=3), dict(precond=1), dict(mixed_ortho=2), dict(nvecx=5),
-                 dict(tol=-1.0), dict(max_iter=-2)]
+                 dict(tol=-1.0), dict(max_iter=-2), dict(fp64_exact=2)]
         msgs = ["unknown precision", "unknown preconditioner", "learned preconditioner without parameters",
-                "mixed_ortho", "nvecx", "tol", "tol"]
+                "mixed_ortho", "nvecx", "tol", "tol", "fp64_exact"]
         for kw, msg in zip(cases, msgs):
             opts = L.DavidsonOpts(**dict(dict(tol=1e-8, max_iter=10), **kw))
             st = lib.qm_davidson(g, 0, 4, fake, npw, fake, 0, None, 0, None, ctypes.byref(opts),
@@ -191,3 +191,22 @@ def test_prepare_check_hold_argument_errors():
     finally:
         Q.qm_gspace_destroy(g)
     assert lib.qm_batch_hold(None, 0, 0) == 1
+
+
+def test_zgemm_argument_errors_before_device_work():
+    """qm_zgemm rejects an unknown op or arithmetic, empty sizes, NULL operands and short
+    leading dimensions with QM_ERR_ARG before any device work (the pointers are never read)."""
+    import ctypes
+    import paper_2308_07277_gb300 as Q
+    lib = _lib()
+    fake = ctypes.c_void_p(1 << 20)
+    cases = [((2, 0, 4, 4, 8, fake, 8, fake, 8, fake, 4), "op or arith"),
+             ((0, 5, 4, 4, 8, fake, 8, fake, 8, fake, 4), "op or arith"),
+             ((0, 1, 0, 4, 8, fake, 8, fake, 8, fake, 4), "bad sizes"),
+             ((1, 0, 4, 4, 8, None, 8, fake, 8, fake, 4), "bad sizes"),
+             ((0, 0, 4, 4, 8, fake, 7, fake, 8, fake, 4), "leading dimension"),
+             ((1, 1, 4, 6, 8, fake, 4, fake, 6, fake, 5), "leading dimension")]
+    for args, msg in cases:
+        st = lib.qm_zgemm(*args, None)
+        assert st == 1 and msg in Q.qm_last_error(), (args, st, Q.qm_last_error())
+
