@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-sample-bands", type=int, default=2,
                     help="--impl reference: oracle bands per host core per step")
-    ap.add_argument("--cpu-baseline-bands", type=int, default=32,
+    ap.add_argument("--cpu-baseline-bands", type=int, default=96,
                     help="cpu_baseline: oracle bands per host core in its one timed step (about 10 s)")
     ap.add_argument("--davidson", type=int, default=1, help="also time block Davidson to tol (0: skip)")
     ap.add_argument("--davidson-tol", type=float, default=1e-8)

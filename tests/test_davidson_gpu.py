@@ -117,6 +117,14 @@ def test_davidson_not_converged_and_errors(Q):
         with pytest.raises(Q.QMError) as e:
             Q.qm_davidson(g, 0, dev(dup), dev(c["v"]), dev(c["beta"]), dev(c["D"]))
         assert e.value.status == 5
+        # dependent rows in later blocks of the blocked Cholesky (columns 40..47 repeat 0..7,
+        # column 70 is a combination of 3 and 65): dropped, reported as a rank-deficient start
+        wide = S.psi_random(2, 72, c["psi"].shape[1])
+        wide[40:48] = wide[0:8]
+        wide[70] = 0.5 * wide[3] - 2.0 * wide[65]
+        with pytest.raises(Q.QMError) as e:
+            Q.qm_davidson(g, 0, dev(wide), dev(c["v"]), dev(c["beta"]), dev(c["D"]))
+        assert e.value.status == 5
     finally:
         Q.qm_gspace_destroy(g)
 
