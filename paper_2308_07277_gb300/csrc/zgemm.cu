@@ -326,8 +326,21 @@ qm_status cn_launch(int M, int N, int K, const C* A, int lda, const C* B, int ld
     constexpr int BM = 16 * TM, BN = 16 * TN;
     const int tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
     const int kSlots = resident_slots(k_gemm_cn<C, W, TM, TN>);
-    // splits: fill the resident slots in whole waves, each split at least 128 deep
-    int splits = std::max(1, std::min({kSlots / std::max(1, tiles), std::max(1, K / 128), max_splits}));
+    // splits: each at least 128 deep, within the caller's partial-sum buffer (max_splits, and
+    // the size gemm_cn_partial_bytes guarantees), chosen so that the CTAs fill the resident
+    // slots in nearly whole waves: the fewest splits whose last wave is not more than 10 %
+    // emptier than the best choice (a grid of 160 tiles on 304 slots otherwise leaves half
+    // of them idle)
+    const long cap = (long)(gemm_cn_partial_bytes(sizeof(C) == 8) / sizeof(C)) / std::max<long>(1, (long)M * N);
+    const int smax = (int)std::max<long>(1, std::min<long>({(long)std::max(1, K / 128), (long)max_splits, cap, 64L}));
+    auto fill = [&](int sp) {
+        const long ctas = (long)tiles * sp, waves = (ctas + kSlots - 1) / kSlots;
+        return (double)ctas / (double)(waves * kSlots);
+    };
+    double best = 0.0;
+    for (int sp = 1; sp <= smax; ++sp) best = std::max(best, fill(sp));
+    int splits = 1;
+    while (splits < smax && fill(splits) < best - 0.1) ++splits;
     if (!partial) splits = 1;
     int kchunk = (K + splits - 1) / splits;
     kchunk = std::max(BK, (kchunk + BK - 1) / BK * BK);
