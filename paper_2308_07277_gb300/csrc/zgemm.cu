@@ -33,7 +33,9 @@ template <> struct Real<float2> { using T = float; };
 // (hi, lo) += p + e with the rounding error of hi + p kept exactly.  About 12 FP32 operations
 // per real multiply-add against one FP64 FMA, on a pipe 64 times wider on this GPU; the per-tile
 // sums go to FP64 accumulators, so the result keeps ~2^-47 relative accuracy per product and
-// no error growth with K.  The _rn intrinsics keep the compiler from fusing the steps.
+// no error growth with K.  The _rn intrinsics keep the compiler from fusing the steps.  The
+// products live in FP32's exponent range: terms below about 1e-38 lose their relative accuracy
+// (they are negligible next to the sums of the plane-wave products this serves).
 struct ds2 {
     float xh, xl, yh, yl;
 };
@@ -63,14 +65,37 @@ __device__ __forceinline__ C czero() {
     return z;
 }
 
+// x = hi + lo with hi = x truncated to 24 significant bits (exact) and lo = the remaining 29
+// mantissa bits rounded to FP32: 48 significant bits, from the bit fields by integer operations
+// (the FP64 conversions and the FP64 subtraction of the plain split run on this GPU's narrow
+// FP64 path and stalled the tile loads).  Exponents outside FP32's normal range take the plain
+// split.
+__device__ __forceinline__ void split_ds(double x, float& hi, float& lo) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned int hw = (unsigned int)(b >> 32), lw = (unsigned int)b;
+    const int e = (int)((hw >> 20) & 0x7FFu);
+    const int ef = e - 1023 + 127;
+    if (ef <= 0 || ef >= 255) {
+        hi = __double2float_rn(x);
+        lo = (ef <= 0 && e == 0) ? 0.f : __double2float_rn(x - (double)hi);
+        return;
+    }
+    const unsigned int sign = hw & 0x80000000u;
+    hi = __uint_as_float(sign | ((unsigned int)ef << 23) | ((hw & 0xFFFFFu) << 3) | (lw >> 29));
+    // lo = m_lo 2^(e - 1075), m_lo < 2^29; dropped (zero) when |x| < 2^-74, where it is below
+    // 2^-97 in absolute value
+    const int es = e - 1075 + 127;
+    const float scale = es >= 1 ? __uint_as_float((unsigned int)es << 23) : 0.f;
+    const float l = __fmul_rn(__uint2float_rn(lw & 0x1FFFFFFFu), scale);
+    lo = sign ? -l : l;
+}
+
 template <class D, class S>
 __device__ __forceinline__ D cvt(S a) {
     if constexpr (is_ds<D>) {
         D r;
-        r.xh = __double2float_rn(a.x);
-        r.xl = __double2float_rn(a.x - (double)r.xh);
-        r.yh = __double2float_rn(a.y);
-        r.yl = __double2float_rn(a.y - (double)r.yh);
+        split_ds(a.x, r.xh, r.xl);
+        split_ds(a.y, r.yh, r.yl);
         return r;
     } else {
         D r;

@@ -52,6 +52,22 @@ def test_cn_fp64_and_double_fp32(Q, M, N, K):
     check(cds, ref, bound, 2e-13)
 
 
+def test_double_fp32_across_exponent_range(Q):
+    """Operands spread over twenty decades, a few tiny elements and one below FP32's normal
+    range (the plain split) keep the 2e-13 bound.  (Double-FP32 products must stay within
+    FP32's range, about 1e-38 to 3e38, to keep their relative accuracy; the Davidson's do.)"""
+    rng = np.random.default_rng(11)
+    M, N, K = 40, 24, 3000
+    A = crandn(rng, M, K) * 10.0 ** rng.uniform(-10, 10, (M, 1))
+    B = crandn(rng, N, K) * 10.0 ** rng.uniform(-10, 10, (1, K))
+    A[:, ::97] *= 1e-25          # a few elements below 2^-74 relative to their row's scale
+    B[3, 5] = 1e-39 + 2e-39j     # below FP32's normal range: the plain split
+    ref = np.conj(A) @ B.T
+    bound = np.abs(A) @ np.abs(B).T
+    cds = Q.qm_zgemm("cn", torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), arith=1).cpu().numpy()
+    check(cds, ref, bound, 2e-13)
+
+
 @pytest.mark.parametrize("M,N,K", [(316, 9000, 316), (33, 5000, 950), (2, 7, 3)])
 def test_tn_fp64_and_double_fp32(Q, M, N, K):
     rng = np.random.default_rng(3 * M + N + K)
