@@ -106,10 +106,16 @@ __device__ __forceinline__ D cvt(S a) {
 }
 template <> __device__ __forceinline__ ds2 czero<ds2>() { return ds2{0.f, 0.f, 0.f, 0.f}; }
 
-// FP32 and double-FP32 arithmetic: move the sum of one K tile into the FP64 sums (nothing in
-// FP64 arithmetic)
+// End of a K tile.  FP32 arithmetic: the tile's sum moves into the FP64 sums.  Double-FP32:
+// the (hi, lo) pairs are renormalised in FP32 (FastTwoSum: hi + lo unchanged, |lo| back to
+// half an ulp of hi) and move into the FP64 sums only every kDsFlush tiles and at the end
+// (`flush`): the conversions and FP64 additions run on this GPU's narrow FP64 path (two lanes
+// per clock per SM), so flushing every tile cost about as much as the products themselves.
+// FP64 arithmetic: nothing.
+constexpr int kDsFlush = 8;
 template <class W, class R, int TM, int TN>
-__device__ __forceinline__ void flush_tile(R (&acc)[TM][TN][2], float (&lo)[TM][TN][2], double (&hi)[TM][TN][2]) {
+__device__ __forceinline__ void flush_tile(R (&acc)[TM][TN][2], float (&lo)[TM][TN][2], double (&hi)[TM][TN][2],
+                                           bool flush) {
     if constexpr (sizeof(R) == 4) {
 #pragma unroll
         for (int i = 0; i < TM; ++i)
@@ -117,11 +123,20 @@ __device__ __forceinline__ void flush_tile(R (&acc)[TM][TN][2], float (&lo)[TM][
             for (int j = 0; j < TN; ++j)
 #pragma unroll
                 for (int c = 0; c < 2; ++c) {
-                    hi[i][j][c] += (double)acc[i][j][c];
-                    acc[i][j][c] = 0;
                     if constexpr (is_ds<W>) {
-                        hi[i][j][c] += (double)lo[i][j][c];
-                        lo[i][j][c] = 0.f;
+                        if (flush) {
+                            hi[i][j][c] += (double)acc[i][j][c];
+                            hi[i][j][c] += (double)lo[i][j][c];
+                            acc[i][j][c] = 0;
+                            lo[i][j][c] = 0.f;
+                        } else {
+                            const float t = __fadd_rn(acc[i][j][c], lo[i][j][c]);
+                            lo[i][j][c] = __fsub_rn(lo[i][j][c], __fsub_rn(t, acc[i][j][c]));
+                            acc[i][j][c] = t;
+                        }
+                    } else {
+                        hi[i][j][c] += (double)acc[i][j][c];
+                        acc[i][j][c] = 0;
                     }
                 }
     }
@@ -202,7 +217,7 @@ k_gemm_cn(int M, int N, int K, const C* __restrict__ A, int lda, const C* __rest
 #pragma unroll
                 for (int j = 0; j < TN; ++j) cmac<W, true>(acc[i][j], lo[i][j], a[i], b[j]);  // conj(a) * b
         }
-        flush_tile<W, R, TM, TN>(acc, lo, hi);
+        flush_tile<W, R, TM, TN>(acc, lo, hi, ((k0 - kb) / BK) % kDsFlush == kDsFlush - 1 || k0 + BK >= ke);
         __syncthreads();
     }
     C* o = out + (size_t)blockIdx.z * M * ldo;
@@ -289,7 +304,7 @@ k_gemm_tn(int M, int N, int K, const C* __restrict__ A, int lda, const double* _
 #pragma unroll
                 for (int j = 0; j < TN; ++j) cmac<W, false>(acc[i][j], lo[i][j], a[i], b[j]);
         }
-        flush_tile<W, R, TM, TN>(acc, lo, hi);
+        flush_tile<W, R, TM, TN>(acc, lo, hi, (k0 / BK) % kDsFlush == kDsFlush - 1 || k0 + BK >= K);
         __syncthreads();
     }
 #pragma unroll
