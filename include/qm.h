@@ -354,7 +354,7 @@ typedef struct {
                             columns, Ritz vectors, orthogonalisation passes, and the nonlocal
                             GEMMs of its H psi) in double-FP32 arithmetic: FP64 operands split into
                             two FP32 halves, products and sums by error-free transformations on the
-                            FP32 pipe, per-tile sums in FP64 (about 2^-47 relative accuracy, 48-bit
+                            FP32 pipe, partial sums in FP64 (about 2^-46 relative accuracy, 47-bit
                             rather than 53-bit); 1 = those products in FP64 arithmetic.  QM_FP64
                             is FP64 arithmetic throughout, whatever this field says */
 } qm_davidson_opts;
@@ -505,10 +505,13 @@ qm_status qm_eigh_lowest(int m, int nev, const void* A, int lda, double* evals, 
  *   op 1 (tn): C[m][n] = sum_k A[k][m] B[k][n]           A: K x M, B: K x N (m, n contiguous)
  *  arith   0 = FP64 arithmetic; 1 = double-FP32 (the precision form's FP64 phase, see
  *          qm_davidson_opts.fp64_exact): operands split into two FP32 halves, error-free
- *          products and sums on the FP32 pipe, per-tile sums in FP64.
+ *          products and sums on the FP32 pipe, per-tile sums in FP64; 2 = 3-term BF16 split
+ *          products on the tensor cores accumulated in FP32 (the precision form's FP32 phase;
+ *          FP32-level accuracy; synchronises the stream).
  *  A, B, C device, complex double, row-major with the leading dimensions given; C is written.
- *  stream  cudaStream_t.  op 0 allocates its split-K partial sums with cudaMallocAsync.
- * M, N, K >= 1.  Errors: QM_ERR_ARG, QM_ERR_CUDA, QM_ERR_OOM.
+ *  stream  cudaStream_t.  Split-K partial sums and tensor-core workspaces are allocated with
+ *          cudaMallocAsync on the stream.
+ * M, N, K >= 1.  Errors: QM_ERR_ARG, QM_ERR_CUDA, QM_ERR_OOM, QM_ERR_TIMEOUT (arith 2).
  */
 qm_status qm_zgemm(int op, int arith, int M, int N, int K, const void* A, int lda, const void* B, int ldb, void* C,
                    int ldc, void* stream);

@@ -195,7 +195,7 @@ qm_status zgemm_tn(int M, int N, int K, const double2* A, int lda, const double*
                    cudaStream_t s, double alpha = 1.0);
 int zgemm_cn_splits(int M, int N, int K);
 // the same two products in double-FP32 arithmetic (FP64 in and out, products and sums on the
-// FP32 pipe with error-free transformations, ~2^-47 relative accuracy): the precision form's
+// FP32 pipe with error-free transformations, ~2^-46 relative accuracy): the precision form's
 // FP64 phase
 qm_status zgemm_cn_ds(int M, int N, int K, const double2* A, int lda, const double2* B, int ldb,
                       double2* C, int ldc, double2* partial, int splits, cudaStream_t s);

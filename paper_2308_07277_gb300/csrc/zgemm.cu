@@ -26,13 +26,13 @@ template <> struct Real<double2> { using T = double; };
 template <> struct Real<float2> { using T = float; };
 
 // Double-FP32 ("double-single") complex arithmetic type: a double value v is held as
-// hi = fl32(v), lo = fl32(v - hi), 48 significant bits.  A product a b accumulates into a
+// hi (v's first 24 significant bits) + lo (the next 23), 47 bits.  A product a b accumulates into a
 // (hi, lo) pair by error-free transformations on the FP32 pipe (Dekker's exact product via an
 // FMA, Knuth's TwoSum): p = fl(a_h b_h) with its exact error e = fma(a_h, b_h, -p), the cross
 // terms a_h b_l + a_l b_h added to e (a_l b_l < 2^-48 |a b| is dropped), then
 // (hi, lo) += p + e with the rounding error of hi + p kept exactly.  About 12 FP32 operations
-// per real multiply-add against one FP64 FMA, on a pipe 64 times wider on this GPU; the per-tile
-// sums go to FP64 accumulators, so the result keeps ~2^-47 relative accuracy per product and
+// per real multiply-add against one FP64 FMA, on a pipe 64 times wider on this GPU; the sums of
+// every few K tiles go to FP64 accumulators, so the result keeps ~2^-46 relative accuracy per product and
 // no error growth with K.  The _rn intrinsics keep the compiler from fusing the steps.  The
 // products live in FP32's exponent range: terms below about 1e-38 lose their relative accuracy
 // (they are negligible next to the sums of the plane-wave products this serves).
@@ -66,27 +66,38 @@ __device__ __forceinline__ C czero() {
 }
 
 // x = hi + lo with hi = x truncated to 24 significant bits (exact) and lo = the remaining 29
-// mantissa bits rounded to FP32: 48 significant bits, from the bit fields by integer operations
+// mantissa bits truncated to 23: 47 significant bits, from the bit fields by integer operations
 // (the FP64 conversions and the FP64 subtraction of the plain split run on this GPU's narrow
 // FP64 path and stalled the tile loads).  Exponents outside FP32's normal range take the plain
 // split.
+// the plain split, for exponents outside FP32's normal range; not inlined, so that the common
+// path branches around it instead of issuing its FP64 instructions predicated off
+__device__ __noinline__ float2 split_ds_slow(double x) {
+    const float hi = __double2float_rn(x);
+    const bool zero_exp = (((unsigned long long)__double_as_longlong(x) >> 52) & 0x7FFu) == 0;
+    return make_float2(hi, zero_exp ? 0.f : __double2float_rn(x - (double)hi));
+}
 __device__ __forceinline__ void split_ds(double x, float& hi, float& lo) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const unsigned int hw = (unsigned int)(b >> 32), lw = (unsigned int)b;
     const int e = (int)((hw >> 20) & 0x7FFu);
     const int ef = e - 1023 + 127;
     if (ef <= 0 || ef >= 255) {
-        hi = __double2float_rn(x);
-        lo = (ef <= 0 && e == 0) ? 0.f : __double2float_rn(x - (double)hi);
+        const float2 r = split_ds_slow(x);
+        hi = r.x;
+        lo = r.y;
         return;
     }
     const unsigned int sign = hw & 0x80000000u;
     hi = __uint_as_float(sign | ((unsigned int)ef << 23) | ((hw & 0xFFFFFu) << 3) | (lw >> 29));
-    // lo = m_lo 2^(e - 1075), m_lo < 2^29; dropped (zero) when |x| < 2^-74, where it is below
-    // 2^-97 in absolute value
-    const int es = e - 1075 + 127;
+    // lo = m_lo 2^(e - 1075), m_lo the low 29 mantissa bits, kept to its top 23: the float
+    // 1 + (m_lo >> 6) 2^-23 minus 1 is exact (Sterbenz), then scaled by 2^(e - 1046) - no
+    // integer-to-float conversion (conversions run on this GPU's narrow FP64 path).  hi + lo
+    // keeps 47 significant bits; lo is dropped (zero) when |x| < 2^-103.
+    const int es = e - 1046 + 127;
     const float scale = es >= 1 ? __uint_as_float((unsigned int)es << 23) : 0.f;
-    const float l = __fmul_rn(__uint2float_rn(lw & 0x1FFFFFFFu), scale);
+    const float f = __fsub_rn(__uint_as_float(0x3F800000u | ((lw & 0x1FFFFFFFu) >> 6)), 1.0f);
+    const float l = __fmul_rn(f, scale);
     lo = sign ? -l : l;
 }
 
@@ -493,7 +504,7 @@ using namespace qm;
 extern "C" qm_status qm_zgemm(int op, int arith, int M, int N, int K, const void* A, int lda, const void* B, int ldb,
                               void* C, int ldc, void* stream) {
     clear_error();
-    if ((op != 0 && op != 1) || (arith != 0 && arith != 1)) return fail(QM_ERR_ARG, "qm_zgemm: op or arith not 0/1");
+    if ((op != 0 && op != 1) || arith < 0 || arith > 2) return fail(QM_ERR_ARG, "qm_zgemm: op not 0/1 or arith not 0..2");
     if (M < 1 || N < 1 || K < 1 || !A || !B || !C) return fail(QM_ERR_ARG, "qm_zgemm: bad sizes or NULL operand");
     if (op == 0 ? (lda < K || ldb < K || ldc < N) : (lda < M || ldb < N || ldc < N))
         return fail(QM_ERR_ARG, "qm_zgemm: leading dimension too small");
@@ -501,6 +512,28 @@ extern "C" qm_status qm_zgemm(int op, int arith, int M, int N, int K, const void
     const double2* a = (const double2*)A;
     const double2* b = (const double2*)B;
     double2* c = (double2*)C;
+    if (arith == 2) {  // BF16x3 split products on the tensor cores (the Davidson's FP32 phase)
+        const size_t wbytes = op == 0 ? subspace_bf16x3_bytes(M, N)
+                                      : std::max(subspace_bf16x3_bytes(M, 1), (size_t)M * K * sizeof(float2));
+        void* work = nullptr;
+        int* err = nullptr;
+        if (cudaMallocAsync(&work, wbytes, s) != cudaSuccess || cudaMallocAsync((void**)&err, sizeof(int), s) != cudaSuccess) {
+            cudaGetLastError();
+            if (work) cudaFreeAsync(work, s);
+            return fail(QM_ERR_OOM, "qm_zgemm: tensor-core workspace");
+        }
+        qm_status st = cuda_check(cudaMemsetAsync(err, 0, sizeof(int), s), "memset");
+        if (!st)
+            st = op == 0 ? zgemm_cn_bf16x3(M, N, K, a, lda, b, ldb, c, ldc, work, wbytes, err, s)
+                         : zgemm_tn_bf16x3(M, N, K, a, lda, b, ldb, c, ldc, false, 1.0, work, wbytes, err, s);
+        int e = 0;
+        if (!st) st = cuda_check(cudaMemcpyAsync(&e, err, sizeof(int), cudaMemcpyDeviceToHost, s), "D2H error word");
+        if (!st) st = cuda_check(cudaStreamSynchronize(s), "stream sync");
+        cudaFreeAsync(work, s);
+        cudaFreeAsync(err, s);
+        if (!st && e) st = fail(QM_ERR_TIMEOUT, "qm_zgemm: a bounded tensor-core wait expired");
+        return st;
+    }
     if (op == 1)
         return (arith ? zgemm_tn_ds : zgemm_tn)(M, N, K, a, lda, nullptr, b, ldb, c, ldc, false, s, 1.0);
     void* part = nullptr;

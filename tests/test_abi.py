@@ -200,8 +200,8 @@ def test_zgemm_argument_errors_before_device_work():
     import paper_2308_07277_gb300 as Q
     lib = _lib()
     fake = ctypes.c_void_p(1 << 20)
-    cases = [((2, 0, 4, 4, 8, fake, 8, fake, 8, fake, 4), "op or arith"),
-             ((0, 5, 4, 4, 8, fake, 8, fake, 8, fake, 4), "op or arith"),
+    cases = [((2, 0, 4, 4, 8, fake, 8, fake, 8, fake, 4), "op not 0/1"),
+             ((0, 5, 4, 4, 8, fake, 8, fake, 8, fake, 4), "arith not 0..2"),
              ((0, 1, 0, 4, 8, fake, 8, fake, 8, fake, 4), "bad sizes"),
              ((1, 0, 4, 4, 8, None, 8, fake, 8, fake, 4), "bad sizes"),
              ((0, 0, 4, 4, 8, fake, 7, fake, 8, fake, 4), "leading dimension"),

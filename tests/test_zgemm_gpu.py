@@ -4,8 +4,11 @@ phase in either arithmetic against plain FP64.
 
 Bars: FP64 arithmetic within 1e-14 of the host product relative to the bound
 sum_k |a_mk| |b_nk| of each element; double-FP32 within 2e-13 of the same bound (its operands
-keep 48 significant bits, its products and per-tile sums are exact up to the dropped
+keep 47 significant bits, its products and per-tile sums are exact up to the dropped
 a_lo b_lo < 2^-48 |a b|, and the tile sums are added in FP64); both far below FP32's 1e-7.
+The BF16x3 tensor-core form (operands rounded to FP32, six BF16 products per product, FP32
+accumulation per K split) within 1e-5: FP32 accumulation over 2K real terms gives about
+sqrt(2K) 2^-24 (1.5e-6 at K = 316) typically, K 2^-24 at worst.
 Davidson: eigenvalues within 1e-9 Ha of the plain FP64 form's.
 """
 import numpy as np
@@ -48,8 +51,10 @@ def test_cn_fp64_and_double_fp32(Q, M, N, K):
     dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
     c64 = Q.qm_zgemm("cn", dA, dB, arith=0).cpu().numpy()
     cds = Q.qm_zgemm("cn", dA, dB, arith=1).cpu().numpy()
+    ctc = Q.qm_zgemm("cn", dA, dB, arith=2).cpu().numpy()
     check(c64, ref, bound, 1e-14)
     check(cds, ref, bound, 2e-13)
+    check(ctc, ref, bound, 1e-5)   # BF16x3 on the tensor cores: FP32-level
 
 
 def test_double_fp32_across_exponent_range(Q):
@@ -78,8 +83,10 @@ def test_tn_fp64_and_double_fp32(Q, M, N, K):
     dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
     c64 = Q.qm_zgemm("tn", dA, dB, arith=0).cpu().numpy()
     cds = Q.qm_zgemm("tn", dA, dB, arith=1).cpu().numpy()
+    ctc = Q.qm_zgemm("tn", dA, dB, arith=2).cpu().numpy()
     check(c64, ref, bound, 1e-14)
     check(cds, ref, bound, 2e-13)
+    check(ctc, ref, bound, 1e-5)
 
 
 def test_precision_form_fp64_phase_arithmetic(Q):
