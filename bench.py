@@ -64,6 +64,7 @@ def parse():
     ap.add_argument("--davidson", type=int, default=1, help="also time block Davidson to tol (0: skip)")
     ap.add_argument("--davidson-tol", type=float, default=1e-8)
     ap.add_argument("--batched", type=int, default=1, help="also time the batched form (0: skip)")
+    ap.add_argument("--tddft", type=int, default=1, help="also time real-time propagation steps (0: skip)")
     ap.add_argument("--large", type=int, default=1, help="also time H psi on the 216- and 255-atom cells (0: skip)")
     ap.add_argument("--profile", default="",
                     help="profiling run: only the precision form's H psi steps (projectors prepared) on the named "
@@ -705,6 +706,48 @@ def run_davidson_255(args, Q, S, dev, theta):
     return out
 
 
+def run_tddft(args, Q, S, dev):
+    """Real-time propagation on the 255-atom cell, k-point 0, all 288 bands: ETRS steps of order 4
+    (two half steps, 8 H psi applications and 8 Taylor updates per step), the precision form
+    (projectors prepared) and plain FP64, CUDA events around the steps."""
+    import torch
+    cell = S.config5()
+    g = Q.GSpace(cell.lattice, cell.kpts[:1], cell.ecut_ha, cell.grid)
+    v = torch.from_numpy(S.vloc_on_grid(cell.lattice, cell.tau, cell.grid)).to(dev)
+    D = torch.from_numpy(S.dvals(cell.nat)).to(dev)
+    _, _, kpg = g.indices(0)
+    dt, order, nb = 0.05, 4, cell.nbnd
+    out = {"workload": "si255_vacancy_96x96x48_k0_288b", "step": "ETRS, Taylor order %d per half step" % order,
+           "dt_au": dt, "hpsi_per_step": 2 * order, "unit": "band-steps/s"}
+    stream = torch.cuda.current_stream()
+    for prec, steps, warm in (("mixed", 5, 2), ("fp64", 1, 1)):
+        cdt = torch.complex64 if prec == "mixed" else torch.complex128
+        psi = torch.from_numpy(S.psi_random(cell.seed, nb, g.npw[0], stream=0)).to(cdt).to(dev)
+        beta = torch.from_numpy(S.beta_of_q(kpg, cell.tau, cell.omega)).to(cdt).to(dev)
+        work = torch.empty(2 * psi.numel(), dtype=cdt, device=dev)
+        if prec == "mixed":
+            Q.qm_hpsi_prepare(g.handle, 0, beta)
+        for _ in range(warm):
+            Q.qm_tddft_etrs(g.handle, 0, psi, v, v, beta, D, dt, order, prec=prec, work=work, stream=stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            Q.qm_tddft_etrs(g.handle, 0, psi, v, v, beta, D, dt, order, prec=prec, work=work, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out[prec] = {"value": nb / (ms * 1e-3), "ms_per_step": ms, "steps": steps,
+                     "band_applies_per_s": 2 * order * nb / (ms * 1e-3)}
+        if prec == "mixed":
+            Q.qm_hpsi_prepare(g.handle, 0, None)
+        del psi, beta, work
+    out["mixed_over_fp64"] = out["mixed"]["value"] / out["fp64"]["value"]
+    g.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -768,6 +811,7 @@ def run_ours(args):
     g2.close()
     torch.cuda.empty_cache()
     batched = run_batched(args, Q, S, dev) if args.batched else None
+    tddft = run_tddft(args, Q, S, dev) if args.tddft else None
     large = run_large_cells(args, Q, S, dev) if args.large else None
     theta, tinfo = train_network(Q, S, dev) if (args.davidson_large or args.davidson_255) else (None, None)
     dav255 = run_davidson_255(args, Q, S, dev, theta) if args.davidson_255 else None
@@ -799,6 +843,7 @@ def run_ours(args):
                 "davidson_255_atoms": dav255,
                 "learned_training": tinfo,
                 "batched": batched,
+                "tddft": tddft,
                 "large_cells": large,
                 "davidson_216_atoms_learned": dav_large,
                 "cpu_baseline": oracle_sample("config5", args.cpu_baseline_bands)}

@@ -517,6 +517,43 @@ qm_status qm_zgemm(int op, int arith, int M, int N, int K, const void* A, int ld
                    int ldc, void* stream);
 
 /*
+ * qm_tddft_taylor - real-time propagation by the truncated Taylor series of the propagator
+ * (Sec. 5, "tddft" module, expoper submodule):
+ *     psi <- sum_{r=0}^{order} (-i dt)^r / r!  H^r psi
+ * with H the operator of qm_hpsi (same g, ik, vloc_r, nproj, beta, ld_beta, D, prec).  The terms
+ * are built as u_r = (-i dt / r) H u_{r-1}, u_0 = psi: one qm_hpsi per term, then one element-wise
+ * kernel that scales u_r in place and adds it to psi.
+ *
+ *  psi     device, in/out, nb rows of npw(ik) complex (double[2] for QM_FP64, float[2] for
+ *          QM_MIXED), row stride ld_psi >= npw.
+ *  dt      time step in atomic units of time (hbar / Ha), finite; order in [0, 64] (order 0 or
+ *          nb 0: nothing is done).
+ *  work    device, caller-owned scratch of 2 * nb * ld_psi complex elements of psi's type; must
+ *          not overlap psi; its contents on return are the last two terms.
+ *  stream  cudaStream_t; asynchronous.  Uses the handle's workspace like qm_hpsi (so the same
+ *          one-stream-per-handle rule applies); with QM_MIXED the projectors prepared by
+ *          qm_hpsi_prepare for this beta are used.
+ * Errors: QM_ERR_ARG (sizes, NULL pointers, order or dt out of range, work overlapping psi;
+ *         nothing launched), QM_ERR_OOM, QM_ERR_CUDA.
+ */
+qm_status qm_tddft_taylor(qm_gspace g, int ik, int nb, void* psi, int ld_psi, const double* vloc_r,
+                          int nproj, const void* beta, int ld_beta, const double* D,
+                          double dt, int order, void* work, qm_precision prec, void* stream);
+
+/*
+ * qm_tddft_etrs - one enforced-time-reversal-symmetry step (Sec. 5, "tddft" module, prop
+ * submodule): psi <- U(dt/2; H_next) U(dt/2; H_now) psi, each U the Taylor series of
+ * qm_tddft_taylor of the given order.  H_now and H_next are the operator of qm_hpsi with the local
+ * potentials vloc_now and vloc_next (device, N_r doubles each); the projectors and D are shared.
+ * The Hamiltonian of this library has no density functional, so the potential at the end of the
+ * step (the H[psibar] of a self-consistent propagation) is supplied by the caller.  Other
+ * arguments, errors and asynchrony as qm_tddft_taylor.
+ */
+qm_status qm_tddft_etrs(qm_gspace g, int ik, int nb, void* psi, int ld_psi, const double* vloc_now,
+                        const double* vloc_next, int nproj, const void* beta, int ld_beta, const double* D,
+                        double dt, int order, void* work, qm_precision prec, void* stream);
+
+/*
  * Learned preconditioner (the learned form): a network K(f) > 0 on per-plane-wave features
  * replaces the Teter-Payne-Allan factor in the Davidson correction, delta_n(G) = K(f_nG) r_n(G).
  *

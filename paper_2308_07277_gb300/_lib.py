@@ -96,6 +96,11 @@ SIGNATURES["qm_zgemm"] = (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_in
                                          ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
                                          ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p])
 
+_TDDFT_COMMON = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+_TDDFT_TAIL = [ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_double, ctypes.c_int,
+               ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+SIGNATURES["qm_tddft_taylor"] = (ctypes.c_int, _TDDFT_COMMON + _TDDFT_TAIL)
+SIGNATURES["qm_tddft_etrs"] = (ctypes.c_int, _TDDFT_COMMON + [ctypes.c_void_p] + _TDDFT_TAIL)
 
 class HpsiJob(ctypes.Structure):
     """qm_hpsi_job of include/qm.h."""

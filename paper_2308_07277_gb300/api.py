@@ -278,6 +278,43 @@ def qm_zgemm(op, A, B, arith=0, stream=None):
     return C
 
 
+
+def _tddft_args(psi, beta, D, work, prec):
+    p = _PREC[prec]
+    cdt = torch.complex128 if p == QM_FP64 else torch.complex64
+    if psi.dim() != 2:
+        raise ValueError("psi must be 2-D (nb, ld)")
+    nb, ld = int(psi.shape[0]), int(psi.stride(0))
+    if work is None:
+        work = torch.empty((2 * nb * ld,), dtype=cdt, device=psi.device)
+    elif work.numel() < 2 * nb * ld or not work.is_contiguous():
+        raise ValueError("work must be a contiguous tensor of at least 2 * nb * ld elements")
+    nproj = 0 if beta is None else int(beta.shape[0])
+    nl = (nproj, _dev_ptr(beta, "beta", cdt), int(beta.stride(0)) if nproj else 0,
+          _dev_ptr(D, "D", torch.float64) if nproj else None)
+    return p, cdt, nb, ld, work, nl
+
+
+def qm_tddft_taylor(g, ik, psi, vloc, beta, D, dt, order=4, prec="fp64", work=None, stream=None):
+    """psi <- sum_{r<=order} (-i dt)^r/r! H^r psi in place (psi: (nb, >=npw) CUDA tensor, complex128
+    for fp64, complex64 for mixed); work: optional scratch of 2 * nb * ld elements."""
+    lib = _lib.load()
+    p, cdt, nb, ld, work, nl = _tddft_args(psi, beta, D, work, prec)
+    _check(lib.qm_tddft_taylor(g, int(ik), nb, _dev_ptr(psi, "psi", cdt), ld, _dev_ptr(vloc, "vloc", torch.float64),
+                               *nl, float(dt), int(order), _dev_ptr(work, "work", cdt), p, _stream_ptr(stream)))
+    return psi
+
+
+def qm_tddft_etrs(g, ik, psi, vloc_now, vloc_next, beta, D, dt, order=4, prec="fp64", work=None, stream=None):
+    """One ETRS step psi <- U(dt/2; H_next) U(dt/2; H_now) psi in place (arguments as qm_tddft_taylor)."""
+    lib = _lib.load()
+    p, cdt, nb, ld, work, nl = _tddft_args(psi, beta, D, work, prec)
+    _check(lib.qm_tddft_etrs(g, int(ik), nb, _dev_ptr(psi, "psi", cdt), ld,
+                             _dev_ptr(vloc_now, "vloc_now", torch.float64),
+                             _dev_ptr(vloc_next, "vloc_next", torch.float64),
+                             *nl, float(dt), int(order), _dev_ptr(work, "work", cdt), p, _stream_ptr(stream)))
+    return psi
+
 class Batch:
     """A batched H psi plan (qm_batch of include/qm.h) bound to its buffers.
 

@@ -210,3 +210,37 @@ def test_zgemm_argument_errors_before_device_work():
         st = lib.qm_zgemm(*args, None)
         assert st == 1 and msg in Q.qm_last_error(), (args, st, Q.qm_last_error())
 
+
+
+def test_tddft_argument_errors_before_device_work():
+    """qm_tddft_taylor / qm_tddft_etrs reject an order outside [0, 64], a non-finite step, NULL or
+    overlapping buffers and short rows with QM_ERR_ARG before any device work (the pointers are
+    never read); order 0 and nb 0 return QM_OK without launching."""
+    import ctypes
+    import paper_2308_07277_gb300 as Q
+    lib = _lib()
+    g = Q.qm_gspace_create(np.eye(3) * 10.0, [[0, 0, 0]], 5.0)
+    try:
+        npw = Q.qm_gspace_query(g)["npw"][0]
+        psi = ctypes.c_void_p(1 << 20)
+        work = ctypes.c_void_p((1 << 20) + (1 << 24))
+        inside = ctypes.c_void_p((1 << 20) + 16 * npw)
+        odd = ctypes.c_void_p((1 << 20) + (1 << 24) + 8)
+        v = ctypes.c_void_p(1 << 26)
+        n0 = lib.qm_launch_count()
+
+        def taylor(ik=0, nb=2, p=psi, ld=npw, dt=0.1, order=4, w=work, prec=0):
+            return lib.qm_tddft_taylor(g, ik, nb, p, ld, v, 0, None, 0, None, dt, order, w, prec, None)
+
+        for kw, msg in [({"order": -1}, "order"), ({"order": 65}, "order"), ({"dt": float("nan")}, "dt"),
+                        ({"dt": float("inf")}, "dt"), ({"ik": 1}, "ik"), ({"nb": -1}, "negative"),
+                        ({"p": None}, "NULL"), ({"w": None}, "NULL"), ({"ld": npw - 1}, "ld_psi"),
+                        ({"w": inside}, "overlaps"), ({"w": odd}, "aligned"), ({"prec": 7}, "precision")]:
+            assert taylor(**kw) == 1 and msg in Q.qm_last_error(), (kw, Q.qm_last_error())
+        assert taylor(order=0) == 0 and taylor(nb=0) == 0
+        st = lib.qm_tddft_etrs(g, 0, 2, psi, npw, v, None, 0, None, 0, None, 0.1, 4, work, 0, None)
+        assert st == 1 and "potential" in Q.qm_last_error()
+        assert lib.qm_tddft_etrs(None, 0, 2, psi, npw, v, v, 0, None, 0, None, 0.1, 4, work, 0, None) == 1
+        assert lib.qm_launch_count() == n0
+    finally:
+        Q.qm_gspace_destroy(g)
