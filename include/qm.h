@@ -131,6 +131,27 @@ qm_status qm_hpsi(qm_gspace g, int ik, int nb,
                   qm_precision prec, void* stream);
 
 /*
+ * qm_hpsi_gamma - out = H(Gamma) psi for real wavefunctions, two bands per FFT: the same operator
+ * and arguments as qm_hpsi, for the Gamma-point cells the paper runs with real wavefunctions.
+ * At k = 0 a state whose real-space values are real has psi(-G) = conj(psi(G)), and H (real V,
+ * projectors with beta_p(-G) = +-conj(beta_p(G))) keeps that property.  Bands 2j and 2j+1 are
+ * transformed together as psi_2j + i psi_2j+1; after the multiplication by V(r) the forward
+ * transform F separates as (V psi_2j)(G) = (F(G) + conj F(-G))/2 and (V psi_2j+1)(G) =
+ * (F(G) - conj F(-G))/(2i), so the FFT path does half the transforms of qm_hpsi.  The nonlocal
+ * part is the same as qm_hpsi's.  An odd nb pairs the last band with zero.
+ *
+ *  Requirements: k-point ik is Gamma (kpts == 0); every band satisfies psi(-G) = conj(psi(G))
+ *  (for other states the local part of the result is not H psi).
+ * Errors: as qm_hpsi, plus QM_ERR_ARG when ik is not the Gamma point.
+ */
+qm_status qm_hpsi_gamma(qm_gspace g, int ik, int nb,
+                        const void* psi, int ld_psi,
+                        const double* vloc_r,
+                        int nproj, const void* beta, int ld_beta, const double* D,
+                        void* out, int ld_out,
+                        qm_precision prec, void* stream);
+
+/*
  * qm_hpsi_check - synchronise `stream` and read (and clear) the handle's sticky error word:
  * QM_ERR_TIMEOUT if a bounded device-side wait of a tensor-core kernel launched by an earlier
  * qm_hpsi(QM_MIXED) or qm_precond_apply call on this handle expired since the last check (the

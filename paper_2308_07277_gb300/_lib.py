@@ -78,6 +78,7 @@ SIGNATURES["qm_davidson"] = (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctype
                                             ctypes.POINTER(DavidsonStats), ctypes.c_void_p])
 
 SIGNATURES["qm_hpsi_noalloc"] = SIGNATURES["qm_hpsi"]
+SIGNATURES["qm_hpsi_gamma"] = SIGNATURES["qm_hpsi"]
 SIGNATURES["qm_hpsi_check"] = (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p])
 SIGNATURES["qm_hpsi_prepare"] = (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
                                                 ctypes.c_void_p])

@@ -123,6 +123,27 @@ def qm_hpsi(g, ik, psi, vloc, beta, D, out=None, prec="fp64", stream=None):
     return out
 
 
+def qm_hpsi_gamma(g, ik, psi, vloc, beta, D, out=None, prec="fp64", stream=None):
+    """out = H(Gamma) psi for real-space-real bands (psi(-G) = conj psi(G)), two bands per FFT;
+    arguments as qm_hpsi."""
+    lib = _lib.load()
+    p = _PREC[prec]
+    cdt = torch.complex128 if p == QM_FP64 else torch.complex64
+    if psi.dim() != 2:
+        raise ValueError("psi must be 2-D (nb, ld)")
+    if out is None:
+        out = torch.empty_like(psi)
+    nproj = 0 if beta is None else int(beta.shape[0])
+    _check(lib.qm_hpsi_gamma(g, int(ik), int(psi.shape[0]),
+                             _dev_ptr(psi, "psi", cdt), int(psi.stride(0)),
+                             _dev_ptr(vloc, "vloc", torch.float64),
+                             nproj, _dev_ptr(beta, "beta", cdt), int(beta.stride(0)) if nproj else 0,
+                             _dev_ptr(D, "D", torch.float64) if nproj else None,
+                             _dev_ptr(out, "out", cdt), int(out.stride(0)),
+                             p, _stream_ptr(stream)))
+    return out
+
+
 def qm_hpsi_prepare(g, ik, beta, stream=None):
     """Prepare the precision form's projectors of k-point ik (beta: (nproj, >=npw) complex64
     CUDA tensor that stays unchanged while prepared; None releases)."""

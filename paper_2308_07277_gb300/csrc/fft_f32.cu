@@ -4,7 +4,7 @@
 
 namespace qm {
 template qm_status local_kinetic_impl<float>(qm_gspace, int, int, const void*, int, const void*, void*, int, void*,
-                                         size_t, cudaStream_t, cudaEvent_t, bool);
+                                         size_t, cudaStream_t, cudaEvent_t, bool, bool);
 template qm_status local_kinetic_tab_impl<float>(const DevTables&, int, const void*, int, const void*, void*, int,
                                              void*, size_t, cudaStream_t);
 }  // namespace qm

@@ -723,7 +723,7 @@ template <class R, bool FUSED>
 __global__ void __launch_bounds__(kThreads, fft_min_ctas<R, FUSED>())
 k_stick_inverse(const typename Cx<R>::T* __restrict__ psi, int ld_psi, const int* __restrict__ stick_g0,
                 const int2* __restrict__ g_code, int nstick, int nstick_pad, const __grid_constant__ AxisPlan px,
-                const typename Cx<R>::T* __restrict__ tw_x, int ldx, typename Cx<R>::T* __restrict__ T) {
+                const typename Cx<R>::T* __restrict__ tw_x, int ldx, typename Cx<R>::T* __restrict__ T, int pair_nb) {
     using C = typename Cx<R>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* lines = reinterpret_cast<C*>(smem_raw);
@@ -737,10 +737,22 @@ k_stick_inverse(const typename Cx<R>::T* __restrict__ psi, int ld_psi, const int
     for (int i = tid; i < ns * ldx; i += nt) lines[i] = mk<C>(0, 0);
     __syncthreads();
     const int gb = __ldg(stick_g0 + s0), ge = __ldg(stick_g0 + s0 + ns);
-    const C* src = psi + (size_t)b * ld_psi;
-    for (int g = gb + tid; g < ge; g += nt) {
-        int2 c = __ldg(g_code + g);
-        lines[(c.x - s0) * ldx + c.y] = src[g];
+    if (pair_nb) {
+        // Gamma-point real wavefunctions: bands 2b and 2b+1 in one transform, psi_a + i psi_b
+        const C* sa = psi + (size_t)(2 * b) * ld_psi;
+        const C* sb = 2 * b + 1 < pair_nb ? sa + ld_psi : nullptr;
+        for (int g = gb + tid; g < ge; g += nt) {
+            int2 c = __ldg(g_code + g);
+            const C a = sa[g];
+            const C v = sb ? sb[g] : mk<C>(0, 0);
+            lines[(c.x - s0) * ldx + c.y] = mk<C>(a.x - v.y, a.y + v.x);
+        }
+    } else {
+        const C* src = psi + (size_t)b * ld_psi;
+        for (int g = gb + tid; g < ge; g += nt) {
+            int2 c = __ldg(g_code + g);
+            lines[(c.x - s0) * ldx + c.y] = src[g];
+        }
     }
     __syncthreads();
     if constexpr (FUSED)
@@ -834,6 +846,86 @@ k_stick_forward(const typename Cx<R>::T* __restrict__ T, int nstick, int nstick_
     }
 }
 
+// ---------------------------------------------------------------- K3, Gamma-point real wavefunctions
+// One CTA per (tile of kGammaTile sticks, band pair b): the tile holds every stick together with
+// the stick of the opposite (i2, i3), so F(G) and F(-G) of the pair's transform F = V(psi_a +
+// i psi_b) are both in shared memory after the x-forward pass.  For real-space-real psi_a, psi_b
+// (psi(-G) = conj psi(G)) the two products separate as
+//     (V psi_a)(G) = (F(G) + conj F(-G)) / 2,   (V psi_b)(G) = (F(G) - conj F(-G)) / (2i),
+// then the kinetic term is added (and the nonlocal part already in `out` when accumulate).
+template <class R, bool FUSED>
+__global__ void __launch_bounds__(kThreads, fft_min_ctas<R, FUSED>())
+k_stick_forward_gamma(const typename Cx<R>::T* __restrict__ T, int nstick_pad, const int2* __restrict__ gtile,
+                      const int* __restrict__ stick_g0, const int2* __restrict__ g_code, const R* __restrict__ kin,
+                      const __grid_constant__ AxisPlan px, const typename Cx<R>::T* __restrict__ tw_x, int ldx,
+                      const typename Cx<R>::T* __restrict__ psi, int ld_psi, typename Cx<R>::T* __restrict__ out,
+                      int ld_out, int accumulate, int nb) {
+    using C = typename Cx<R>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* lines = reinterpret_cast<C*>(smem_raw);
+    C* tw = lines + kGammaTile * ldx;
+    __shared__ int2 slot[kGammaTile];
+    __shared__ int gstart[kGammaTile], goff[kGammaTile + 1];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int b = blockIdx.y;
+    const int N1 = px.n;
+    for (int i = tid; i < N1; i += nt) tw[i] = tw_x[i];
+    if (tid < kGammaTile) {
+        const int2 sl = __ldg(gtile + (size_t)blockIdx.x * kGammaTile + tid);
+        slot[tid] = sl;
+        const int g0 = sl.x >= 0 ? __ldg(stick_g0 + sl.x) : 0;
+        gstart[tid] = g0;
+        goff[tid + 1] = sl.x >= 0 ? __ldg(stick_g0 + sl.x + 1) - g0 : 0;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        goff[0] = 0;
+        for (int l = 0; l < kGammaTile; ++l) goff[l + 1] += goff[l];
+    }
+    const C* srcT = T + (size_t)b * N1 * nstick_pad;
+    for (int i = tid; i < N1 * kGammaTile; i += nt) {
+        const int p = i / kGammaTile, l = i - p * kGammaTile;
+        const int st = slot[l].x;
+        lines[l * ldx + p] = st >= 0 ? srcT[(size_t)p * nstick_pad + st] : mk<C>(0, 0);
+    }
+    __syncthreads();
+    if constexpr (FUSED)
+        fft2_lines<C, -1, false, false>(lines, 1, ldx, kGammaTile, nullptr, px, tw, tid, nt);
+    else
+        fft_lines<C, -1, false, false>(lines, 1, ldx, kGammaTile, nullptr, px, tw, tid, nt);
+    const int ba = 2 * b;
+    const bool has_b = ba + 1 < nb;
+    const C* pa = psi + (size_t)ba * ld_psi;
+    C* oa = out + (size_t)ba * ld_out;
+    const int total = goff[kGammaTile];
+    for (int t = tid; t < total; t += nt) {
+        int lo = 0, hi = kGammaTile;  // slot l with goff[l] <= t < goff[l + 1]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (goff[mid] <= t) lo = mid;
+            else hi = mid;
+        }
+        const int l = lo;
+        const int g = gstart[l] + (t - goff[l]);
+        const int x = __ldg(g_code + g).y;
+        const int xm = x ? N1 - x : 0;
+        const C F = lines[l * ldx + x];
+        const C Fm = lines[slot[l].y * ldx + xm];
+        const R k = __ldg(kin + g);
+        const R h = (R)0.5;
+        C y = pa[g];
+        C r = mk<C>(h * (F.x + Fm.x) + k * y.x, h * (F.y - Fm.y) + k * y.y);
+        if (accumulate) r = add(r, oa[g]);
+        oa[g] = r;
+        if (has_b) {
+            y = pa[(size_t)ld_psi + g];
+            r = mk<C>(h * (F.y + Fm.y) + k * y.x, h * (Fm.x - F.x) + k * y.y);
+            if (accumulate) r = add(r, oa[(size_t)ld_out + g]);
+            oa[(size_t)ld_out + g] = r;
+        }
+    }
+}
+
 // ---------------------------------------------------------------- V layout
 template <class R>
 __global__ void k_vt(const double* __restrict__ V, R* __restrict__ Vt, int N1, int N2, int N3,
@@ -867,25 +959,31 @@ inline int plane_threads(const void* kernel, size_t smem) {
 // ---------------------------------------------------------------- per-precision launch sequences
 // wait_k3: event the stream waits for before the first x-forward pass (the nonlocal part
 // running concurrently on another stream); accumulate: the x-forward pass adds to `out`.
+// gamma: the Gamma-point real-wavefunction form (two bands per transform, k_stick_forward_gamma)
 template <class R>
 qm_status local_kinetic_impl(qm_gspace g, int ik, int nb, const void* psi, int ld_psi, const void* vt,
                                     void* out, int ld_out, void* tbuf, size_t tbuf_bytes, cudaStream_t s,
-                                    cudaEvent_t wait_k3, bool accumulate) {
+                                    cudaEvent_t wait_k3, bool accumulate, bool gamma) {
     using C = typename Cx<R>::T;
     const KTables& kt = g->k[ik];
     const int N1 = g->n[0], N2 = g->n[1], N3 = g->n[2];
     const size_t per_band = (size_t)N1 * kt.nstick_pad * sizeof(C);
-    const int nbc = (int)std::max<size_t>(1, std::min<size_t>((size_t)nb, tbuf_bytes / per_band));
+    if (gamma && !kt.gamma) return fail(QM_ERR_ARG, "FFT path: the k-point is not the Gamma point");
+    const int ntr = gamma ? (nb + 1) / 2 : nb;  // transforms (band pairs in the Gamma form)
+    const int nbc = (int)std::max<size_t>(1, std::min<size_t>((size_t)ntr, tbuf_bytes / per_band));
     const size_t sm_stick = (size_t)(sticks_per_cta<R>() * g->ldx + N1) * sizeof(C);
     const size_t sm_plane = (size_t)(N3 * g->ldy + N2 + N3) * sizeof(C) + (size_t)N3 * sizeof(int);
     qm_status st;
     const bool fx = fused_length(N1), fyz = fused_length(N2) || fused_length(N3);
     auto kin_ = fx ? k_stick_inverse<R, true> : k_stick_inverse<R, false>;
     auto kfw_ = fx ? k_stick_forward<R, true> : k_stick_forward<R, false>;
+    auto kfg_ = fx ? k_stick_forward_gamma<R, true> : k_stick_forward_gamma<R, false>;
     auto kpl_ = fyz ? k_plane<R, true> : k_plane<R, false>;
+    static_assert(kGammaTile == sticks_per_cta<R>(), "the Gamma tiles use the stick kernels' shared memory");
     if ((st = allow_dynamic_smem((const void*)kpl_, sm_plane, "qm_hpsi: FFT plane in shared memory")) ||
         (st = allow_dynamic_smem((const void*)kin_, sm_stick, "qm_hpsi: FFT sticks in shared memory")) ||
-        (st = allow_dynamic_smem((const void*)kfw_, sm_stick, "qm_hpsi: FFT sticks in shared memory")))
+        (st = allow_dynamic_smem(gamma ? (const void*)kfg_ : (const void*)kfw_, sm_stick,
+                                 "qm_hpsi: FFT sticks in shared memory")))
         return st;
     const int nt_plane = plane_threads((const void*)kpl_, sm_plane);
     const int ntile = (kt.nstick + sticks_per_cta<R>() - 1) / sticks_per_cta<R>();
@@ -894,14 +992,17 @@ qm_status local_kinetic_impl(qm_gspace g, int ik, int nb, const void* psi, int l
     const C* tw_z = (const C*)(sizeof(R) == 8 ? (const void*)g->tw64[2] : (const void*)g->tw32[2]);
     const R* kin = (const R*)(sizeof(R) == 8 ? (const void*)kt.kin : (const void*)kt.kin_f);
     C* T = (C*)tbuf;
-    for (int b0 = 0; b0 < nb; b0 += nbc) {
-        const int nbx = std::min(nbc, nb - b0);
-        const C* ps = (const C*)psi + (size_t)b0 * ld_psi;
-        C* po = (C*)out + (size_t)b0 * ld_out;
+    for (int b0 = 0; b0 < ntr; b0 += nbc) {
+        const int nbx = std::min(nbc, ntr - b0);
+        const int band0 = gamma ? 2 * b0 : b0;
+        const int nbands = gamma ? std::min(2 * nbx, nb - band0) : nbx;
+        const C* ps = (const C*)psi + (size_t)band0 * ld_psi;
+        C* po = (C*)out + (size_t)band0 * ld_out;
         {
             ProfScope pf(PF_STICK_INV, s);
             kin_<<<dim3(ntile, nbx), stick_threads<R>(), sm_stick, s>>>(
-                ps, ld_psi, kt.stick_g0, kt.g_code, kt.nstick, kt.nstick_pad, g->plan[0], tw_x, g->ldx, T);
+                ps, ld_psi, kt.stick_g0, kt.g_code, kt.nstick, kt.nstick_pad, g->plan[0], tw_x, g->ldx, T,
+                gamma ? nbands : 0);
         }
         {
             ProfScope pf(PF_PLANE, s);
@@ -915,9 +1016,14 @@ qm_status local_kinetic_impl(qm_gspace g, int ik, int nb, const void* psi, int l
         }
         {
             ProfScope pf(PF_STICK_FWD, s);
-            kfw_<<<dim3(ntile, nbx), stick_threads<R>(), sm_stick, s>>>(
-                T, kt.nstick, kt.nstick_pad, kt.stick_g0, kt.g_code, kin, g->plan[0], tw_x, g->ldx, ps, ld_psi, po,
-                ld_out, accumulate ? 1 : 0);
+            if (gamma)
+                kfg_<<<dim3(kt.ngtile, nbx), stick_threads<R>(), sm_stick, s>>>(
+                    T, kt.nstick_pad, kt.gtile, kt.stick_g0, kt.g_code, kin, g->plan[0], tw_x, g->ldx, ps, ld_psi, po,
+                    ld_out, accumulate ? 1 : 0, nbands);
+            else
+                kfw_<<<dim3(ntile, nbx), stick_threads<R>(), sm_stick, s>>>(
+                    T, kt.nstick, kt.nstick_pad, kt.stick_g0, kt.g_code, kin, g->plan[0], tw_x, g->ldx, ps, ld_psi,
+                    po, ld_out, accumulate ? 1 : 0);
         }
     }
     return cuda_check(cudaGetLastError(), "FFT path launch");
@@ -956,7 +1062,7 @@ qm_status local_kinetic_tab_impl(const DevTables& t, int nb, const void* psi, in
         {
             ProfScope pf(PF_STICK_INV, s);
             kin_<<<dim3(ntile, nbx), stick_threads<R>(), sm_stick, s>>>(
-                ps, ld_psi, t.stick_g0, t.g_code, t.nstick, t.nstick_pad, t.plan[0], tw_x, t.ldx, T);
+                ps, ld_psi, t.stick_g0, t.g_code, t.nstick, t.nstick_pad, t.plan[0], tw_x, t.ldx, T, 0);
         }
         {
             ProfScope pf(PF_PLANE, s);

@@ -5,9 +5,9 @@
 namespace qm {
 
 extern template qm_status local_kinetic_impl<double>(qm_gspace, int, int, const void*, int, const void*, void*, int,
-                                                     void*, size_t, cudaStream_t, cudaEvent_t, bool);
+                                                     void*, size_t, cudaStream_t, cudaEvent_t, bool, bool);
 extern template qm_status local_kinetic_impl<float>(qm_gspace, int, int, const void*, int, const void*, void*, int,
-                                                    void*, size_t, cudaStream_t, cudaEvent_t, bool);
+                                                    void*, size_t, cudaStream_t, cudaEvent_t, bool, bool);
 extern template qm_status local_kinetic_tab_impl<double>(const DevTables&, int, const void*, int, const void*, void*,
                                                          int, void*, size_t, cudaStream_t);
 extern template qm_status local_kinetic_tab_impl<float>(const DevTables&, int, const void*, int, const void*, void*,
@@ -32,12 +32,12 @@ qm_status launch_vt_prepare(qm_gspace g, const double* vloc, void* vt, bool fp32
 
 qm_status launch_local_kinetic(qm_gspace g, int ik, int nb, const void* psi, int ld_psi, const void* vt,
                                void* out, int ld_out, void* tbuf, size_t tbuf_bytes, bool fp32, cudaStream_t s,
-                               cudaEvent_t wait_k3, bool accumulate) {
+                               cudaEvent_t wait_k3, bool accumulate, bool gamma) {
     if (fp32)
         return local_kinetic_impl<float>(g, ik, nb, psi, ld_psi, vt, out, ld_out, tbuf, tbuf_bytes, s, wait_k3,
-                                         accumulate);
+                                         accumulate, gamma);
     return local_kinetic_impl<double>(g, ik, nb, psi, ld_psi, vt, out, ld_out, tbuf, tbuf_bytes, s, wait_k3,
-                                      accumulate);
+                                      accumulate, gamma);
 }
 
 

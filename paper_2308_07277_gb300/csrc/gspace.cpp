@@ -207,6 +207,8 @@ qm_status ensure_device(qm_gspace g) {
             (st = upload((void**)&kt.kin, kt.h_kin.data(), sizeof(double) * kt.h_kin.size())) ||
             (st = upload((void**)&kt.kin_f, kinf.data(), sizeof(float) * kinf.size())))
             return st;
+        if (kt.gamma && (st = upload((void**)&kt.gtile, kt.h_gtile.data(), sizeof(int2) * kt.h_gtile.size())))
+            return st;
     }
     if ((st = cuda_check(cudaStreamCreateWithFlags(&g->aux, cudaStreamNonBlocking), "gspace stream")) ||
         (st = cuda_check(cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming), "gspace event")) ||
@@ -384,6 +386,47 @@ extern "C" qm_status qm_gspace_create(const double lattice[9], int nk, const dou
                 kt.h_kpg[3 * i + x] = pws[i].q[x];
             }
         }
+        if (kc[0] == 0.0 && kc[1] == 0.0 && kc[2] == 0.0) {
+            // Gamma point: pair every stick (i2, i3) with the stick (-i2, -i3) that holds the -G of
+            // its plane waves (the sphere is symmetric under G -> -G at k = 0); pairs fill slots
+            // j and j + kGammaTile/2 of a tile, sticks that are their own partner (i2, i3 each 0
+            // or N/2) get tiles of their own
+            const int half = kGammaTile / 2;
+            std::vector<int> partner(kt.nstick, -1);
+            std::vector<int64_t> keys(kt.nstick);
+            for (int s2 = 0; s2 < kt.nstick; ++s2) keys[s2] = (int64_t)pws[g0[s2]].idx / N1;
+            bool ok = true;
+            for (int s2 = 0; s2 < kt.nstick && ok; ++s2) {
+                const int i2 = (int)(keys[s2] % N2), i3 = (int)(keys[s2] / N2);
+                const int64_t pk = (int64_t)((N2 - i2) % N2) + (int64_t)N2 * ((N3 - i3) % N3);
+                auto it = std::lower_bound(keys.begin(), keys.end(), pk);
+                if (it == keys.end() || *it != pk) ok = false;
+                else partner[s2] = (int)(it - keys.begin());
+            }
+            if (ok) {
+                std::vector<int2> tiles, self_tiles;
+                int np = 0, nself = 0;
+                for (int s2 = 0; s2 < kt.nstick; ++s2) {
+                    const int p2 = partner[s2];
+                    if (p2 == s2) {
+                        if (nself % kGammaTile == 0) self_tiles.resize(self_tiles.size() + kGammaTile, make_int2(-1, 0));
+                        const int slot = nself % kGammaTile;
+                        self_tiles[self_tiles.size() - kGammaTile + slot] = make_int2(s2, slot);
+                        ++nself;
+                    } else if (p2 > s2) {
+                        if (np % half == 0) tiles.resize(tiles.size() + kGammaTile, make_int2(-1, 0));
+                        const int slot = np % half;
+                        tiles[tiles.size() - kGammaTile + slot] = make_int2(s2, slot + half);
+                        tiles[tiles.size() - kGammaTile + slot + half] = make_int2(p2, slot);
+                        ++np;
+                    }
+                }
+                tiles.insert(tiles.end(), self_tiles.begin(), self_tiles.end());
+                kt.gamma = true;
+                kt.ngtile = (int)(tiles.size() / kGammaTile);
+                kt.h_gtile = std::move(tiles);
+            }
+        }
         kt.h_g0 = std::move(g0);
         kt.h_plane = std::move(plane);
         kt.h_rows = std::move(rows);
@@ -434,6 +477,7 @@ extern "C" void qm_gspace_destroy(qm_gspace g) {
             cudaFree(kt.g_code);
             cudaFree(kt.kin);
             cudaFree(kt.kin_f);
+            cudaFree(kt.gtile);
         }
         for (int d = 0; d < 3 && !g->shared_tables; ++d) {
             cudaFree(g->tw64[d]);

@@ -28,7 +28,7 @@ struct HpsiLayout {
     int splits;
 };
 
-static HpsiLayout hpsi_layout(qm_gspace g, int ik, int nb, int nproj, bool fp32, bool own_beta) {
+static HpsiLayout hpsi_layout(qm_gspace g, int ik, int nb, int nproj, bool fp32, bool own_beta, bool gamma) {
     HpsiLayout L{};
     const size_t cs = fp32 ? sizeof(float2) : sizeof(double2);
     const size_t rs = fp32 ? sizeof(float) : sizeof(double);
@@ -48,7 +48,8 @@ static HpsiLayout hpsi_layout(qm_gspace g, int ik, int nb, int nproj, bool fp32,
     // the precision form keeps every band's stick buffer (K1 and K2 of all bands overlap the
     // nonlocal part; K3 runs once it is done), the FP64 form chunks the bands to stay in L2
     const size_t budget = (fp32 && nproj > 0) ? kStickBudgetOverlap : kStickBudget;
-    const size_t nbc = std::max<size_t>(1, std::min<size_t>((size_t)nb, budget / per_band));
+    const size_t ntr = gamma ? (size_t)(nb + 1) / 2 : (size_t)nb;  // transforms (band pairs at Gamma)
+    const size_t nbc = std::max<size_t>(1, std::min<size_t>(ntr, budget / per_band));
     L.t_bytes = nbc * per_band;
     off = align_up(off + L.t_bytes, 256);
     L.nl_off = off;  // tensor-core split operands (precision form)
@@ -71,7 +72,7 @@ extern "C" qm_status qm_hpsi(qm_gspace g, int ik, int nb, const void* psi, int l
 
 qm_status qm::hpsi_run(qm_gspace g, int ik, int nb, const void* psi, int ld_psi, const double* vloc_r, int nproj,
                        const void* beta, int ld_beta, const void* beta_prepared, const double* D, void* out,
-                       int ld_out, qm_precision prec, cudaStream_t s, bool ds_nonlocal) {
+                       int ld_out, qm_precision prec, cudaStream_t s, bool ds_nonlocal, bool gamma) {
     if (!g) return fail(QM_ERR_ARG, "qm_hpsi: NULL gspace");
     if (ik < 0 || ik >= g->nk) return fail(QM_ERR_ARG, "qm_hpsi: ik out of range");
     if (nb < 0 || nproj < 0) return fail(QM_ERR_ARG, "qm_hpsi: negative nb or nproj");
@@ -94,6 +95,7 @@ qm_status qm::hpsi_run(qm_gspace g, int ik, int nb, const void* psi, int ld_psi,
         const char* b1 = b0 + ((size_t)(nb - 1) * ld_out + npw) * cs;
         if (a0 < b1 && b0 < a1) return fail(QM_ERR_ARG, "qm_hpsi: out overlaps psi");
     }
+    if (gamma && !g->k[ik].gamma) return fail(QM_ERR_ARG, "qm_hpsi_gamma: k-point ik is not the Gamma point");
 
     qm_status st = ensure_device(g);
     if (st) return st;
@@ -102,7 +104,7 @@ qm_status qm::hpsi_run(qm_gspace g, int ik, int nb, const void* psi, int ld_psi,
         if (p.dev && p.beta == beta && p.ld == ld_beta && p.nproj == nproj) beta_prepared = p.dev;
     }
 
-    const HpsiLayout L = hpsi_layout(g, ik, nb, nproj, fp32, beta_prepared == nullptr);
+    const HpsiLayout L = hpsi_layout(g, ik, nb, nproj, fp32, beta_prepared == nullptr, gamma);
     if ((st = ensure_workspace(g, L.total, s))) return st;
     char* ws = (char*)g->ws.ptr;
     void* vt = ws + L.vt_off;
@@ -123,7 +125,7 @@ qm_status qm::hpsi_run(qm_gspace g, int ik, int nb, const void* psi, int ld_psi,
         if ((st = cuda_check(cudaEventRecord(g->ev_join, a), "join event"))) return st;
         if ((st = launch_vt_prepare(g, vloc_r, vt, fp32, s))) return st;
         return launch_local_kinetic(g, ik, nb, psi, ld_psi, vt, out, ld_out, T, L.t_bytes, fp32, s, g->ev_join,
-                                    true);
+                                    true, gamma);
     }
     if ((st = launch_vt_prepare(g, vloc_r, vt, fp32, s))) return st;
     if (nproj > 0 && !fp32) {
@@ -132,13 +134,23 @@ qm_status qm::hpsi_run(qm_gspace g, int ik, int nb, const void* psi, int ld_psi,
                                                     L.splits, s);
         if (st) return st;
     }
-    if ((st = launch_local_kinetic(g, ik, nb, psi, ld_psi, vt, out, ld_out, T, L.t_bytes, fp32, s))) return st;
+    if ((st = launch_local_kinetic(g, ik, nb, psi, ld_psi, vt, out, ld_out, T, L.t_bytes, fp32, s, nullptr, false,
+                                   gamma)))
+        return st;
     if (nproj > 0 && !fp32) {
         st = (ds_nonlocal ? zgemm_tn_ds : zgemm_tn)(nb, npw, nproj, (const double2*)P, nb, D, (const double2*)beta,
                                                     ld_beta, (double2*)out, ld_out, true, s, 1.0);
         if (st) return st;
     }
     return QM_OK;
+}
+
+extern "C" qm_status qm_hpsi_gamma(qm_gspace g, int ik, int nb, const void* psi, int ld_psi, const double* vloc_r,
+                                   int nproj, const void* beta, int ld_beta, const double* D, void* out, int ld_out,
+                                   qm_precision prec, void* stream) {
+    clear_error();
+    return hpsi_run(g, ik, nb, psi, ld_psi, vloc_r, nproj, beta, ld_beta, nullptr, D, out, ld_out, prec,
+                    (cudaStream_t)stream, false, true);
 }
 
 extern "C" qm_status qm_hpsi_prepare(qm_gspace g, int ik, int nproj, const void* beta, int ld_beta, void* stream) {

@@ -22,6 +22,9 @@ struct AxisPlan {
     int L[kMaxStages];
 };
 
+// sticks per tile of the Gamma-point x-forward pass (pairs in slots j and j + kGammaTile / 2)
+constexpr int kGammaTile = 32;
+
 // Per-k-point tables (device pointers unless noted).
 struct KTables {
     int npw = 0;
@@ -34,11 +37,17 @@ struct KTables {
     int2* g_code = nullptr;      // [npw]     {stick id, i1}
     double* kin = nullptr;       // [npw]     |k+G|^2 / 2
     float* kin_f = nullptr;      // [npw]     same, FP32
+    // Gamma point only (k = 0): tiles of the x-forward pass of the real-wavefunction form, each
+    // of kGammaTile slots {stick id (-1: empty), slot of the stick holding -G}; a stick and its
+    // partner (-i2, -i3) sit in one tile, so that both G and -G are in the tile's shared memory
+    bool gamma = false;
+    int ngtile = 0;
+    int2* gtile = nullptr;       // [ngtile * kGammaTile]
     // host copies (the device tables are uploaded from these on first use)
     std::vector<int32_t> h_idx, h_miller;
     std::vector<double> h_kpg, h_kin;
     std::vector<int> h_g0, h_plane, h_rows;
-    std::vector<int2> h_code;
+    std::vector<int2> h_code, h_gtile;
 };
 
 struct Workspace {
@@ -161,7 +170,7 @@ qm_status launch_vt_prepare(qm_gspace g, const double* vloc, void* vt, bool fp32
 qm_status launch_local_kinetic(qm_gspace g, int ik, int nb, const void* psi, int ld_psi,
                                const void* vt, void* out, int ld_out, void* tbuf,
                                size_t tbuf_bytes, bool fp32, cudaStream_t s,
-                               cudaEvent_t wait_k3 = nullptr, bool accumulate = false);
+                               cudaEvent_t wait_k3 = nullptr, bool accumulate = false, bool gamma = false);
 size_t stick_buffer_bytes_per_band(qm_gspace g, int ik, bool fp32);
 
 // The FFT path's tables of one k-point given by explicit device pointers (twiddles and kin
@@ -221,9 +230,10 @@ qm_status nonlocal_tc_prepare(int nproj, int nb, int npw, const float2* beta, in
 // qm_hpsi with the precision form's projectors optionally pre-split (beta_prepared, see
 // nonlocal_tc); qm_hpsi itself passes NULL.  ds_nonlocal (QM_FP64 only): the nonlocal GEMMs in
 // double-FP32 arithmetic (zgemm_cn_ds / zgemm_tn_ds), for the precision form's FP64 phase.
+// gamma: the Gamma-point real-wavefunction FFT path (qm_hpsi_gamma; two bands per transform).
 qm_status hpsi_run(qm_gspace g, int ik, int nb, const void* psi, int ld_psi, const double* vloc_r, int nproj,
                    const void* beta, int ld_beta, const void* beta_prepared, const double* D, void* out, int ld_out,
-                   qm_precision prec, cudaStream_t s, bool ds_nonlocal = false);
+                   qm_precision prec, cudaStream_t s, bool ds_nonlocal = false, bool gamma = false);
 // Subspace products of the Davidson FP32 phase on the tensor cores: FP64 storage rounded to
 // FP32 on load, BF16x3 split products accumulated in FP32 per K split, splits summed in FP64.
 //   cn: C[i][j] = sum_k conj(A[i][k]) B[j][k]                (as zgemm_cn)

@@ -9,9 +9,9 @@ test consume exactly the arrays produced here.
 """
 from .cells import (Cell, config1, config2, config3_cells, config4, config5, small_cells, fcc_si2, cubic_si8,
                     fcc_supercell, KPTS_MP222_SHIFTED_FULL)
-from .fields import vloc_on_grid, beta_of_q, dvals, psi_random
+from .fields import vloc_on_grid, beta_of_q, dvals, psi_random, psi_random_real
 
 __all__ = [
     "Cell", "config1", "config2", "config3_cells", "fcc_supercell", "KPTS_MP222_SHIFTED_FULL", "config4", "config5", "small_cells", "fcc_si2",
-    "cubic_si8", "vloc_on_grid", "beta_of_q", "dvals", "psi_random",
+    "cubic_si8", "vloc_on_grid", "beta_of_q", "dvals", "psi_random", "psi_random_real",
 ]

@@ -150,3 +150,15 @@ def psi_random(seed, nb, npw, stream=0):
     rng = np.random.default_rng([int(seed), int(stream)])
     z = rng.standard_normal((nb, npw, 2))
     return (z[..., 0] + 1j * z[..., 1]) / math.sqrt(2.0)
+
+
+def psi_random_real(seed, nb, miller, stream=0):
+    """Seeded coefficients (nb, npw) complex128 of functions that are real in real space: the
+    random numbers of psi_random symmetrised as c(G) = (z(G) + conj(z(-G))) / sqrt(2) over the
+    plane-wave list given by its integer indices miller (npw, 3), which must contain -G with
+    every G (a Gamma-point sphere)."""
+    m = np.asarray(miller, np.int64)
+    z = psi_random(seed, nb, len(m), stream)
+    pos = {tuple(r): i for i, r in enumerate(m.tolist())}
+    neg = np.array([pos[(-a, -b, -c)] for a, b, c in m.tolist()])
+    return np.ascontiguousarray((z + z[:, neg].conj()) / math.sqrt(2.0))

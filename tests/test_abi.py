@@ -244,3 +244,21 @@ def test_tddft_argument_errors_before_device_work():
         assert lib.qm_launch_count() == n0
     finally:
         Q.qm_gspace_destroy(g)
+
+
+def test_hpsi_gamma_rejects_other_k_points():
+    """qm_hpsi_gamma needs the Gamma point: any other k-point of the handle is QM_ERR_ARG before
+    any device work (the pointers are never read)."""
+    import ctypes
+    import paper_2308_07277_gb300 as Q
+    lib = _lib()
+    g = Q.qm_gspace_create(np.eye(3) * 10.0, [[0, 0, 0], [0.25, 0, 0]], 5.0)
+    try:
+        npw = Q.qm_gspace_query(g)["npw"][1]
+        a, b, v = ctypes.c_void_p(1 << 20), ctypes.c_void_p(1 << 26), ctypes.c_void_p(1 << 28)
+        n0 = lib.qm_launch_count()
+        st = lib.qm_hpsi_gamma(g, 1, 2, a, npw, v, 0, None, 0, None, b, npw, 0, None)
+        assert st == 1 and "Gamma" in Q.qm_last_error()
+        assert lib.qm_launch_count() == n0
+    finally:
+        Q.qm_gspace_destroy(g)
