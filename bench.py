@@ -64,6 +64,7 @@ def parse():
     ap.add_argument("--davidson", type=int, default=1, help="also time block Davidson to tol (0: skip)")
     ap.add_argument("--davidson-tol", type=float, default=1e-8)
     ap.add_argument("--batched", type=int, default=1, help="also time the batched form (0: skip)")
+    ap.add_argument("--gw", type=int, default=1, help="also time GW plane-wave matrix elements (0: skip)")
     ap.add_argument("--tddft", type=int, default=1, help="also time real-time propagation steps (0: skip)")
     ap.add_argument("--large", type=int, default=1, help="also time H psi on the 216- and 255-atom cells (0: skip)")
     ap.add_argument("--profile", default="",
@@ -752,6 +753,43 @@ def run_tddft(args, Q, S, dev):
     return out
 
 
+def run_gw(args, Q, S, dev):
+    """GW plane-wave matrix elements on the 64-atom cell (72^3): k and k+q two points of its shifted
+    set, 32 states at k+q times 64 at k (2048 pairs), E_eps a quarter of the wavefunction cutoff;
+    both precisions, CUDA events around the calls."""
+    import numpy as np
+    import torch
+    cell = S.config2()
+    k, kq = cell.kpts[0], cell.kpts[1]
+    g = Q.GSpace(cell.lattice, [kq, k], cell.ecut_ha, cell.grid)
+    ge = Q.GSpace(cell.lattice, [kq - k], 0.25 * cell.ecut_ha, cell.grid)
+    nl, nr = 32, 64
+    out = {"workload": "si64_cubic_72^3_%dx%d_pairs_eps_quarter" % (nl, nr), "pairs": nl * nr,
+           "npw_eps": ge.npw[0], "unit": "pairs/s"}
+    stream = torch.cuda.current_stream()
+    for prec, steps in (("mixed", 5), ("fp64", 2)):
+        cdt = torch.complex64 if prec == "mixed" else torch.complex128
+        pl = torch.from_numpy(S.psi_random(cell.seed, nl, g.npw[0], stream=1)).to(cdt).to(dev)
+        pr = torch.from_numpy(S.psi_random(cell.seed, nr, g.npw[1], stream=0)).to(cdt).to(dev)
+        M = torch.empty((nl * nr, ge.npw[0]), dtype=cdt, device=dev)
+        Q.qm_gw_mel(g.handle, 0, 1, pl, pr, ge.handle, 0, ge.npw[0], M=M, prec=prec, stream=stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            Q.qm_gw_mel(g.handle, 0, 1, pl, pr, ge.handle, 0, ge.npw[0], M=M, prec=prec, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out[prec] = {"value": nl * nr / (ms * 1e-3), "ms_per_call": ms, "steps": steps}
+        del pl, pr, M
+    out["mixed_over_fp64"] = out["mixed"]["value"] / out["fp64"]["value"]
+    ge.close()
+    g.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -816,6 +854,7 @@ def run_ours(args):
     torch.cuda.empty_cache()
     batched = run_batched(args, Q, S, dev) if args.batched else None
     tddft = run_tddft(args, Q, S, dev) if args.tddft else None
+    gw = run_gw(args, Q, S, dev) if args.gw else None
     large = run_large_cells(args, Q, S, dev) if args.large else None
     theta, tinfo = train_network(Q, S, dev) if (args.davidson_large or args.davidson_255) else (None, None)
     dav255 = run_davidson_255(args, Q, S, dev, theta) if args.davidson_255 else None
@@ -848,6 +887,7 @@ def run_ours(args):
                 "learned_training": tinfo,
                 "batched": batched,
                 "tddft": tddft,
+                "gw_matrix_elements": gw,
                 "large_cells": large,
                 "davidson_216_atoms_learned": dav_large,
                 "cpu_baseline": oracle_sample("config5", args.cpu_baseline_bands)}

@@ -575,6 +575,31 @@ qm_status qm_tddft_etrs(qm_gspace g, int ik, int nb, void* psi, int ld_psi, cons
                         double dt, int order, void* work, qm_precision prec, void* stream);
 
 /*
+ * qm_gw_mel - plane-wave matrix elements of the GW module (Sec. 5, "gw" module, matrix_elements):
+ *     M_nn'(G) = <n k+q| exp(i(q+G).r) |n' k> = sum_{G2} conj(c_{n,k+q}(G + G2)) c_{n',k}(G2)
+ * for G on the sphere |q+G|^2/2 <= E_eps, by the paper's route: both sets of states to real space
+ * with the stick-pruned inverse FFT of qm_hpsi, the product conj(u_n(r)) u_n'(r) of every pair,
+ * one forward FFT per pair gathered onto the sphere of q.
+ *
+ *  g, ik_left, ik_right  wavefunction gspace and the k-points k+q (left states) and k (right).
+ *  nl, psi_l, ld_l       device, nl rows on the sphere of ik_left (ld_l >= its npw).
+ *  nr, psi_r, ld_r       device, nr rows on the sphere of ik_right.
+ *  geps, iq              gspace of the E_eps sphere: the same FFT grid as g, and its k-point iq
+ *                        equal to kpts[ik_left] - kpts[ik_right] (crystal coordinates, 1e-10).
+ *  M, ld_m               device, nl * nr rows (row n * nr + n') of npw(geps, iq) complex, ld_m >=
+ *                        that npw; overwritten.
+ *  prec                  QM_FP64 (double[2] everywhere) or QM_MIXED (float[2]: FP32 transforms).
+ *  stream                asynchronous on the stream; uses g's workspace (two full FFT boxes per
+ *                        state, N1 N2 N3 complex each, plus stick buffers of at most 256 MB each).
+ * The result is exact (to rounding) when the grid holds every G + G2 without wrap-around, as the
+ * grid rule's density grid does for E_eps <= the wavefunction cutoff.
+ * Errors: QM_ERR_ARG (sizes, NULL pointers, grids or q that do not match), QM_ERR_OOM, QM_ERR_CUDA.
+ */
+qm_status qm_gw_mel(qm_gspace g, int ik_left, int ik_right, int nl, const void* psi_l, int ld_l, int nr,
+                    const void* psi_r, int ld_r, qm_gspace geps, int iq, void* M, int ld_m,
+                    qm_precision prec, void* stream);
+
+/*
  * Learned preconditioner (the learned form): a network K(f) > 0 on per-plane-wave features
  * replaces the Teter-Payne-Allan factor in the Davidson correction, delta_n(G) = K(f_nG) r_n(G).
  *

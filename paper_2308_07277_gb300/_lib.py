@@ -102,6 +102,9 @@ _TDDFT_TAIL = [ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, cty
                ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
 SIGNATURES["qm_tddft_taylor"] = (ctypes.c_int, _TDDFT_COMMON + _TDDFT_TAIL)
 SIGNATURES["qm_tddft_etrs"] = (ctypes.c_int, _TDDFT_COMMON + [ctypes.c_void_p] + _TDDFT_TAIL)
+SIGNATURES["qm_gw_mel"] = (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                          ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                          ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p])
 
 class HpsiJob(ctypes.Structure):
     """qm_hpsi_job of include/qm.h."""

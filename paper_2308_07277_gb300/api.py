@@ -336,6 +336,21 @@ def qm_tddft_etrs(g, ik, psi, vloc_now, vloc_next, beta, D, dt, order=4, prec="f
                              *nl, float(dt), int(order), _dev_ptr(work, "work", cdt), p, _stream_ptr(stream)))
     return psi
 
+
+def qm_gw_mel(g, ik_left, ik_right, psi_l, psi_r, geps, iq, npw_eps, M=None, prec="fp64", stream=None):
+    """GW plane-wave matrix elements M (nl * nr, npw_eps): row n * nr + n' holds
+    <n k+q| exp(i(q+G).r) |n' k> on the sphere of q of the handle geps (k-point iq)."""
+    lib = _lib.load()
+    p = _PREC[prec]
+    cdt = torch.complex128 if p == QM_FP64 else torch.complex64
+    nl, nr = int(psi_l.shape[0]), int(psi_r.shape[0])
+    if M is None:
+        M = torch.empty((nl * nr, int(npw_eps)), dtype=cdt, device=psi_r.device)
+    _check(lib.qm_gw_mel(g, int(ik_left), int(ik_right), nl, _dev_ptr(psi_l, "psi_l", cdt), int(psi_l.stride(0)),
+                         nr, _dev_ptr(psi_r, "psi_r", cdt), int(psi_r.stride(0)), geps, int(iq),
+                         _dev_ptr(M, "M", cdt), int(M.stride(0)), p, _stream_ptr(stream)))
+    return M
+
 class Batch:
     """A batched H psi plan (qm_batch of include/qm.h) bound to its buffers.
 

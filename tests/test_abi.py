@@ -262,3 +262,36 @@ def test_hpsi_gamma_rejects_other_k_points():
         assert lib.qm_launch_count() == n0
     finally:
         Q.qm_gspace_destroy(g)
+
+
+def test_gw_mel_argument_errors_before_device_work():
+    """qm_gw_mel rejects handles on different grids, a q that is not k_left - k_right, short rows,
+    NULL buffers and bad indices with QM_ERR_ARG before any device work; nl or nr 0 is QM_OK."""
+    import ctypes
+    import paper_2308_07277_gb300 as Q
+    lib = _lib()
+    lat = np.eye(3) * 10.0
+    g = Q.qm_gspace_create(lat, [[0.25, 0, 0], [0, 0, 0]], 5.0, (20, 20, 20))
+    ge = Q.qm_gspace_create(lat, [[0.25, 0, 0]], 2.0, (20, 20, 20))
+    ge_grid = Q.qm_gspace_create(lat, [[0.25, 0, 0]], 2.0, (24, 20, 20))
+    ge_q = Q.qm_gspace_create(lat, [[0.5, 0, 0]], 2.0, (20, 20, 20))
+    try:
+        npw = Q.qm_gspace_query(g)["npw"]
+        npe = Q.qm_gspace_query(ge)["npw"][0]
+        f, h, m = ctypes.c_void_p(1 << 20), ctypes.c_void_p(1 << 24), ctypes.c_void_p(1 << 28)
+        n0 = lib.qm_launch_count()
+
+        def call(gw=g, ikl=0, ikr=1, nl=2, pl=f, ldl=npw[0], nr=3, pr=h, ldr=npw[1], e=ge, iq=0, M=m, ldm=npe, prec=0):
+            return lib.qm_gw_mel(gw, ikl, ikr, nl, pl, ldl, nr, pr, ldr, e, iq, M, ldm, prec, None)
+
+        for kw, msg in [({"e": ge_grid}, "grids"), ({"e": ge_q}, "not k(ik_left)"), ({"ikl": 2}, "out of range"),
+                        ({"iq": 1}, "iq"), ({"nl": -1}, "negative"), ({"pl": None}, "NULL"), ({"M": None}, "NULL"),
+                        ({"ldl": npw[0] - 1}, "leading dimension"), ({"ldm": npe - 1}, "leading dimension"),
+                        ({"prec": 5}, "precision"), ({"gw": None}, "NULL gspace"),
+                        ({"M": ctypes.c_void_p((1 << 28) + 8)}, "aligned")]:
+            assert call(**kw) == 1 and msg in Q.qm_last_error(), (kw, Q.qm_last_error())
+        assert call(nl=0) == 0 and call(nr=0) == 0
+        assert lib.qm_launch_count() == n0
+    finally:
+        for h_ in (g, ge, ge_grid, ge_q):
+            Q.qm_gspace_destroy(h_)
