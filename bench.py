@@ -64,6 +64,7 @@ def parse():
     ap.add_argument("--davidson", type=int, default=1, help="also time block Davidson to tol (0: skip)")
     ap.add_argument("--davidson-tol", type=float, default=1e-8)
     ap.add_argument("--batched", type=int, default=1, help="also time the batched form (0: skip)")
+    ap.add_argument("--scf", type=int, default=1, help="also time a self-consistency run (0: skip)")
     ap.add_argument("--gw", type=int, default=1, help="also time GW plane-wave matrix elements (0: skip)")
     ap.add_argument("--tddft", type=int, default=1, help="also time real-time propagation steps (0: skip)")
     ap.add_argument("--large", type=int, default=1, help="also time H psi on the 216- and 255-atom cells (0: skip)")
@@ -790,6 +791,47 @@ def run_gw(args, Q, S, dev):
     return out
 
 
+def run_scf(args, Q, S, dev):
+    """Kohn-Sham self-consistency (qm_scf) on the 8-atom cubic cell (15 Ry, the grid rule's grid,
+    the shifted 2x2x2 k-points, 8 bands, the lowest band occupied: 2 electrons), from random states
+    and the uniform density to a density residual of 1e-8 electrons; wall time of the call."""
+    import torch
+    cell = S.cubic_si8(15.0, nbnd=8, kpts=S.config2().kpts)
+    g = Q.GSpace(cell.lattice, cell.kpts, cell.ecut_ha, None)
+    grid = g.grid
+    vion = torch.from_numpy(S.vloc_on_grid(cell.lattice, cell.tau, grid)).to(dev)
+    D = torch.from_numpy(S.dvals(cell.nat)).to(dev)
+    ld = max(g.npw)   # one row stride for every k-point
+    betas = []
+    for ik in range(len(cell.kpts)):
+        _, _, kpg = g.indices(ik)
+        b = torch.zeros((cell.nproj, ld), dtype=torch.complex128)
+        b[:, :g.npw[ik]] = torch.from_numpy(S.beta_of_q(kpg, cell.tau, cell.omega))
+        betas.append(b.to(dev))
+    w = [1.0 / len(cell.kpts)] * len(cell.kpts)
+    out = {"workload": "si8_cubic_15Ry_%dx%dx%d_4k_8b_2e" % tuple(grid), "npw": g.npw, "tol_electrons": 1e-8}
+    for prec in ("fp64", "mixed"):
+        psis = []
+        for ik in range(len(cell.kpts)):
+            p = torch.zeros((cell.nbnd, ld), dtype=torch.complex128)
+            p[:, :g.npw[ik]] = torch.from_numpy(S.psi_random(cell.seed, cell.nbnd, g.npw[ik], stream=ik))
+            psis.append(p.to(dev))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        eig, rho, v, info = Q.qm_scf(g.handle, 2, w, psis, vion, betas, D, tol=1e-8, prec=prec)
+        torch.cuda.synchronize()
+        out[prec] = {"seconds": time.perf_counter() - t0, "iterations": info["iterations"],
+                     "converged": info["converged"], "band_applies": info["band_applies"],
+                     "lowest_eigenvalue_ha": float(eig[:, 0].min())}
+        if prec == "mixed":
+            out["max_eig_diff_vs_fp64_ha"] = float(abs(eig - out["fp64"].pop("_eig")).max())
+        else:
+            out[prec]["_eig"] = eig
+    out["fp64_over_mixed_seconds"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
+    g.close()
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -855,6 +897,7 @@ def run_ours(args):
     batched = run_batched(args, Q, S, dev) if args.batched else None
     tddft = run_tddft(args, Q, S, dev) if args.tddft else None
     gw = run_gw(args, Q, S, dev) if args.gw else None
+    scf = run_scf(args, Q, S, dev) if args.scf else None
     large = run_large_cells(args, Q, S, dev) if args.large else None
     theta, tinfo = train_network(Q, S, dev) if (args.davidson_large or args.davidson_255) else (None, None)
     dav255 = run_davidson_255(args, Q, S, dev, theta) if args.davidson_255 else None
@@ -888,6 +931,7 @@ def run_ours(args):
                 "batched": batched,
                 "tddft": tddft,
                 "gw_matrix_elements": gw,
+                "scf": scf,
                 "large_cells": large,
                 "davidson_216_atoms_learned": dav_large,
                 "cpu_baseline": oracle_sample("config5", args.cpu_baseline_bands)}

@@ -600,6 +600,59 @@ qm_status qm_gw_mel(qm_gspace g, int ik_left, int ik_right, int nl, const void* 
                     qm_precision prec, void* stream);
 
 /*
+ * qm_scf - Kohn-Sham self-consistency around qm_davidson (Sec. 2.1: n -> V -> {psi} -> n_out ->
+ * mix, until n_out = n; Sec. 5, dft module scf with density mixing).
+ *   V(r) = V_ext(r) + V_H[n](r) + v_xc(n(r)):  V_H(G) = 4 pi n(G) / |G|^2 on the density sphere
+ *          |G|^2/2 <= 4 E_c (G = 0 left out: neutralising background); v_xc the local density
+ *          approximation (Slater exchange + Perdew-Zunger correlation, unpolarised; no
+ *          exchange-correlation where n <= 1e-12).
+ *   n(r)  = sum_k w_k sum_{n < nelec/2} 2 |psi_nk(r)|^2 (insulating occupations, spin-degenerate).
+ *   mixing: Anderson (equal-weight modified Broyden) on the density residual F = n_out - n_in with
+ *          the last `history` differences and factor alpha, from the uniform density nelec / Omega.
+ *   converged when (Omega / N_r) sum_r |n_out - n_in| <= tol (electrons).
+ *
+ *  g          wavefunction gspace (all its k-points take part); the grid must hold the density
+ *             sphere (the grid rule's grid does), else QM_ERR_ARG.
+ *  nelec      electrons, even, >= 2; nb >= nelec/2 bands are solved per k-point.
+ *  wk         host, nk weights summing to 1.
+ *  psi        host array of nk device pointers: nb rows of complex double (ld_psi >= npw); the
+ *             starting states in, the last Ritz vectors out.
+ *  vion_r     device, N_r doubles: V_ext on the grid (x fastest).
+ *  nproj, beta, ld_beta, D   projectors: beta is a host array of nk device pointers (or NULL when
+ *             nproj == 0), each as qm_hpsi's; D device.
+ *  opts       host, may be NULL (defaults below).
+ *  eigs       host, nk * nb doubles: the last Ritz values.
+ *  rho_r, vloc_r   device, N_r doubles each: the last input density and its potential.
+ *  stats      host, may be NULL.
+ *  stream     cudaStream_t; synchronous with respect to the host.  Allocates its densities and
+ *             transform buffers with cudaMalloc for the call; qm_davidson uses g's workspaces.
+ * Errors: QM_ERR_ARG, QM_ERR_OOM, QM_ERR_CUDA, QM_ERR_NUMERIC; QM_ERR_NOT_CONVERGED (max_iter
+ *         reached: the outputs hold the last step).
+ */
+typedef struct {
+    double tol;        /* density residual (electrons); default 1e-8 */
+    int max_iter;      /* self-consistency steps; default 50 */
+    double alpha;      /* mixing factor in (0, 1]; default 0.5 */
+    int history;       /* differences kept by the mixing, 0..8 (0: linear mixing); default 4 */
+    double dav_tol;    /* qm_davidson residual tolerance (Ha) of every step; default 1e-9 */
+    int dav_max_iter;  /* qm_davidson max_iter; default 100 */
+    qm_precision prec; /* qm_davidson form; default QM_FP64 */
+} qm_scf_opts;
+
+typedef struct {
+    int iterations;          /* self-consistency steps taken */
+    int converged;           /* 1 if the density residual reached tol */
+    double drho;             /* last density residual (electrons) */
+    long long band_applies;  /* H psi band applications of all the Davidson calls */
+    double seconds;          /* host wall time of the call */
+} qm_scf_stats;
+
+qm_status qm_scf(qm_gspace g, int nelec, const double* wk, int nb, void* const* psi, int ld_psi,
+                 const double* vion_r, int nproj, const void* const* beta, int ld_beta, const double* D,
+                 const qm_scf_opts* opts, double* eigs, double* rho_r, double* vloc_r,
+                 qm_scf_stats* stats, void* stream);
+
+/*
  * Learned preconditioner (the learned form): a network K(f) > 0 on per-plane-wave features
  * replaces the Teter-Payne-Allan factor in the Davidson correction, delta_n(G) = K(f_nG) r_n(G).
  *

@@ -106,6 +106,26 @@ SIGNATURES["qm_gw_mel"] = (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.
                                           ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                           ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p])
 
+
+class ScfOpts(ctypes.Structure):
+    """qm_scf_opts of include/qm.h."""
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("alpha", ctypes.c_double),
+                ("history", ctypes.c_int), ("dav_tol", ctypes.c_double), ("dav_max_iter", ctypes.c_int),
+                ("prec", ctypes.c_int)]
+
+
+class ScfStats(ctypes.Structure):
+    """qm_scf_stats of include/qm.h."""
+    _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("drho", ctypes.c_double),
+                ("band_applies", ctypes.c_longlong), ("seconds", ctypes.c_double)]
+
+
+SIGNATURES["qm_scf"] = (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_double_p, ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_void_p,
+                                       ctypes.POINTER(ScfOpts), c_double_p, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.POINTER(ScfStats), ctypes.c_void_p])
+
 class HpsiJob(ctypes.Structure):
     """qm_hpsi_job of include/qm.h."""
     _fields_ = [("g", ctypes.c_void_p), ("ik", ctypes.c_int), ("nb", ctypes.c_int), ("psi", ctypes.c_void_p),

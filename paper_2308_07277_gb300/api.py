@@ -351,6 +351,42 @@ def qm_gw_mel(g, ik_left, ik_right, psi_l, psi_r, geps, iq, npw_eps, M=None, pre
                          _dev_ptr(M, "M", cdt), int(M.stride(0)), p, _stream_ptr(stream)))
     return M
 
+
+def qm_scf(g, nelec, weights, psis, vion, betas, D, tol=1e-8, max_iter=50, alpha=0.5, history=4, dav_tol=1e-9,
+           dav_max_iter=100, prec="fp64", stream=None, raise_not_converged=True):
+    """Kohn-Sham self-consistency: psis (one (nb, >=npw) complex128 CUDA tensor per k-point, updated in
+    place), vion (N_r,) float64, betas (one tensor per k-point) or None, D.  Returns (eigenvalues
+    ndarray (nk, nb), density (N_r,), potential (N_r,), stats dict)."""
+    lib = _lib.load()
+    nk = len(psis)
+    nb = int(psis[0].shape[0])
+    ld = int(psis[0].stride(0))
+    for p in psis:
+        if int(p.shape[0]) != nb or int(p.stride(0)) != ld:
+            raise ValueError("every k-point's psi must have the same shape and row stride")
+    w = np.ascontiguousarray(np.asarray(weights, np.float64))
+    pp = (ctypes.c_void_p * nk)(*[_dev_ptr(p, "psi", torch.complex128).value for p in psis])
+    nproj = 0 if betas is None else int(betas[0].shape[0])
+    bp = None
+    ldb = 0
+    if nproj:
+        bp = (ctypes.c_void_p * nk)(*[_dev_ptr(b, "beta", torch.complex128).value for b in betas])
+        ldb = int(betas[0].stride(0))
+    rho = torch.empty_like(vion)
+    vl = torch.empty_like(vion)
+    eig = np.zeros(nk * nb)
+    opts = _lib.ScfOpts(float(tol), int(max_iter), float(alpha), int(history), float(dav_tol), int(dav_max_iter),
+                        _PREC[prec])
+    st = _lib.ScfStats()
+    status = lib.qm_scf(g, int(nelec), _dp(w), nb, pp, ld, _dev_ptr(vion, "vion", torch.float64), nproj, bp, ldb,
+                        _dev_ptr(D, "D", torch.float64) if nproj else None, ctypes.byref(opts), _dp(eig),
+                        _dev_ptr(rho, "rho", torch.float64), _dev_ptr(vl, "vloc", torch.float64), ctypes.byref(st),
+                        _stream_ptr(stream))
+    info = {k: getattr(st, k) for k, _ in _lib.ScfStats._fields_}
+    if status != 0 and not (status == 4 and not raise_not_converged):
+        _check(status)
+    return eig.reshape(nk, nb), rho, vl, info
+
 class Batch:
     """A batched H psi plan (qm_batch of include/qm.h) bound to its buffers.
 

@@ -87,10 +87,10 @@ k_plane_pair(const typename Cx<R>::T* __restrict__ UL, const typename Cx<R>::T* 
     for (int i = tid; i < nrow; i += nt) srow[i] = __ldg(rows + i);
     const size_t nplane = (size_t)N3 * N2;
     const C* a = UL + ((size_t)n * N1 + p1) * nplane;
-    const C* c = UR + ((size_t)m * N1 + p1) * nplane;
+    const C* c = UR ? UR + ((size_t)m * N1 + p1) * nplane : nullptr;  // no right factor: the plane of UL
     for (int i = tid; i < N3 * N2; i += nt) {
         const int p3 = i / N2, p2 = i - p3 * N2;
-        const C x = a[i], y = c[i];
+        const C x = a[i], y = c ? c[i] : mk<C>(1, 0);
         plane[p3 * ldy + p2] = mk<C>(x.x * y.x + x.y * y.y, x.y * y.x - x.x * y.y);  // x conj(y)
     }
     __syncthreads();
@@ -105,13 +105,14 @@ k_plane_pair(const typename Cx<R>::T* __restrict__ UL, const typename Cx<R>::T* 
     for (int s = tid; s < nstick; s += nt) Tp[s] = plane[__ldg(stick_plane + s)];
 }
 
-// forward x on the q sphere's sticks and the gather M[j][g] = conj(F(G)) / N_r
+// forward x on the q sphere's sticks and the gather M[j][g] = conj(F(G)) / N_r (conj_out = 0:
+// F(G) / N_r, the Fourier coefficient of a function given in real space)
 template <class R, bool FUSED>
 __global__ void __launch_bounds__(kThreads, fft_min_ctas<R, FUSED>())
 k_stick_mel(const typename Cx<R>::T* __restrict__ Te, int nstick, int nstick_pad, const int* __restrict__ stick_g0,
             const int2* __restrict__ g_code, const __grid_constant__ AxisPlan px,
             const typename Cx<R>::T* __restrict__ tw_x, int ldx, R inv_nr, typename Cx<R>::T* __restrict__ M,
-            int ld_m) {
+            int ld_m, int conj_out) {
     using C = typename Cx<R>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* lines = reinterpret_cast<C*>(smem_raw);
@@ -137,7 +138,7 @@ k_stick_mel(const typename Cx<R>::T* __restrict__ Te, int nstick, int nstick_pad
     for (int g = gb + tid; g < ge; g += nt) {
         const int2 cd = __ldg(g_code + g);
         const C x = lines[(cd.x - s0) * ldx + cd.y];
-        out[g] = mk<C>(x.x * inv_nr, -x.y * inv_nr);
+        out[g] = mk<C>(x.x * inv_nr, conj_out ? -x.y * inv_nr : x.y * inv_nr);
     }
 }
 
@@ -224,7 +225,7 @@ qm_status gw_mel_impl(qm_gspace g, int ikl, int ikr, int nl, const void* psi_l, 
             ProfScope pf(PF_STICK_FWD, s);
             kme_<<<dim3(ntile_e, npx), stick_threads<R>(), sm_stick, s>>>(Te, ke.nstick, ke.nstick_pad, ke.stick_g0,
                                                                          ke.g_code, g->plan[0], tw[0], g->ldx, inv_nr,
-                                                                         (C*)M + (size_t)p0 * ld_m, ld_m);
+                                                                         (C*)M + (size_t)p0 * ld_m, ld_m, 1);
         }
     }
     return cuda_check(cudaGetLastError(), "qm_gw_mel launch");

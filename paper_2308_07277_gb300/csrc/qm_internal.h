@@ -162,6 +162,15 @@ class ProfScope {
 // order 1 = the same radices reversed (an alternative for the batched form's autotuner).
 void fft_plan(int n, int order, AxisPlan& p, std::vector<int>& rev);
 
+// ---- self-consistency loop (FFT-path parts in fft_f64.cu) ----
+// work bytes for the two calls below; n_nat += the density (weight w per |u(r)|^2) of the first
+// nocc rows of psi (k-point ik of g); v_nat = vion + V_H[n] + v_xc(n) with grho the density sphere
+size_t scf_work_size(qm_gspace g, qm_gspace grho, int nocc);
+qm_status scf_density_run(qm_gspace g, int ik, int nocc, const double2* psi, int ld, double w, double* n_nat,
+                          void* work, cudaStream_t s);
+qm_status scf_potential_run(qm_gspace g, qm_gspace grho, const double* n_nat, const double* vion, double* v_nat,
+                            void* work, size_t work_bytes, cudaStream_t s);
+
 // ---- FFT path (fft_path.cu) ----
 // Vt[p1][p3][p2] = V(rev1[p1], rev2[p2], rev3[p3]) / N_r   (real type R)
 qm_status launch_vt_prepare(qm_gspace g, const double* vloc, void* vt, bool fp32, cudaStream_t s);

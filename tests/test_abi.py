@@ -295,3 +295,38 @@ def test_gw_mel_argument_errors_before_device_work():
     finally:
         for h_ in (g, ge, ge_grid, ge_q):
             Q.qm_gspace_destroy(h_)
+
+
+def test_scf_argument_errors_before_device_work():
+    """qm_scf rejects bad options, odd or too many electrons, weights that do not sum to 1, NULL
+    buffers and a grid that cannot hold the density sphere, with QM_ERR_ARG before device work."""
+    import ctypes
+    import paper_2308_07277_gb300 as Q
+    from paper_2308_07277_gb300 import _lib as L
+    lib = _lib()
+    g = Q.qm_gspace_create(np.eye(3) * 10.0, [[0, 0, 0], [0.25, 0, 0]], 3.0)
+    small = Q.qm_gspace_create(np.eye(3) * 10.0, [[0, 0, 0]], 3.0, (12, 12, 12))
+    try:
+        npw = max(Q.qm_gspace_query(g)["npw"])
+        f = ctypes.c_void_p(1 << 20)
+        psis = (ctypes.c_void_p * 2)(1 << 20, 1 << 24)
+        eig = np.zeros(8)
+        n0 = lib.qm_launch_count()
+
+        def call(h=g, nelec=2, w=(0.5, 0.5), nb=4, p=psis, ld=npw, opts=None, out=f):
+            wa = np.ascontiguousarray(np.asarray(w, np.float64))
+            return lib.qm_scf(h, nelec, wa.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), nb, p, ld, f, 0, None, 0,
+                              None, opts, eig.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), out, out, None, None)
+
+        bad = L.ScfOpts(1e-8, 50, 1.5, 4, 1e-9, 100, 0)
+        for kw, msg in [({"nelec": 3}, "even"), ({"nelec": 10}, "nb"), ({"w": (0.5, 0.6)}, "weights"),
+                        ({"w": (-0.5, 1.5)}, "negative"), ({"ld": npw - 1}, "leading dimension"),
+                        ({"out": None}, "NULL"), ({"opts": ctypes.byref(bad)}, "option"),
+                        ({"p": (ctypes.c_void_p * 2)(1 << 20, None)}, "NULL psi")]:
+            assert call(**kw) == 1 and msg in Q.qm_last_error(), (kw, Q.qm_last_error())
+        st = call(h=small, w=(1.0,), ld=Q.qm_gspace_query(small)["npw"][0])
+        assert st == 1 and "density sphere" in Q.qm_last_error(), Q.qm_last_error()
+        assert lib.qm_launch_count() == n0
+    finally:
+        Q.qm_gspace_destroy(small)
+        Q.qm_gspace_destroy(g)
