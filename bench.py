@@ -746,6 +746,26 @@ def run_tddft(args, Q, S, dev):
         out[prec] = {"value": nb / (ms * 1e-3), "ms_per_step": ms, "steps": steps,
                      "band_applies_per_s": 2 * order * nb / (ms * 1e-3)}
         if prec == "mixed":
+            # the Taylor update kernel (family "other" here) against HBM: it reads and writes the new
+            # term and psi, 4 complex values per element
+            lib = Q.api._lib.load()
+            lib.qm_prof_enable(1)
+            Q.qm_tddft_etrs(g.handle, 0, psi, v, v, beta, D, dt, order, prec=prec, work=work, stream=stream)
+            torch.cuda.synchronize()
+            fam = read_prof(lib)
+            lib.qm_prof_enable(0)
+            acc = fam.get("other")
+            if acc:
+                avg = acc["ms_total"] / acc["launches"]
+                nbytes = 4 * 8.0 * nb * g.npw[0]
+                out["taylor_update_roofline"] = {
+                    "kernel": "k_taylor_acc", "bound": "hbm", "achieved": nbytes / (avg * 1e-3) / 1e9,
+                    "peak": load_peaks()[0].get("hbm_gbs"), "unit": "GB/s", "avg_launch_ms": avg,
+                    "bytes_per_launch": nbytes, "launches_per_step": acc["launches"]}
+                r = out["taylor_update_roofline"]
+                r["frac"] = r["achieved"] / r["peak"] if r["peak"] else None
+                out["taylor_update_share_of_step"] = acc["ms_total"] / ms
+        if prec == "mixed":
             Q.qm_hpsi_prepare(g.handle, 0, None)
         del psi, beta, work
     out["mixed_over_fp64"] = out["mixed"]["value"] / out["fp64"]["value"]
