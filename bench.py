@@ -70,7 +70,8 @@ def parse():
     ap.add_argument("--large", type=int, default=1, help="also time H psi on the 216- and 255-atom cells (0: skip)")
     ap.add_argument("--profile", default="",
                     help="profiling run: only the precision form's H psi steps (projectors prepared) on the named "
-                         "cell (config2, config4, config5) for --warmup + --steps steps, for ncu command lines")
+                         "cell (config2, config4, config5) for --warmup + --steps steps, or 'gw' (the GW matrix "
+                         "elements of the benchmark), for ncu command lines")
     ap.add_argument("--profile-k", type=int, default=0, help="--profile: k-points to use (0: all)")
     ap.add_argument("--profile-prec", default="mixed", choices=["mixed", "fp64"], help="--profile: precision form")
     ap.add_argument("--profile-batched", default="", help="profiling run of the batched form: mixed or fp64 "
@@ -803,6 +804,13 @@ def run_gw(args, Q, S, dev):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / steps
         out[prec] = {"value": nl * nr / (ms * 1e-3), "ms_per_call": ms, "steps": steps}
+        # the pair phase reads two real-space boxes per pair: those bytes over the whole call's time
+        # (the states' transforms to real space and the gathers included in the time)
+        nbytes = nl * nr * 2.0 * (cell.grid[0] * cell.grid[1] * cell.grid[2]) * (8 if prec == "mixed" else 16)
+        pk = load_peaks()[0].get("hbm_gbs")
+        out[prec]["pair_reads"] = {"bound": "hbm", "achieved": nbytes / (ms * 1e-3) / 1e9, "peak": pk, "unit": "GB/s",
+                                   "frac": nbytes / (ms * 1e-3) / 1e9 / pk if pk else None,
+                                   "bytes_per_call": nbytes}
         del pl, pr, M
     out["mixed_over_fp64"] = out["mixed"]["value"] / out["fp64"]["value"]
     ge.close()
@@ -993,6 +1001,24 @@ def run_profile(args):
         b.check()
         torch.cuda.synchronize()
         print(json.dumps({"profile": "batched", "prec": prec, "replays": args.warmup + args.steps, **b.info()}))
+        return
+    if args.profile == "gw":
+        # the GW matrix elements of the benchmark's workload (64-atom cell, 32 x 64 pairs), one
+        # call per step in the --profile-prec precision
+        cell = S.config2()
+        k, kq = cell.kpts[0], cell.kpts[1]
+        g = Q.GSpace(cell.lattice, [kq, k], cell.ecut_ha, cell.grid)
+        ge = Q.GSpace(cell.lattice, [kq - k], 0.25 * cell.ecut_ha, cell.grid)
+        cdt = torch.complex64 if args.profile_prec == "mixed" else torch.complex128
+        pl = torch.from_numpy(S.psi_random(cell.seed, 32, g.npw[0], stream=1)).to(cdt).to(dev)
+        pr = torch.from_numpy(S.psi_random(cell.seed, 64, g.npw[1], stream=0)).to(cdt).to(dev)
+        M = torch.empty((32 * 64, ge.npw[0]), dtype=cdt, device=dev)
+        for _ in range(args.warmup + args.steps):
+            Q.qm_gw_mel(g.handle, 0, 1, pl, pr, ge.handle, 0, ge.npw[0], M=M, prec=args.profile_prec)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": "gw", "precision": args.profile_prec, "steps": args.warmup + args.steps}))
+        ge.close()
+        g.close()
         return
     cell = getattr(S, args.profile)()
     nk = args.profile_k or len(cell.kpts)
