@@ -322,40 +322,53 @@ def measure_hpsi(steps, warmup, Q, lib, g, cell, wl, v, D, world, dev, peaks, sa
     clk = clocks.stop() if clocks else None
 
     # end to end: pinned host psi -> device, H psi, device -> pinned host, every step, through
-    # the public API as a user pipelines it: the input copies run on one copy stream and the
-    # result copies on another, so that k-point k+1's input and k-point k-1's result move while
-    # k-point k is applied (events order each copy with its H psi; a step's copies wait for the
-    # previous step's use of the same buffers)
+    # the public API as a user pipelines a steady stream of steps: the input copies run on one
+    # copy stream and the result copies on another, so that k-point k+1's input and k-point
+    # k-1's result move while k-point k is applied.  Events order each copy with the H psi that
+    # uses its buffer: k-point k's next input waits only for its own H psi of the previous step,
+    # and its next H psi only for the copy-out of its previous result, so one step's copies also
+    # overlap the neighbouring steps' compute.
     h2d_s, d2h_s = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+    used = [None] * nk      # H psi of k-point k done (its psi buffer free again)
+    copied = [None] * nk    # copy-out of k-point k's result done (its out buffer free again)
 
     def e2e_step():
-        h2d_s.wait_stream(stream)
         ev_in = []
-        with torch.cuda.stream(h2d_s):
-            for ik in range(nk):
+        for ik in range(nk):
+            if used[ik] is not None:
+                h2d_s.wait_event(used[ik])
+            with torch.cuda.stream(h2d_s):
                 wl.psi[ik].copy_(wl.psi_host[ik], non_blocking=True)
-                ev_in.append(torch.cuda.Event())
-                ev_in[-1].record(h2d_s)
+            ev_in.append(torch.cuda.Event())
+            ev_in[-1].record(h2d_s)
         for ik in range(nk):
             stream.wait_event(ev_in[ik])
+            if copied[ik] is not None:
+                stream.wait_event(copied[ik])
             Q.qm_hpsi(g.handle, ik, wl.psi[ik], v, wl.beta[ik], D, out=wl.out[ik], prec=wl.prec, stream=stream)
-            done = torch.cuda.Event()
-            done.record(stream)
-            d2h_s.wait_event(done)
+            used[ik] = torch.cuda.Event()
+            used[ik].record(stream)
+            d2h_s.wait_event(used[ik])
             with torch.cuda.stream(d2h_s):
                 wl.out_host[ik].copy_(wl.out[ik], non_blocking=True)
-        stream.wait_stream(d2h_s)
+            copied[ik] = torch.cuda.Event()
+            copied[ik].record(d2h_s)
 
     ems = None
     if with_e2e:
         for _ in range(2):
             e2e_step()
         barrier()
+        stream.wait_stream(d2h_s)
+        stream.wait_stream(h2d_s)
         e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e2.record(stream)
+        h2d_s.wait_stream(stream)
+        d2h_s.wait_stream(stream)
         esteps = max(3, steps // 3)
         for _ in range(esteps):
             e2e_step()
+        stream.wait_stream(d2h_s)     # the timed region ends when the last result is on the host
         e3.record(stream)
         barrier()
         ems = e2.elapsed_time(e3) / esteps
