@@ -432,6 +432,51 @@ def measure_hpsi(steps, warmup, Q, lib, g, cell, wl, v, D, world, dev, peaks, sa
     return out
 
 
+def measure_fft_path(steps, warmup, Q, g, cell, wl, v, fam_live, ms_live, peaks):
+    """The FFT path (scatter, stick-pruned 3D FFTs, V multiply, gather, kinetic term: K1-K3) of the
+    precision form against HBM, on the fused design's bytes per band-apply: psi read twice, H psi
+    written once, four passes over the stick buffer (N1 x nstick complex values per band).  Alone:
+    qm_hpsi without projectors (only the FFT kernels run; without the tensor-core stream to overlap,
+    the library chunks the bands so that the stick buffer stays in L2), CUDA events around the
+    steps.  Live: the
+    three kernels' summed event time inside the headline step, where they share the SMs with the
+    tensor-core stream."""
+    import numpy as np
+    import torch
+    nk, nb = len(cell.kpts), cell.nbnd
+    cs = 8
+    nbytes = 0.0
+    for ik in range(nk):
+        idx, _, _ = g.indices(ik)
+        nstick = int(np.unique(idx // cell.grid[0]).size)
+        nbytes += nb * (3.0 * g.npw[ik] * cs + 4.0 * cell.grid[0] * nstick * cs)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        for ik in range(nk):
+            Q.qm_hpsi(g.handle, ik, wl.psi[ik], v, None, None, out=wl.out[ik], prec="mixed", stream=stream)
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    pk = peaks.get("hbm_gbs")
+    out = {"bytes_per_band_apply": nbytes / (nb * nk), "bytes_per_step": nbytes, "peak": pk, "unit": "GB/s",
+           "alone": {"ms_per_step": ms, "achieved": nbytes / (ms * 1e-3) / 1e9}}
+    out["alone"]["frac"] = out["alone"]["achieved"] / pk if pk else None
+    live = sum(fam_live[k]["ms_total"] for k in ("k_stick_inverse", "k_plane", "k_stick_forward") if k in fam_live)
+    if live > 0:
+        lms = live / steps
+        out["live"] = {"ms_per_step": lms, "achieved": nbytes / (lms * 1e-3) / 1e9}
+        out["live"]["frac"] = out["live"]["achieved"] / pk if pk else None
+    return out
+
+
 def run_davidson(args, Q, lib, g, cell, wl64, v, D):
     """Block Davidson to args.davidson_tol at every k-point from the seeded random start:
     the plain FP64 form, FP64 with 10 % buffer bands (only the lowest 160 must converge), the
@@ -914,6 +959,9 @@ def run_ours(args):
                                      sample_clocks=head_clocks and prec == "mixed",
                                      with_e2e=e2e_mixed and prec == "mixed")
             res[prec]["steps"] = steps
+            if prec == "mixed" and head_clocks:
+                res["fft_path"] = measure_fft_path(steps, warm, Q, g, cell, wl, v, res[prec]["kernels"],
+                                                   res[prec]["ms_per_step"], peaks)
             if prec == "mixed":
                 res[prec]["prepare_seconds"] = prep_s
                 for ik in range(len(cell.kpts)):
@@ -957,6 +1005,7 @@ def run_ours(args):
                            "nproj": cell.nproj, "grid": list(cell.grid), "l2": head["l2"]},
                 "e2e": head["e2e"], "gpu_launches": head["gpu_launches"], "kernels": head["kernels"],
                 "roofline": head["roofline"], "roofline_other": head["roofline_other"],
+                "fft_path": forms.get("fft_path"),
                 "clocks": head["clocks"],
                 "forms": {"fp64": {k: forms["fp64"][k] for k in keep},
                           "mixed_per_call": {k: forms["mixed_per_call"][k] for k in keep if k in forms["mixed_per_call"]},

@@ -18,8 +18,8 @@
 
 namespace qm {
 
-// Stick-buffer budget per chunk of bands: small enough that a chunk's intermediate data
-// stays resident in the 129 MB L2 between the three FFT kernels.
+// Stick-buffer budget per chunk of bands of the FP64 form: small enough that a chunk's
+// intermediate data stays resident in the 129 MB L2 between the three FFT kernels.
 constexpr size_t kStickBudget = 48ull << 20;
 constexpr size_t kStickBudgetOverlap = 1ull << 30;
 
@@ -46,8 +46,9 @@ static HpsiLayout hpsi_layout(qm_gspace g, int ik, int nb, int nproj, bool fp32,
     L.t_off = off;
     const size_t per_band = stick_buffer_bytes_per_band(g, ik, fp32);
     // the precision form keeps every band's stick buffer (K1 and K2 of all bands overlap the
-    // nonlocal part; K3 runs once it is done), the FP64 form chunks the bands to stay in L2
-    const size_t budget = (fp32 && nproj > 0) ? kStickBudgetOverlap : kStickBudget;
+    // nonlocal part; K3 runs once it is done; without projectors the larger launches are faster
+    // too), the FP64 form chunks the bands to stay in L2
+    const size_t budget = fp32 ? kStickBudgetOverlap : kStickBudget;
     const size_t ntr = gamma ? (size_t)(nb + 1) / 2 : (size_t)nb;  // transforms (band pairs at Gamma)
     const size_t nbc = std::max<size_t>(1, std::min<size_t>(ntr, budget / per_band));
     L.t_bytes = nbc * per_band;
