@@ -56,8 +56,9 @@ k_plane_real(const typename Cx<R>::T* __restrict__ T, int nstick, int nstick_pad
         fft_lines<C, +1, true, true>(plane, ldy, 1, N2, nullptr, pz, twz, tid, nt);
     }
     C* Up = U + ((size_t)b * N1 + p1) * ((size_t)N3 * N2);
+    const RDiv d2{N2, 1.0f / (float)N2};
     for (int i = tid; i < N3 * N2; i += nt) {
-        const int p3 = i / N2, p2 = i - p3 * N2;
+        const int p3 = d2.div(i), p2 = i - p3 * N2;
         Up[i] = plane[p3 * ldy + p2];
     }
 }
@@ -88,8 +89,9 @@ k_plane_pair(const typename Cx<R>::T* __restrict__ UL, const typename Cx<R>::T* 
     const size_t nplane = (size_t)N3 * N2;
     const C* a = UL + ((size_t)n * N1 + p1) * nplane;
     const C* c = UR ? UR + ((size_t)m * N1 + p1) * nplane : nullptr;  // no right factor: the plane of UL
+    const RDiv d2{N2, 1.0f / (float)N2};
     for (int i = tid; i < N3 * N2; i += nt) {
-        const int p3 = i / N2, p2 = i - p3 * N2;
+        const int p3 = d2.div(i), p2 = i - p3 * N2;
         const C x = a[i], y = c ? c[i] : mk<C>(1, 0);
         plane[p3 * ldy + p2] = mk<C>(x.x * y.x + x.y * y.y, x.y * y.x - x.x * y.y);  // x conj(y)
     }
