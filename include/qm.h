@@ -95,6 +95,20 @@ qm_status qm_gspace_query(qm_gspace g, int grid[3], int* npw, int* npw_max, int*
  */
 qm_status qm_gspace_indices(qm_gspace g, int ik, int32_t* idx, int32_t* miller, double* kpg);
 
+/*
+ * qm_gspace_sticks - host copies of the x-stick layout of k-point ik (the pruning of Sec. 4.3.3):
+ *  nstick    host, may be NULL: number of x-sticks (distinct (i2, i3) holding a plane wave).
+ *  stick_yz  host, may be NULL: nstick * 2 int32, (i2, i3) of each stick in the order the FFT
+ *            kernels use (increasing i2 + N2 i3).
+ *  ngtile    host, may be NULL: at the Gamma point, the tiles of qm_hpsi_gamma's forward x pass
+ *            (0 at other k-points).
+ *  gtile     host, may be NULL: ngtile * 32 * 2 int32, per tile slot (stick index or -1 for an
+ *            empty slot, slot of the stick holding -G); a stick (i2, i3) and its partner
+ *            (-i2, -i3) share a tile.
+ * Host-only.
+ */
+qm_status qm_gspace_sticks(qm_gspace g, int ik, int* nstick, int32_t* stick_yz, int* ngtile, int32_t* gtile);
+
 /* qm_gspace_destroy - free the handle and its device tables/workspace (NULL is a no-op).
  * Synchronises the device first, so in-flight work that uses the handle completes. */
 void qm_gspace_destroy(qm_gspace g);

@@ -21,6 +21,7 @@ SIGNATURES = {
                                         ctypes.POINTER(ctypes.c_void_p)]),
     "qm_gspace_query": (ctypes.c_int, [ctypes.c_void_p, c_int_p, c_int_p, c_int_p, c_int_p]),
     "qm_gspace_indices": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_int32_p, c_int32_p, c_double_p]),
+    "qm_gspace_sticks": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_int_p, c_int32_p, c_int_p, c_int32_p]),
     "qm_gspace_destroy": (None, [ctypes.c_void_p]),
     "qm_hpsi": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                ctypes.c_void_p, ctypes.c_int,

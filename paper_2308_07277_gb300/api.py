@@ -97,6 +97,18 @@ def qm_gspace_indices(g, ik):
     return idx, mil, kpg
 
 
+def qm_gspace_sticks(g, ik):
+    """(stick_yz (nstick, 2) int32, gamma tiles (ngtile, 32, 2) int32) of k-point ik (host tables)."""
+    lib = _lib.load()
+    ns, nt = ctypes.c_int(), ctypes.c_int()
+    _check(lib.qm_gspace_sticks(g, int(ik), ctypes.byref(ns), None, ctypes.byref(nt), None))
+    yz = np.empty((ns.value, 2), np.int32)
+    tiles = np.empty((nt.value, 32, 2), np.int32)
+    i32 = ctypes.POINTER(ctypes.c_int32)
+    _check(lib.qm_gspace_sticks(g, int(ik), None, yz.ctypes.data_as(i32), None, tiles.ctypes.data_as(i32)))
+    return yz, tiles
+
+
 def qm_gspace_destroy(g):
     if g is not None and g.value:
         _lib.load().qm_gspace_destroy(g)

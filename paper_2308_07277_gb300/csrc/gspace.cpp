@@ -462,6 +462,29 @@ extern "C" qm_status qm_gspace_indices(qm_gspace g, int ik, int32_t* idx, int32_
     return QM_OK;
 }
 
+extern "C" qm_status qm_gspace_sticks(qm_gspace g, int ik, int* nstick, int32_t* stick_yz, int* ngtile,
+                                      int32_t* gtile) {
+    clear_error();
+    if (!g) return fail(QM_ERR_ARG, "qm_gspace_sticks: NULL handle");
+    if (ik < 0 || ik >= g->nk) return fail(QM_ERR_ARG, "qm_gspace_sticks: ik out of range");
+    const KTables& kt = g->k[ik];
+    const int N2 = g->n[1];
+    if (nstick) *nstick = kt.nstick;
+    if (ngtile) *ngtile = kt.gamma ? kt.ngtile : 0;
+    if (stick_yz)
+        for (int s = 0; s < kt.nstick; ++s) {
+            const int64_t key = (int64_t)kt.h_idx[kt.h_g0[s]] / g->n[0];
+            stick_yz[2 * s] = (int32_t)(key % N2);
+            stick_yz[2 * s + 1] = (int32_t)(key / N2);
+        }
+    if (gtile && kt.gamma)
+        for (size_t i = 0; i < kt.h_gtile.size(); ++i) {
+            gtile[2 * i] = kt.h_gtile[i].x;
+            gtile[2 * i + 1] = kt.h_gtile[i].y;
+        }
+    return QM_OK;
+}
+
 extern "C" void qm_gspace_destroy(qm_gspace g) {
     if (!g) return;
     if (g->uploaded) {

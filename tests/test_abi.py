@@ -330,3 +330,39 @@ def test_scf_argument_errors_before_device_work():
     finally:
         Q.qm_gspace_destroy(small)
         Q.qm_gspace_destroy(g)
+
+
+@pytest.mark.parametrize("cell", [S.config1(), S.config4(), S.small_cells()[2], S.cubic_si8(12.0, reps=(2, 1, 1))],
+                         ids=["si2_24", "si216_90", "si2_25", "si8x211"])
+def test_sticks_and_gamma_tiles(cell):
+    """The x-stick list equals the oracle sphere's distinct (i2, i3) in flat order; at the Gamma
+    point every stick sits in exactly one tile slot, beside the slot of its partner (-i2, -i3) (the
+    partner of the partner is the slot itself), empty slots are marked -1; elsewhere no tiles."""
+    import paper_2308_07277_gb300 as Q
+    grid = tuple(cell.grid) if cell.grid else OG.fft_grid(cell.lattice, 4 * cell.ecut_ha)
+    kpts = [[0, 0, 0], [0.25, -0.25, 0.25]]
+    g = Q.qm_gspace_create(cell.lattice, kpts, cell.ecut_ha, grid)
+    try:
+        n1, n2, n3 = grid
+        for ik, k in enumerate(kpts):
+            gs = OG.gsphere(cell.lattice, grid, cell.ecut_ha, k)
+            keys = np.unique(gs["idx"] // n1)
+            yz, tiles = Q.qm_gspace_sticks(g, ik)
+            np.testing.assert_array_equal(yz[:, 0] + n2 * yz[:, 1], keys)
+            if ik == 1:
+                assert tiles.shape[0] == 0
+                continue
+            st, par = tiles[..., 0], tiles[..., 1]
+            used = st[st >= 0]
+            assert sorted(used.tolist()) == list(range(len(keys)))
+            for t in range(tiles.shape[0]):
+                for j in range(32):
+                    s = st[t, j]
+                    if s < 0:
+                        continue
+                    p = par[t, j]
+                    assert 0 <= p < 32 and par[t, p] == j
+                    i2, i3 = yz[s]
+                    assert tuple(yz[st[t, p]]) == ((-i2) % n2, (-i3) % n3)
+    finally:
+        Q.qm_gspace_destroy(g)
