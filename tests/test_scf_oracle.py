@@ -108,9 +108,10 @@ def test_free_electron_gas_is_self_consistent_at_once():
 
 def test_si_cell_converges_to_a_fixed_point():
     """Si2-like fcc cell with the synthetic wells, two k-points, 2 electrons (the lowest band,
-    0.4 Ha below the next at Gamma; with 8 electrons the fourth and fifth bands of this weak
-    potential are nearly degenerate and no fixed occupation converges): the loop converges; at its
-    density the potential's occupied states give the same density back, which holds 2 electrons."""
+    0.4 Ha below the next at Gamma; with 8 electrons and these two k-points the fourth and fifth
+    bands of this weak potential trade places and the loop does not settle): the loop converges; at
+    its density the potential's occupied states give the same density back, which holds 2
+    electrons."""
     cell = S.fcc_si2(8.0)
     grid = OG.fft_grid(cell.lattice, 4 * cell.ecut_ha)
     ks, w = [[0, 0, 0], [0.25, -0.25, 0.25]], [0.25, 0.75]
@@ -126,3 +127,19 @@ def test_si_cell_converges_to_a_fixed_point():
                                        S.dvals(cell.nat)))[1][:, :1].T for gs, b in zip(sph, betas)]
     n_out = OS.density(coefs, sph, w, 1, cell.omega)
     assert cell.omega / n.size * np.abs(n_out - n).sum() <= 1e-9
+
+
+def test_si_cell_eight_electrons_three_k_points():
+    """Four occupied bands (8 electrons, Si-like) with the k-points Gamma, (1/4, -1/4, 1/4) and
+    (1/2, 0, 0) (weights 1/8, 1/2, 3/8): the loop converges to a fixed point that holds 8 electrons."""
+    cell = S.fcc_si2(8.0)
+    grid = OG.fft_grid(cell.lattice, 4 * cell.ecut_ha)
+    ks, w = [[0, 0, 0], [0.25, -0.25, 0.25], [0.5, 0, 0]], [0.125, 0.5, 0.375]
+    sph = [OG.gsphere(cell.lattice, grid, cell.ecut_ha, k) for k in ks]
+    betas = [S.beta_of_q(gs["q"], cell.tau, cell.omega) for gs in sph]
+    vion = S.vloc_on_grid(cell.lattice, cell.tau, grid)
+    eigs, n, v, it = OS.scf(cell.lattice, cell.omega, cell.ecut_ha, grid, ks, w, 8, 6, vion, betas,
+                            S.dvals(cell.nat), tol=1e-10, max_iter=80)
+    assert it < 80
+    assert abs(cell.omega / n.size * n.sum() - 8.0) < 1e-9
+    assert n.min() > 0
