@@ -711,6 +711,7 @@ inline bool fused_length(int n) {
 template <class R> constexpr int sticks_per_cta() { return 32; }
 template <class R> constexpr int stick_threads() { return sizeof(R) == 4 ? 128 : 256; }
 constexpr int kThreads = 256;
+constexpr size_t kMaxGridY = 65535;  // largest y extent of a launch grid (bands or pairs per launch)
 // resident CTAs the register budget is sized for: FP32 4 (stage-per-pass) or 3 (two register
 // passes, groups of up to 18 complex values); FP64 2, which the shared memory of an FP64
 // plane or stick tile allows at most anyway (fewer would force spills of the 64-bit values)
@@ -970,7 +971,9 @@ qm_status local_kinetic_impl(qm_gspace g, int ik, int nb, const void* psi, int l
     const size_t per_band = (size_t)N1 * kt.nstick_pad * sizeof(C);
     if (gamma && !kt.gamma) return fail(QM_ERR_ARG, "FFT path: the k-point is not the Gamma point");
     const int ntr = gamma ? (nb + 1) / 2 : nb;  // transforms (band pairs in the Gamma form)
-    const int nbc = (int)std::max<size_t>(1, std::min<size_t>((size_t)ntr, tbuf_bytes / per_band));
+    // transforms per launch: the stick buffer's budget, at most the 65535 CTAs a grid's y extent allows
+    const int nbc = (int)std::max<size_t>(1, std::min<size_t>(std::min<size_t>((size_t)ntr, tbuf_bytes / per_band),
+                                                              kMaxGridY));
     const size_t sm_stick = (size_t)(sticks_per_cta<R>() * g->ldx + N1) * sizeof(C);
     const size_t sm_plane = (size_t)(N3 * g->ldy + N2 + N3) * sizeof(C) + (size_t)N3 * sizeof(int);
     qm_status st;
@@ -1036,7 +1039,8 @@ qm_status local_kinetic_tab_impl(const DevTables& t, int nb, const void* psi, in
     const int N1 = t.n[0], N2 = t.n[1], N3 = t.n[2];
     const size_t per_band = (size_t)N1 * t.nstick_pad * sizeof(C);
     if (tbuf_bytes < per_band) return fail(QM_ERR_ARG, "stick buffer smaller than one band");
-    const int nbc = (int)std::max<size_t>(1, std::min<size_t>((size_t)nb, tbuf_bytes / per_band));
+    const int nbc = (int)std::max<size_t>(1, std::min<size_t>(std::min<size_t>((size_t)nb, tbuf_bytes / per_band),
+                                                              kMaxGridY));
     const size_t sm_stick = (size_t)(sticks_per_cta<R>() * t.ldx + N1) * sizeof(C);
     const size_t sm_plane = (size_t)(N3 * t.ldy + N2 + N3) * sizeof(C) + (size_t)N3 * sizeof(int);
     qm_status st;

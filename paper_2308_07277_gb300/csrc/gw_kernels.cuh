@@ -174,9 +174,11 @@ qm_status gw_mel_impl(qm_gspace g, int ikl, int ikr, int nl, const void* psi_l, 
     const size_t box = nrr * sizeof(C);
     const size_t per_t = (size_t)N1 * std::max(kl.nstick_pad, kr.nstick_pad) * sizeof(C);
     const size_t per_e = (size_t)N1 * ke.nstick_pad * sizeof(C);
-    const int nbc = (int)std::max<size_t>(1, std::min<size_t>((size_t)std::max(nl, nr), kChunk / per_t));
+    // states and pairs per launch: 256 MB stick buffers, at most the grid's 65535 y extent
+    const int nbc =
+        (int)std::max<size_t>(1, std::min<size_t>(std::min<size_t>((size_t)std::max(nl, nr), kChunk / per_t), kMaxGridY));
     const int npair = nl * nr;
-    const int npc = (int)std::max<size_t>(1, std::min<size_t>((size_t)npair, kChunk / per_e));
+    const int npc = (int)std::max<size_t>(1, std::min<size_t>(std::min<size_t>((size_t)npair, kChunk / per_e), kMaxGridY));
     const size_t off_ul = kWsHeader;
     const size_t off_ur = align_up(off_ul + (size_t)nl * box, 256);
     const size_t off_t = align_up(off_ur + (size_t)nr * box, 256);
