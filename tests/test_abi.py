@@ -366,3 +366,27 @@ def test_sticks_and_gamma_tiles(cell):
                     assert tuple(yz[st[t, p]]) == ((-i2) % n2, (-i3) % n3)
     finally:
         Q.qm_gspace_destroy(g)
+
+
+def test_bindings_refuse_host_tensors():
+    """Every compute call of the binding refuses CPU tensors (there is no CPU path): the H psi
+    forms, real-time propagation, GW matrix elements and self-consistency."""
+    import torch
+    import paper_2308_07277_gb300 as Q
+    g = Q.qm_gspace_create(np.eye(3) * 10.0, [[0, 0, 0]], 3.0)
+    try:
+        npw = Q.qm_gspace_query(g)["npw"][0]
+        nr = int(np.prod(Q.qm_gspace_query(g)["grid"]))
+        psi = torch.zeros((2, npw), dtype=torch.complex128)
+        v = torch.zeros(nr, dtype=torch.float64)
+        calls = [lambda: Q.qm_hpsi(g, 0, psi, v, None, None),
+                 lambda: Q.qm_hpsi_gamma(g, 0, psi, v, None, None),
+                 lambda: Q.qm_tddft_taylor(g, 0, psi, v, None, None, 0.1, 4),
+                 lambda: Q.qm_tddft_etrs(g, 0, psi, v, v, None, None, 0.1, 4),
+                 lambda: Q.qm_gw_mel(g, 0, 0, psi, psi, g, 0, npw, M=torch.zeros((4, npw), dtype=torch.complex128)),
+                 lambda: Q.qm_scf(g, 2, [1.0], [psi], v, None, torch.zeros(0, dtype=torch.float64))]
+        for c in calls:
+            with pytest.raises(ValueError, match="CUDA tensor"):
+                c()
+    finally:
+        Q.qm_gspace_destroy(g)
